@@ -1,0 +1,261 @@
+/*
+ * lgc.h -- C ABI of liblgc, GB300 (sm_103a) local graph clustering.
+ *
+ * Implements the parallel local clustering methods of Shun,
+ * Roosta-Khorasani, Fountoulakis and Mahoney, "Parallel Local Graph
+ * Clustering" (arXiv:1604.07515): the synchronous frontier push of PR-Nibble
+ * (Sec. 3.3), Nibble (Sec. 3.2), deterministic heat-kernel PageRank
+ * (Sec. 3.4), randomized heat-kernel PageRank (Sec. 3.5) and the parallel
+ * sweep cut (Sec. 3.1, Theorem thm:sweep).  Every step runs in the library's
+ * own CUDA kernels on one GPU; all values are IEEE binary64.
+ *
+ * Conventions
+ *  - Every function returns LGC_OK (0) on success or a negative LGC_E* code;
+ *    lgc_poll also returns LGC_PENDING (1).  Nothing aborts the process.
+ *  - Inputs are copied; the library keeps no caller pointer after a call
+ *    returns.  Outputs (lgc_svec, lgc_cluster, lgc_result) are owned by the
+ *    library and released with the matching *_free function.
+ *  - Graphs are undirected and unweighted: CSR with int64 offsets[n+1] and
+ *    int32 cols[offsets[n]], every edge stored in both directions, each
+ *    adjacency list sorted ascending, no self loops, no duplicate edges
+ *    (Sec. 2, "Graph Notation"; Sec. 4, "Input Graphs").
+ *  - A seed x must satisfy 0 <= x < n and d(x) >= 1, else LGC_EINVAL.
+ *  - Calls on one context are serialised by the caller (one stream per
+ *    context); lgc_submit / lgc_poll are thread-safe.
+ */
+#ifndef LGC_H_
+#define LGC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LGC_OK 0
+#define LGC_PENDING 1          /* lgc_poll: request not finished yet */
+#define LGC_EINVAL (-1)        /* bad argument (seed, parameter, graph) */
+#define LGC_ENOMEM (-2)        /* device or host allocation failed */
+#define LGC_ETABLEFULL (-3)    /* a hash table probe exceeded its bound */
+#define LGC_EMAXROUNDS (-4)    /* max_rounds reached; the partial p is still returned */
+#define LGC_ECUDA (-5)         /* a CUDA runtime call failed */
+#define LGC_EBUSY (-6)         /* submit refused: queue full or over memory budget */
+#define LGC_ENOTFOUND (-7)     /* unknown ticket */
+#define LGC_ETIMEOUT (-8)      /* a bounded device wait gave up */
+
+typedef struct lgc_ctx lgc_ctx;
+typedef struct lgc_graph lgc_graph;
+
+/* Sparse vector: nnz entries, idx ascending, values > 0 (the sparse sets of
+ * Sec. 2, "Sparse Sets", with only the non-zero entries kept).  idx/val are
+ * device pointers when on_device != 0, host pointers otherwise. */
+typedef struct {
+  int64_t nnz;
+  int32_t *idx;
+  double *val;
+  int on_device;
+} lgc_svec;
+
+/* Sweep-cut result (Sec. 3.1): ids = S_{i*} in sweep order (non-increasing
+ * p/d, ties by ascending id), vol = vol(S_{i*}), cut = |boundary(S_{i*})|,
+ * conductance = cut / min(vol, 2m - vol) (+inf for an empty result). */
+typedef struct {
+  int64_t size;
+  int32_t *ids;
+  int64_t vol, cut;
+  double conductance;
+  int on_device;
+} lgc_cluster;
+
+/* Per-call counters.  rounds: push rounds (levels for HK-PR, steps for
+ * Nibble); pushes: sum of frontier sizes; pushed_edges: sum over rounds of
+ * the frontier's degrees (walk steps for rand-HK-PR); touched: keys in the
+ * result's sparse set; table_capacity: final hash-table slots. */
+typedef struct {
+  int64_t rounds, pushes, pushed_edges, touched, table_capacity;
+  int status_detail;
+} lgc_stats;
+
+enum { LGC_RULE_OPT = 0, LGC_RULE_ORIG = 1 };
+/* LGC_MODE_ATOMIC: scatter with fetch-and-add (Sec. 2, "Atomic Operations"),
+ *   result within rounding of the canonical order.
+ * LGC_MODE_DET: every destination sums its contributions starting from the
+ *   value it holds when the edge phase begins, then in ascending source id;
+ *   results, frontiers and rounds are bit-reproducible. */
+enum { LGC_MODE_ATOMIC = 0, LGC_MODE_DET = 1 };
+
+/* PR-Nibble (Sec. 3.3; Fig. alg:pr-nibble with the original rule,
+ * Fig. alg:pr-nibble2 with the optimized rule).  0 < alpha < 1, eps > 0;
+ * max_rounds <= 0 means no limit. */
+typedef struct {
+  double alpha, eps;
+  int rule;
+  int mode;
+  int64_t max_rounds;
+} lgc_prnibble_params;
+
+/* Nibble (Sec. 3.2, Fig. alg:nibble): T >= 0 lazy-walk steps, eps >= 0. */
+typedef struct {
+  int T;
+  double eps;
+  int mode;
+} lgc_nibble_params;
+
+/* HK-PR (Sec. 3.4, Fig. alg:hkpr): t > 0, N >= 1 Taylor terms, eps >= 0.
+ * The entry threshold for level j is e^t eps d(v) / (2 N psi_j). */
+typedef struct {
+  double t, eps;
+  int N;
+  int mode;
+} lgc_hkpr_params;
+
+/* rand-HK-PR (Sec. 3.5): n_walks >= 1 walks of Poisson(t) length capped at
+ * K >= 0, random stream Philox4x32-10 keyed by rng_seed. */
+typedef struct {
+  double t;
+  int K;
+  int64_t n_walks;
+  uint64_t rng_seed;
+} lgc_rand_hkpr_params;
+
+/* ---- context ---- */
+
+/* Creates a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * owned by the caller (for example torch.cuda.current_stream().cuda_stream),
+ * or NULL for a stream owned by the context.  All work of the context is
+ * ordered on that stream. */
+int lgc_ctx_create(int device, void *cuda_stream, lgc_ctx **out);
+void lgc_ctx_destroy(lgc_ctx *ctx);
+
+enum {
+  LGC_OPT_RESULT_ON_DEVICE = 1, /* 1: outputs stay in device memory (default 0: host) */
+  LGC_OPT_TRACE = 2,            /* 1: record every round's frontier (tests) */
+  LGC_OPT_SERVE_MEM_BUDGET = 3, /* bytes of hash-table memory admitted at once */
+  LGC_OPT_SERVE_MAX_BATCH = 4   /* requests resident on the device at once */
+};
+int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
+/* Waits for all work issued on the context's stream. */
+int lgc_ctx_synchronize(lgc_ctx *ctx);
+
+/* ---- graph ---- */
+#define LGC_GRAPH_VALIDATE 1     /* check symmetry, order, no self loops / duplicates */
+#define LGC_GRAPH_DEVICE_INPUT 2 /* offsets / cols are device pointers */
+/* Copies the CSR (Sec. 2) to the device.  Errors: LGC_EINVAL for n < 0, NULL
+ * arrays, or a failed validation; LGC_ENOMEM. */
+int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *cols,
+                     int flags, lgc_graph **out);
+void lgc_graph_destroy(lgc_graph *g);
+int64_t lgc_graph_num_vertices(const lgc_graph *g);
+int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
+
+/* ---- diffusions: seed + parameters -> sparse vector p ---- */
+/* Synchronous PR-Nibble (Sec. 3.3, "Parallel Implementation"): every vertex
+ * with r[v] >= eps d(v) pushes in the same round, reading r from the start of
+ * the round; returns p.  st may be NULL. */
+int lgc_prnibble(lgc_graph *g, int32_t seed, const lgc_prnibble_params *prm, lgc_svec **p,
+                 lgc_stats *st);
+/* Parallel Nibble (Sec. 3.2, Fig. alg:nibble); returns p_T, or p_{i-1} when
+ * the frontier of step i is empty. */
+int lgc_nibble(lgc_graph *g, int32_t seed, const lgc_nibble_params *prm, lgc_svec **p,
+               lgc_stats *st);
+/* Parallel HK-PR (Sec. 3.4, Fig. alg:hkpr); returns the unscaled p. */
+int lgc_hkpr(lgc_graph *g, int32_t seed, const lgc_hkpr_params *prm, lgc_svec **p,
+             lgc_stats *st);
+/* Parallel rand-HK-PR (Sec. 3.5): p[v] = (walks ending at v) / n_walks.
+ * Walk i uses Philox4x32-10 with key (rng_seed low, high word) and counter
+ * (i low, i high, s, 0) for its draw s: draw 0 sets the length (53-bit
+ * uniform against the Poisson(t) CDF, capped at K), draw s >= 1 picks the
+ * neighbour floor(word0 * d / 2^32). */
+int lgc_rand_hkpr(lgc_graph *g, int32_t seed, const lgc_rand_hkpr_params *prm, lgc_svec **p,
+                  lgc_stats *st);
+/* Optional: the endpoints A[0..n_walks) of the last lgc_rand_hkpr call on
+ * this context, copied to host memory `out` (n_walks int32).  Tests only. */
+int lgc_rand_hkpr_endpoints(lgc_ctx *ctx, int32_t *out, int64_t n_walks);
+
+/* ---- sweep cut (Sec. 3.1, Theorem thm:sweep) ---- */
+/* Sorts the entries of p with p > 0 by p[v]/d(v) non-increasing (ties by
+ * ascending id), computes vol and boundary of every prefix by prefix sums,
+ * and returns the prefix of smallest conductance (exact rational comparison,
+ * first index on ties; prefixes with min(vol, 2m - vol) = 0 are skipped).
+ * p may be on the host or the device (p->on_device). */
+int lgc_sweep(lgc_graph *g, const lgc_svec *p, lgc_cluster **out);
+
+/* ---- tracing (deterministic-mode parity tests) ---- */
+/* Frontiers of the last diffusion call recorded under LGC_OPT_TRACE:
+ * *rounds receives the round count; if sizes != NULL it receives the size of
+ * each round's frontier (up to cap_rounds entries); if frontiers != NULL it
+ * receives the frontiers concatenated (up to cap_ids ids).  Frontiers are in
+ * ascending id in LGC_MODE_DET and in arrival order in LGC_MODE_ATOMIC. */
+int lgc_get_trace(lgc_ctx *ctx, int64_t *rounds, int64_t *sizes, int64_t cap_rounds,
+                  int32_t *frontiers, int64_t cap_ids);
+/* The residual r of the last lgc_prnibble call made under LGC_OPT_TRACE:
+ * every key of r's sparse set (the seed and every neighbour of a pushed
+ * vertex, Sec. 3.3), zeros included, in a host svec that the caller frees.
+ * LGC_ENOTFOUND if there is none.  Tests only. */
+int lgc_prnibble_residual(lgc_ctx *ctx, lgc_svec **r);
+
+/* ---- measurement ---- */
+/* Kernels launched on this context so far (all of the library's kernels). */
+int64_t lgc_launch_count(const lgc_ctx *ctx);
+/* Per-kernel timing, recorded with CUDA events on the context's stream
+ * around every launch of the named kernel while LGC_OPT_PROFILE is 1.
+ * bytes = the algorithmic bytes of those launches (what the method must
+ * move: 24 per pushed edge, 24 per frontier vertex staged, 8 per next
+ * frontier entry for the edgeMap; 20 per walk step and 4 per walk for the
+ * walk kernel; 12 per edge of vol(S_N) plus 24 per swept vertex for the
+ * sweep's crossing count). */
+enum {
+  LGC_PROF_EDGEMAP = 0,    /* atomic-mode edgeMap (push scatter) */
+  LGC_PROF_VERTEXMAP = 1,  /* vertexMap kernels */
+  LGC_PROF_DET_EDGE = 2,   /* deterministic-mode emit + sort + fold + compact */
+  LGC_PROF_WALK = 3,       /* rand-HK-PR walk kernel */
+  LGC_PROF_SWEEP = 4,      /* sweep crossing-count kernel */
+  LGC_PROF_COUNT = 5
+};
+#define LGC_OPT_PROFILE 5
+typedef struct {
+  int64_t launches;
+  double ms;    /* summed event-timed duration */
+  double bytes; /* summed algorithmic bytes */
+} lgc_kernel_profile;
+int lgc_profile_read(lgc_ctx *ctx, int kernel, lgc_kernel_profile *out);
+int lgc_profile_reset(lgc_ctx *ctx);
+
+/* ---- request loop (continuous batching) ---- */
+enum { LGC_ALGO_PRNIBBLE = 0, LGC_ALGO_NIBBLE = 1, LGC_ALGO_HKPR = 2, LGC_ALGO_RAND_HKPR = 3 };
+typedef struct {
+  int algo;
+  int32_t seed;
+  int want_sweep;
+  lgc_prnibble_params pr;
+  lgc_nibble_params nb;
+  lgc_hkpr_params hk;
+  lgc_rand_hkpr_params rh;
+} lgc_request;
+typedef struct {
+  int status;            /* LGC_OK or the request's error code */
+  lgc_svec *p;           /* host-resident */
+  lgc_cluster *cluster;  /* host-resident; NULL unless want_sweep */
+  lgc_stats stats;
+  double submit_s, start_s, end_s; /* host monotonic clock, seconds */
+} lgc_result;
+/* Queues one request against graph g (which must outlive it).  Admission is
+ * by the hash-table memory the request may need (bounded by
+ * LGC_OPT_SERVE_MEM_BUDGET) and by LGC_OPT_SERVE_MAX_BATCH; requests that do
+ * not fit wait in the queue.  Returns LGC_EBUSY if the queue is full. */
+int lgc_submit(lgc_ctx *ctx, lgc_graph *g, const lgc_request *req, uint64_t *ticket);
+/* LGC_PENDING while the request runs; LGC_OK and *out when done (the ticket
+ * is then released); LGC_ENOTFOUND for an unknown ticket. */
+int lgc_poll(lgc_ctx *ctx, uint64_t ticket, lgc_result **out);
+
+/* ---- release ---- */
+void lgc_svec_free(lgc_svec *p);
+void lgc_cluster_free(lgc_cluster *c);
+void lgc_result_free(lgc_result *r);
+const char *lgc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGC_H_ */

@@ -1,0 +1,529 @@
+// Public C ABI (include/lgc.h): contexts, graphs, entry points, releases,
+// and the request loop behind lgc_submit / lgc_poll.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+#include "prim.cuh"
+
+using namespace lgc;
+
+namespace {
+
+__global__ void degree_kernel(const int64_t* __restrict__ off, int64_t n,
+                              int32_t* __restrict__ deg, int* maxdeg) {
+  int m = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = off[v + 1] - off[v];
+    deg[v] = (int32_t)d;
+    m = max(m, (int)d);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, m);
+}
+
+// Flags: 1 offsets not monotone / out of range, 2 column out of range,
+// 4 self loop, 8 adjacency not strictly ascending (unsorted or duplicate),
+// 16 asymmetric (w lists v does not hold for v lists w).
+__global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                int64_t n, int64_t nnz, int* flags) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[v], e = off[v + 1];
+    if (b < 0 || e < b || e > nnz) {
+      atomicOr(flags, 1);
+      continue;
+    }
+    for (int64_t k = b; k < e; k++) {
+      const int32_t w = col[k];
+      if (w < 0 || w >= n) {
+        atomicOr(flags, 2);
+        continue;
+      }
+      if (w == v) atomicOr(flags, 4);
+      if (k > b && col[k - 1] >= w) atomicOr(flags, 8);
+      // binary search v in w's list
+      int64_t lo = off[w], hi = off[w + 1];
+      bool found = false;
+      if (lo >= 0 && hi <= nnz && lo <= hi) {
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          int32_t c = col[mid];
+          if (c == v) {
+            found = true;
+            break;
+          }
+          if (c < v) lo = mid + 1;
+          else hi = mid;
+        }
+      }
+      if (!found) atomicOr(flags, 16);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// request loop: continuous batching over worker streams
+// ---------------------------------------------------------------------------
+namespace lgc {
+
+struct Serve {
+  struct Item {
+    uint64_t ticket;
+    lgc_graph* g;
+    lgc_request req;
+    double submit_s;
+    int64_t bytes;
+  };
+  lgc_ctx* owner = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Item> queue;
+  std::map<uint64_t, lgc_result*> done;
+  std::map<uint64_t, int> known;  // ticket -> 1 while queued or running
+  int64_t inflight_bytes = 0;
+  int inflight = 0;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::vector<std::thread> workers;
+  std::vector<lgc_ctx*> wctx;
+  size_t max_queue = 1 << 20;
+};
+
+// Hash-table bytes a request may need: slots at load 1/2, 16 bytes per slot
+// plus 8 for PR-Nibble's p, bounded by the graph size.
+static int64_t request_bytes(const lgc_graph* g, const lgc_request& r) {
+  const int64_t n = g->n;
+  auto slots = [&](int64_t keys) { return pow2_at_least(2 * std::max<int64_t>(keys, 32)); };
+  switch (r.algo) {
+    case LGC_ALGO_PRNIBBLE: {
+      double bound = 1.0 + 1.0 / (r.pr.alpha * r.pr.eps);
+      int64_t keys = bound < (double)n ? (int64_t)bound : n;
+      return slots(keys) * 24 + keys * 24;
+    }
+    case LGC_ALGO_NIBBLE:
+      return 2 * slots(n) * 16 + n * 24;
+    case LGC_ALGO_HKPR:
+      return 3 * slots(n) * 16 + n * 24;
+    default:
+      return r.rh.n_walks * 40;
+  }
+}
+
+static void serve_worker(Serve* S, lgc_ctx* wc) {
+  for (;;) {
+    Serve::Item it;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] {
+        if (S->stop) return true;
+        if (S->queue.empty()) return false;
+        const Serve::Item& h = S->queue.front();
+        const bool fits = S->inflight == 0 ||
+                          (S->inflight < S->owner->serve_max_batch &&
+                           S->inflight_bytes + h.bytes <= S->owner->serve_mem_budget);
+        return fits;
+      });
+      if (S->stop) return;
+      it = S->queue.front();
+      S->queue.pop_front();
+      S->inflight++;
+      S->inflight_bytes += it.bytes;
+    }
+    lgc_result* res = new lgc_result();
+    memset(res, 0, sizeof(*res));
+    res->submit_s = it.submit_s;
+    res->start_s = now_seconds();
+    wc->result_on_device = false;
+    lgc_svec* p = nullptr;
+    int st = LGC_EINVAL;
+    switch (it.req.algo) {
+      case LGC_ALGO_PRNIBBLE:
+        st = run_prnibble(wc, it.g, it.req.seed, &it.req.pr, &p, &res->stats, nullptr);
+        break;
+      case LGC_ALGO_NIBBLE:
+        st = run_nibble(wc, it.g, it.req.seed, &it.req.nb, &p, &res->stats);
+        break;
+      case LGC_ALGO_HKPR:
+        st = run_hkpr(wc, it.g, it.req.seed, &it.req.hk, &p, &res->stats);
+        break;
+      case LGC_ALGO_RAND_HKPR:
+        st = run_rand_hkpr(wc, it.g, it.req.seed, &it.req.rh, &p, &res->stats);
+        break;
+    }
+    if (st == LGC_EMAXROUNDS) st = LGC_OK;
+    res->p = p;
+    if (st == LGC_OK && it.req.want_sweep && p) st = run_sweep(wc, it.g, p, &res->cluster);
+    cudaStreamSynchronize(wc->stream);
+    res->status = st;
+    res->end_s = now_seconds();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->inflight--;
+      S->inflight_bytes -= it.bytes;
+      S->done[it.ticket] = res;
+    }
+    S->cv.notify_all();
+  }
+}
+
+static void serve_shutdown(lgc_ctx* ctx) {
+  Serve* S = ctx->serve;
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (lgc_ctx* w : S->wctx) {
+    ctx_fini(w);
+    delete w;
+  }
+  for (auto& kv : S->done) lgc_result_free(kv.second);
+  delete S;
+  ctx->serve = nullptr;
+}
+
+}  // namespace lgc
+
+extern "C" {
+
+const char* lgc_strerror(int s) {
+  switch (s) {
+    case LGC_OK: return "ok";
+    case LGC_PENDING: return "pending";
+    case LGC_EINVAL: return "invalid argument";
+    case LGC_ENOMEM: return "out of memory";
+    case LGC_ETABLEFULL: return "hash table full";
+    case LGC_EMAXROUNDS: return "maximum number of rounds reached";
+    case LGC_ECUDA: return "CUDA error";
+    case LGC_EBUSY: return "busy";
+    case LGC_ENOTFOUND: return "not found";
+    case LGC_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int lgc_ctx_create(int device, void* cuda_stream, lgc_ctx** out) {
+  if (!out) return LGC_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return LGC_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return LGC_EINVAL;
+  lgc_ctx* ctx = new (std::nothrow) lgc_ctx();
+  if (!ctx) return LGC_ENOMEM;
+  int s = ctx_init(ctx, device, (cudaStream_t)cuda_stream);
+  if (s != LGC_OK) {
+    ctx_fini(ctx);
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return LGC_OK;
+}
+
+void lgc_ctx_destroy(lgc_ctx* ctx) {
+  if (!ctx) return;
+  serve_shutdown(ctx);
+  if (ctx->last_residual) lgc_svec_free(ctx->last_residual);
+  ctx_fini(ctx);
+  delete ctx;
+}
+
+int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
+  if (!ctx) return LGC_EINVAL;
+  switch (option) {
+    case LGC_OPT_RESULT_ON_DEVICE: ctx->result_on_device = value != 0; return LGC_OK;
+    case LGC_OPT_TRACE: ctx->trace = value != 0; return LGC_OK;
+    case LGC_OPT_PROFILE: ctx->profile = value != 0; return LGC_OK;
+    case LGC_OPT_SERVE_MEM_BUDGET:
+      if (value <= 0) return LGC_EINVAL;
+      ctx->serve_mem_budget = value;
+      return LGC_OK;
+    case LGC_OPT_SERVE_MAX_BATCH:
+      if (value <= 0 || value > 1024) return LGC_EINVAL;
+      if (ctx->serve) return LGC_EBUSY;  // fixed once the loop has started
+      ctx->serve_max_batch = value;
+      return LGC_OK;
+    default: return LGC_EINVAL;
+  }
+}
+
+int lgc_ctx_synchronize(lgc_ctx* ctx) {
+  if (!ctx) return LGC_EINVAL;
+  LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LGC_OK;
+}
+
+int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int32_t* cols,
+                     int flags, lgc_graph** out) {
+  if (!ctx || !out || n < 0 || !offsets || (n > 0 && !cols) || n >= INT32_MAX) return LGC_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = ctx->stream;
+  const bool dev = flags & LGC_GRAPH_DEVICE_INPUT;
+  int64_t nnz = 0;
+  LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, offsets + n, 8,
+                               dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  LGC_CUDA_TRY(cudaStreamSynchronize(s));
+  nnz = ctx->h_scratch[0];
+  if (nnz < 0) return LGC_EINVAL;
+  lgc_graph* g = new (std::nothrow) lgc_graph();
+  if (!g) return LGC_ENOMEM;
+  g->ctx = ctx;
+  g->n = n;
+  g->nnz = nnz;
+  int st = LGC_OK;
+  do {
+    if ((st = dalloc_t(ctx, &g->off, n + 1)) != LGC_OK) break;
+    if ((st = dalloc_t(ctx, &g->col, nnz)) != LGC_OK) break;
+    if ((st = dalloc_t(ctx, &g->deg, n)) != LGC_OK) break;
+    const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(g->off, offsets, 8 * (n + 1), k, s) != cudaSuccess) {
+      st = LGC_ECUDA;
+      break;
+    }
+    if (nnz && cudaMemcpyAsync(g->col, cols, 4 * nnz, k, s) != cudaSuccess) {
+      st = LGC_ECUDA;
+      break;
+    }
+    int* dflags = nullptr;
+    if ((st = dalloc_t(ctx, &dflags, 2)) != LGC_OK) break;
+    cudaMemsetAsync(dflags, 0, 8, s);
+    if (n > 0) {
+      if (flags & LGC_GRAPH_VALIDATE) {
+        validate_kernel<<<grid_for(n), kBlock, 0, s>>>(g->off, g->col, n, nnz, dflags);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      degree_kernel<<<std::min(grid_for(n), 152 * 64), kBlock, 0, s>>>(g->off, n, g->deg,
+                                                                       dflags + 1);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    cudaMemcpyAsync(ctx->h_scratch, dflags, 8, cudaMemcpyDeviceToHost, s);
+    dfree(ctx, dflags);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      st = LGC_ECUDA;
+      break;
+    }
+    int32_t* hf = (int32_t*)ctx->h_scratch;
+    if (hf[0] != 0) st = LGC_EINVAL;
+    g->max_deg = hf[1];
+  } while (0);
+  if (st != LGC_OK) {
+    dfree(ctx, g->off);
+    dfree(ctx, g->col);
+    dfree(ctx, g->deg);
+    cudaStreamSynchronize(s);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return LGC_OK;
+}
+
+void lgc_graph_destroy(lgc_graph* g) {
+  if (!g) return;
+  lgc_ctx* ctx = g->ctx;
+  if (ctx->serve) {
+    // wait until no queued or running request uses g
+    Serve* S = ctx->serve;
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv.wait(lk, [&] {
+      for (auto& it : S->queue)
+        if (it.g == g) return false;
+      return S->inflight == 0;
+    });
+  }
+  dfree(ctx, g->off);
+  dfree(ctx, g->col);
+  dfree(ctx, g->deg);
+  cudaStreamSynchronize(ctx->stream);
+  delete g;
+}
+
+int64_t lgc_graph_num_vertices(const lgc_graph* g) { return g ? g->n : -1; }
+int64_t lgc_graph_num_entries(const lgc_graph* g) { return g ? g->nnz : -1; }
+
+int lgc_prnibble(lgc_graph* g, int32_t seed, const lgc_prnibble_params* prm, lgc_svec** p,
+                 lgc_stats* st) {
+  if (!g || !prm || !p) return LGC_EINVAL;
+  lgc_ctx* ctx = g->ctx;
+  if (ctx->last_residual) {
+    lgc_svec_free(ctx->last_residual);
+    ctx->last_residual = nullptr;
+  }
+  return run_prnibble(ctx, g, seed, prm, p, st, ctx->trace ? &ctx->last_residual : nullptr);
+}
+
+int lgc_prnibble_residual(lgc_ctx* ctx, lgc_svec** r) {
+  if (!ctx || !r) return LGC_EINVAL;
+  *r = nullptr;
+  if (!ctx->last_residual) return LGC_ENOTFOUND;
+  *r = ctx->last_residual;
+  ctx->last_residual = nullptr;
+  return LGC_OK;
+}
+
+int lgc_nibble(lgc_graph* g, int32_t seed, const lgc_nibble_params* prm, lgc_svec** p,
+               lgc_stats* st) {
+  if (!g || !prm || !p) return LGC_EINVAL;
+  return run_nibble(g->ctx, g, seed, prm, p, st);
+}
+
+int lgc_hkpr(lgc_graph* g, int32_t seed, const lgc_hkpr_params* prm, lgc_svec** p,
+             lgc_stats* st) {
+  if (!g || !prm || !p) return LGC_EINVAL;
+  return run_hkpr(g->ctx, g, seed, prm, p, st);
+}
+
+int lgc_rand_hkpr(lgc_graph* g, int32_t seed, const lgc_rand_hkpr_params* prm, lgc_svec** p,
+                  lgc_stats* st) {
+  if (!g || !prm || !p) return LGC_EINVAL;
+  return run_rand_hkpr(g->ctx, g, seed, prm, p, st);
+}
+
+int lgc_rand_hkpr_endpoints(lgc_ctx* ctx, int32_t* out, int64_t n_walks) {
+  if (!ctx || !out) return LGC_EINVAL;
+  if (!ctx->d_endpoints) return LGC_ENOTFOUND;
+  if (n_walks != ctx->n_endpoints) return LGC_EINVAL;
+  LGC_CUDA_TRY(cudaMemcpyAsync(out, ctx->d_endpoints, 4 * n_walks, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LGC_OK;
+}
+
+int lgc_sweep(lgc_graph* g, const lgc_svec* p, lgc_cluster** out) {
+  if (!g || !p || !out) return LGC_EINVAL;
+  return run_sweep(g->ctx, g, p, out);
+}
+
+int lgc_get_trace(lgc_ctx* ctx, int64_t* rounds, int64_t* sizes, int64_t cap_rounds,
+                  int32_t* frontiers, int64_t cap_ids) {
+  if (!ctx || !rounds) return LGC_EINVAL;
+  *rounds = (int64_t)ctx->trace_sizes.size();
+  if (sizes) {
+    int64_t k = std::min<int64_t>(cap_rounds, *rounds);
+    memcpy(sizes, ctx->trace_sizes.data(), 8 * k);
+  }
+  if (frontiers) {
+    int64_t k = std::min<int64_t>(cap_ids, (int64_t)ctx->trace_ids.size());
+    memcpy(frontiers, ctx->trace_ids.data(), 4 * k);
+  }
+  return LGC_OK;
+}
+
+int64_t lgc_launch_count(const lgc_ctx* ctx) { return ctx ? ctx->n_launches : -1; }
+
+int lgc_profile_read(lgc_ctx* ctx, int kernel, lgc_kernel_profile* out) {
+  if (!ctx || !out || kernel < 0 || kernel >= LGC_PROF_COUNT) return LGC_EINVAL;
+  profile_collect(ctx);
+  *out = ctx->prof[kernel];
+  return LGC_OK;
+}
+
+int lgc_profile_reset(lgc_ctx* ctx) {
+  if (!ctx) return LGC_EINVAL;
+  profile_collect(ctx);
+  for (int k = 0; k < LGC_PROF_COUNT; k++) ctx->prof[k] = lgc_kernel_profile{0, 0.0, 0.0};
+  return LGC_OK;
+}
+
+int lgc_submit(lgc_ctx* ctx, lgc_graph* g, const lgc_request* req, uint64_t* ticket) {
+  if (!ctx || !g || !req || !ticket) return LGC_EINVAL;
+  if (req->algo < LGC_ALGO_PRNIBBLE || req->algo > LGC_ALGO_RAND_HKPR) return LGC_EINVAL;
+  if (req->seed < 0 || req->seed >= g->n) return LGC_EINVAL;
+  if (!ctx->serve) {
+    Serve* S = new (std::nothrow) Serve();
+    if (!S) return LGC_ENOMEM;
+    S->owner = ctx;
+    int nw = (int)std::min<int64_t>(ctx->serve_max_batch, 64);
+    for (int i = 0; i < nw; i++) {
+      lgc_ctx* w = new (std::nothrow) lgc_ctx();
+      if (!w || ctx_init(w, ctx->device, nullptr) != LGC_OK) {
+        if (w) {
+          ctx_fini(w);
+          delete w;
+        }
+        break;
+      }
+      S->wctx.push_back(w);
+    }
+    if (S->wctx.empty()) {
+      delete S;
+      return LGC_ECUDA;
+    }
+    for (lgc_ctx* w : S->wctx) S->workers.emplace_back(serve_worker, S, w);
+    ctx->serve = S;
+  }
+  Serve* S = ctx->serve;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->queue.size() >= S->max_queue) return LGC_EBUSY;
+    Serve::Item it;
+    it.ticket = S->next_ticket++;
+    it.g = g;
+    it.req = *req;
+    it.submit_s = now_seconds();
+    it.bytes = request_bytes(g, *req);
+    S->queue.push_back(it);
+    S->known[it.ticket] = 1;
+    *ticket = it.ticket;
+  }
+  S->cv.notify_all();
+  return LGC_OK;
+}
+
+int lgc_poll(lgc_ctx* ctx, uint64_t ticket, lgc_result** out) {
+  if (!ctx || !out) return LGC_EINVAL;
+  *out = nullptr;
+  Serve* S = ctx->serve;
+  if (!S) return LGC_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->done.find(ticket);
+  if (it != S->done.end()) {
+    *out = it->second;
+    S->done.erase(it);
+    S->known.erase(ticket);
+    return LGC_OK;
+  }
+  return S->known.count(ticket) ? LGC_PENDING : LGC_ENOTFOUND;
+}
+
+void lgc_svec_free(lgc_svec* p) {
+  if (!p) return;
+  SvecBox* b = (SvecBox*)p;
+  if (p->on_device) {
+    dfree(b->ctx, p->idx);
+    dfree(b->ctx, p->val);
+  } else {
+    free(p->idx);
+    free(p->val);
+  }
+  delete b;
+}
+
+void lgc_cluster_free(lgc_cluster* c) {
+  if (!c) return;
+  ClusterBox* b = (ClusterBox*)c;
+  if (c->on_device) dfree(b->ctx, c->ids);
+  else free(c->ids);
+  delete b;
+}
+
+void lgc_result_free(lgc_result* r) {
+  if (!r) return;
+  lgc_svec_free(r->p);
+  lgc_cluster_free(r->cluster);
+  delete r;
+}
+
+}  // extern "C"

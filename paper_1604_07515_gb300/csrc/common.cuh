@@ -1,0 +1,298 @@
+// Internal definitions shared by the liblgc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/lgc.h"
+
+#define LGC_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) {                                \
+      lgc::set_last_cuda_error(e_, #expr, __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? LGC_ENOMEM : LGC_ECUDA; \
+    }                                                       \
+  } while (0)
+
+#define LGC_TRY(expr)            \
+  do {                           \
+    int s_ = (expr);             \
+    if (s_ < 0) return s_;       \
+  } while (0)
+
+namespace lgc {
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+constexpr int kBlock = 256;
+constexpr int kWarp = 32;
+// Bound on linear-probing steps.  Tables are kept at most half full, so a
+// probe sequence this long means the table is corrupt or full.
+constexpr uint32_t kMaxProbe = 1u << 20;
+
+// Device-side error flags (bit mask in Counters::err).
+constexpr int kErrTableFull = 1;
+constexpr int kErrFrontierOverflow = 2;
+
+// ---------------------------------------------------------------------------
+// Hash table slot: key = vertex + 1 (0 = empty, so a zero memset clears the
+// table), aux = per-algorithm integer (sweep rank), val = the sparse set's
+// double.  Key and value share one 16-byte slot, so a probe and the
+// following atomic add touch the same 32-byte sector.
+// ---------------------------------------------------------------------------
+struct __align__(16) Slot {
+  int32_t key;
+  int32_t aux;
+  double val;
+};
+
+struct Table {
+  Slot* s = nullptr;
+  double* p = nullptr;  // optional second value per slot (PR-Nibble's p)
+  int64_t cap = 0;      // power of two
+  int shift = 32;       // 32 - log2(cap)
+};
+
+__host__ __device__ inline uint32_t hash_slot(int32_t v, int shift) {
+  // Fibonacci hashing: multiply by 2^32 / golden ratio, keep the top bits.
+  return shift >= 32 ? 0u : (uint32_t)((uint32_t)v * 0x9E3779B1u) >> shift;
+}
+
+// Returns the slot of vertex v, inserting it if absent; *inserted = 1 if
+// this call created the key.  Returns -1 (and sets the error flag) if the
+// probe bound is exceeded.
+__device__ inline int64_t ht_find_or_insert(const Table& T, int32_t v, int* inserted, int* err) {
+  const uint32_t mask = (uint32_t)(T.cap - 1);
+  const int32_t k = v + 1;
+  uint32_t h = hash_slot(v, T.shift);
+  for (uint32_t probe = 0; probe < kMaxProbe && probe <= mask; probe++) {
+    int32_t cur = *((volatile int32_t*)&T.s[h].key);
+    if (cur == k) return h;
+    if (cur == 0) {
+      int32_t prev = atomicCAS(&T.s[h].key, 0, k);
+      if (prev == 0) {
+        *inserted = 1;
+        return h;
+      }
+      if (prev == k) return h;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(err, kErrTableFull);
+  return -1;
+}
+
+// Lookup only; -1 if absent.
+__device__ inline int64_t ht_find(const Table& T, int32_t v) {
+  const uint32_t mask = (uint32_t)(T.cap - 1);
+  const int32_t k = v + 1;
+  uint32_t h = hash_slot(v, T.shift);
+  for (uint32_t probe = 0; probe < kMaxProbe && probe <= mask; probe++) {
+    int32_t cur = T.s[h].key;
+    if (cur == k) return h;
+    if (cur == 0) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// Per-round device counters, read back by the host once per round.
+struct Counters {
+  int32_t next_size;   // entries appended to the next frontier
+  int32_t err;         // kErr* bits
+  int64_t next_edges;  // sum of degrees of the next frontier
+  int64_t inserted;    // keys inserted into the destination table
+  int64_t aux;         // algorithm-specific
+};
+
+// Warp-aggregated append of (v, slot, degree) to a frontier list.  Every
+// lane of the calling group must call it (pred selects the appending lanes).
+__device__ inline void frontier_append(bool pred, int32_t v, int32_t slot, int64_t d,
+                                       int32_t* fv, int32_t* fs, Counters* C, int32_t cap) {
+  const unsigned active = __activemask();
+  const unsigned mask = __ballot_sync(active, pred);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  const int rank = __popc(mask & ((1u << lane) - 1));
+  const unsigned dd = pred ? (unsigned)d : 0u;  // degrees < 2^31
+  const unsigned lo = __reduce_add_sync(active, dd & 0xFFFFu);
+  const unsigned hi = __reduce_add_sync(active, dd >> 16);
+  int32_t base = 0;
+  if (lane == leader) {
+    base = atomicAdd(&C->next_size, __popc(mask));
+    atomicAdd((unsigned long long*)&C->next_edges,
+              (unsigned long long)lo + ((unsigned long long)hi << 16));
+  }
+  base = __shfl_sync(active, base, leader);
+  if (pred) {
+    int32_t pos = base + rank;
+    if (pos < cap) {
+      fv[pos] = v;
+      fs[pos] = slot;
+    } else {
+      atomicOr(&C->err, kErrFrontierOverflow);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side objects
+// ---------------------------------------------------------------------------
+struct Serve;  // request loop (serve.cu)
+
+}  // namespace lgc
+
+struct lgc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool result_on_device = false;
+  bool trace = false;
+  int64_t serve_mem_budget = 40ll << 30;
+  int64_t serve_max_batch = 64;
+  // small pinned host block for per-round read-back
+  lgc::Counters* h_counters = nullptr;
+  lgc::Counters* d_counters = nullptr;
+  int64_t* h_scratch = nullptr;  // pinned, 8 int64
+  // residual of the last PR-Nibble call (host svec), kept under LGC_OPT_TRACE
+  lgc_svec* last_residual = nullptr;
+  // trace of the last call
+  std::vector<int64_t> trace_sizes;
+  std::vector<int32_t> trace_ids;
+  // endpoints of the last rand-HK-PR call (device, owned)
+  int32_t* d_endpoints = nullptr;
+  int64_t n_endpoints = 0;
+  lgc::Serve* serve = nullptr;
+  // measurement
+  int64_t n_launches = 0;
+  bool profile = false;
+  struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> event_pool;
+  lgc_kernel_profile prof[LGC_PROF_COUNT] = {};
+};
+
+struct lgc_graph {
+  lgc_ctx* ctx = nullptr;
+  int64_t n = 0, nnz = 0;
+  int64_t* off = nullptr;  // device, n + 1
+  int32_t* col = nullptr;  // device, nnz
+  int32_t* deg = nullptr;  // device, n (int32 degree, read where off[] pairs would cost more)
+  int32_t max_deg = 0;
+};
+
+namespace lgc {
+
+// Stream-ordered device allocation (CUDA memory pool of the device; freed
+// memory is cached by the pool).
+int dalloc(lgc_ctx* ctx, void** p, size_t bytes);
+void dfree(lgc_ctx* ctx, void* p);
+
+template <class T>
+int dalloc_t(lgc_ctx* ctx, T** p, size_t count) {
+  return dalloc(ctx, (void**)p, count * sizeof(T));
+}
+
+// A growable device buffer.
+template <class T>
+struct DBuf {
+  T* ptr = nullptr;
+  size_t cap = 0;
+  int reserve(lgc_ctx* ctx, size_t count) {
+    if (count <= cap) return LGC_OK;
+    size_t nc = cap ? cap : 1024;
+    while (nc < count) nc *= 2;
+    if (ptr) dfree(ctx, ptr);
+    ptr = nullptr;
+    cap = 0;
+    LGC_TRY(dalloc_t(ctx, &ptr, nc));
+    cap = nc;
+    return LGC_OK;
+  }
+  void release(lgc_ctx* ctx) {
+    if (ptr) dfree(ctx, ptr);
+    ptr = nullptr;
+    cap = 0;
+  }
+};
+
+// Allocates a cleared table with capacity >= min_cap (power of two).
+int table_create(lgc_ctx* ctx, Table* T, int64_t min_cap, bool with_p);
+void table_destroy(lgc_ctx* ctx, Table* T);
+int table_clear(lgc_ctx* ctx, Table* T);
+// Rehashes into a table of capacity >= new_cap; the frontier slots fs[0..nf)
+// (if given) are re-resolved from their vertex ids fv.
+int table_grow(lgc_ctx* ctx, Table* T, int64_t new_cap, const int32_t* fv, int32_t* fs,
+               int64_t nf);
+int64_t pow2_at_least(int64_t x);
+
+// Library-owned outputs carry their context for release.
+struct SvecBox {
+  lgc_svec pub;
+  lgc_ctx* ctx;
+};
+struct ClusterBox {
+  lgc_cluster pub;
+  lgc_ctx* ctx;
+};
+// Builds an lgc_svec from device arrays (copied into a fresh allocation,
+// on the device or the host according to on_device).
+int make_svec(lgc_ctx* ctx, const int32_t* d_idx, const double* d_val, int64_t nnz,
+              bool on_device, lgc_svec** out);
+
+// Extracts {(key - 1, value) : value > 0} from a table, sorted by vertex id.
+// vals == nullptr uses T.s[].val, else vals[slot].
+int table_extract_sorted(lgc_ctx* ctx, const Table& T, const double* vals, int64_t n_vertices,
+                         int32_t** d_idx, double** d_val, int64_t* nnz,
+                         bool positive_only = true);
+
+// Algorithm drivers (diffuse.cu, rwalk.cu, sweep.cu).  ctx supplies the
+// stream and scratch; g is read-only and may be shared by several contexts.
+int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm,
+                 lgc_svec** p, lgc_stats* st, lgc_svec** r_out);
+int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* prm, lgc_svec** p,
+               lgc_stats* st);
+int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, lgc_svec** p,
+             lgc_stats* st);
+int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_params* prm,
+                  lgc_svec** p, lgc_stats* st);
+int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out);
+// d(x) of a seed, checked: LGC_EINVAL unless 0 <= x < n and d(x) >= 1.
+int validate_seed(lgc_ctx* ctx, lgc_graph* g, int32_t x, int64_t* dx);
+int ctx_init(lgc_ctx* ctx, int device, cudaStream_t stream);
+void ctx_fini(lgc_ctx* ctx);
+
+double now_seconds();
+
+// Profiling scope: records CUDA events around the launches made between
+// begin and end when ctx->profile is set, and counts launches always.
+struct ProfScope {
+  lgc_ctx* ctx;
+  int kernel;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(lgc_ctx* c, int k, double b);
+  ~ProfScope();
+};
+cudaEvent_t take_event(lgc_ctx* ctx);
+// Folds completed event pairs into ctx->prof (synchronizes the stream).
+void profile_collect(lgc_ctx* ctx);
+
+}  // namespace lgc
+
+// Counts one kernel launch on ctx.
+#define LGC_COUNT_LAUNCH(ctx) ((ctx)->n_launches++)

@@ -1,0 +1,895 @@
+// Synchronous frontier diffusions: PR-Nibble (Sec. 3.3), Nibble (Sec. 3.2)
+// and HK-PR (Sec. 3.4).
+//
+// One round = vertexMap over the frontier F (per-algorithm kernel: reads the
+// frontier values, updates the vertex's own entries, computes the share it
+// sends along each edge) followed by an edgeMap (generic: adds the share to
+// the destination's entry of a hash table) and the filter that forms the
+// next frontier.
+//
+// Atomic mode: the edgeMap adds with atomicAdd (the paper's fetchAdd).  The
+// next frontier is formed during the edgeMap itself: the one add that takes
+// a destination from below its threshold c*d(w) to at least it appends w
+// (values only grow, so exactly one add crosses).  Only F and N(F) can
+// change, so this equals the paper's filter over the whole sparse set.
+//
+// Deterministic mode: the edgeMap emits one (destination, share) record per
+// edge in frontier order (the frontier is kept in ascending id), sorts the
+// records stably by destination, and folds each destination's run left to
+// right starting from the value it holds after the vertexMap.  That is the
+// order a sequential loop over ascending sources produces, so p, r and every
+// frontier are bit-identical to it.  The filter then compacts the runs whose
+// result reaches the threshold; runs are in ascending id, so the next
+// frontier is too.
+//
+// All arithmetic is IEEE binary64 with FMA contraction disabled (--fmad=false),
+// each expression evaluated in the order written.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "prim.cuh"
+
+namespace lgc {
+
+namespace {
+
+constexpr int kEdgeItems = 4;
+constexpr int kEdgeTile = kBlock * kEdgeItems;  // edges per CTA tile
+
+enum FrontierMode { kFmNone = 0, kFmThreshold = 1, kFmInserted = 2 };
+
+__device__ inline int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Stages, for the block's record range [e0, e1), the exclusive prefix sums of
+// the sources owning those records into s_epos[0..cnt] (the last entry is
+// the end of the last staged source) and returns cnt <= kEdgeTile.  All
+// threads of the block must call it; the caller synchronizes after staging
+// its own per-source arrays.
+__device__ inline int stage_sources(const int64_t* __restrict__ epos, int64_t nf, int64_t total,
+                                    int64_t e0, int64_t e1, int64_t* s_i0, int64_t* s_i1,
+                                    int64_t* s_epos) {
+  if (threadIdx.x == 0) *s_i0 = upper_bound_i64(epos, nf, e0) - 1;
+  if (threadIdx.x == 32) *s_i1 = upper_bound_i64(epos, nf, e1 - 1) - 1;
+  __syncthreads();
+  const int64_t i0 = *s_i0;
+  int64_t c = *s_i1 - i0 + 1;
+  if (i0 < 0 || c < 0) c = 0;
+  if (c > kEdgeTile) c = kEdgeTile;
+  const int cnt = (int)c;
+  for (int j = threadIdx.x; j <= cnt; j += kBlock)
+    s_epos[j] = (i0 + j < nf) ? epos[i0 + j] : total;
+  __syncthreads();
+  return cnt;
+}
+
+// Source j (within the staged range) of record e and its local index *q;
+// -1 if e is not a record of a staged source.
+__device__ inline int find_source(const int64_t* s_epos, int cnt, int64_t e, int64_t* q) {
+  int lo = 0, hi = cnt;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s_epos[mid] <= e) lo = mid + 1;
+    else hi = mid;
+  }
+  const int j = lo - 1;
+  if (j < 0) return -1;
+  const int64_t local = e - s_epos[j];
+  if (local >= s_epos[j + 1] - s_epos[j]) return -1;
+  *q = local;
+  return j;
+}
+
+__device__ inline void count_inserted(int ins, int64_t* counter) {
+  const unsigned active = __activemask();
+  const unsigned m = __ballot_sync(active, ins);
+  if (m && (threadIdx.x & 31) == __ffs(active) - 1)
+    atomicAdd((unsigned long long*)counter, (unsigned long long)__popc(m));
+}
+
+// ---------------------------------------------------------------------------
+// vertexMap kernels.  Each writes, per frontier entry i: share[i], the
+// record count cnt[i] (d(v), plus one self record in deterministic mode when
+// the vertex itself is a key of the destination table) and foff[i] = off[v].
+// ---------------------------------------------------------------------------
+
+// PR-Nibble, Fig. alg:pr-nibble (rule 1) / alg:pr-nibble2 (rule 0).  T holds
+// r in slot.val and p in T.p[slot]; r' is updated in place (every read of r
+// in the round is of a frontier vertex, done here before the edgeMap).
+__global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                     const int32_t* __restrict__ fs, Table T,
+                                     const int64_t* __restrict__ off, double alpha, double cs,
+                                     double cn, double eps, int rule, int det,
+                                     double* __restrict__ share, int64_t* __restrict__ cnt,
+                                     int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
+                                     int32_t ncap, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool pred = false;
+    int32_t v = 0, s = 0;
+    int64_t d = 0;
+    if (i < nf) {
+      v = fv[i];
+      s = fs[i];
+      const bool ok = s >= 0;  // always true unless a table overflowed (flagged)
+      const double r = ok ? T.s[s].val : 0.0;
+      const int64_t o0 = off[v];
+      d = off[v + 1] - o0;
+      double sh, rbase;
+      if (rule == 0) {
+        if (ok) T.p[s] = T.p[s] + cs * r;
+        rbase = 0.0;
+        sh = (cn * r) / (double)d;
+      } else {
+        if (ok) T.p[s] = T.p[s] + alpha * r;
+        rbase = ((1.0 - alpha) * r) / 2.0;
+        sh = ((1.0 - alpha) * r) / (2.0 * (double)d);
+      }
+      if (ok) T.s[s].val = rbase;
+      share[i] = sh;
+      cnt[i] = d + (det ? 1 : 0);
+      foff[i] = o0;
+      pred = ok && !det && rule == 1 && rbase >= eps * (double)d;
+    }
+    frontier_append(pred, v, s, d, nfv, nfs, C, ncap);
+  }
+}
+
+// Nibble, Fig. alg:nibble: p'[v] = p[v]/2 on the frontier (S = p, D = p',
+// fresh), share p[v]/(2 d(v)).
+__global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                   const int32_t* __restrict__ fs, Table S, Table D,
+                                   const int64_t* __restrict__ off, double eps, int fmode,
+                                   int det, double* __restrict__ share, int64_t* __restrict__ cnt,
+                                   int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
+                                   int32_t ncap, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool pred = false;
+    int ins = 0;
+    int32_t v = 0, ds = 0;
+    int64_t d = 0;
+    if (i < nf) {
+      v = fv[i];
+      const double pv = fs[i] >= 0 ? S.s[fs[i]].val : 0.0;
+      const int64_t o0 = off[v];
+      d = off[v + 1] - o0;
+      ds = (int32_t)ht_find_or_insert(D, v, &ins, &C->err);
+      const double self = pv / 2.0;
+      if (ds >= 0) D.s[ds].val = self;
+      share[i] = pv / (2.0 * (double)d);
+      cnt[i] = d + (det ? 1 : 0);
+      foff[i] = o0;
+      if (!det && ds >= 0)
+        pred = fmode == kFmInserted ? true : self >= eps * (double)d;
+    }
+    count_inserted(ins, &C->aux);
+    frontier_append(pred, v, ds, d, nfv, nfs, C, ncap);
+  }
+}
+
+// HK-PR, Fig. alg:hkpr: p[v] += r[v] on the frontier; share
+// t r[v]/((j+1) d(v)) or, on the last level, r[v]/d(v).
+__global__ void vmap_hkpr_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                 const int32_t* __restrict__ fs, Table S, Table P,
+                                 const int64_t* __restrict__ off, double t, int j, int last,
+                                 double* __restrict__ share, int64_t* __restrict__ cnt,
+                                 int64_t* __restrict__ foff, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int ins = 0;
+    if (i < nf) {
+      const int32_t v = fv[i];
+      const double r = fs[i] >= 0 ? S.s[fs[i]].val : 0.0;
+      const int64_t o0 = off[v];
+      const int64_t d = off[v + 1] - o0;
+      const int64_t ps = ht_find_or_insert(P, v, &ins, &C->err);
+      if (ps >= 0) P.s[ps].val = P.s[ps].val + r;
+      share[i] = last ? r / (double)d : (t * r) / ((double)(j + 1) * (double)d);
+      cnt[i] = d;
+      foff[i] = o0;
+    }
+    count_inserted(ins, &C->aux);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// edgeMap, atomic mode.  Edge-balanced: CTA tile k covers edges
+// [k*kEdgeTile, (k+1)*kEdgeTile) of the frontier's concatenated adjacency
+// lists; the tile's sources are found by binary search in the exclusive
+// prefix sums of the frontier degrees and staged in shared memory, and each
+// thread then finds its edge's source there.  Consecutive threads read
+// consecutive col[] entries.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock)
+    emap_atomic_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+                       const double* __restrict__ share, const int64_t* __restrict__ epos,
+                       const int64_t* __restrict__ foff, int64_t nf, int64_t E_host,
+                       const int64_t* __restrict__ E_dev, Table D, double c, int fmode,
+                       int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
+  __shared__ int64_t s_epos[kEdgeTile + 1];
+  __shared__ int64_t s_off[kEdgeTile];
+  __shared__ double s_share[kEdgeTile];
+  __shared__ int64_t s_i0, s_i1;
+  // the device-computed total bounds every edge index, whatever the host passed
+  const int64_t E = min(E_host, *E_dev);
+  const int64_t ntiles = (E + kEdgeTile - 1) / kEdgeTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kEdgeTile;
+    const int64_t e1 = min(E, e0 + kEdgeTile);
+    const int cntsrc = stage_sources(epos, nf, E, e0, e1, &s_i0, &s_i1, s_epos);
+    const int64_t i0 = s_i0;
+    for (int j = threadIdx.x; j < cntsrc; j += kBlock) {
+      s_off[j] = foff[i0 + j];
+      s_share[j] = share[i0 + j];
+    }
+    __syncthreads();
+    int32_t w[kEdgeItems];
+    double sh[kEdgeItems];
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      const int64_t e = e0 + k * kBlock + threadIdx.x;
+      w[k] = -1;
+      int64_t q;
+      const int j = e < e1 ? find_source(s_epos, cntsrc, e, &q) : -1;
+      if (j >= 0) {
+        w[k] = col[s_off[j] + q];
+        sh[k] = s_share[j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      bool pred = false;
+      int ins = 0;
+      int32_t slot = -1;
+      int64_t dw = 0;
+      if (w[k] >= 0) {
+        slot = (int32_t)ht_find_or_insert(D, w[k], &ins, &C->err);
+        if (slot >= 0) {
+          const double old = atomicAdd(&D.s[slot].val, sh[k]);
+          if (fmode == kFmThreshold) {
+            const double nv = old + sh[k];
+            if (nv >= c) {  // c*d(w) >= c for d(w) >= 1: cheap pre-test
+              dw = deg[w[k]];
+              const double thr = c * (double)dw;
+              pred = old < thr && nv >= thr;
+            }
+          } else if (fmode == kFmInserted && ins) {
+            dw = deg[w[k]];
+            pred = true;
+          }
+        }
+      }
+      count_inserted(ins, &C->inserted);
+      frontier_append(pred, w[k], slot, dw, nfv, nfs, C, ncap);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// edgeMap, deterministic mode.
+// ---------------------------------------------------------------------------
+// Emits record e of source i: with a self record, local index 0 is
+// (v, +0.0) (adding +0.0 to a non-negative value changes nothing) and local
+// index q >= 1 is edge q-1; without, local index q is edge q.
+__global__ void __launch_bounds__(kBlock)
+    emit_records_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ fv,
+                        const double* __restrict__ share, const int64_t* __restrict__ epos,
+                        const int64_t* __restrict__ foff, int64_t nf, int64_t R, int self_rec,
+                        uint32_t* __restrict__ rkey, double* __restrict__ rval) {
+  __shared__ int64_t s_epos[kEdgeTile + 1];
+  __shared__ int64_t s_off[kEdgeTile];
+  __shared__ double s_share[kEdgeTile];
+  __shared__ int32_t s_v[kEdgeTile];
+  __shared__ int64_t s_i0, s_i1;
+  const int64_t ntiles = (R + kEdgeTile - 1) / kEdgeTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kEdgeTile;
+    const int64_t e1 = min(R, e0 + kEdgeTile);
+    const int cntsrc = stage_sources(epos, nf, R, e0, e1, &s_i0, &s_i1, s_epos);
+    const int64_t i0 = s_i0;
+    for (int j = threadIdx.x; j < cntsrc; j += kBlock) {
+      s_off[j] = foff[i0 + j];
+      s_share[j] = share[i0 + j];
+      s_v[j] = fv[i0 + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < kEdgeItems; k++) {
+      const int64_t e = e0 + k * kBlock + threadIdx.x;
+      int64_t q = 0;
+      const int j = e < e1 ? find_source(s_epos, cntsrc, e, &q) : -1;
+      if (j >= 0) {
+        if (self_rec && q == 0) {
+          rkey[e] = (uint32_t)s_v[j];
+          rval[e] = 0.0;
+        } else {
+          if (self_rec) q -= 1;
+          rkey[e] = (uint32_t)col[s_off[j] + q];
+          rval[e] = s_share[j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void head_flags_kernel(const uint32_t* __restrict__ rkey, int64_t R,
+                                  int64_t* __restrict__ flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < R;
+       e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = (e == 0 || rkey[e] != rkey[e - 1]) ? 1 : 0;
+}
+
+// flag[] was scanned (exclusive) into segid[]; heads record their start.
+__global__ void head_starts_kernel(const uint32_t* __restrict__ rkey, int64_t R,
+                                   const int64_t* __restrict__ segid,
+                                   int64_t* __restrict__ segstart) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < R;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (e == 0 || rkey[e] != rkey[e - 1]) segstart[segid[e]] = e;
+}
+
+// One thread per destination run: left fold from the current table value,
+// in ascending source order (the order of the run after the stable sort).
+__global__ void fold_kernel(const uint32_t* __restrict__ rkey, const double* __restrict__ rval,
+                            int64_t R, const int64_t* __restrict__ segstart, int64_t nseg,
+                            Table D, const int32_t* __restrict__ deg, double c, int fmode,
+                            int64_t* __restrict__ qflag, int32_t* __restrict__ segv,
+                            int32_t* __restrict__ segslot, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = base + threadIdx.x;
+    int ins = 0;
+    if (sg < nseg) {
+      const int64_t b = segstart[sg];
+      const int64_t e = sg + 1 < nseg ? segstart[sg + 1] : R;
+      const int32_t w = (int32_t)rkey[b];
+      const int64_t slot = ht_find_or_insert(D, w, &ins, &C->err);
+      int64_t q = 0;
+      if (slot >= 0) {
+        double acc = D.s[slot].val;
+        for (int64_t k = b; k < e; k++) acc = acc + rval[k];
+        D.s[slot].val = acc;
+        if (fmode == kFmThreshold) q = acc >= c * (double)deg[w] ? 1 : 0;
+        else if (fmode == kFmInserted) q = 1;
+      }
+      qflag[sg] = q;
+      segv[sg] = w;
+      segslot[sg] = (int32_t)slot;
+    }
+    count_inserted(ins, &C->inserted);
+  }
+}
+
+// Order-preserving compaction of the qualifying runs into the next frontier.
+__global__ void compact_frontier_kernel(const int64_t* __restrict__ qflag,
+                                        const int64_t* __restrict__ qpos, int64_t nseg,
+                                        const int32_t* __restrict__ segv,
+                                        const int32_t* __restrict__ segslot,
+                                        const int32_t* __restrict__ deg, int32_t* nfv,
+                                        int32_t* nfs, int32_t ncap, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = base + threadIdx.x;
+    int64_t d = 0;
+    if (sg < nseg && qflag[sg]) {
+      const int64_t pos = qpos[sg];
+      if (pos < ncap) {
+        nfv[pos] = segv[sg];
+        nfs[pos] = segslot[sg];
+      } else {
+        atomicOr(&C->err, kErrFrontierOverflow);
+      }
+      d = deg[segv[sg]];
+    }
+    // integer sum of degrees: order-independent
+    const unsigned active = __activemask();
+    unsigned long long lo = __reduce_add_sync(active, (unsigned)(d & 0xFFFF));
+    unsigned long long hi = __reduce_add_sync(active, (unsigned)(d >> 16));
+    if ((threadIdx.x & 31) == __ffs(active) - 1 && (lo | hi))
+      atomicAdd((unsigned long long*)&C->next_edges, lo + (hi << 16));
+  }
+}
+
+__global__ void set_counter_size_kernel(Counters* C, const int64_t* total) {
+  C->next_size = (int32_t)*total;
+}
+
+__global__ void init_seed_kernel(Table T, int32_t x, double r0, int32_t* fv, int32_t* fs,
+                                 Counters* C) {
+  int ins = 0;
+  int64_t s = ht_find_or_insert(T, x, &ins, &C->err);
+  if (s >= 0) T.s[s].val = r0;
+  fv[0] = x;
+  fs[0] = (int32_t)s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Frontier {
+  DBuf<int32_t> v, s;
+  int64_t size = 0, edges = 0;
+  void release(lgc_ctx* ctx) {
+    v.release(ctx);
+    s.release(ctx);
+  }
+};
+
+struct PushWork {
+  lgc_ctx* ctx;
+  lgc_graph* g;
+  Frontier F, G;
+  DBuf<double> share;
+  DBuf<int64_t> cnt, epos, foff;
+  DBuf<uint32_t> rk, rk2;
+  DBuf<double> rv, rv2;
+  DBuf<int64_t> flag, segid, segstart, qflag, qpos;
+  DBuf<int32_t> segv, segslot;
+  DBuf<int64_t> total;  // one device int64
+  lgc_stats st{};
+  explicit PushWork(lgc_ctx* c, lgc_graph* gr) : ctx(c), g(gr) {}
+  ~PushWork() {
+    F.release(ctx);
+    G.release(ctx);
+    share.release(ctx);
+    cnt.release(ctx);
+    epos.release(ctx);
+    foff.release(ctx);
+    rk.release(ctx);
+    rk2.release(ctx);
+    rv.release(ctx);
+    rv2.release(ctx);
+    flag.release(ctx);
+    segid.release(ctx);
+    segstart.release(ctx);
+    qflag.release(ctx);
+    qpos.release(ctx);
+    segv.release(ctx);
+    segslot.release(ctx);
+    total.release(ctx);
+  }
+
+  int reset_counters() {
+    LGC_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(Counters), ctx->stream));
+    return LGC_OK;
+  }
+  int read_counters(Counters* out) {
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_counters, ctx->d_counters, sizeof(Counters),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *out = *ctx->h_counters;
+    if (out->err & kErrTableFull) return LGC_ETABLEFULL;
+    if (out->err & kErrFrontierOverflow) return LGC_ETABLEFULL;
+    return LGC_OK;
+  }
+  int reserve_frontier_scratch(int64_t nf) {
+    LGC_TRY(share.reserve(ctx, nf));
+    LGC_TRY(cnt.reserve(ctx, nf));
+    LGC_TRY(epos.reserve(ctx, nf));
+    LGC_TRY(foff.reserve(ctx, nf));
+    LGC_TRY(total.reserve(ctx, 1));
+    return LGC_OK;
+  }
+  int reserve_next(int64_t cap) {
+    LGC_TRY(G.v.reserve(ctx, cap));
+    LGC_TRY(G.s.reserve(ctx, cap));
+    return LGC_OK;
+  }
+  void record_trace() {
+    if (!ctx->trace) return;
+    size_t at = ctx->trace_ids.size();
+    ctx->trace_ids.resize(at + F.size);
+    if (F.size)
+      cudaMemcpyAsync(ctx->trace_ids.data() + at, F.v.ptr, 4 * F.size, cudaMemcpyDeviceToHost,
+                      ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->trace_sizes.push_back(F.size);
+  }
+
+  // edgeMap + filter into table D.  Records per source are cnt[] (scanned
+  // into epos by the caller's vertexMap step).  Returns the counters.
+  int edge_phase(const Table& D, double c, int fmode, bool det, bool self_rec, int64_t nrec,
+                 Counters* out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t nf = F.size;
+    const int32_t ncap = (int32_t)G.v.cap;
+    // algorithmic bytes: 24 per pushed edge (col 4, key 4, value read-modify-write 16),
+    // 24 per frontier source staged (epos, off, share), 8 per next-frontier entry
+    const double alg_bytes = 24.0 * (double)(nrec - (self_rec && det ? nf : 0)) + 24.0 * nf;
+    if (!det) {
+      if (nrec > 0) {
+        int64_t tiles = ceil_div(nrec, kEdgeTile);
+        int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+        ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
+        emap_atomic_kernel<<<grid, kBlock, 0, s>>>(g->col, g->deg, share.ptr, epos.ptr, foff.ptr,
+                                                    nf, nrec, total.ptr, D, c, fmode, G.v.ptr,
+                                                    G.s.ptr, ncap, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        LGC_CUDA_TRY(cudaGetLastError());
+      }
+      int st = read_counters(out);
+      if (ctx->profile && nrec > 0 && !ctx->prof_pending.empty())
+        ctx->prof_pending.back().bytes += 8.0 * out->next_size;
+      return st;
+    }
+    // deterministic: emit, stable sort by destination, fold, compact
+    LGC_TRY(rk.reserve(ctx, nrec));
+    LGC_TRY(rk2.reserve(ctx, nrec));
+    LGC_TRY(rv.reserve(ctx, nrec));
+    LGC_TRY(rv2.reserve(ctx, nrec));
+    LGC_TRY(flag.reserve(ctx, nrec));
+    LGC_TRY(segid.reserve(ctx, nrec));
+    if (nrec > 0) {
+      int64_t tiles = ceil_div(nrec, kEdgeTile);
+      int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+      ProfScope ps(ctx, LGC_PROF_DET_EDGE, alg_bytes);
+      emit_records_kernel<<<grid, kBlock, 0, s>>>(g->col, F.v.ptr, share.ptr, epos.ptr, foff.ptr,
+                                                   nf, nrec, self_rec ? 1 : 0, rk.ptr, rv.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_CUDA_TRY(cudaGetLastError());
+      LGC_TRY(radix_sort_u32_f64(ctx, rk.ptr, rv.ptr, rk2.ptr, rv2.ptr, nrec, bits_for(g->n)));
+      head_flags_kernel<<<grid_for(nrec), kBlock, 0, s>>>(rk.ptr, nrec, flag.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_TRY(scan_i64(ctx, flag.ptr, segid.ptr, nrec, false, total.ptr));
+    }
+    int64_t nseg = 0;
+    if (nrec > 0) {
+      LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost, s));
+      LGC_CUDA_TRY(cudaStreamSynchronize(s));
+      nseg = ctx->h_counters->aux;
+    }
+    LGC_TRY(segstart.reserve(ctx, nseg));
+    LGC_TRY(qflag.reserve(ctx, nseg));
+    LGC_TRY(qpos.reserve(ctx, nseg));
+    LGC_TRY(segv.reserve(ctx, nseg));
+    LGC_TRY(segslot.reserve(ctx, nseg));
+    if (nseg > 0) {
+      ProfScope ps(ctx, LGC_PROF_DET_EDGE, 0.0);
+      head_starts_kernel<<<grid_for(nrec), kBlock, 0, s>>>(rk.ptr, nrec, segid.ptr, segstart.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      fold_kernel<<<grid_for(nseg), kBlock, 0, s>>>(rk.ptr, rv.ptr, nrec, segstart.ptr, nseg, D,
+                                                     g->deg, c, fmode, qflag.ptr, segv.ptr,
+                                                     segslot.ptr, ctx->d_counters);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_CUDA_TRY(cudaGetLastError());
+      if (fmode != kFmNone) {
+        LGC_TRY(scan_i64(ctx, qflag.ptr, qpos.ptr, nseg, false, total.ptr));
+        compact_frontier_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
+            qflag.ptr, qpos.ptr, nseg, segv.ptr, segslot.ptr, g->deg, G.v.ptr, G.s.ptr, ncap,
+            ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        LGC_CUDA_TRY(cudaGetLastError());
+      }
+    }
+    return read_counters(out);
+  }
+
+  int scan_counts(int64_t* nrec_out) {
+    LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, F.size, false, total.ptr));
+    LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *nrec_out = ctx->h_counters->aux;
+    return LGC_OK;
+  }
+
+  void swap_frontiers() {
+    std::swap(F.v, G.v);
+    std::swap(F.s, G.s);
+    F.size = G.size;
+    F.edges = G.edges;
+    G.size = 0;
+    G.edges = 0;
+  }
+};
+
+int vgrid(int64_t nf) {
+  int64_t g = ceil_div(nf, kBlock);
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Makes D a cleared table able to take `need` keys at load <= 1/2.
+int fresh_table(lgc_ctx* ctx, Table* D, int64_t need) {
+  int64_t want = pow2_at_least(2 * (need < 32 ? 32 : need));
+  if (D->s && D->cap >= want && D->cap <= 8 * want) return table_clear(ctx, D);
+  table_destroy(ctx, D);
+  return table_create(ctx, D, want, false);
+}
+
+int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, lgc_svec** p,
+                lgc_stats* st_out, lgc_stats& st) {
+  int32_t* d_idx = nullptr;
+  double* d_val = nullptr;
+  int64_t nnz = 0;
+  LGC_TRY(table_extract_sorted(ctx, T, vals, g->n, &d_idx, &d_val, &nnz));
+  int s = make_svec(ctx, d_idx, d_val, nnz, ctx->result_on_device, p);
+  dfree(ctx, d_idx);
+  dfree(ctx, d_val);
+  st.table_capacity = T.cap;
+  if (st_out) *st_out = st;
+  return s;
+}
+
+}  // namespace
+
+int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm, lgc_svec** p,
+                 lgc_stats* st_out, lgc_svec** r_out) {
+  int64_t dx = 0;
+  LGC_TRY(validate_seed(ctx, g, x, &dx));
+  const double alpha = prm->alpha, eps = prm->eps;
+  if (!(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0) || (prm->rule != 0 && prm->rule != 1) ||
+      (prm->mode != 0 && prm->mode != 1))
+    return LGC_EINVAL;
+  const bool det = prm->mode == LGC_MODE_DET;
+  const double cs = (2.0 * alpha) / (1.0 + alpha);
+  const double cn = (1.0 - alpha) / (1.0 + alpha);
+  const int64_t max_rounds = prm->max_rounds > 0 ? prm->max_rounds : INT64_MAX;
+  ctx->trace_ids.clear();
+  ctx->trace_sizes.clear();
+
+  PushWork W(ctx, g);
+  Table T;
+  LGC_TRY(table_create(ctx, &T, 2 * (1 + dx), true));
+  int64_t count = 1;  // keys in T
+  int status = LGC_OK;
+  do {
+    if ((status = W.F.v.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.F.s.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.reset_counters()) != LGC_OK) break;
+    init_seed_kernel<<<1, 1, 0, ctx->stream>>>(T, x, 1.0, W.F.v.ptr, W.F.s.ptr, ctx->d_counters);
+    LGC_COUNT_LAUNCH(ctx);
+    W.F.size = 1;
+    W.F.edges = dx;
+    lgc_stats& st = W.st;
+    while (W.F.size > 0) {
+      if (st.rounds >= max_rounds) {
+        status = LGC_EMAXROUNDS;
+        break;
+      }
+      W.record_trace();
+      // grow T so the round's new keys (at most the frontier's edges) fit at load 1/2
+      int64_t need = min64(count + W.F.edges, g->n);
+      if (2 * need > T.cap) {
+        if ((status = table_grow(ctx, &T, 2 * need, W.F.v.ptr, W.F.s.ptr, W.F.size)) != LGC_OK)
+          break;
+      }
+      const int64_t nf = W.F.size;
+      if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
+      if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) break;
+      if ((status = W.reset_counters()) != LGC_OK) break;
+      {
+        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+        vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+            nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
+            W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap,
+            ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (cudaGetLastError() != cudaSuccess) {
+        status = LGC_ECUDA;
+        break;
+      }
+      int64_t nrec = W.F.edges;
+      if (det) {
+        if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+      } else {
+        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
+      }
+      Counters C;
+      status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C);
+      if (status != LGC_OK) break;
+      st.rounds++;
+      st.pushes += nf;
+      st.pushed_edges += W.F.edges;
+      count += C.inserted;
+      W.G.size = C.next_size;
+      W.G.edges = C.next_edges;
+      W.swap_frontiers();
+    }
+    st.touched = count;
+  } while (0);
+  if (status == LGC_OK || status == LGC_EMAXROUNDS) {
+    int s2 = finish_svec(ctx, g, T, T.p, p, st_out, W.st);
+    if (s2 == LGC_OK && r_out) {
+      // residual of every key (including zeros), for tests
+      int32_t* d_idx = nullptr;
+      double* d_val = nullptr;
+      int64_t nnz = 0;
+      s2 = table_extract_sorted(ctx, T, nullptr, g->n, &d_idx, &d_val, &nnz, false);
+      if (s2 == LGC_OK) s2 = make_svec(ctx, d_idx, d_val, nnz, false, r_out);
+      dfree(ctx, d_idx);
+      dfree(ctx, d_val);
+    }
+    if (s2 != LGC_OK) status = s2;
+  }
+  table_destroy(ctx, &T);
+  return status;
+}
+
+int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* prm, lgc_svec** p,
+               lgc_stats* st_out) {
+  int64_t dx = 0;
+  LGC_TRY(validate_seed(ctx, g, x, &dx));
+  const double eps = prm->eps;
+  if (prm->T < 0 || !(eps >= 0.0) || (prm->mode != 0 && prm->mode != 1)) return LGC_EINVAL;
+  const bool det = prm->mode == LGC_MODE_DET;
+  const int fmode = eps > 0.0 ? kFmThreshold : kFmInserted;
+  ctx->trace_ids.clear();
+  ctx->trace_sizes.clear();
+
+  PushWork W(ctx, g);
+  Table Pc, Pn;  // p and p'
+  LGC_TRY(table_create(ctx, &Pc, 64, false));
+  int64_t count = 1;
+  int status = LGC_OK;
+  do {
+    if ((status = W.F.v.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.F.s.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.reset_counters()) != LGC_OK) break;
+    init_seed_kernel<<<1, 1, 0, ctx->stream>>>(Pc, x, 1.0, W.F.v.ptr, W.F.s.ptr, ctx->d_counters);
+    LGC_COUNT_LAUNCH(ctx);
+    W.F.size = 1;
+    W.F.edges = dx;
+    lgc_stats& st = W.st;
+    for (int t = 1; t <= prm->T; t++) {
+      W.record_trace();
+      const int64_t nf = W.F.size;
+      const int64_t need = min64(g->n, nf + W.F.edges);
+      if ((status = fresh_table(ctx, &Pn, need)) != LGC_OK) break;  // p' = {}
+      if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
+      if ((status = W.reserve_next(need)) != LGC_OK) break;
+      if ((status = W.reset_counters()) != LGC_OK) break;
+      {
+        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+        vmap_nibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+            nf, W.F.v.ptr, W.F.s.ptr, Pc, Pn, g->off, eps, fmode, det ? 1 : 0, W.share.ptr,
+            W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (cudaGetLastError() != cudaSuccess) {
+        status = LGC_ECUDA;
+        break;
+      }
+      int64_t nrec = W.F.edges;
+      if (det) {
+        if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+      } else {
+        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
+      }
+      Counters C;
+      status = W.edge_phase(Pn, eps, fmode, det, true, nrec, &C);
+      if (status != LGC_OK) break;
+      st.rounds++;
+      st.pushes += nf;
+      st.pushed_edges += W.F.edges;
+      W.G.size = C.next_size;
+      W.G.edges = C.next_edges;
+      if (W.G.size == 0) break;  // return the previous p
+      std::swap(Pc, Pn);         // p = p'
+      count = C.aux + C.inserted;
+      W.swap_frontiers();
+    }
+    st.touched = count;
+  } while (0);
+  if (status == LGC_OK) status = finish_svec(ctx, g, Pc, nullptr, p, st_out, W.st);
+  table_destroy(ctx, &Pc);
+  table_destroy(ctx, &Pn);
+  return status;
+}
+
+int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, lgc_svec** p,
+             lgc_stats* st_out) {
+  int64_t dx = 0;
+  LGC_TRY(validate_seed(ctx, g, x, &dx));
+  const double t = prm->t, eps = prm->eps;
+  const int N = prm->N;
+  if (N < 1 || !(t > 0.0) || !(eps >= 0.0) || (prm->mode != 0 && prm->mode != 1))
+    return LGC_EINVAL;
+  const bool det = prm->mode == LGC_MODE_DET;
+  // psi_N = 1, psi_k = 1 + (t/(k+1)) psi_{k+1}; c_j = e^t eps / (2 N psi_j)
+  std::vector<double> psi(N + 1), c(N + 1);
+  psi[N] = 1.0;
+  for (int k = N - 1; k >= 0; k--) psi[k] = 1.0 + (t / (double)(k + 1)) * psi[k + 1];
+  for (int j = 0; j <= N; j++) c[j] = (exp(t) * eps) / (2.0 * (double)N * psi[j]);
+  ctx->trace_ids.clear();
+  ctx->trace_sizes.clear();
+
+  PushWork W(ctx, g);
+  Table P, Rc, Rn;
+  LGC_TRY(table_create(ctx, &P, 2 * (1 + dx), false));
+  int status = table_create(ctx, &Rc, 64, false);
+  int64_t pcount = 0;
+  do {
+    if (status != LGC_OK) break;
+    if ((status = W.F.v.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.F.s.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.reset_counters()) != LGC_OK) break;
+    init_seed_kernel<<<1, 1, 0, ctx->stream>>>(Rc, x, 1.0, W.F.v.ptr, W.F.s.ptr, ctx->d_counters);
+    LGC_COUNT_LAUNCH(ctx);
+    W.F.size = 1;
+    W.F.edges = dx;
+    lgc_stats& st = W.st;
+    int j = 0;
+    while (W.F.size > 0) {
+      W.record_trace();
+      const int64_t nf = W.F.size;
+      const bool last = j + 1 >= N;
+      // p takes the frontier (and, on the last level, its neighbours)
+      int64_t pneed = min64(g->n, pcount + nf + (last ? W.F.edges : 0));
+      if (2 * pneed > P.cap)
+        if ((status = table_grow(ctx, &P, 2 * pneed, nullptr, nullptr, 0)) != LGC_OK) break;
+      if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
+      if ((status = W.reset_counters()) != LGC_OK) break;
+      {
+        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+        vmap_hkpr_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+            nf, W.F.v.ptr, W.F.s.ptr, Rc, P, g->off, t, j, last ? 1 : 0, W.share.ptr, W.cnt.ptr,
+            W.foff.ptr, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (cudaGetLastError() != cudaSuccess) {
+        status = LGC_ECUDA;
+        break;
+      }
+      if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
+      Counters C;
+      if (!last) {
+        const int64_t need = min64(g->n, W.F.edges);
+        if ((status = fresh_table(ctx, &Rn, need)) != LGC_OK) break;  // r' = {}
+        if ((status = W.reserve_next(need)) != LGC_OK) break;
+        const double cj = c[j + 1];
+        status = W.edge_phase(Rn, cj, cj > 0.0 ? kFmThreshold : kFmInserted, det, false,
+                              W.F.edges, &C);
+        if (status != LGC_OK) break;
+        pcount += C.aux;
+        st.rounds++;
+        st.pushes += nf;
+        st.pushed_edges += W.F.edges;
+        std::swap(Rc, Rn);  // r = r'
+        W.G.size = C.next_size;
+        W.G.edges = C.next_edges;
+        W.swap_frontiers();
+        j++;
+      } else {
+        if ((status = W.reserve_next(1)) != LGC_OK) break;
+        status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C);
+        if (status != LGC_OK) break;
+        pcount += C.aux + C.inserted;
+        st.rounds++;
+        st.pushes += nf;
+        st.pushed_edges += W.F.edges;
+        break;
+      }
+    }
+    st.touched = pcount;
+  } while (0);
+  if (status == LGC_OK) status = finish_svec(ctx, g, P, nullptr, p, st_out, W.st);
+  table_destroy(ctx, &P);
+  table_destroy(ctx, &Rc);
+  table_destroy(ctx, &Rn);
+  return status;
+}
+
+}  // namespace lgc

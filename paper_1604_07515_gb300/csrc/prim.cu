@@ -1,0 +1,279 @@
+// Prefix sums and LSD radix sort, written for sm_103a.
+#include "prim.cuh"
+
+namespace lgc {
+
+namespace {
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;  // 2048
+
+// Inclusive block-wide scan of one int64 per thread; returns the inclusive
+// value and the block total.
+__device__ inline int64_t block_inclusive_scan(int64_t x, int64_t* warp_tot, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < (kBlock / 32) ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < (kBlock / 32)) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  int64_t offset = warp > 0 ? warp_tot[warp - 1] : 0;
+  *total = warp_tot[kBlock / 32 - 1];
+  __syncthreads();
+  return x + offset;
+}
+
+__global__ void scan_reduce_kernel(const int64_t* __restrict__ in, int64_t n,
+                                   int64_t* __restrict__ partial) {
+  __shared__ int64_t warp_tot[kBlock / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  int64_t tot;
+  block_inclusive_scan(s, warp_tot, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Scans one tile; offsets[blockIdx.x] (exclusive block prefix) or 0.
+__global__ void scan_tile_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                 int64_t n, const int64_t* __restrict__ offsets, int inclusive,
+                                 int64_t* __restrict__ total) {
+  __shared__ int64_t tile[kScanTile];
+  __shared__ int64_t warp_tot[kBlock / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    tile[k * kBlock + threadIdx.x] = i < n ? in[i] : 0;
+  }
+  __syncthreads();
+  int64_t v[kScanItems];
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = tile[threadIdx.x * kScanItems + k];
+    s += v[k];
+  }
+  int64_t tot;
+  int64_t incl = block_inclusive_scan(s, warp_tot, &tot);
+  int64_t run = incl - s + (offsets ? offsets[blockIdx.x] : 0);
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t x = v[k];
+    tile[threadIdx.x * kScanItems + k] = inclusive ? run + x : run;
+    run += x;
+  }
+  __syncthreads();
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) out[i] = tile[k * kBlock + threadIdx.x];
+  }
+  if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kBlock - 1) {
+    // last element's inclusive value = grand total
+    *total = run;
+  }
+}
+
+__global__ void write_zero_kernel(int64_t* p) { *p = 0; }
+
+}  // namespace
+
+int grid_for(int64_t work, int block) {
+  int64_t g = ceil_div(work, block);
+  if (g < 1) g = 1;
+  if (g > (1ll << 30)) g = 1ll << 30;
+  return (int)g;
+}
+
+int bits_for(int64_t max_value) {
+  int b = 0;
+  while (b < 63 && ((int64_t)1 << b) < max_value) b++;
+  return b < 1 ? 1 : b;
+}
+
+int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+             int64_t* total) {
+  cudaStream_t st = ctx->stream;
+  if (n <= 0) {
+    if (total) {
+      write_zero_kernel<<<1, 1, 0, st>>>(total);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    return LGC_OK;
+  }
+  int64_t nb = ceil_div(n, kScanTile);
+  if (nb == 1) {
+    scan_tile_kernel<<<1, kBlock, 0, st>>>(in, out, n, nullptr, inclusive, total);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_CUDA_TRY(cudaGetLastError());
+    return LGC_OK;
+  }
+  int64_t* partial = nullptr;
+  LGC_TRY(dalloc_t(ctx, &partial, nb));
+  scan_reduce_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, n, partial);
+  LGC_COUNT_LAUNCH(ctx);
+  LGC_CUDA_TRY(cudaGetLastError());
+  int s = scan_i64(ctx, partial, partial, nb, false, nullptr);
+  if (s == LGC_OK) {
+    scan_tile_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, out, n, partial, inclusive, total);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaGetLastError() != cudaSuccess) s = LGC_ECUDA;
+  }
+  dfree(ctx, partial);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits.  Per pass: per-tile digit histograms, an
+// exclusive scan over (digit, tile) in digit-major order, and a stable
+// scatter.  Inside a tile each warp owns a contiguous run of 32 * kItems
+// elements and ranks equal digits with __match_any_sync, so the order of
+// equal keys is kept.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kItems = 8;
+constexpr int kTile = kBlock * kItems;  // 2048
+constexpr int kWarps = kBlock / 32;
+constexpr int kRadix = 256;
+
+template <class K>
+__global__ void radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
+                                  int64_t* __restrict__ hist, int64_t ntiles) {
+  __shared__ int h[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += kBlock) h[d] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int k = 0; k < kItems; k++) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & (K)0xFF)], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += kBlock)
+    hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+template <class K, class V>
+__global__ void radix_scatter_kernel(const K* __restrict__ keys_in, const V* __restrict__ vals_in,
+                                     K* __restrict__ keys_out, V* __restrict__ vals_out,
+                                     int64_t n, int shift, const int64_t* __restrict__ offs,
+                                     int64_t ntiles, int has_vals) {
+  __shared__ int wcnt[kWarps][kRadix];
+  __shared__ int64_t goff[kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += kBlock) {
+    goff[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    for (int w = 0; w < kWarps; w++) wcnt[w][d] = 0;
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * (32 * kItems);
+  K key[kItems];
+  V val[kItems];
+  int rank[kItems];
+  int digit[kItems];
+  const unsigned lt = (1u << lane) - 1;
+  for (int k = 0; k < kItems; k++) {
+    int64_t i = base + (int64_t)k * 32 + lane;
+    bool ok = i < n;
+    key[k] = ok ? keys_in[i] : (K)0;
+    if (has_vals) val[k] = ok ? vals_in[i] : V();
+    int d = ok ? (int)((key[k] >> shift) & (K)0xFF) : kRadix;  // kRadix = padding
+    digit[k] = d;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int r = __popc(peers & lt);
+    int before = d < kRadix ? wcnt[warp][d] : 0;
+    __syncwarp();
+    rank[k] = before + r;
+    int leader = __ffs(peers) - 1;
+    if (lane == leader && d < kRadix) wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps, per digit
+  for (int d = threadIdx.x; d < kRadix; d += kBlock) {
+    int run = 0;
+    for (int w = 0; w < kWarps; w++) {
+      int c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < kItems; k++) {
+    int d = digit[k];
+    if (d < kRadix) {
+      int64_t pos = goff[d] + wcnt[warp][d] + rank[k];
+      keys_out[pos] = key[k];
+      if (has_vals) vals_out[pos] = val[k];
+    }
+  }
+}
+
+template <class K, class V>
+int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
+                    int bits) {
+  if (n <= 1) return LGC_OK;
+  cudaStream_t st = ctx->stream;
+  const int64_t ntiles = ceil_div(n, kTile);
+  int64_t* hist = nullptr;
+  LGC_TRY(dalloc_t(ctx, &hist, (size_t)kRadix * ntiles));
+  K* a = keys;
+  V* va = vals;
+  K* b = keys_tmp;
+  V* vb = vals_tmp;
+  int passes = 0;
+  int status = LGC_OK;
+  for (int shift = 0; shift < bits; shift += 8, passes++) {
+    radix_hist_kernel<K><<<(unsigned)ntiles, kBlock, 0, st>>>(a, n, shift, hist, ntiles);
+    LGC_COUNT_LAUNCH(ctx);
+    status = scan_i64(ctx, hist, hist, (int64_t)kRadix * ntiles, false, nullptr);
+    if (status != LGC_OK) break;
+    radix_scatter_kernel<K, V><<<(unsigned)ntiles, kBlock, 0, st>>>(
+        a, va, b, vb, n, shift, hist, ntiles, vals != nullptr);
+    LGC_COUNT_LAUNCH(ctx);
+    K* t = a;
+    a = b;
+    b = t;
+    V* tv = va;
+    va = vb;
+    vb = tv;
+  }
+  if (status == LGC_OK && a != keys) {
+    cudaMemcpyAsync(keys, a, sizeof(K) * n, cudaMemcpyDeviceToDevice, st);
+    if (vals) cudaMemcpyAsync(vals, va, sizeof(V) * n, cudaMemcpyDeviceToDevice, st);
+  }
+  dfree(ctx, hist);
+  if (status == LGC_OK && cudaGetLastError() != cudaSuccess) status = LGC_ECUDA;
+  return status;
+}
+
+}  // namespace
+
+int radix_sort_u32_f64(lgc_ctx* ctx, uint32_t* keys, double* vals, uint32_t* keys_tmp,
+                       double* vals_tmp, int64_t n, int bits) {
+  return radix_sort_impl<uint32_t, double>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
+}
+int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                       int32_t* vals_tmp, int64_t n, int bits) {
+  return radix_sort_impl<uint64_t, int32_t>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
+}
+int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
+                       int32_t* vals_tmp, int64_t n, int bits) {
+  return radix_sort_impl<uint32_t, int32_t>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
+}
+int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, int bits) {
+  return radix_sort_impl<uint32_t, int32_t>(ctx, keys, (int32_t*)nullptr, keys_tmp,
+                                            (int32_t*)nullptr, n, bits);
+}
+
+}  // namespace lgc

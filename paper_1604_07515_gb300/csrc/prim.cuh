@@ -1,0 +1,32 @@
+// Device-wide primitives: prefix sums and LSD radix sort (Sec. 2,
+// "Parallel Primitives": prefix sum, filter, integer sort).
+#pragma once
+
+#include "common.cuh"
+
+namespace lgc {
+
+// out[i] = sum_{j < i} in[j] (exclusive) or sum_{j <= i} in[j] (inclusive),
+// int64.  If total != nullptr, the sum of all n inputs is written to
+// *total (device).  in and out may alias.
+int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+             int64_t* total);
+
+// Stable LSD radix sort of (key, value) pairs by key bits [0, bits), 8 bits
+// per pass.  keys/vals hold the input; the sorted result ends in keys/vals
+// (the tmp buffers are scratch of the same length).
+int radix_sort_u32_f64(lgc_ctx* ctx, uint32_t* keys, double* vals, uint32_t* keys_tmp,
+                       double* vals_tmp, int64_t n, int bits);
+int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                       int32_t* vals_tmp, int64_t n, int bits);
+int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
+                       int32_t* vals_tmp, int64_t n, int bits);
+// Keys only.
+int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, int bits);
+
+int bits_for(int64_t max_value);  // number of bits needed for values < max_value
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int grid_for(int64_t work, int block = kBlock);
+
+}  // namespace lgc

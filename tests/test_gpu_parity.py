@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Deterministic mode: p, r, every frontier, rounds and push counts must be
+bit-identical.  Atomic mode: p within 1e-12 relative L1 of the oracle and the
+sweep's conductance within 1e-9.  The sweep cut and rand-HK-PR endpoints are
+exact.  Sizes span many CTA tiles with ragged tails; the scale-16 and
+scale-22 R-MAT graphs are the two smallest benchmark workloads in full."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_07515_gb300 import inputs, lgc
+
+pytestmark = pytest.mark.gpu
+
+ATOL_REL_L1 = 1e-12
+PHI_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lgc.Context(0)
+    c.set_option(lgc.OPT_TRACE, 1)
+    yield c
+    c.close()
+
+
+_graph_cache = {}
+
+
+def gpu_graph(ctx, name):
+    if name not in _graph_cache:
+        off, col = GRAPHS[name]()
+        _graph_cache[name] = (off, col, lgc.Graph(ctx, off, col, validate=True))
+    return _graph_cache[name]
+
+
+GRAPHS = {
+    "paper": inputs.paper_example,
+    "path9": lambda: inputs.path(9),
+    "star40": lambda: inputs.star(40),
+    "cliques6": lambda: inputs.clique_pair(6),
+    "grid6": lambda: inputs.grid3d(6),
+    "rand500": lambda: inputs.random_graph(500, 2000, seed=3),
+    "rmat10": lambda: inputs.rmat(10, seed=5),
+    "rmat13": lambda: inputs.rmat(13, seed=9),
+    "rmat16": lambda: inputs.rmat(16, seed=1),
+}
+
+
+def seeds_for(off, col, k=3, salt=0):
+    s = [inputs.config1_seed(off, col)]
+    s += inputs.seeds_deg2(off, k - 1, 1000 + salt).tolist() if (np.diff(off) >= 2).any() else []
+    return s
+
+
+def rel_l1(idx_a, val_a, idx_b, val_b):
+    n = int(max(idx_a.max(initial=0), idx_b.max(initial=0))) + 1
+    a = np.zeros(n)
+    b = np.zeros(n)
+    a[idx_a] = val_a
+    b[idx_b] = val_b
+    return np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300)
+
+
+def assert_trace_equal(got, ref_trace):
+    assert len(got) == len(ref_trace)
+    for k, (f, r) in enumerate(zip(got, ref_trace)):
+        assert np.array_equal(f, r), f"frontier of round {k} differs"
+
+
+# ---------------------------------------------------------------------------
+# sweep cut
+# ---------------------------------------------------------------------------
+def test_sweep_paper_example(ctx):
+    off, col, g = gpu_graph(ctx, "paper")
+    c = lgc.sweep(g, lgc.host_svec([0, 1, 2, 3], [0.4, 0.3, 0.3, 0.2]))
+    assert c.ids.tolist() == [0, 1, 2] and c.vol == 7 and c.cut == 1
+    assert c.conductance == 1.0 / 7.0
+
+
+@pytest.mark.parametrize("name", ["rand500", "rmat10", "rmat13", "rmat16"])
+def test_sweep_matches_oracle(ctx, name):
+    off, col, g = gpu_graph(ctx, name)
+    n = len(off) - 1
+    d = np.diff(off)
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        k = int(rng.integers(1, n))
+        idx = np.sort(rng.choice(np.flatnonzero(d > 0), size=min(k, int((d > 0).sum())),
+                                 replace=False)).astype(np.int32)
+        if trial % 2 == 0:  # coarse values: many ties in p/d
+            val = rng.integers(0, 5, size=len(idx)) * 0.125 * d[idx]
+        else:
+            val = rng.random(len(idx)) ** 3
+        ref = oracle.sweep(off, col, idx, val)
+        c = lgc.sweep(g, lgc.host_svec(idx, val))
+        assert c.size == ref.best
+        assert c.vol == ref.best_vol and c.cut == ref.best_cut
+        assert np.array_equal(c.ids, ref.cluster)
+        assert c.conductance == ref.conductance or (math.isinf(c.conductance)
+                                                    and math.isinf(ref.conductance))
+
+
+def test_sweep_edge_cases(ctx):
+    off, col, g = gpu_graph(ctx, "cliques6")
+    n = len(off) - 1
+    c = lgc.sweep(g, lgc.host_svec(np.zeros(0, np.int32), np.zeros(0)))
+    assert c.size == 0 and math.isinf(c.conductance)
+    c = lgc.sweep(g, lgc.host_svec([3], [0.0]))  # zeros are not in the support
+    assert c.size == 0
+    ref = oracle.sweep(off, col, np.arange(n), np.ones(n))
+    c = lgc.sweep(g, lgc.host_svec(np.arange(n), np.ones(n)))
+    assert c.size == ref.best and c.cut == ref.best_cut and c.vol == ref.best_vol
+
+
+# ---------------------------------------------------------------------------
+# PR-Nibble
+# ---------------------------------------------------------------------------
+PR_CASES = [("paper", 0.15, 1e-4), ("path9", 0.1, 1e-5), ("star40", 0.05, 1e-4),
+            ("cliques6", 0.1, 1e-6), ("grid6", 0.05, 1e-6), ("rand500", 0.02, 1e-6),
+            ("rmat10", 0.01, 1e-5), ("rmat13", 0.01, 1e-6)]
+
+
+@pytest.mark.parametrize("rule", ["opt", "orig"])
+@pytest.mark.parametrize("name,alpha,eps", PR_CASES)
+def test_prnibble_det_bitexact(ctx, name, alpha, eps, rule):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2):
+        ref = oracle.prnibble(off, col, x, alpha, eps, rule=1 if rule == "orig" else 0,
+                              trace=True)
+        p, st = lgc.prnibble(g, x, alpha, eps, rule=rule, mode="det")
+        assert np.array_equal(p.idx, ref.idx)
+        assert np.array_equal(p.val, ref.val), "p differs"
+        r = ctx.residual()
+        assert np.array_equal(r.idx, ref.idx2)
+        assert np.array_equal(r.val, ref.val2), "r differs"
+        assert_trace_equal(ctx.trace(), ref.trace)
+        assert (st.rounds, st.pushes, st.pushed_edges, st.touched) == (
+            ref.rounds, ref.pushes, ref.pushed_edges, ref.touched)
+
+
+@pytest.mark.parametrize("name,alpha,eps", PR_CASES)
+def test_prnibble_atomic_within_tolerance(ctx, name, alpha, eps):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2):
+        ref = oracle.prnibble(off, col, x, alpha, eps)
+        p, st = lgc.prnibble(g, x, alpha, eps, mode="atomic")
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+        c = lgc.sweep(g, p)
+        rs = oracle.sweep(off, col, ref.idx, ref.val)
+        assert abs(c.conductance - rs.conductance) <= PHI_TOL
+        # the atomic frontiers are the same sets, in arrival order
+        tr = ctx.trace()
+        rt = oracle.prnibble(off, col, x, alpha, eps, trace=True).trace
+        assert [np.sort(f).tolist() for f in tr] == [f.tolist() for f in rt]
+
+
+def test_prnibble_config1_full_size(ctx):
+    """Scale-16 R-MAT, seed = vertex 0's highest-degree neighbour, alpha 0.01,
+    eps 1e-6, deterministic mode: bit-exact p, r, frontiers; exact sweep."""
+    off, col, g = gpu_graph(ctx, "rmat16")
+    x = inputs.config1_seed(off, col)
+    ref = oracle.prnibble(off, col, x, 0.01, 1e-6, trace=True)
+    p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="det")
+    assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+    r = ctx.residual()
+    assert np.array_equal(r.idx, ref.idx2) and np.array_equal(r.val, ref.val2)
+    assert_trace_equal(ctx.trace(), ref.trace)
+    c = lgc.sweep(g, p)
+    rs = oracle.sweep(off, col, ref.idx, ref.val)
+    assert np.array_equal(c.ids, rs.cluster) and c.vol == rs.best_vol and c.cut == rs.best_cut
+    assert c.conductance == rs.conductance
+
+
+def test_prnibble_invalid_inputs(ctx):
+    off, col, g = gpu_graph(ctx, "rmat10")
+    iso = int(np.flatnonzero(np.diff(off) == 0)[0])
+    for seed in (-1, len(off) - 1, iso):
+        with pytest.raises(lgc.LgcError) as e:
+            lgc.prnibble(g, seed, 0.01, 1e-5)
+        assert e.value.status == lgc.LGC_EINVAL
+    for alpha, eps in [(0.0, 1e-5), (1.0, 1e-5), (0.1, 0.0), (0.1, -1.0)]:
+        with pytest.raises(lgc.LgcError):
+            lgc.prnibble(g, 1, alpha, eps)
+
+
+def test_prnibble_max_rounds(ctx):
+    off, col, g = gpu_graph(ctx, "rmat13")
+    x = inputs.config1_seed(off, col)
+    for k in (1, 2, 3):
+        ref = oracle.prnibble(off, col, x, 0.01, 1e-6, max_rounds=k)
+        p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="det", max_rounds=k)
+        assert st.rounds == k
+        assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+
+
+# ---------------------------------------------------------------------------
+# Nibble
+# ---------------------------------------------------------------------------
+NIB_CASES = [("paper", 5, 1e-3), ("path9", 12, 1e-3), ("grid6", 8, 1e-4),
+             ("rand500", 10, 1e-5), ("rmat10", 20, 1e-5), ("rmat13", 20, 1e-6),
+             ("rmat13", 4, 0.0)]
+
+
+@pytest.mark.parametrize("name,T,eps", NIB_CASES)
+def test_nibble_det_bitexact(ctx, name, T, eps):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2, salt=1):
+        ref = oracle.nibble(off, col, x, T, eps, trace=True)
+        p, st = lgc.nibble(g, x, T, eps, mode="det")
+        assert np.array_equal(p.idx, ref.idx)
+        assert np.array_equal(p.val, ref.val)
+        assert_trace_equal(ctx.trace(), ref.trace)
+        assert (st.rounds, st.pushes, st.pushed_edges) == (ref.rounds, ref.pushes,
+                                                            ref.pushed_edges)
+
+
+@pytest.mark.parametrize("name,T,eps", NIB_CASES)
+def test_nibble_atomic_within_tolerance(ctx, name, T, eps):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2, salt=1):
+        ref = oracle.nibble(off, col, x, T, eps)
+        p, st = lgc.nibble(g, x, T, eps, mode="atomic")
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+
+
+def test_nibble_early_exit(ctx):
+    off, col, g = gpu_graph(ctx, "path9")
+    ref = oracle.nibble(off, col, 0, 10, 0.3)
+    for mode in ("det", "atomic"):
+        p, st = lgc.nibble(g, 0, 10, 0.3, mode=mode)
+        assert p.idx.tolist() == ref.idx.tolist() and p.val.tolist() == ref.val.tolist()
+
+
+# ---------------------------------------------------------------------------
+# HK-PR
+# ---------------------------------------------------------------------------
+HK_CASES = [("paper", 2.0, 6, 1e-3), ("grid6", 3.0, 10, 1e-4), ("rand500", 5.0, 12, 1e-4),
+            ("rmat10", 5.0, 15, 1e-5), ("rmat13", 10.0, 20, 1e-7), ("rmat13", 3.0, 5, 0.0),
+            ("cliques6", 1.0, 1, 1e-3)]
+
+
+@pytest.mark.parametrize("name,t,N,eps", HK_CASES)
+def test_hkpr_det_bitexact(ctx, name, t, N, eps):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2, salt=2):
+        ref = oracle.hkpr(off, col, x, t, N, eps, trace=True)
+        p, st = lgc.hkpr(g, x, t, N, eps, mode="det")
+        assert np.array_equal(p.idx, ref.idx)
+        assert np.array_equal(p.val, ref.val)
+        assert_trace_equal(ctx.trace(), ref.trace)
+        assert (st.rounds, st.pushes, st.pushed_edges) == (ref.rounds, ref.pushes,
+                                                            ref.pushed_edges)
+
+
+@pytest.mark.parametrize("name,t,N,eps", HK_CASES)
+def test_hkpr_atomic_within_tolerance(ctx, name, t, N, eps):
+    off, col, g = gpu_graph(ctx, name)
+    for x in seeds_for(off, col, 2, salt=2):
+        ref = oracle.hkpr(off, col, x, t, N, eps)
+        p, st = lgc.hkpr(g, x, t, N, eps, mode="atomic")
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+
+
+# ---------------------------------------------------------------------------
+# rand-HK-PR
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,t,K,walks", [("paper", 2.0, 5, 10000), ("rmat13", 10.0, 10, 300001),
+                                            ("grid6", 3.0, 0, 999), ("rmat16", 10.0, 10, 100000)])
+def test_rand_hkpr_bitexact(ctx, name, t, K, walks):
+    off, col, g = gpu_graph(ctx, name)
+    x = inputs.config1_seed(off, col)
+    ref = oracle.rand_hkpr(off, col, x, t, K, walks, 7)
+    p, st = lgc.rand_hkpr(g, x, t, K, walks, 7)
+    assert np.array_equal(ctx.rand_hkpr_endpoints(walks), ref.endpoints)
+    assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+    assert st.pushed_edges == ref.pushed_edges
+
+
+# ---------------------------------------------------------------------------
+# graph validation
+# ---------------------------------------------------------------------------
+def test_graph_validation_rejects_bad_csr(ctx):
+    bad = [
+        (np.array([0, 1, 1], np.int64), np.array([1], np.int32)),        # asymmetric
+        (np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32)),     # self loops
+        (np.array([0, 2, 3, 4], np.int64), np.array([2, 1, 0, 0], np.int32)),  # unsorted
+        (np.array([0, 2, 3], np.int64), np.array([1, 1, 0], np.int32)),  # duplicate
+    ]
+    for off, col in bad:
+        with pytest.raises(lgc.LgcError):
+            lgc.Graph(ctx, off, col, validate=True)
