@@ -47,10 +47,26 @@ def dist_env():
 
 
 def rank_seed(off, col, rank):
+    """Rank 0 takes vertex 0's highest-degree neighbour; rank r > 0 the r-th
+    degree->=2 vertex of the seeded sampler (independent problems)."""
     from paper_1604_07515_gb300 import inputs
     if rank == 0:
         return inputs.config1_seed(off, col)
     return int(inputs.seeds_deg2(off, rank, 2)[rank - 1])
+
+
+def reduce_ranks(maxed, summed, world, device):
+    """Max over ranks of `maxed` (times) and sum over ranks of `summed`
+    (work); identity when world == 1."""
+    if world == 1:
+        return list(maxed), list(summed)
+    import torch
+    import torch.distributed as dist
+    a = torch.tensor(list(maxed), dtype=torch.float64, device=device)
+    b = torch.tensor(list(summed), dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
 
 
 class ClockSampler:
@@ -246,13 +262,8 @@ def main():
     clk = clocks.stop()
     ctx.set_option(lgc.OPT_PROFILE, 0)
     prof = {lgc.PROF_NAMES[k]: ctx.profile(k) for k in lgc.PROF_NAMES}
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms, pushed, clusters], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        total_ms, pushed, clusters = mx[0].item(), t[1].item(), t[2].item()
+    (total_ms,), (pushed, clusters) = reduce_ranks([sum(step_ms)], [pushed, clusters], world,
+                                                    "cuda")
     value = pushed / (total_ms / 1e3)
 
     # ---- end to end through the public API with host buffers ----
@@ -269,12 +280,7 @@ def main():
         e2e_s += time.perf_counter() - s0
         e_pushed += pe
         d2h += db
-    if world > 1:
-        t = torch.tensor([e2e_s, e_pushed], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        e2e_s, e_pushed = mx[0].item(), t[1].item()
+    (e2e_s,), (e_pushed,) = reduce_ranks([e2e_s], [e_pushed], world, "cuda")
     e2e_value = e_pushed / e2e_s
 
     # ---- roofline of the dominant kernel ----

@@ -1,0 +1,108 @@
+"""Request loop (lgc_submit / lgc_poll): requests that arrive while others run
+are admitted as slots and memory free up, run concurrently on worker
+streams, and each result is the same alone and in the mix (bit-identical in
+deterministic mode, within 1e-12 relative L1 in atomic mode)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1604_07515_gb300 import inputs, lgc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = lgc.Context(0)
+    off, col = inputs.rmat(14, seed=11)
+    g = lgc.Graph(ctx, off, col)
+    yield ctx, g, off, col
+    g.close()
+    ctx.close()
+
+
+def requests(off, count, mode):
+    seeds = inputs.seeds_deg2(off, count, 5)
+    eps = inputs.eps_loguniform(count, 5, -7.0, -5.0)
+    ts = 10.0 ** (np.log10(3.0) + inputs.uniform(6, count))
+    out = []
+    for i in range(count):
+        if i % 5 == 4:
+            out.append(("hkpr", dict(t=float(ts[i]), N=20, eps=1e-6, mode=mode), int(seeds[i])))
+        elif i % 7 == 3:
+            out.append(("rand", dict(t=5.0, K=10, n_walks=20000, rng_seed=i), int(seeds[i])))
+        else:
+            out.append(("pr", dict(alpha=0.01, eps=float(eps[i]), mode=mode), int(seeds[i])))
+    return out
+
+
+def alone(g, kind, kw, seed):
+    if kind == "pr":
+        p, _ = lgc.prnibble(g, seed, kw["alpha"], kw["eps"], mode=kw["mode"])
+    elif kind == "hkpr":
+        p, _ = lgc.hkpr(g, seed, kw["t"], kw["N"], kw["eps"], mode=kw["mode"])
+    else:
+        p, _ = lgc.rand_hkpr(g, seed, kw["t"], kw["K"], kw["n_walks"], kw["rng_seed"])
+    c = lgc.sweep(g, p)
+    return p, c
+
+
+def submit_all(ctx, g, reqs):
+    tickets = []
+    for kind, kw, seed in reqs:
+        if kind == "pr":
+            r = lgc.make_request(lgc.ALGO_PRNIBBLE, seed, True, **kw)
+        elif kind == "hkpr":
+            r = lgc.make_request(lgc.ALGO_HKPR, seed, True, **kw)
+        else:
+            r = lgc.make_request(lgc.ALGO_RAND_HKPR, seed, True, **kw)
+        tickets.append(lgc.submit(ctx, g, r))
+    results = {}
+    deadline = time.time() + 300
+    while len(results) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in results:
+                res = lgc.poll(ctx, t)
+                if res is not None:
+                    results[t] = res
+        time.sleep(0.001)
+    assert len(results) == len(tickets), "requests did not finish"
+    return [results[t] for t in tickets]
+
+
+@pytest.mark.parametrize("mode", ["det", "atomic"])
+def test_results_same_alone_and_in_mix(setup, mode):
+    ctx, g, off, col = setup
+    reqs = requests(off, 40, mode)
+    mixed = submit_all(ctx, g, reqs)
+    for (kind, kw, seed), res in zip(reqs, mixed):
+        assert res["status"] == 0
+        p, c = alone(g, kind, kw, seed)
+        if mode == "det" or kind == "rand":
+            assert np.array_equal(res["idx"], p.idx) and np.array_equal(res["val"], p.val)
+            assert res["cluster"]["size"] == c.size and res["cluster"]["cut"] == c.cut
+            assert np.array_equal(res["cluster"]["ids"], c.ids)
+        else:
+            n = len(off) - 1
+            a, b = np.zeros(n), np.zeros(n)
+            a[res["idx"]] = res["val"]
+            b[p.idx] = p.val
+            assert np.abs(a - b).sum() <= 1e-12 * np.abs(b).sum()
+        assert res["end_s"] >= res["start_s"] >= res["submit_s"]
+
+
+def test_requests_overlap_on_device(setup):
+    """With several worker streams, request lifetimes overlap."""
+    ctx, g, off, col = setup
+    res = submit_all(ctx, g, requests(off, 24, "atomic"))
+    spans = sorted((r["start_s"], r["end_s"]) for r in res)
+    overlaps = sum(1 for a, b in zip(spans, spans[1:]) if b[0] < a[1])
+    assert overlaps > 0
+
+
+def test_poll_unknown_ticket(setup):
+    ctx, g, off, col = setup
+    with pytest.raises(lgc.LgcError) as e:
+        lgc.poll(ctx, 10 ** 12)
+    assert e.value.status == lgc.LGC_ENOTFOUND
