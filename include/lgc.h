@@ -132,7 +132,9 @@ enum {
   LGC_OPT_RESULT_ON_DEVICE = 1, /* 1: outputs stay in device memory (default 0: host) */
   LGC_OPT_TRACE = 2,            /* 1: record every round's frontier (tests) */
   LGC_OPT_SERVE_MEM_BUDGET = 3, /* bytes of hash-table memory admitted at once */
-  LGC_OPT_SERVE_MAX_BATCH = 4   /* requests resident on the device at once */
+  LGC_OPT_SERVE_MAX_BATCH = 4,  /* requests resident on the device at once */
+  LGC_OPT_TABLE_FORM = 6        /* sparse sets: 0 automatic (dense once a set may reach
+                                   n/8 keys), 1 always hashed, 2 always dense */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */

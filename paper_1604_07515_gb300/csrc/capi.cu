@@ -246,6 +246,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
     case LGC_OPT_RESULT_ON_DEVICE: ctx->result_on_device = value != 0; return LGC_OK;
     case LGC_OPT_TRACE: ctx->trace = value != 0; return LGC_OK;
     case LGC_OPT_PROFILE: ctx->profile = value != 0; return LGC_OK;
+    case LGC_OPT_TABLE_FORM:
+      if (value < 0 || value > 2) return LGC_EINVAL;
+      ctx->table_form = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;

@@ -146,10 +146,9 @@ int table_create(lgc_ctx* ctx, Table* T, int64_t min_cap, bool with_p) {
   int lg = 0;
   while (((int64_t)1 << lg) < cap) lg++;
   if (lg > 31) return LGC_EINVAL;
+  *T = Table();
   T->cap = cap;
   T->shift = 32 - lg;
-  T->s = nullptr;
-  T->p = nullptr;
   LGC_TRY(dalloc_t(ctx, &T->s, (size_t)cap));
   if (with_p) {
     int s = dalloc_t(ctx, &T->p, (size_t)cap);
@@ -162,18 +161,51 @@ int table_create(lgc_ctx* ctx, Table* T, int64_t min_cap, bool with_p) {
   return table_clear(ctx, T);
 }
 
+int table_create_dense(lgc_ctx* ctx, Table* T, int64_t n, bool with_p) {
+  *T = Table();
+  T->dense = 1;
+  T->cap = n;
+  int s = dalloc_t(ctx, &T->dval, (size_t)n);
+  if (s == LGC_OK) s = dalloc_t(ctx, &T->bits, (size_t)((n + 31) / 32));
+  if (s == LGC_OK && with_p) s = dalloc_t(ctx, &T->p, (size_t)n);
+  if (s != LGC_OK) {
+    table_destroy(ctx, T);
+    return s;
+  }
+  return table_clear(ctx, T);
+}
+
 void table_destroy(lgc_ctx* ctx, Table* T) {
   dfree(ctx, T->s);
   dfree(ctx, T->p);
-  T->s = nullptr;
-  T->p = nullptr;
-  T->cap = 0;
+  dfree(ctx, T->dval);
+  dfree(ctx, T->bits);
+  *T = Table();
 }
 
 int table_clear(lgc_ctx* ctx, Table* T) {
-  LGC_CUDA_TRY(cudaMemsetAsync(T->s, 0, sizeof(Slot) * T->cap, ctx->stream));
+  if (T->dense) {
+    LGC_CUDA_TRY(cudaMemsetAsync(T->dval, 0, sizeof(double) * T->cap, ctx->stream));
+    LGC_CUDA_TRY(cudaMemsetAsync(T->bits, 0, sizeof(uint32_t) * ((T->cap + 31) / 32),
+                                 ctx->stream));
+  } else {
+    LGC_CUDA_TRY(cudaMemsetAsync(T->s, 0, sizeof(Slot) * T->cap, ctx->stream));
+  }
   if (T->p) LGC_CUDA_TRY(cudaMemsetAsync(T->p, 0, sizeof(double) * T->cap, ctx->stream));
   return LGC_OK;
+}
+
+int table_fresh(lgc_ctx* ctx, Table* T, int64_t need, int64_t n, bool with_p) {
+  if (want_dense(ctx, need, n)) {
+    if (T->dense && T->cap == n && (T->p != nullptr) == with_p) return table_clear(ctx, T);
+    table_destroy(ctx, T);
+    return table_create_dense(ctx, T, n, with_p);
+  }
+  const int64_t want = pow2_at_least(2 * (need < 32 ? 32 : need));
+  if (!T->dense && T->s && T->cap >= want && T->cap <= 8 * want && (T->p != nullptr) == with_p)
+    return table_clear(ctx, T);
+  table_destroy(ctx, T);
+  return table_create(ctx, T, want, with_p);
 }
 
 namespace {
@@ -192,10 +224,22 @@ __global__ void rehash_kernel(Table from, Table to, int* err) {
   }
 }
 
+__global__ void to_dense_kernel(Table from, Table to) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < from.cap;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    Slot s = from.s[i];
+    if (s.key == 0) continue;
+    const int32_t v = s.key - 1;
+    to.dval[v] = s.val;
+    if (from.p) to.p[v] = from.p[i];
+    atomicOr(&to.bits[v >> 5], 1u << (v & 31));
+  }
+}
+
 __global__ void reresolve_kernel(Table T, const int32_t* fv, int32_t* fs, int64_t nf) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
        i += (int64_t)gridDim.x * blockDim.x)
-    fs[i] = (int32_t)ht_find(T, fv[i]);
+    fs[i] = (int32_t)tb_find(T, fv[i]);
 }
 
 __global__ void extract_kernel(Table T, const double* vals, Counters* C, uint32_t* keys,
@@ -212,7 +256,68 @@ __global__ void extract_kernel(Table T, const double* vals, Counters* C, uint32_
   }
 }
 
+// Dense extraction in vertex order: count the kept keys of each bitmap word,
+// then (after a scan of the counts) write them in ascending id.
+__device__ inline uint32_t dense_kept(const Table& T, const double* vals, int64_t w, int64_t n,
+                                      int positive_only) {
+  uint32_t m = T.bits[w];
+  if (positive_only) {
+    uint32_t k = 0;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t v = w * 32 + b;
+      if (v < n && (vals ? vals[v] : T.dval[v]) > 0.0) k |= 1u << b;
+    }
+    return k;
+  }
+  return m;
+}
+
+__global__ void dense_count_kernel(Table T, const double* vals, int64_t n, int positive_only,
+                                   int64_t* cnt) {
+  const int64_t words = (n + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(dense_kept(T, vals, w, n, positive_only));
+}
+
+__global__ void dense_write_kernel(Table T, const double* vals, int64_t n, int positive_only,
+                                   const int64_t* pos, uint32_t* keys, double* out) {
+  const int64_t words = (n + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t m = dense_kept(T, vals, w, n, positive_only);
+    int64_t at = pos[w];
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t v = w * 32 + b;
+      keys[at] = (uint32_t)v;
+      out[at] = vals ? vals[v] : T.dval[v];
+      at++;
+    }
+  }
+}
+
 }  // namespace
+
+int table_to_dense(lgc_ctx* ctx, Table* T, int64_t n, const int32_t* fv, int32_t* fs,
+                   int64_t nf) {
+  if (T->dense) return LGC_OK;
+  Table nt;
+  LGC_TRY(table_create_dense(ctx, &nt, n, T->p != nullptr));
+  to_dense_kernel<<<grid_for(T->cap), kBlock, 0, ctx->stream>>>(*T, nt);
+  LGC_COUNT_LAUNCH(ctx);
+  if (nf > 0 && fv && fs) {
+    reresolve_kernel<<<grid_for(nf), kBlock, 0, ctx->stream>>>(nt, fv, fs, nf);
+    LGC_COUNT_LAUNCH(ctx);
+  }
+  LGC_CUDA_TRY(cudaGetLastError());
+  table_destroy(ctx, T);
+  *T = nt;
+  return LGC_OK;
+}
 
 int table_grow(lgc_ctx* ctx, Table* T, int64_t new_cap, const int32_t* fv, int32_t* fs,
                int64_t nf) {
@@ -237,6 +342,45 @@ int table_extract_sorted(lgc_ctx* ctx, const Table& T, const double* vals, int64
   *d_idx = nullptr;
   *d_val = nullptr;
   *nnz = 0;
+  if (T.dense) {
+    const int64_t n = T.cap, words = (n + 31) / 32;
+    int64_t *cnt = nullptr, *tot = nullptr;
+    uint32_t* k = nullptr;
+    double* v = nullptr;
+    int s = dalloc_t(ctx, &cnt, words);
+    if (s == LGC_OK) s = dalloc_t(ctx, &tot, 1);
+    if (s == LGC_OK) {
+      dense_count_kernel<<<grid_for(words), kBlock, 0, st>>>(T, vals, n, positive_only, cnt);
+      LGC_COUNT_LAUNCH(ctx);
+      s = scan_i64(ctx, cnt, cnt, words, false, tot);
+    }
+    int64_t count = 0;
+    if (s == LGC_OK) {
+      if (cudaMemcpyAsync(ctx->h_scratch, tot, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        s = LGC_ECUDA;
+      else
+        count = ctx->h_scratch[0];
+    }
+    if (s == LGC_OK) s = dalloc_t(ctx, &k, count);
+    if (s == LGC_OK) s = dalloc_t(ctx, &v, count);
+    if (s == LGC_OK) {
+      dense_write_kernel<<<grid_for(words), kBlock, 0, st>>>(T, vals, n, positive_only, cnt, k, v);
+      LGC_COUNT_LAUNCH(ctx);
+      if (cudaGetLastError() != cudaSuccess) s = LGC_ECUDA;
+    }
+    dfree(ctx, cnt);
+    dfree(ctx, tot);
+    if (s != LGC_OK) {
+      dfree(ctx, k);
+      dfree(ctx, v);
+      return s;
+    }
+    *d_idx = (int32_t*)k;
+    *d_val = v;
+    *nnz = count;
+    return LGC_OK;
+  }
   LGC_CUDA_TRY(cudaMemsetAsync(&ctx->d_counters->next_size, 0, sizeof(int32_t), st));
   // at most min(cap, n) keys
   int64_t maxk = T.cap < n_vertices ? T.cap : n_vertices;

@@ -55,11 +55,23 @@ struct __align__(16) Slot {
   double val;
 };
 
+// A sparse set (vertex -> double, missing keys read as 0), in one of two
+// representations chosen by the host per table:
+//  - hashed: open addressing with linear probing over `cap` Slots (at most
+//    half full), slot = probe position;
+//  - dense: dval[v] indexed by the vertex id itself plus a presence bitmap
+//    (bit v of bits[] says v is a key), slot = v.  Used once a set may hold
+//    n/8 keys or more: no probing, and a value array that fits in L2 at the
+//    sizes where hashing would not.
+// `p` is an optional second double per slot (PR-Nibble's p) in either form.
 struct Table {
   Slot* s = nullptr;
   double* p = nullptr;  // optional second value per slot (PR-Nibble's p)
-  int64_t cap = 0;      // power of two
-  int shift = 32;       // 32 - log2(cap)
+  int64_t cap = 0;      // hashed: power of two; dense: n
+  int shift = 32;       // hashed: 32 - log2(cap)
+  int dense = 0;
+  double* dval = nullptr;   // dense values, n entries
+  uint32_t* bits = nullptr; // dense presence bitmap, ceil(n/32) words
 };
 
 __host__ __device__ inline uint32_t hash_slot(int32_t v, int shift) {
@@ -103,6 +115,29 @@ __device__ inline int64_t ht_find(const Table& T, int32_t v) {
     h = (h + 1) & mask;
   }
   return -1;
+}
+
+// Representation-independent accessors.  T.dense is uniform across a launch.
+__device__ inline int64_t tb_find_or_insert(const Table& T, int32_t v, int* inserted, int* err) {
+  if (T.dense) {
+    const uint32_t m = 1u << (v & 31);
+    uint32_t* w = &T.bits[v >> 5];
+    if (!(*(volatile uint32_t*)w & m)) {
+      const uint32_t old = atomicOr(w, m);
+      if (!(old & m)) *inserted = 1;
+    }
+    return v;
+  }
+  return ht_find_or_insert(T, v, inserted, err);
+}
+
+__device__ inline int64_t tb_find(const Table& T, int32_t v) {
+  if (T.dense) return (T.bits[v >> 5] >> (v & 31)) & 1u ? v : -1;
+  return ht_find(T, v);
+}
+
+__device__ inline double* tb_val(const Table& T, int64_t slot) {
+  return T.dense ? &T.dval[slot] : &T.s[slot].val;
 }
 
 // Per-round device counters, read back by the host once per round.
@@ -158,6 +193,7 @@ struct lgc_ctx {
   bool own_stream = false;
   bool result_on_device = false;
   bool trace = false;
+  int table_form = 0;  // LGC_OPT_TABLE_FORM
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back
@@ -230,8 +266,23 @@ struct DBuf {
   }
 };
 
-// Allocates a cleared table with capacity >= min_cap (power of two).
+// Allocates a cleared hashed table with capacity >= min_cap (power of two).
 int table_create(lgc_ctx* ctx, Table* T, int64_t min_cap, bool with_p);
+// Allocates a cleared dense table over n vertices.
+int table_create_dense(lgc_ctx* ctx, Table* T, int64_t n, bool with_p);
+// Converts a hashed table to the dense form over n vertices; frontier slots
+// fs[0..nf) are re-resolved (they become the vertex ids).
+int table_to_dense(lgc_ctx* ctx, Table* T, int64_t n, const int32_t* fv, int32_t* fs,
+                   int64_t nf);
+// Makes *T an empty table able to take `need` keys: dense if need >= n/8,
+// else hashed at load <= 1/2 (reusing the allocation when it fits).
+int table_fresh(lgc_ctx* ctx, Table* T, int64_t need, int64_t n, bool with_p);
+// A set that may reach n/8 keys is kept dense.
+inline bool want_dense(const lgc_ctx* ctx, int64_t need, int64_t n) {
+  if (ctx->table_form == 1) return false;
+  if (ctx->table_form == 2) return true;
+  return need >= n / 8 && n >= 1024;
+}
 void table_destroy(lgc_ctx* ctx, Table* T);
 int table_clear(lgc_ctx* ctx, Table* T);
 // Rehashes into a table of capacity >= new_cap; the frontier slots fs[0..nf)

@@ -107,7 +107,7 @@ __device__ inline void count_inserted(int ins, int64_t* counter) {
 __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                      const int32_t* __restrict__ fs, Table T,
                                      const int64_t* __restrict__ off, double alpha, double cs,
-                                     double cn, double eps, int rule, int det,
+                                     double cn, double eps, int rule, int det, int self_append,
                                      double* __restrict__ share, int64_t* __restrict__ cnt,
                                      int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
                                      int32_t ncap, Counters* C) {
@@ -121,7 +121,7 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
       v = fv[i];
       s = fs[i];
       const bool ok = s >= 0;  // always true unless a table overflowed (flagged)
-      const double r = ok ? T.s[s].val : 0.0;
+      const double r = ok ? *tb_val(T, s) : 0.0;
       const int64_t o0 = off[v];
       d = off[v + 1] - o0;
       double sh, rbase;
@@ -134,11 +134,11 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
         rbase = ((1.0 - alpha) * r) / 2.0;
         sh = ((1.0 - alpha) * r) / (2.0 * (double)d);
       }
-      if (ok) T.s[s].val = rbase;
+      if (ok) *tb_val(T, s) = rbase;
       share[i] = sh;
       cnt[i] = d + (det ? 1 : 0);
       foff[i] = o0;
-      pred = ok && !det && rule == 1 && rbase >= eps * (double)d;
+      pred = ok && self_append && rule == 1 && rbase >= eps * (double)d;
     }
     frontier_append(pred, v, s, d, nfv, nfs, C, ncap);
   }
@@ -149,7 +149,8 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
 __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                    const int32_t* __restrict__ fs, Table S, Table D,
                                    const int64_t* __restrict__ off, double eps, int fmode,
-                                   int det, double* __restrict__ share, int64_t* __restrict__ cnt,
+                                   int det, int self_append, double* __restrict__ share,
+                                   int64_t* __restrict__ cnt,
                                    int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
                                    int32_t ncap, Counters* C) {
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
@@ -161,16 +162,16 @@ __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
     int64_t d = 0;
     if (i < nf) {
       v = fv[i];
-      const double pv = fs[i] >= 0 ? S.s[fs[i]].val : 0.0;
+      const double pv = fs[i] >= 0 ? *tb_val(S, fs[i]) : 0.0;
       const int64_t o0 = off[v];
       d = off[v + 1] - o0;
-      ds = (int32_t)ht_find_or_insert(D, v, &ins, &C->err);
+      ds = (int32_t)tb_find_or_insert(D, v, &ins, &C->err);
       const double self = pv / 2.0;
-      if (ds >= 0) D.s[ds].val = self;
+      if (ds >= 0) *tb_val(D, ds) = self;
       share[i] = pv / (2.0 * (double)d);
       cnt[i] = d + (det ? 1 : 0);
       foff[i] = o0;
-      if (!det && ds >= 0)
+      if (self_append && ds >= 0)
         pred = fmode == kFmInserted ? true : self >= eps * (double)d;
     }
     count_inserted(ins, &C->aux);
@@ -191,11 +192,11 @@ __global__ void vmap_hkpr_kernel(int64_t nf, const int32_t* __restrict__ fv,
     int ins = 0;
     if (i < nf) {
       const int32_t v = fv[i];
-      const double r = fs[i] >= 0 ? S.s[fs[i]].val : 0.0;
+      const double r = fs[i] >= 0 ? *tb_val(S, fs[i]) : 0.0;
       const int64_t o0 = off[v];
       const int64_t d = off[v + 1] - o0;
-      const int64_t ps = ht_find_or_insert(P, v, &ins, &C->err);
-      if (ps >= 0) P.s[ps].val = P.s[ps].val + r;
+      const int64_t ps = tb_find_or_insert(P, v, &ins, &C->err);
+      if (ps >= 0) *tb_val(P, ps) = *tb_val(P, ps) + r;
       share[i] = last ? r / (double)d : (t * r) / ((double)(j + 1) * (double)d);
       cnt[i] = d;
       foff[i] = o0;
@@ -248,33 +249,193 @@ __global__ void __launch_bounds__(kBlock)
         sh[k] = s_share[j];
       }
     }
+    // Resolve every item's slot before any atomic, so the first-probe loads
+    // (or bitmap loads) of all items are in flight together.
+    int32_t slot[kEdgeItems];
+    int ins[kEdgeItems];
+    uint32_t probe[kEdgeItems];
 #pragma unroll
     for (int k = 0; k < kEdgeItems; k++) {
-      bool pred = false;
-      int ins = 0;
-      int32_t slot = -1;
-      int64_t dw = 0;
-      if (w[k] >= 0) {
-        slot = (int32_t)ht_find_or_insert(D, w[k], &ins, &C->err);
-        if (slot >= 0) {
-          const double old = atomicAdd(&D.s[slot].val, sh[k]);
-          if (fmode == kFmThreshold) {
-            const double nv = old + sh[k];
-            if (nv >= c) {  // c*d(w) >= c for d(w) >= 1: cheap pre-test
-              dw = deg[w[k]];
-              const double thr = c * (double)dw;
-              pred = old < thr && nv >= thr;
-            }
-          } else if (fmode == kFmInserted && ins) {
-            dw = deg[w[k]];
-            pred = true;
-          }
-        }
+      ins[k] = 0;
+      probe[k] = 0;
+      if (w[k] >= 0)
+        probe[k] = D.dense ? __ldcg(&D.bits[w[k] >> 5])
+                           : (uint32_t)__ldcg(&D.s[hash_slot(w[k], D.shift)].key);
+    }
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      slot[k] = -1;
+      if (w[k] < 0) continue;
+      if (D.dense) {
+        slot[k] = w[k];
+        const uint32_t m = 1u << (w[k] & 31);
+        if (!(probe[k] & m) && !(atomicOr(&D.bits[w[k] >> 5], m) & m)) ins[k] = 1;
+      } else if ((int32_t)probe[k] == w[k] + 1) {
+        slot[k] = (int32_t)hash_slot(w[k], D.shift);
+      } else {
+        slot[k] = (int32_t)ht_find_or_insert(D, w[k], &ins[k], &C->err);
       }
-      count_inserted(ins, &C->inserted);
-      frontier_append(pred, w[k], slot, dw, nfv, nfs, C, ncap);
+    }
+    // All adds issued back to back; their returned old values decide the
+    // threshold crossings.
+    double old[kEdgeItems];
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++)
+      old[k] = slot[k] >= 0 ? atomicAdd(tb_val(D, slot[k]), sh[k]) : 0.0;
+    bool pred[kEdgeItems];
+    int64_t dw[kEdgeItems];
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      pred[k] = false;
+      dw[k] = 0;
+      if (slot[k] < 0) continue;
+      if (fmode == kFmThreshold) {
+        const double nv = old[k] + sh[k];
+        if (nv >= c) {  // c*d(w) >= c for d(w) >= 1: cheap pre-test
+          dw[k] = deg[w[k]];
+          const double thr = c * (double)dw[k];
+          pred[k] = old[k] < thr && nv >= thr;
+        }
+      } else if (fmode == kFmInserted && ins[k]) {
+        dw[k] = deg[w[k]];
+        pred[k] = true;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      count_inserted(ins[k], &C->inserted);
+      frontier_append(pred[k], w[k], slot[k], dw[k], nfv, nfs, C, ncap);
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// edgeMap for bulk rounds (atomic mode, dense destination): the adds are
+// fire-and-forget reductions (no returned value, so nothing waits on them)
+// and the key is marked in the presence bitmap; the next frontier is formed
+// afterwards by dense_filter_*.  Also used for the last HK-PR level (no
+// frontier) in either table form.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock)
+    emap_red_kernel(const int32_t* __restrict__ col, const double* __restrict__ share,
+                    const int64_t* __restrict__ epos, const int64_t* __restrict__ foff,
+                    int64_t nf, int64_t E_host, const int64_t* __restrict__ E_dev, Table D,
+                    Counters* C) {
+  __shared__ int64_t s_epos[kEdgeTile + 1];
+  __shared__ int64_t s_off[kEdgeTile];
+  __shared__ double s_share[kEdgeTile];
+  __shared__ int64_t s_i0, s_i1;
+  const int64_t E = min(E_host, *E_dev);
+  const int64_t ntiles = (E + kEdgeTile - 1) / kEdgeTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kEdgeTile;
+    const int64_t e1 = min(E, e0 + kEdgeTile);
+    const int cntsrc = stage_sources(epos, nf, E, e0, e1, &s_i0, &s_i1, s_epos);
+    const int64_t i0 = s_i0;
+    for (int j = threadIdx.x; j < cntsrc; j += kBlock) {
+      s_off[j] = foff[i0 + j];
+      s_share[j] = share[i0 + j];
+    }
+    __syncthreads();
+    int32_t w[kEdgeItems];
+    double sh[kEdgeItems];
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) {
+      const int64_t e = e0 + k * kBlock + threadIdx.x;
+      w[k] = -1;
+      int64_t q;
+      const int j = e < e1 ? find_source(s_epos, cntsrc, e, &q) : -1;
+      if (j >= 0) {
+        w[k] = col[s_off[j] + q];
+        sh[k] = s_share[j];
+      }
+    }
+    int ins[kEdgeItems];
+    if (D.dense) {
+      uint32_t bw[kEdgeItems];
+#pragma unroll
+      for (int k = 0; k < kEdgeItems; k++)
+        bw[k] = w[k] >= 0 ? __ldcg(&D.bits[w[k] >> 5]) : 0u;
+#pragma unroll
+      for (int k = 0; k < kEdgeItems; k++) {
+        ins[k] = 0;
+        if (w[k] < 0) continue;
+        atomicAdd(&D.dval[w[k]], sh[k]);  // result unused: compiled as a reduction
+        const uint32_t m = 1u << (w[k] & 31);
+        if (!(bw[k] & m) && !(atomicOr(&D.bits[w[k] >> 5], m) & m)) ins[k] = 1;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kEdgeItems; k++) {
+        ins[k] = 0;
+        if (w[k] < 0) continue;
+        const int64_t s = ht_find_or_insert(D, w[k], &ins[k], &C->err);
+        if (s >= 0) atomicAdd(&D.s[s].val, sh[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEdgeItems; k++) count_inserted(ins[k], &C->inserted);
+    __syncthreads();
+  }
+}
+
+// Filter of a dense set, in ascending vertex order: vertex v qualifies when it
+// is a key and its value reaches c*d(v) (kFmThreshold) or always
+// (kFmInserted).  Pass 1 counts per bitmap word; after an exclusive scan of
+// the counts, pass 2 writes the next frontier and sums its degrees.
+__device__ inline uint32_t dense_qualifying(const Table& D, const int32_t* __restrict__ deg,
+                                            int64_t w, int64_t n, double c, int fmode) {
+  uint32_t m = D.bits[w];
+  if (fmode != kFmThreshold) return m;
+  uint32_t q = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    m &= m - 1;
+    const int64_t v = w * 32 + b;
+    if (v < n && D.dval[v] >= c * (double)deg[v]) q |= 1u << b;
+  }
+  return q;
+}
+
+__global__ void dense_filter_count_kernel(Table D, const int32_t* __restrict__ deg, int64_t n,
+                                          double c, int fmode, int64_t* __restrict__ cnt) {
+  const int64_t words = (n + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(dense_qualifying(D, deg, w, n, c, fmode));
+}
+
+__global__ void dense_filter_write_kernel(Table D, const int32_t* __restrict__ deg, int64_t n,
+                                          double c, int fmode, const int64_t* __restrict__ pos,
+                                          int32_t* nfv, int32_t* nfs, int32_t ncap,
+                                          Counters* C) {
+  const int64_t words = (n + 31) / 32;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    int64_t dsum = 0;
+    if (w < words) {
+      uint32_t q = dense_qualifying(D, deg, w, n, c, fmode);
+      int64_t at = pos[w];
+      while (q) {
+        const int b = __ffs(q) - 1;
+        q &= q - 1;
+        const int32_t v = (int32_t)(w * 32 + b);
+        if (at < ncap) {
+          nfv[at] = v;
+          nfs[at] = v;
+        } else {
+          atomicOr(&C->err, kErrFrontierOverflow);
+        }
+        at++;
+        dsum += deg[v];
+      }
+    }
+    // integer sums are order-independent
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((threadIdx.x & 31) == 0 && dsum)
+      atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)dsum);
   }
 }
 
@@ -356,12 +517,12 @@ __global__ void fold_kernel(const uint32_t* __restrict__ rkey, const double* __r
       const int64_t b = segstart[sg];
       const int64_t e = sg + 1 < nseg ? segstart[sg + 1] : R;
       const int32_t w = (int32_t)rkey[b];
-      const int64_t slot = ht_find_or_insert(D, w, &ins, &C->err);
+      const int64_t slot = tb_find_or_insert(D, w, &ins, &C->err);
       int64_t q = 0;
       if (slot >= 0) {
-        double acc = D.s[slot].val;
+        double acc = *tb_val(D, slot);
         for (int64_t k = b; k < e; k++) acc = acc + rval[k];
-        D.s[slot].val = acc;
+        *tb_val(D, slot) = acc;
         if (fmode == kFmThreshold) q = acc >= c * (double)deg[w] ? 1 : 0;
         else if (fmode == kFmInserted) q = 1;
       }
@@ -410,8 +571,8 @@ __global__ void set_counter_size_kernel(Counters* C, const int64_t* total) {
 __global__ void init_seed_kernel(Table T, int32_t x, double r0, int32_t* fv, int32_t* fs,
                                  Counters* C) {
   int ins = 0;
-  int64_t s = ht_find_or_insert(T, x, &ins, &C->err);
-  if (s >= 0) T.s[s].val = r0;
+  int64_t s = tb_find_or_insert(T, x, &ins, &C->err);
+  if (s >= 0) *tb_val(T, s) = r0;
   fv[0] = x;
   fs[0] = (int32_t)s;
 }
@@ -506,13 +667,42 @@ struct PushWork {
   // edgeMap + filter into table D.  Records per source are cnt[] (scanned
   // into epos by the caller's vertexMap step).  Returns the counters.
   int edge_phase(const Table& D, double c, int fmode, bool det, bool self_rec, int64_t nrec,
-                 Counters* out) {
+                 Counters* out, bool bulk = false) {
     cudaStream_t s = ctx->stream;
     const int64_t nf = F.size;
     const int32_t ncap = (int32_t)G.v.cap;
     // algorithmic bytes: 24 per pushed edge (col 4, key 4, value read-modify-write 16),
     // 24 per frontier source staged (epos, off, share), 8 per next-frontier entry
     const double alg_bytes = 24.0 * (double)(nrec - (self_rec && det ? nf : 0)) + 24.0 * nf;
+    if (bulk) {
+      if (nrec > 0) {
+        int64_t tiles = ceil_div(nrec, kEdgeTile);
+        int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+        ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
+        emap_red_kernel<<<grid, kBlock, 0, s>>>(g->col, share.ptr, epos.ptr, foff.ptr, nf, nrec,
+                                                 total.ptr, D, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        LGC_CUDA_TRY(cudaGetLastError());
+      }
+      if (fmode != kFmNone) {
+        const int64_t words = (g->n + 31) / 32;
+        LGC_TRY(flag.reserve(ctx, words));
+        dense_filter_count_kernel<<<grid_for(words), kBlock, 0, s>>>(D, g->deg, g->n, c, fmode,
+                                                                      flag.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        LGC_TRY(scan_i64(ctx, flag.ptr, flag.ptr, words, false, total.ptr));
+        dense_filter_write_kernel<<<grid_for(words), kBlock, 0, s>>>(
+            D, g->deg, g->n, c, fmode, flag.ptr, G.v.ptr, G.s.ptr, ncap, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        LGC_CUDA_TRY(cudaGetLastError());
+      }
+      int st = read_counters(out);
+      if (ctx->profile && nrec > 0 && !ctx->prof_pending.empty())
+        ctx->prof_pending.back().bytes += 8.0 * out->next_size;
+      return st;
+    }
     if (!det) {
       if (nrec > 0) {
         int64_t tiles = ceil_div(nrec, kEdgeTile);
@@ -610,12 +800,23 @@ int vgrid(int64_t nf) {
 
 int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-// Makes D a cleared table able to take `need` keys at load <= 1/2.
-int fresh_table(lgc_ctx* ctx, Table* D, int64_t need) {
-  int64_t want = pow2_at_least(2 * (need < 32 ? 32 : need));
-  if (D->s && D->cap >= want && D->cap <= 8 * want) return table_clear(ctx, D);
-  table_destroy(ctx, D);
-  return table_create(ctx, D, want, false);
+// Bulk rounds (atomic mode): the destination is dense and the round pushes at
+// least n/32 edges, so a filter pass over the n-bit presence bitmap costs no
+// more than a constant times the round's own work.
+bool use_bulk(bool det, const Table& D, int64_t round_edges, int64_t n) {
+  return !det && D.dense && round_edges >= n / 32;
+}
+
+// Before a round that may add up to `add` keys to a persistent table holding
+// `count`: switch to the dense form once it may reach n/8 keys, else grow the
+// hashed form to stay at most half full.  Frontier slots are re-resolved.
+int ensure_capacity(lgc_ctx* ctx, Table* T, int64_t count, int64_t add, int64_t n,
+                    const int32_t* fv, int32_t* fs, int64_t nf) {
+  if (T->dense) return LGC_OK;
+  const int64_t need = min64(count + add, n);
+  if (want_dense(ctx, need, n)) return table_to_dense(ctx, T, n, fv, fs, nf);
+  if (2 * need > T->cap) return table_grow(ctx, T, 2 * need, fv, fs, nf);
+  return LGC_OK;
 }
 
 int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, lgc_svec** p,
@@ -669,13 +870,12 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
         break;
       }
       W.record_trace();
-      // grow T so the round's new keys (at most the frontier's edges) fit at load 1/2
-      int64_t need = min64(count + W.F.edges, g->n);
-      if (2 * need > T.cap) {
-        if ((status = table_grow(ctx, &T, 2 * need, W.F.v.ptr, W.F.s.ptr, W.F.size)) != LGC_OK)
-          break;
-      }
+      // room for the round's new keys (at most the frontier's edges)
+      if ((status = ensure_capacity(ctx, &T, count, W.F.edges, g->n, W.F.v.ptr, W.F.s.ptr,
+                                    W.F.size)) != LGC_OK)
+        break;
       const int64_t nf = W.F.size;
+      const bool bulk = use_bulk(det, T, W.F.edges, g->n);
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
@@ -683,7 +883,7 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
         vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
-            W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap,
+            (!det && !bulk) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap,
             ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
@@ -698,7 +898,7 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
         if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
       }
       Counters C;
-      status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C);
+      status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C, bulk);
       if (status != LGC_OK) break;
       st.rounds++;
       st.pushes += nf;
@@ -757,14 +957,16 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
       W.record_trace();
       const int64_t nf = W.F.size;
       const int64_t need = min64(g->n, nf + W.F.edges);
-      if ((status = fresh_table(ctx, &Pn, need)) != LGC_OK) break;  // p' = {}
+      if ((status = table_fresh(ctx, &Pn, need, g->n, false)) != LGC_OK) break;  // p' = {}
+      const bool bulk = use_bulk(det, Pn, W.F.edges, g->n);
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reserve_next(need)) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
       {
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
         vmap_nibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
-            nf, W.F.v.ptr, W.F.s.ptr, Pc, Pn, g->off, eps, fmode, det ? 1 : 0, W.share.ptr,
+            nf, W.F.v.ptr, W.F.s.ptr, Pc, Pn, g->off, eps, fmode, det ? 1 : 0,
+            (!det && !bulk) ? 1 : 0, W.share.ptr,
             W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
@@ -779,7 +981,7 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
         if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
       }
       Counters C;
-      status = W.edge_phase(Pn, eps, fmode, det, true, nrec, &C);
+      status = W.edge_phase(Pn, eps, fmode, det, true, nrec, &C, bulk);
       if (status != LGC_OK) break;
       st.rounds++;
       st.pushes += nf;
@@ -837,9 +1039,9 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       const int64_t nf = W.F.size;
       const bool last = j + 1 >= N;
       // p takes the frontier (and, on the last level, its neighbours)
-      int64_t pneed = min64(g->n, pcount + nf + (last ? W.F.edges : 0));
-      if (2 * pneed > P.cap)
-        if ((status = table_grow(ctx, &P, 2 * pneed, nullptr, nullptr, 0)) != LGC_OK) break;
+      if ((status = ensure_capacity(ctx, &P, pcount, nf + (last ? W.F.edges : 0), g->n, nullptr,
+                                    nullptr, 0)) != LGC_OK)
+        break;
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
       {
@@ -857,11 +1059,11 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       Counters C;
       if (!last) {
         const int64_t need = min64(g->n, W.F.edges);
-        if ((status = fresh_table(ctx, &Rn, need)) != LGC_OK) break;  // r' = {}
+        if ((status = table_fresh(ctx, &Rn, need, g->n, false)) != LGC_OK) break;  // r' = {}
         if ((status = W.reserve_next(need)) != LGC_OK) break;
         const double cj = c[j + 1];
         status = W.edge_phase(Rn, cj, cj > 0.0 ? kFmThreshold : kFmInserted, det, false,
-                              W.F.edges, &C);
+                              W.F.edges, &C, use_bulk(det, Rn, W.F.edges, g->n));
         if (status != LGC_OK) break;
         pcount += C.aux;
         st.rounds++;
@@ -874,7 +1076,8 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
         j++;
       } else {
         if ((status = W.reserve_next(1)) != LGC_OK) break;
-        status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C);
+        // no frontier after the last level: fire-and-forget adds in either form
+        status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C, !det);
         if (status != LGC_OK) break;
         pcount += C.aux + C.inserted;
         st.rounds++;

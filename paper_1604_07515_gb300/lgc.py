@@ -122,6 +122,7 @@ SIGNATURES = {
 }
 
 OPT_PROFILE = 5
+OPT_TABLE_FORM = 6
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}

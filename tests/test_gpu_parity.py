@@ -27,6 +27,14 @@ def ctx():
     c.close()
 
 
+@pytest.fixture(params=[0, 1, 2], ids=["auto", "hashed", "dense"])
+def form(request, ctx):
+    """Sparse-set representation: automatic, always hashed, always dense."""
+    ctx.set_option(lgc.OPT_TABLE_FORM, request.param)
+    yield request.param
+    ctx.set_option(lgc.OPT_TABLE_FORM, 0)
+
+
 _graph_cache = {}
 
 
@@ -126,7 +134,7 @@ PR_CASES = [("paper", 0.15, 1e-4), ("path9", 0.1, 1e-5), ("star40", 0.05, 1e-4),
 
 @pytest.mark.parametrize("rule", ["opt", "orig"])
 @pytest.mark.parametrize("name,alpha,eps", PR_CASES)
-def test_prnibble_det_bitexact(ctx, name, alpha, eps, rule):
+def test_prnibble_det_bitexact(ctx, form, name, alpha, eps, rule):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2):
         ref = oracle.prnibble(off, col, x, alpha, eps, rule=1 if rule == "orig" else 0,
@@ -143,7 +151,7 @@ def test_prnibble_det_bitexact(ctx, name, alpha, eps, rule):
 
 
 @pytest.mark.parametrize("name,alpha,eps", PR_CASES)
-def test_prnibble_atomic_within_tolerance(ctx, name, alpha, eps):
+def test_prnibble_atomic_within_tolerance(ctx, form, name, alpha, eps):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2):
         ref = oracle.prnibble(off, col, x, alpha, eps)
@@ -206,7 +214,7 @@ NIB_CASES = [("paper", 5, 1e-3), ("path9", 12, 1e-3), ("grid6", 8, 1e-4),
 
 
 @pytest.mark.parametrize("name,T,eps", NIB_CASES)
-def test_nibble_det_bitexact(ctx, name, T, eps):
+def test_nibble_det_bitexact(ctx, form, name, T, eps):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2, salt=1):
         ref = oracle.nibble(off, col, x, T, eps, trace=True)
@@ -219,7 +227,7 @@ def test_nibble_det_bitexact(ctx, name, T, eps):
 
 
 @pytest.mark.parametrize("name,T,eps", NIB_CASES)
-def test_nibble_atomic_within_tolerance(ctx, name, T, eps):
+def test_nibble_atomic_within_tolerance(ctx, form, name, T, eps):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2, salt=1):
         ref = oracle.nibble(off, col, x, T, eps)
@@ -244,7 +252,7 @@ HK_CASES = [("paper", 2.0, 6, 1e-3), ("grid6", 3.0, 10, 1e-4), ("rand500", 5.0, 
 
 
 @pytest.mark.parametrize("name,t,N,eps", HK_CASES)
-def test_hkpr_det_bitexact(ctx, name, t, N, eps):
+def test_hkpr_det_bitexact(ctx, form, name, t, N, eps):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2, salt=2):
         ref = oracle.hkpr(off, col, x, t, N, eps, trace=True)
@@ -257,7 +265,7 @@ def test_hkpr_det_bitexact(ctx, name, t, N, eps):
 
 
 @pytest.mark.parametrize("name,t,N,eps", HK_CASES)
-def test_hkpr_atomic_within_tolerance(ctx, name, t, N, eps):
+def test_hkpr_atomic_within_tolerance(ctx, form, name, t, N, eps):
     off, col, g = gpu_graph(ctx, name)
     for x in seeds_for(off, col, 2, salt=2):
         ref = oracle.hkpr(off, col, x, t, N, eps)
