@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_uint64, c_void_p
 
 import numpy as np
@@ -186,6 +187,7 @@ class Context:
         _check(lib.lgc_ctx_create(device, stream, byref(h)), "lgc_ctx_create")
         self.handle = h
         self.device = device
+        self._graphs = weakref.WeakSet()  # graphs must be destroyed before the context
 
     def set_option(self, option: int, value: int):
         _check(load().lgc_ctx_set_option(self.handle, option, int(value)), "lgc_ctx_set_option")
@@ -233,8 +235,17 @@ class Context:
     def profile_reset(self):
         _check(load().lgc_profile_reset(self.handle), "lgc_profile_reset")
 
+    def _own(self, obj):
+        """Registers a graph or device-resident result released before the context."""
+        self._graphs.add(obj)
+
     def close(self):
         if getattr(self, "handle", None):
+            for obj in list(self._graphs):  # results first, then graphs
+                if not isinstance(obj, Graph):
+                    obj.close()
+            for obj in list(self._graphs):
+                obj.close()
             load().lgc_ctx_destroy(self.handle)
             self.handle = None
 
@@ -265,10 +276,12 @@ class Graph:
         self.ctx = ctx
         self.n = n
         self.nnz = lib.lgc_graph_num_entries(h)
+        ctx._own(self)
 
     def close(self):
         if getattr(self, "handle", None):
-            load().lgc_graph_destroy(self.handle)
+            if getattr(self.ctx, "handle", None):  # the context destroys nothing of ours
+                load().lgc_graph_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -282,16 +295,20 @@ class SparseVec:
     """A library sparse vector.  Host results are copied to numpy (idx, val)
     and released at once; device results keep the library handle."""
 
-    def __init__(self, ptr):
+    def __init__(self, ptr, ctx: Context | None = None):
         self._ptr = ptr
         s = ptr.contents
         self.nnz = s.nnz
         self.on_device = bool(s.on_device)
         if not self.on_device:
-            self.idx = np.ctypeslib.as_array((c_int32 * max(1, s.nnz)).from_address(s.idx))[: s.nnz].copy() if s.nnz else np.zeros(0, np.int32)
-            self.val = np.ctypeslib.as_array((c_double * max(1, s.nnz)).from_address(s.val))[: s.nnz].copy() if s.nnz else np.zeros(0)
+            self.idx = (np.ctypeslib.as_array((c_int32 * s.nnz).from_address(s.idx)).copy()
+                        if s.nnz else np.zeros(0, np.int32))
+            self.val = (np.ctypeslib.as_array((c_double * s.nnz).from_address(s.val)).copy()
+                        if s.nnz else np.zeros(0))
             load().lgc_svec_free(ptr)
             self._ptr = None
+        elif ctx is not None:
+            ctx._own(self)
 
     def c_struct(self):
         """Pointer to an lgc_svec describing this vector (for lgc_sweep)."""
@@ -300,11 +317,14 @@ class SparseVec:
         self._keep = Svec(self.nnz, self.idx.ctypes.data, self.val.ctypes.data, 0)
         return ctypes.pointer(self._keep)
 
+    def close(self):
+        if getattr(self, "_ptr", None) is not None:
+            load().lgc_svec_free(self._ptr)
+            self._ptr = None
+
     def __del__(self):
         try:
-            if self._ptr is not None:
-                load().lgc_svec_free(self._ptr)
-                self._ptr = None
+            self.close()
         except Exception:
             pass
 
@@ -325,7 +345,7 @@ def _take_svec(ptr) -> SparseVec:
 
 
 class ClusterResult:
-    def __init__(self, ptr):
+    def __init__(self, ptr, ctx: Context | None = None):
         c = ptr.contents
         self.size, self.vol, self.cut = c.size, c.vol, c.cut
         self.conductance = c.conductance
@@ -336,12 +356,17 @@ class ClusterResult:
                         if c.size else np.zeros(0, np.int32))
             load().lgc_cluster_free(ptr)
             self._ptr = None
+        elif ctx is not None:
+            ctx._own(self)
+
+    def close(self):
+        if getattr(self, "_ptr", None) is not None:
+            load().lgc_cluster_free(self._ptr)
+            self._ptr = None
 
     def __del__(self):
         try:
-            if self._ptr is not None:
-                load().lgc_cluster_free(self._ptr)
-                self._ptr = None
+            self.close()
         except Exception:
             pass
 
@@ -352,21 +377,21 @@ def prnibble(g: Graph, seed: int, alpha: float, eps: float, rule="opt", mode="at
     out, st = POINTER(Svec)(), Stats()
     s = load().lgc_prnibble(g.handle, seed, byref(prm), byref(out), byref(st))
     _check(s, "lgc_prnibble", ok=(LGC_OK, LGC_EMAXROUNDS))
-    return SparseVec(out), st
+    return SparseVec(out, g.ctx), st
 
 
 def nibble(g: Graph, seed: int, T: int, eps: float, mode="atomic"):
     prm = NibbleParams(T, eps, _MODES[mode])
     out, st = POINTER(Svec)(), Stats()
     _check(load().lgc_nibble(g.handle, seed, byref(prm), byref(out), byref(st)), "lgc_nibble")
-    return SparseVec(out), st
+    return SparseVec(out, g.ctx), st
 
 
 def hkpr(g: Graph, seed: int, t: float, N: int, eps: float, mode="atomic"):
     prm = HKPRParams(t, eps, N, _MODES[mode])
     out, st = POINTER(Svec)(), Stats()
     _check(load().lgc_hkpr(g.handle, seed, byref(prm), byref(out), byref(st)), "lgc_hkpr")
-    return SparseVec(out), st
+    return SparseVec(out, g.ctx), st
 
 
 def rand_hkpr(g: Graph, seed: int, t: float, K: int, n_walks: int, rng_seed: int):
@@ -374,13 +399,13 @@ def rand_hkpr(g: Graph, seed: int, t: float, K: int, n_walks: int, rng_seed: int
     out, st = POINTER(Svec)(), Stats()
     _check(load().lgc_rand_hkpr(g.handle, seed, byref(prm), byref(out), byref(st)),
            "lgc_rand_hkpr")
-    return SparseVec(out), st
+    return SparseVec(out, g.ctx), st
 
 
 def sweep(g: Graph, p: SparseVec) -> ClusterResult:
     out = POINTER(Cluster)()
     _check(load().lgc_sweep(g.handle, p.c_struct(), byref(out)), "lgc_sweep")
-    return ClusterResult(out)
+    return ClusterResult(out, g.ctx)
 
 
 def make_request(algo: int, seed: int, want_sweep: bool = True, **kw) -> Request:
