@@ -183,6 +183,36 @@ int lgc_rand_hkpr_endpoints(lgc_ctx *ctx, int32_t *out, int64_t n_walks);
  * p may be on the host or the device (p->on_device). */
 int lgc_sweep(lgc_graph *g, const lgc_svec *p, lgc_cluster **out);
 
+/* ---- sweep cut without device allocation ---- */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory during a call: processes
+ * whose device memory is all handed to their own allocator up front (for
+ * example a serving process that reserved the GPU's memory), or
+ * latency-critical paths that cannot risk an out-of-memory failure or an
+ * allocation's device synchronisation mid-request.
+ *
+ * Same result as lgc_sweep on the entries (d_idx[i], d_val[i]), i < nnz,
+ * which are DEVICE pointers (idx ascending, as for lgc_sweep).  The caller
+ * provides d_ids, a device buffer of at least nnz int32, which receives the
+ * cluster in sweep order; *out (host memory owned by the caller) receives
+ * size, vol, cut and conductance, with out->ids = d_ids and out->on_device = 1.
+ * Do not pass *out to lgc_cluster_free.
+ *
+ * No device memory is allocated or freed: all temporaries live in one
+ * fixed-size device array (about 5.6 MB) that every device loading the
+ * library holds until the process exits.  Limits and behaviour:
+ *  - nnz > LGC_SWEEP_NOALLOC_MAX_N is rejected with LGC_EINVAL;
+ *  - an entry that is not a vertex of degree >= 1: LGC_EINVAL;
+ *  - all calls share the array, so calls that overlap on the GPU (different
+ *    streams, contexts or threads) race and return wrong results; serialise
+ *    them;
+ *  - the first call on a device looks up the array's device address; make it
+ *    before any stream capture;
+ *  - runs on the graph's context stream and waits for it before returning. */
+#define LGC_SWEEP_NOALLOC_MAX_N 65536
+int lgc_sweep_noalloc(lgc_graph *g, int64_t nnz, const int32_t *d_idx, const double *d_val,
+                      int32_t *d_ids, lgc_cluster *out);
+
 /* ---- tracing (deterministic-mode parity tests) ---- */
 /* Frontiers of the last diffusion call recorded under LGC_OPT_TRACE:
  * *rounds receives the round count; if sizes != NULL it receives the size of

@@ -117,6 +117,7 @@ SIGNATURES = {
     "lgc_cluster_free": (None, [POINTER(Cluster)]),
     "lgc_result_free": (None, [POINTER(Result)]),
     "lgc_strerror": (ctypes.c_char_p, [c_int]),
+    "lgc_sweep_noalloc": (c_int, [_P, c_int64, _P, _P, _P, POINTER(Cluster)]),
     "lgc_launch_count": (c_int64, [_P]),
     "lgc_profile_read": (c_int, [_P, c_int, _P]),
     "lgc_profile_reset": (c_int, [_P]),
