@@ -133,8 +133,11 @@ enum {
   LGC_OPT_TRACE = 2,            /* 1: record every round's frontier (tests) */
   LGC_OPT_SERVE_MEM_BUDGET = 3, /* bytes of hash-table memory admitted at once */
   LGC_OPT_SERVE_MAX_BATCH = 4,  /* requests resident on the device at once */
-  LGC_OPT_TABLE_FORM = 6        /* sparse sets: 0 automatic (dense once a set may reach
+  LGC_OPT_TABLE_FORM = 6,       /* sparse sets: 0 automatic (dense once a set may reach
                                    n/8 keys), 1 always hashed, 2 always dense */
+  LGC_OPT_PULL = 7              /* deterministic rounds gather from the frontier instead of
+                                   sorting pushed records: 0 automatic (rounds of >= 2m/16
+                                   edges), 1 never, 2 always; same results either way */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */
@@ -174,6 +177,20 @@ int lgc_rand_hkpr(lgc_graph *g, int32_t seed, const lgc_rand_hkpr_params *prm, l
 /* Optional: the endpoints A[0..n_walks) of the last lgc_rand_hkpr call on
  * this context, copied to host memory `out` (n_walks int32).  Tests only. */
 int lgc_rand_hkpr_endpoints(lgc_ctx *ctx, int32_t *out, int64_t n_walks);
+
+/* ---- many seeds at once ---- */
+/* PR-Nibble (Sec. 3.3) for B seeds in one batch: every round runs the push of
+ * all seeds that still have a frontier with one launch per kernel, each seed
+ * on its own sparse sets with its own parameters (seeds[b], prm[b]), so each
+ * result is the same as lgc_prnibble's for that seed (bit-identical in
+ * LGC_MODE_DET; within rounding in LGC_MODE_ATOMIC).  All prm[b].mode must
+ * be equal.  p_out[b] receives seed b's vector (host or device per
+ * LGC_OPT_RESULT_ON_DEVICE); st (nullable) B counters.  The paper names
+ * running many local computations independently in parallel as the
+ * straightforward use of parallelism (Sec. 1), and its network community
+ * profiles run PR-Nibble from 10^5 seeds (Sec. 4). */
+int lgc_prnibble_batch(lgc_graph *g, int64_t B, const int32_t *seeds,
+                       const lgc_prnibble_params *prm, lgc_svec **p_out, lgc_stats *st);
 
 /* ---- sweep cut (Sec. 3.1, Theorem thm:sweep) ---- */
 /* Sorts the entries of p with p > 0 by p[v]/d(v) non-increasing (ties by

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblgc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["common.cu", "prim.cu", "diffuse.cu", "rwalk.cu", "sweep.cu", "capi.cu",
-           "sweep_noalloc.cu"]
+           "sweep_noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler",
                      "-fPIC,-ffp-contract=off,-O2", "-Xptxas", "-O3"]

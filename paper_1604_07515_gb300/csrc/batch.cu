@@ -1,0 +1,699 @@
+// Batched PR-Nibble: B seeds advance together, one launch per kernel per
+// round for all of them.  Every seed keeps its own hashed sparse set (r in
+// the slot value, p alongside) and its own parameters, and runs exactly the
+// synchronous rounds of Sec. 3.3 (Fig. alg:pr-nibble / alg:pr-nibble2): a
+// seed's round reads only its own residuals from the start of the round, so
+// sharing launches changes nothing in its arithmetic.
+//
+// The frontiers of all seeds form one list of (seed, vertex, slot) entries,
+// grouped by seed.  The vertexMap runs over that list, the edgeMap is
+// edge-balanced over the concatenation of all their adjacency lists, and
+// the next frontier is appended with per-seed counters (entries, their
+// degrees, keys inserted) that the host reads once per round for the whole
+// batch to grow each seed's table before its next round.
+//
+// Deterministic mode emits (seed, destination, share) records, sorts them by
+// (seed, destination) stably and folds each run in ascending source order,
+// as the single-seed deterministic mode does per seed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "prim.cuh"
+
+namespace lgc {
+namespace {
+
+constexpr int kItemsB = 4;
+constexpr int kTileB = kBlock * kItemsB;
+
+struct SeedParam {
+  double alpha, eps, cs, cn;
+  int rule;
+  int pad;
+};
+
+struct SeedCount {
+  int32_t next_size;
+  int32_t err;
+  int64_t next_edges;
+  int64_t inserted;
+};
+
+// Appends (seed, v, slot) to the next frontier: warp-aggregated position,
+// per-seed counters by atomics.  Every lane of the calling group must call it.
+__device__ inline void batch_append(bool pred, int32_t seed, int32_t v, int32_t slot, int64_t d,
+                                    int32_t* nseed, int32_t* nfv, int32_t* nfs, int32_t ncap,
+                                    int32_t* gsize, int32_t* gerr, SeedCount* sc) {
+  const unsigned active = __activemask();
+  const unsigned mask = __ballot_sync(active, pred);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(gsize, __popc(mask));
+  base = __shfl_sync(active, base, leader);
+  if (pred) {
+    const int32_t pos = base + __popc(mask & ((1u << lane) - 1));
+    if (pos < ncap) {
+      nseed[pos] = seed;
+      nfv[pos] = v;
+      nfs[pos] = slot;
+    } else {
+      atomicOr(gerr, kErrFrontierOverflow);
+    }
+    atomicAdd(&sc[seed].next_size, 1);
+    atomicAdd((unsigned long long*)&sc[seed].next_edges, (unsigned long long)d);
+  }
+}
+
+__global__ void batch_init_kernel(int64_t B, const int32_t* __restrict__ seeds,
+                                  const Table* __restrict__ tabs, int32_t* fseed, int32_t* fv,
+                                  int32_t* fs, SeedCount* sc) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const Table T = tabs[b];
+    int ins = 0;
+    const int64_t s = ht_find_or_insert(T, seeds[b], &ins, &sc[b].err);
+    if (s >= 0) T.s[s].val = 1.0;
+    fseed[b] = (int32_t)b;
+    fv[b] = seeds[b];
+    fs[b] = (int32_t)s;
+  }
+}
+
+// vertexMap of every seed's frontier (same arithmetic as the single-seed
+// kernel, with the seed's own parameters and table).
+__global__ void batch_vmap_kernel(int64_t nf, const int32_t* __restrict__ fseed,
+                                  const int32_t* __restrict__ fv, const int32_t* __restrict__ fs,
+                                  const Table* __restrict__ tabs,
+                                  const SeedParam* __restrict__ prm,
+                                  const int64_t* __restrict__ off, int det,
+                                  double* __restrict__ share, int64_t* __restrict__ cnt,
+                                  int64_t* __restrict__ foff, int32_t* nseed, int32_t* nfv,
+                                  int32_t* nfs, int32_t ncap, int32_t* gsize, int32_t* gerr,
+                                  SeedCount* sc) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool pred = false;
+    int32_t seed = 0, v = 0, slot = 0;
+    int64_t d = 0;
+    if (i < nf) {
+      seed = fseed[i];
+      v = fv[i];
+      slot = fs[i];
+      const Table T = tabs[seed];
+      const SeedParam P = prm[seed];
+      const bool ok = slot >= 0;
+      const double r = ok ? T.s[slot].val : 0.0;
+      const int64_t o0 = off[v];
+      d = off[v + 1] - o0;
+      double sh, rbase;
+      if (P.rule == 0) {
+        if (ok) T.p[slot] = T.p[slot] + P.cs * r;
+        rbase = 0.0;
+        sh = (P.cn * r) / (double)d;
+      } else {
+        if (ok) T.p[slot] = T.p[slot] + P.alpha * r;
+        rbase = ((1.0 - P.alpha) * r) / 2.0;
+        sh = ((1.0 - P.alpha) * r) / (2.0 * (double)d);
+      }
+      if (ok) T.s[slot].val = rbase;
+      share[i] = sh;
+      cnt[i] = d + (det ? 1 : 0);
+      foff[i] = o0;
+      pred = ok && !det && P.rule == 1 && rbase >= P.eps * (double)d;
+    }
+    batch_append(pred, seed, v, slot, d, nseed, nfv, nfs, ncap, gsize, gerr, sc);
+  }
+}
+
+__device__ inline int64_t ub_i64(const int64_t* a, int64_t n, int64_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Stages the sources owning records [e0, e1) (see the single-seed edgeMap).
+__device__ inline int batch_stage(const int64_t* __restrict__ epos, int64_t nf, int64_t total,
+                                  int64_t e0, int64_t e1, int64_t* s_i0, int64_t* s_i1,
+                                  int64_t* s_epos) {
+  if (threadIdx.x == 0) *s_i0 = ub_i64(epos, nf, e0) - 1;
+  if (threadIdx.x == 32) *s_i1 = ub_i64(epos, nf, e1 - 1) - 1;
+  __syncthreads();
+  const int64_t i0 = *s_i0;
+  int64_t c = *s_i1 - i0 + 1;
+  if (i0 < 0 || c < 0) c = 0;
+  if (c > kTileB) c = kTileB;
+  for (int j = threadIdx.x; j <= (int)c; j += kBlock)
+    s_epos[j] = (i0 + j < nf) ? epos[i0 + j] : total;
+  __syncthreads();
+  return (int)c;
+}
+
+__device__ inline int batch_find(const int64_t* s_epos, int cnt, int64_t e, int64_t* q) {
+  int lo = 0, hi = cnt;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s_epos[mid] <= e) lo = mid + 1;
+    else hi = mid;
+  }
+  const int j = lo - 1;
+  if (j < 0) return -1;
+  const int64_t local = e - s_epos[j];
+  if (local >= s_epos[j + 1] - s_epos[j]) return -1;
+  *q = local;
+  return j;
+}
+
+// edgeMap (atomic mode) over all seeds' edges.
+__global__ void __launch_bounds__(kBlock)
+    batch_emap_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+                      const double* __restrict__ share, const int64_t* __restrict__ epos,
+                      const int64_t* __restrict__ foff, const int32_t* __restrict__ fseed,
+                      int64_t nf, int64_t E_host, const int64_t* __restrict__ E_dev,
+                      const Table* __restrict__ tabs, const SeedParam* __restrict__ prm,
+                      int32_t* nseed, int32_t* nfv, int32_t* nfs, int32_t ncap, int32_t* gsize,
+                      int32_t* gerr, SeedCount* sc) {
+  __shared__ int64_t s_epos[kTileB + 1];
+  __shared__ int64_t s_off[kTileB];
+  __shared__ double s_share[kTileB];
+  __shared__ int32_t s_seed[kTileB];
+  __shared__ int64_t s_i0, s_i1;
+  const int64_t E = min(E_host, *E_dev);
+  const int64_t ntiles = (E + kTileB - 1) / kTileB;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kTileB, e1 = min(E, e0 + kTileB);
+    const int cntsrc = batch_stage(epos, nf, E, e0, e1, &s_i0, &s_i1, s_epos);
+    const int64_t i0 = s_i0;
+    for (int j = threadIdx.x; j < cntsrc; j += kBlock) {
+      s_off[j] = foff[i0 + j];
+      s_share[j] = share[i0 + j];
+      s_seed[j] = fseed[i0 + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItemsB; k++) {
+      const int64_t e = e0 + k * kBlock + threadIdx.x;
+      int64_t q = 0;
+      const int j = e < e1 ? batch_find(s_epos, cntsrc, e, &q) : -1;
+      bool pred = false;
+      int32_t seed = 0, w = 0, slot = -1;
+      int64_t dw = 0;
+      if (j >= 0) {
+        seed = s_seed[j];
+        w = col[s_off[j] + q];
+        const Table T = tabs[seed];
+        int ins = 0;
+        slot = (int32_t)ht_find_or_insert(T, w, &ins, &sc[seed].err);
+        if (ins) atomicAdd((unsigned long long*)&sc[seed].inserted, 1ull);
+        if (slot >= 0) {
+          const double sh = s_share[j];
+          const double old = atomicAdd(&T.s[slot].val, sh);
+          const double nv = old + sh;
+          const double eps = prm[seed].eps;
+          if (nv >= eps) {
+            dw = deg[w];
+            const double thr = eps * (double)dw;
+            pred = old < thr && nv >= thr;
+          }
+        }
+      }
+      batch_append(pred, seed, w, slot, dw, nseed, nfv, nfs, ncap, gsize, gerr, sc);
+    }
+    __syncthreads();
+  }
+}
+
+// Deterministic mode: records keyed (seed << vbits) | destination.
+__global__ void __launch_bounds__(kBlock)
+    batch_emit_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ fv,
+                      const int32_t* __restrict__ fseed, const double* __restrict__ share,
+                      const int64_t* __restrict__ epos, const int64_t* __restrict__ foff,
+                      int64_t nf, int64_t R, int vbits, uint64_t* __restrict__ rkey,
+                      double* __restrict__ rval) {
+  __shared__ int64_t s_epos[kTileB + 1];
+  __shared__ int64_t s_off[kTileB];
+  __shared__ double s_share[kTileB];
+  __shared__ int32_t s_v[kTileB];
+  __shared__ int32_t s_seed[kTileB];
+  __shared__ int64_t s_i0, s_i1;
+  const int64_t ntiles = (R + kTileB - 1) / kTileB;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kTileB, e1 = min(R, e0 + kTileB);
+    const int cntsrc = batch_stage(epos, nf, R, e0, e1, &s_i0, &s_i1, s_epos);
+    const int64_t i0 = s_i0;
+    for (int j = threadIdx.x; j < cntsrc; j += kBlock) {
+      s_off[j] = foff[i0 + j];
+      s_share[j] = share[i0 + j];
+      s_v[j] = fv[i0 + j];
+      s_seed[j] = fseed[i0 + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < kItemsB; k++) {
+      const int64_t e = e0 + k * kBlock + threadIdx.x;
+      int64_t q = 0;
+      const int j = e < e1 ? batch_find(s_epos, cntsrc, e, &q) : -1;
+      if (j < 0) continue;
+      const uint64_t hi = (uint64_t)s_seed[j] << vbits;
+      if (q == 0) {  // self record (+0.0) keeps the frontier vertex a candidate
+        rkey[e] = hi | (uint64_t)s_v[j];
+        rval[e] = 0.0;
+      } else {
+        rkey[e] = hi | (uint64_t)col[s_off[j] + q - 1];
+        rval[e] = s_share[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void batch_heads_kernel(const uint64_t* __restrict__ rkey, int64_t R,
+                                   int64_t* __restrict__ flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < R;
+       e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = (e == 0 || rkey[e] != rkey[e - 1]) ? 1 : 0;
+}
+
+__global__ void batch_starts_kernel(const uint64_t* __restrict__ rkey, int64_t R,
+                                    const int64_t* __restrict__ segid,
+                                    int64_t* __restrict__ segstart) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < R;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (e == 0 || rkey[e] != rkey[e - 1]) segstart[segid[e]] = e;
+}
+
+// One thread per (seed, destination) run: left fold from the current value.
+__global__ void batch_fold_kernel(const uint64_t* __restrict__ rkey,
+                                  const double* __restrict__ rval, int64_t R,
+                                  const int64_t* __restrict__ segstart, int64_t nseg, int vbits,
+                                  const Table* __restrict__ tabs,
+                                  const SeedParam* __restrict__ prm,
+                                  const int32_t* __restrict__ deg, int64_t* __restrict__ qflag,
+                                  int32_t* __restrict__ segseed, int32_t* __restrict__ segv,
+                                  int32_t* __restrict__ segslot, SeedCount* sc) {
+  for (int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sg < nseg;
+       sg += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = segstart[sg];
+    const int64_t e = sg + 1 < nseg ? segstart[sg + 1] : R;
+    const int32_t seed = (int32_t)(rkey[b] >> vbits);
+    const int32_t w = (int32_t)(rkey[b] & ((1ull << vbits) - 1));
+    const Table T = tabs[seed];
+    int ins = 0;
+    const int64_t slot = ht_find_or_insert(T, w, &ins, &sc[seed].err);
+    if (ins) atomicAdd((unsigned long long*)&sc[seed].inserted, 1ull);
+    int64_t q = 0;
+    if (slot >= 0) {
+      double acc = T.s[slot].val;
+      for (int64_t k = b; k < e; k++) acc = acc + rval[k];
+      T.s[slot].val = acc;
+      q = acc >= prm[seed].eps * (double)deg[w] ? 1 : 0;
+    }
+    qflag[sg] = q;
+    segseed[sg] = seed;
+    segv[sg] = w;
+    segslot[sg] = (int32_t)slot;
+  }
+}
+
+__global__ void batch_compact_kernel(const int64_t* __restrict__ qflag,
+                                     const int64_t* __restrict__ qpos, int64_t nseg,
+                                     const int32_t* __restrict__ segseed,
+                                     const int32_t* __restrict__ segv,
+                                     const int32_t* __restrict__ segslot,
+                                     const int32_t* __restrict__ deg, int32_t* nseed, int32_t* nfv,
+                                     int32_t* nfs, int32_t ncap, int32_t* gerr, SeedCount* sc) {
+  for (int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sg < nseg;
+       sg += (int64_t)gridDim.x * blockDim.x) {
+    if (!qflag[sg]) continue;
+    const int64_t pos = qpos[sg];
+    const int32_t seed = segseed[sg], v = segv[sg];
+    if (pos < ncap) {
+      nseed[pos] = seed;
+      nfv[pos] = v;
+      nfs[pos] = segslot[sg];
+    } else {
+      atomicOr(gerr, kErrFrontierOverflow);
+    }
+    atomicAdd(&sc[seed].next_size, 1);
+    atomicAdd((unsigned long long*)&sc[seed].next_edges, (unsigned long long)deg[v]);
+  }
+}
+
+// Frontier slots of seeds whose table was rebuilt are looked up again.
+__global__ void batch_reresolve_kernel(int64_t nf, const int32_t* __restrict__ fseed,
+                                       const int32_t* __restrict__ fv, int32_t* __restrict__ fs,
+                                       const Table* __restrict__ tabs,
+                                       const int32_t* __restrict__ grown) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (grown[fseed[i]]) fs[i] = (int32_t)ht_find(tabs[fseed[i]], fv[i]);
+}
+
+// Keeps the frontier entries of seeds that are still running (order kept).
+__global__ void batch_keep_flags_kernel(int64_t nf, const int32_t* __restrict__ fseed,
+                                        const int32_t* __restrict__ alive,
+                                        int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = alive[fseed[i]] ? 1 : 0;
+}
+
+__global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ flag,
+                                        const int64_t* __restrict__ pos,
+                                        const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                                        const int32_t* __restrict__ c, int32_t* oa, int32_t* ob,
+                                        int32_t* oc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) {
+      oa[pos[i]] = a[i];
+      ob[pos[i]] = b[i];
+      oc[pos[i]] = c[i];
+    }
+}
+
+__global__ void gather_degrees_kernel(int64_t B, const int32_t* __restrict__ seeds, int64_t n,
+                                      const int32_t* __restrict__ deg, int64_t* __restrict__ out) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = seeds[b];
+    out[b] = (x >= 0 && x < n) ? deg[x] : -1;
+  }
+}
+
+}  // namespace
+
+int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,
+                       const lgc_prnibble_params* prm_h, lgc_svec** p_out, lgc_stats* st_out) {
+  if (!g || B < 1 || B > (1 << 24) || !seeds_h || !prm_h || !p_out) return LGC_EINVAL;
+  const int mode = prm_h[0].mode;
+  for (int64_t b = 0; b < B; b++) {
+    const lgc_prnibble_params& P = prm_h[b];
+    if (!(P.alpha > 0.0 && P.alpha < 1.0) || !(P.eps > 0.0) || (P.rule != 0 && P.rule != 1) ||
+        P.mode != mode || (mode != 0 && mode != 1))
+      return LGC_EINVAL;
+    p_out[b] = nullptr;
+  }
+  const bool det = mode == LGC_MODE_DET;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = g->n;
+  const int vbits = bits_for(n);
+  if (det && vbits + bits_for(B) > 64) return LGC_EINVAL;
+
+  // per-seed host state
+  std::vector<int64_t> dseed(B), count(B, 1), nfs(B, 1), edges(B), rounds(B, 0), pushes(B, 0),
+      pushed(B, 0), max_rounds(B);
+  std::vector<SeedParam> sp(B);
+  std::vector<Table> tabs(B);
+  std::vector<int32_t> grown(B, 0), alive(B, 1);
+  std::vector<SeedCount> sc_h(B);
+
+  int32_t *d_seeds = nullptr, *d_grown = nullptr, *d_alive = nullptr, *gsize = nullptr;
+  int64_t* d_deg = nullptr;
+  Table* d_tabs = nullptr;
+  SeedParam* d_prm = nullptr;
+  SeedCount* d_sc = nullptr;
+  DBuf<int32_t> Fs, Fv, Fslot, Gs, Gv, Gslot;
+  DBuf<double> share, rv, rv2;
+  DBuf<int64_t> cnt, epos, foff, total, flag, segid, segstart, qflag, qpos;
+  DBuf<uint64_t> rk, rk2;
+  DBuf<int32_t> segseed, segv, segslot;
+  int status = LGC_OK;
+  int64_t nf = B;
+
+  auto fail = [&](int st) {
+    status = st;
+    return st;
+  };
+  do {
+    if (fail(dalloc_t(ctx, &d_seeds, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_deg, B)) != LGC_OK) break;
+    if (cudaMemcpyAsync(d_seeds, seeds_h, 4 * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      fail(LGC_ECUDA);
+      break;
+    }
+    gather_degrees_kernel<<<grid_for(B), kBlock, 0, s>>>(B, d_seeds, n, g->deg, d_deg);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaMemcpyAsync(dseed.data(), d_deg, 8 * B, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      fail(LGC_ECUDA);
+      break;
+    }
+    bool bad = false;
+    for (int64_t b = 0; b < B; b++) bad = bad || dseed[b] < 1;
+    if (bad) {
+      fail(LGC_EINVAL);
+      break;
+    }
+    for (int64_t b = 0; b < B; b++) {
+      const lgc_prnibble_params& P = prm_h[b];
+      sp[b].alpha = P.alpha;
+      sp[b].eps = P.eps;
+      sp[b].cs = (2.0 * P.alpha) / (1.0 + P.alpha);
+      sp[b].cn = (1.0 - P.alpha) / (1.0 + P.alpha);
+      sp[b].rule = P.rule;
+      sp[b].pad = 0;
+      edges[b] = dseed[b];
+      max_rounds[b] = P.max_rounds > 0 ? P.max_rounds : INT64_MAX;
+      if (fail(table_create(ctx, &tabs[b], 2 * (1 + dseed[b]), true)) != LGC_OK) break;
+    }
+    if (status != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_tabs, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_prm, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_sc, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_grown, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &d_alive, B)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &gsize, 2)) != LGC_OK) break;
+    cudaMemcpyAsync(d_prm, sp.data(), sizeof(SeedParam) * B, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(d_sc, 0, sizeof(SeedCount) * B, s);
+    if (fail(Fs.reserve(ctx, B)) || fail(Fv.reserve(ctx, B)) || fail(Fslot.reserve(ctx, B)) ||
+        fail(total.reserve(ctx, 1)))
+      break;
+    batch_init_kernel<<<grid_for(B), kBlock, 0, s>>>(B, d_seeds, d_tabs, Fs.ptr, Fv.ptr,
+                                                      Fslot.ptr, d_sc);
+    LGC_COUNT_LAUNCH(ctx);
+
+    while (nf > 0) {
+      // seeds at their round limit leave the batch
+      bool drop = false;
+      for (int64_t b = 0; b < B; b++)
+        if (alive[b] && nfs[b] > 0 && rounds[b] >= max_rounds[b]) {
+          alive[b] = 0;
+          drop = true;
+        }
+      if (drop) {
+        cudaMemcpyAsync(d_alive, alive.data(), 4 * B, cudaMemcpyHostToDevice, s);
+        if (fail(flag.reserve(ctx, nf)) || fail(qpos.reserve(ctx, nf)) ||
+            fail(Gs.reserve(ctx, nf)) || fail(Gv.reserve(ctx, nf)) || fail(Gslot.reserve(ctx, nf)))
+          break;
+        batch_keep_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, d_alive, flag.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        if (fail(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr)) != LGC_OK) break;
+        batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr,
+                                                                 Fv.ptr, Fslot.ptr, Gs.ptr, Gv.ptr,
+                                                                 Gslot.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        std::swap(Fs, Gs);
+        std::swap(Fv, Gv);
+        std::swap(Fslot, Gslot);
+        nf = 0;
+        for (int64_t b = 0; b < B; b++) {
+          if (!alive[b]) nfs[b] = 0;
+          nf += nfs[b];
+        }
+        if (nf == 0) break;
+      }
+      // grow each seed's table so its round's new keys fit at load 1/2
+      bool any_grown = false;
+      int64_t next_cap = 0, E = 0;
+      for (int64_t b = 0; b < B; b++) {
+        grown[b] = 0;
+        if (nfs[b] == 0) continue;
+        const int64_t need = std::min<int64_t>(count[b] + edges[b], n);
+        if (2 * need > tabs[b].cap) {
+          if (fail(table_grow(ctx, &tabs[b], 2 * need, nullptr, nullptr, 0)) != LGC_OK) break;
+          grown[b] = 1;
+          any_grown = true;
+        }
+        next_cap += std::min<int64_t>(n, count[b] + edges[b] + nfs[b]);
+        E += edges[b];
+      }
+      if (status != LGC_OK) break;
+      if (any_grown) {
+        cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_grown, grown.data(), 4 * B, cudaMemcpyHostToDevice, s);
+        batch_reresolve_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, Fv.ptr, Fslot.ptr,
+                                                                d_tabs, d_grown);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (fail(share.reserve(ctx, nf)) || fail(cnt.reserve(ctx, nf)) ||
+          fail(epos.reserve(ctx, nf)) || fail(foff.reserve(ctx, nf)) ||
+          fail(Gs.reserve(ctx, next_cap)) || fail(Gv.reserve(ctx, next_cap)) ||
+          fail(Gslot.reserve(ctx, next_cap)))
+        break;
+      const int32_t ncap = (int32_t)std::min<size_t>(Gv.cap, INT32_MAX);
+      cudaMemsetAsync(d_sc, 0, sizeof(SeedCount) * B, s);
+      cudaMemsetAsync(gsize, 0, 8, s);
+      {
+        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+        batch_vmap_kernel<<<std::min(grid_for(nf), 152 * 32), kBlock, 0, s>>>(
+            nf, Fs.ptr, Fv.ptr, Fslot.ptr, d_tabs, d_prm, g->off, det ? 1 : 0, share.ptr,
+            cnt.ptr, foff.ptr, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (fail(scan_i64(ctx, cnt.ptr, epos.ptr, nf, false, total.ptr)) != LGC_OK) break;
+      if (!det) {
+        if (E > 0) {
+          const int64_t tiles = ceil_div(E, kTileB);
+          ProfScope ps(ctx, LGC_PROF_EDGEMAP, 24.0 * (double)E + 28.0 * nf);
+          batch_emap_kernel<<<(int)std::min<int64_t>(tiles, 152 * 16), kBlock, 0, s>>>(
+              g->col, g->deg, share.ptr, epos.ptr, foff.ptr, Fs.ptr, nf, E, total.ptr, d_tabs,
+              d_prm, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
+          LGC_COUNT_LAUNCH(ctx);
+        }
+      } else {
+        const int64_t R = E + nf;  // one self record per frontier entry
+        if (fail(rk.reserve(ctx, R)) || fail(rk2.reserve(ctx, R)) || fail(rv.reserve(ctx, R)) ||
+            fail(rv2.reserve(ctx, R)) || fail(flag.reserve(ctx, R)) ||
+            fail(segid.reserve(ctx, R)))
+          break;
+        {
+          const int64_t tiles = ceil_div(R, kTileB);
+          ProfScope ps(ctx, LGC_PROF_DET_EDGE, 24.0 * (double)E + 28.0 * nf);
+          batch_emit_kernel<<<(int)std::min<int64_t>(tiles, 152 * 16), kBlock, 0, s>>>(
+              g->col, Fv.ptr, Fs.ptr, share.ptr, epos.ptr, foff.ptr, nf, R, vbits, rk.ptr,
+              rv.ptr);
+          LGC_COUNT_LAUNCH(ctx);
+          if (fail(radix_sort_u64_f64(ctx, rk.ptr, rv.ptr, rk2.ptr, rv2.ptr, R,
+                                      vbits + bits_for(B))) != LGC_OK)
+            break;
+          batch_heads_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, flag.ptr);
+          LGC_COUNT_LAUNCH(ctx);
+          if (fail(scan_i64(ctx, flag.ptr, segid.ptr, R, false, total.ptr)) != LGC_OK) break;
+        }
+        if (cudaMemcpyAsync(ctx->h_scratch, total.ptr, 8, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          fail(LGC_ECUDA);
+          break;
+        }
+        const int64_t nseg = ctx->h_scratch[0];
+        if (fail(segstart.reserve(ctx, nseg)) || fail(qflag.reserve(ctx, nseg)) ||
+            fail(qpos.reserve(ctx, nseg)) || fail(segseed.reserve(ctx, nseg)) ||
+            fail(segv.reserve(ctx, nseg)) || fail(segslot.reserve(ctx, nseg)))
+          break;
+        ProfScope ps(ctx, LGC_PROF_DET_EDGE, 0.0);
+        batch_starts_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, segid.ptr, segstart.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        batch_fold_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
+            rk.ptr, rv.ptr, R, segstart.ptr, nseg, vbits, d_tabs, d_prm, g->deg, qflag.ptr,
+            segseed.ptr, segv.ptr, segslot.ptr, d_sc);
+        LGC_COUNT_LAUNCH(ctx);
+        if (fail(scan_i64(ctx, qflag.ptr, qpos.ptr, nseg, false, total.ptr)) != LGC_OK) break;
+        batch_compact_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
+            qflag.ptr, qpos.ptr, nseg, segseed.ptr, segv.ptr, segslot.ptr, g->deg, Gs.ptr,
+            Gv.ptr, Gslot.ptr, ncap, gsize + 1, d_sc);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (cudaGetLastError() != cudaSuccess) {
+        fail(LGC_ECUDA);
+        break;
+      }
+      // one read-back per round for the whole batch
+      if (cudaMemcpyAsync(sc_h.data(), d_sc, sizeof(SeedCount) * B, cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(ctx->h_scratch, gsize, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        fail(LGC_ECUDA);
+        break;
+      }
+      const int32_t* gs = (const int32_t*)ctx->h_scratch;
+      if (gs[1] != 0) {
+        fail(LGC_ETABLEFULL);
+        break;
+      }
+      int64_t next = 0;
+      for (int64_t b = 0; b < B; b++) {
+        if (sc_h[b].err) status = LGC_ETABLEFULL;
+        if (nfs[b] > 0) {
+          rounds[b]++;
+          pushes[b] += nfs[b];
+          pushed[b] += edges[b];
+        }
+        count[b] += sc_h[b].inserted;
+        nfs[b] = sc_h[b].next_size;
+        edges[b] = sc_h[b].next_edges;
+        next += nfs[b];
+      }
+      if (status != LGC_OK) break;
+      // the deterministic next frontier is in (seed, vertex) order; the
+      // atomic one is grouped by nothing, which the round does not need
+      std::swap(Fs, Gs);
+      std::swap(Fv, Gv);
+      std::swap(Fslot, Gslot);
+      nf = next;
+    }
+    if (status != LGC_OK) break;
+    // results
+    for (int64_t b = 0; b < B && status == LGC_OK; b++) {
+      int32_t* d_idx = nullptr;
+      double* d_val = nullptr;
+      int64_t nnz = 0;
+      status = table_extract_sorted(ctx, tabs[b], tabs[b].p, n, &d_idx, &d_val, &nnz);
+      if (status == LGC_OK) status = make_svec(ctx, d_idx, d_val, nnz, ctx->result_on_device,
+                                               &p_out[b]);
+      dfree(ctx, d_idx);
+      dfree(ctx, d_val);
+      if (st_out) {
+        st_out[b] = lgc_stats{};
+        st_out[b].rounds = rounds[b];
+        st_out[b].pushes = pushes[b];
+        st_out[b].pushed_edges = pushed[b];
+        st_out[b].touched = count[b];
+        st_out[b].table_capacity = tabs[b].cap;
+        st_out[b].status_detail = rounds[b] >= max_rounds[b] ? LGC_EMAXROUNDS : 0;
+      }
+    }
+  } while (0);
+  for (int64_t b = 0; b < B; b++) table_destroy(ctx, &tabs[b]);
+  dfree(ctx, d_seeds);
+  dfree(ctx, d_deg);
+  dfree(ctx, d_tabs);
+  dfree(ctx, d_prm);
+  dfree(ctx, d_sc);
+  dfree(ctx, d_grown);
+  dfree(ctx, d_alive);
+  dfree(ctx, gsize);
+  for (auto* d : {&Fs, &Fv, &Fslot, &Gs, &Gv, &Gslot, &segseed, &segv, &segslot}) d->release(ctx);
+  for (auto* d : {&share, &rv, &rv2}) d->release(ctx);
+  for (auto* d : {&cnt, &epos, &foff, &total, &flag, &segid, &segstart, &qflag, &qpos})
+    d->release(ctx);
+  rk.release(ctx);
+  rk2.release(ctx);
+  if (status != LGC_OK) {
+    for (int64_t b = 0; b < B; b++) {
+      lgc_svec_free(p_out[b]);
+      p_out[b] = nullptr;
+    }
+  }
+  return status;
+}
+
+}  // namespace lgc
+
+extern "C" int lgc_prnibble_batch(lgc_graph* g, int64_t B, const int32_t* seeds,
+                                  const lgc_prnibble_params* prm, lgc_svec** p_out,
+                                  lgc_stats* st) {
+  if (!g) return LGC_EINVAL;
+  return lgc::run_prnibble_batch(g->ctx, g, B, seeds, prm, p_out, st);
+}

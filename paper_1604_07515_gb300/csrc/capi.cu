@@ -66,6 +66,102 @@ __global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* 
   }
 }
 
+__global__ void heavy_flag_kernel(const int32_t* __restrict__ deg, int64_t n,
+                                  int64_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = deg[v] > kPullLight ? 1 : 0;
+}
+
+__global__ void heavy_write_kernel(const int32_t* __restrict__ deg, int64_t n,
+                                   const int64_t* __restrict__ pos, int32_t* __restrict__ out) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (deg[v] > kPullLight) out[pos[v]] = (int32_t)v;
+}
+
+__global__ void items_count_kernel(const int32_t* __restrict__ heavy, int64_t nh,
+                                   const int32_t* __restrict__ deg, int64_t* __restrict__ cnt,
+                                   int32_t* __restrict__ items_of) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = ((int64_t)deg[heavy[h]] + kPullItem - 1) / kPullItem;
+    cnt[h] = c;
+    items_of[h] = (int32_t)c;
+  }
+}
+
+__global__ void items_fill_kernel(const int32_t* __restrict__ heavy, int64_t nh,
+                                  const int64_t* __restrict__ off, const int64_t* __restrict__ pos,
+                                  const int32_t* __restrict__ items_of, int32_t* __restrict__ ih,
+                                  int64_t* __restrict__ ibeg) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o0 = off[heavy[h]];
+    for (int k = 0; k < items_of[h]; k++) {
+      ih[pos[h] + k] = (int32_t)h;
+      ibeg[pos[h] + k] = o0 + (int64_t)k * kPullItem;
+    }
+  }
+}
+
+// The vertices of degree > kPullLight, ascending, for pull rounds, and their
+// adjacency cut into work items.
+int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = g->n;
+  if (n == 0) return LGC_OK;
+  int64_t *flag = nullptr, *tot = nullptr;
+  int st = dalloc_t(ctx, &flag, n);
+  if (st == LGC_OK) st = dalloc_t(ctx, &tot, 1);
+  if (st == LGC_OK) {
+    heavy_flag_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, flag);
+    LGC_COUNT_LAUNCH(ctx);
+    st = scan_i64(ctx, flag, flag, n, false, tot);
+  }
+  if (st == LGC_OK) {
+    if (cudaMemcpyAsync(ctx->h_scratch, tot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = LGC_ECUDA;
+  }
+  if (st == LGC_OK) {
+    g->nheavy = ctx->h_scratch[0];
+    st = dalloc_t(ctx, &g->heavy, g->nheavy);
+  }
+  if (st == LGC_OK && g->nheavy > 0) {
+    heavy_write_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, flag, g->heavy);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaGetLastError() != cudaSuccess) st = LGC_ECUDA;
+  }
+  // work items of at most kPullItem edges over the heavy vertices' lists
+  const int64_t nh = g->nheavy;
+  if (st == LGC_OK && nh > 0) st = dalloc_t(ctx, &g->items_of, nh);
+  if (st == LGC_OK && nh > 0) {
+    items_count_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->deg, flag, g->items_of);
+    LGC_COUNT_LAUNCH(ctx);
+    st = scan_i64(ctx, flag, flag, nh, false, tot);
+  }
+  if (st == LGC_OK && nh > 0) {
+    if (cudaMemcpyAsync(ctx->h_scratch, tot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = LGC_ECUDA;
+  }
+  if (st == LGC_OK && nh > 0) {
+    g->nitems = ctx->h_scratch[0];
+    st = dalloc_t(ctx, &g->item_h, g->nitems);
+    if (st == LGC_OK) st = dalloc_t(ctx, &g->item_beg, g->nitems);
+  }
+  if (st == LGC_OK && nh > 0) {
+    items_fill_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->off, flag, g->items_of,
+                                                       g->item_h, g->item_beg);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaGetLastError() != cudaSuccess) st = LGC_ECUDA;
+  }
+  dfree(ctx, flag);
+  dfree(ctx, tot);
+  return st;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -250,6 +346,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value < 0 || value > 2) return LGC_EINVAL;
       ctx->table_form = (int)value;
       return LGC_OK;
+    case LGC_OPT_PULL:
+      if (value < 0 || value > 2) return LGC_EINVAL;
+      ctx->pull_policy = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -319,13 +419,21 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
       break;
     }
     int32_t* hf = (int32_t*)ctx->h_scratch;
-    if (hf[0] != 0) st = LGC_EINVAL;
+    if (hf[0] != 0) {
+      st = LGC_EINVAL;
+      break;
+    }
     g->max_deg = hf[1];
+    st = build_heavy_list(ctx, g);
   } while (0);
   if (st != LGC_OK) {
     dfree(ctx, g->off);
     dfree(ctx, g->col);
     dfree(ctx, g->deg);
+    dfree(ctx, g->heavy);
+  dfree(ctx, g->item_h);
+  dfree(ctx, g->item_beg);
+  dfree(ctx, g->items_of);
     cudaStreamSynchronize(s);
     delete g;
     return st;
@@ -350,6 +458,10 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->off);
   dfree(ctx, g->col);
   dfree(ctx, g->deg);
+  dfree(ctx, g->heavy);
+  dfree(ctx, g->item_h);
+  dfree(ctx, g->item_beg);
+  dfree(ctx, g->items_of);
   cudaStreamSynchronize(ctx->stream);
   delete g;
 }

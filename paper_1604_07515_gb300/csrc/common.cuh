@@ -193,7 +193,8 @@ struct lgc_ctx {
   bool own_stream = false;
   bool result_on_device = false;
   bool trace = false;
-  int table_form = 0;  // LGC_OPT_TABLE_FORM
+  int table_form = 0;   // LGC_OPT_TABLE_FORM
+  int pull_policy = 0;  // LGC_OPT_PULL: 0 automatic, 1 never, 2 every deterministic round
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back
@@ -229,7 +230,24 @@ struct lgc_graph {
   int32_t* col = nullptr;  // device, nnz
   int32_t* deg = nullptr;  // device, n (int32 degree, read where off[] pairs would cost more)
   int32_t max_deg = 0;
+  // vertices of degree > kPullLight in ascending id, for the pull edge phase
+  int32_t* heavy = nullptr;
+  int64_t nheavy = 0;
+  // their adjacency cut into work items of at most kPullItem edges:
+  // item i covers edges [item_beg[i], item_beg[i] + len) of heavy vertex
+  // item_h[i] (an index into heavy), len = min(kPullItem, rest of the list)
+  int32_t* item_h = nullptr;
+  int64_t* item_beg = nullptr;
+  int32_t* items_of = nullptr;  // per heavy vertex: number of items
+  int64_t nitems = 0;
 };
+
+namespace lgc {
+// A pull round handles vertices of degree <= kPullLight with one thread each
+// and the rest in work items of at most kPullItem edges.
+constexpr int kPullLight = 32;
+constexpr int kPullItem = 4096;
+}  // namespace lgc
 
 namespace lgc {
 

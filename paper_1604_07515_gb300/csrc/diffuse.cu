@@ -440,6 +440,267 @@ __global__ void dense_filter_write_kernel(Table D, const int32_t* __restrict__ d
 }
 
 // ---------------------------------------------------------------------------
+// Pull edgeMap (deterministic mode, dense rounds).  Instead of scattering
+// from the frontier, every vertex w gathers from its neighbours that are in
+// the frontier.  Adjacency lists are sorted, so w meets its in-frontier
+// neighbours in ascending id: folding their shares left to right from w's
+// current value is exactly the canonical order, with no records and no sort.
+// The frontier is given as one double per vertex, sh[v]: +0.0 (all bits
+// zero) for a vertex outside the frontier, its share for a frontier vertex,
+// and -0.0 for a frontier vertex whose share is zero.  So one gather gives
+// both membership (any bit set) and the value, and adding a member's -0.0 to
+// a non-negative value changes nothing, exactly as its +0.0 share would.
+// Vertices of degree <= kPullLight use one thread, the rest (ascending list
+// g->heavy) are read in batches by warps.  Qualifying vertices are marked in
+// qbits for an ordered compaction.
+// ---------------------------------------------------------------------------
+__device__ inline bool pull_member(double s) { return __double_as_longlong(s) != 0; }
+
+__global__ void pull_scatter_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                    const double* __restrict__ share, double* __restrict__ sh,
+                                    int clear) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = fv[i];
+    const double x = share[i];
+    sh[v] = clear ? 0.0 : (pull_member(x) ? x : -0.0);
+  }
+}
+
+__device__ inline bool pull_qualifies(double acc, int64_t d, double c, int fmode) {
+  if (fmode == kFmThreshold) return acc >= c * (double)d;
+  return fmode == kFmInserted;
+}
+
+__global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                  int64_t n, const double* __restrict__ sh, Table D, double c,
+                                  int fmode, uint32_t* __restrict__ qbits, Counters* C) {
+  const int64_t words = (n + 31) / 32;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words * 32;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    bool q = false;
+    int ins = 0;
+    if (w < n) {
+      const int64_t o0 = off[w], d = off[w + 1] - o0;
+      if (d >= 1 && d <= kPullLight) {
+        const uint32_t m = 1u << (w & 31);
+        const bool present = (D.bits[w >> 5] & m) != 0;
+        double acc = present ? D.dval[w] : 0.0;
+        bool touched = present;
+        for (int64_t k = 0; k < d; k++) {
+          const double x = sh[col[o0 + k]];
+          if (pull_member(x)) {
+            acc = acc + x;
+            touched = true;
+          }
+        }
+        if (touched) {
+          D.dval[w] = acc;
+          if (!present) {
+            atomicOr(&D.bits[w >> 5], m);
+            ins = 1;
+          }
+          q = pull_qualifies(acc, d, c, fmode);
+        }
+      }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, q);
+    if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
+      qbits[(base + threadIdx.x) >> 5] = word;
+    count_inserted(ins, &C->inserted);
+  }
+}
+
+// Heavy vertices read their lists in batches of 32 * kPullBatch edges: every
+// lane issues the loads of kPullBatch edges (column, then share) before any
+// of them is used, so one batch costs two memory round trips.
+constexpr int kPullBatch = 8;
+
+// Loads batch [k0, k0 + 256) of a list: lane l holds edge k0 + 32 j + l in
+// slot j (adjacency order is j-major, then lane).  s[j] is +0.0 for an edge
+// whose source is not in the frontier.
+__device__ inline void pull_batch(const int32_t* __restrict__ col, int64_t o0, int64_t k0,
+                                  int64_t kend, const double* __restrict__ sh, int lane,
+                                  double s[kPullBatch], unsigned in[kPullBatch]) {
+  int32_t u[kPullBatch];
+#pragma unroll
+  for (int j = 0; j < kPullBatch; j++) {
+    const int64_t k = k0 + 32 * j + lane;
+    u[j] = k < kend ? col[o0 + k] : -1;
+  }
+#pragma unroll
+  for (int j = 0; j < kPullBatch; j++) {
+    s[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
+    in[j] = __ballot_sync(0xffffffffu, pull_member(s[j]));
+  }
+}
+
+// Writes a heavy vertex's gathered value (lane 0 calls it).
+__device__ inline void pull_finish(const Table& D, int32_t w, int64_t d, double acc, bool touched,
+                                   bool present, double c, int fmode, uint32_t* qbits,
+                                   Counters* C) {
+  if (!touched) return;
+  const uint32_t m = 1u << (w & 31);
+  D.dval[w] = acc;
+  if (!present && !(atomicOr(&D.bits[w >> 5], m) & m))
+    atomicAdd((unsigned long long*)&C->inserted, 1ull);
+  if (pull_qualifies(acc, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
+}
+
+// Deterministic mode: one warp per heavy vertex; after each batch, lane 0
+// folds the in-frontier shares from shared memory in adjacency order
+// (= ascending source id), starting from the vertex's current value.
+__global__ void __launch_bounds__(kBlock)
+    pull_heavy_det_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ heavy, int64_t nheavy,
+                          const double* __restrict__ sh, Table D, double c, int fmode,
+                          uint32_t* __restrict__ qbits, Counters* C) {
+  __shared__ double s_val[kBlock / 32][32 * kPullBatch];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t h = warp0; h < nheavy; h += nwarps) {
+    const int32_t w = heavy[h];
+    const int64_t o0 = off[w], d = off[w + 1] - o0;
+    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
+    double acc = present ? D.dval[w] : 0.0;  // lane 0's running value, >= +0
+    bool touched = present;
+    for (int64_t k0 = 0; k0 < d; k0 += 32 * kPullBatch) {
+      double s[kPullBatch];
+      unsigned in[kPullBatch];
+      pull_batch(col, o0, k0, d, sh, lane, s, in);
+      int members = 0;
+#pragma unroll
+      for (int j = 0; j < kPullBatch; j++) {
+        s_val[wib][32 * j + lane] = s[j];
+        touched = touched || in[j] != 0;
+        members += __popc(in[j]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        if (members >= 64) {
+          // dense batch: add every slot in order; a non-member's +0.0 (or a
+          // member's -0.0) leaves a non-negative sum unchanged
+#pragma unroll 16
+          for (int t = 0; t < 32 * kPullBatch; t++) acc = acc + s_val[wib][t];
+        } else {
+#pragma unroll
+          for (int j = 0; j < kPullBatch; j++) {
+            unsigned mask = in[j];
+            while (mask) {
+              const int l = __ffs(mask) - 1;
+              mask &= mask - 1;
+              acc = acc + s_val[wib][32 * j + l];
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0) pull_finish(D, w, d, acc, touched, present, c, fmode, qbits, C);
+  }
+}
+
+// Atomic mode: one warp per work item (at most kPullItem edges of one heavy
+// vertex).  Lanes sum strided parts and the warp reduces by a butterfly.  A
+// vertex with one item is finished at once; otherwise the partial sums are
+// added into hacc[h] and the warp that completes the vertex's last item
+// finishes it (and resets the vertex's accumulators for the next round).
+__global__ void __launch_bounds__(kBlock)
+    pull_heavy_tree_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ heavy, const int32_t* __restrict__ item_h,
+                           const int64_t* __restrict__ item_beg,
+                           const int32_t* __restrict__ items_of, int64_t nitems,
+                           const double* __restrict__ sh,
+                           Table D, double c, int fmode, uint32_t* __restrict__ qbits,
+                           double* __restrict__ hacc, int32_t* __restrict__ hcnt,
+                           int32_t* __restrict__ htouch, Counters* C) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = warp0; it < nitems; it += nwarps) {
+    const int32_t h = item_h[it];
+    const int32_t w = heavy[h];
+    const int64_t o0 = off[w], d = off[w + 1] - o0;
+    const int64_t k_beg = item_beg[it] - o0;
+    const int64_t k_end = min(d, k_beg + kPullItem);
+    double part = 0.0;
+    bool any = false;
+    for (int64_t k0 = k_beg; k0 < k_end; k0 += 32 * kPullBatch) {
+      double s[kPullBatch];
+      unsigned in[kPullBatch];
+      pull_batch(col, o0, k0, k_end, sh, lane, s, in);
+#pragma unroll
+      for (int j = 0; j < kPullBatch; j++) {
+        part = part + s[j];
+        any = any || in[j] != 0;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) part = part + __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane != 0) continue;
+    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
+    if (items_of[h] == 1) {
+      const double base = present ? D.dval[w] : 0.0;
+      pull_finish(D, w, d, base + part, present || any, present, c, fmode, qbits, C);
+      continue;
+    }
+    if (part != 0.0) atomicAdd(&hacc[h], part);
+    if (any) atomicOr(&htouch[h], 1);
+    __threadfence();
+    if (atomicAdd(&hcnt[h], 1) == items_of[h] - 1) {
+      __threadfence();
+      const double total = atomicAdd(&hacc[h], 0.0);
+      const bool touched = present || atomicOr(&htouch[h], 0) != 0;
+      const double base = present ? D.dval[w] : 0.0;
+      pull_finish(D, w, d, base + total, touched, present, c, fmode, qbits, C);
+      hacc[h] = 0.0;
+      hcnt[h] = 0;
+      htouch[h] = 0;
+    }
+  }
+}
+
+// Ordered compaction of a vertex bitmap into a frontier (ascending id), with
+// the sum of the frontier's degrees.
+__global__ void bits_count_kernel(const uint32_t* __restrict__ bits, int64_t words,
+                                  int64_t* __restrict__ cnt) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(bits[w]);
+}
+
+__global__ void bits_write_kernel(const uint32_t* __restrict__ bits, int64_t words,
+                                  const int64_t* __restrict__ pos, const int32_t* __restrict__ deg,
+                                  int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    int64_t dsum = 0;
+    if (w < words) {
+      uint32_t q = bits[w];
+      int64_t at = pos[w];
+      while (q) {
+        const int b = __ffs(q) - 1;
+        q &= q - 1;
+        const int32_t v = (int32_t)(w * 32 + b);
+        if (at < ncap) {
+          nfv[at] = v;
+          nfs[at] = v;
+        } else {
+          atomicOr(&C->err, kErrFrontierOverflow);
+        }
+        at++;
+        dsum += deg[v];
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((threadIdx.x & 31) == 0 && dsum)
+      atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)dsum);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // edgeMap, deterministic mode.
 // ---------------------------------------------------------------------------
 // Emits record e of source i: with a self record, local index 0 is
@@ -604,6 +865,13 @@ struct PushWork {
   DBuf<int64_t> flag, segid, segstart, qflag, qpos;
   DBuf<int32_t> segv, segslot;
   DBuf<int64_t> total;  // one device int64
+  // pull rounds: per-vertex frontier share (membership encoded), qualify bitmap
+  DBuf<double> psh;
+  DBuf<uint32_t> pq;
+  DBuf<int64_t> pcnt;
+  DBuf<double> phacc;              // per heavy vertex: partial sums of its items
+  DBuf<int32_t> phcnt, phtouch;    // per heavy vertex: items done, any frontier neighbour
+  bool pull_ready = false;
   lgc_stats st{};
   explicit PushWork(lgc_ctx* c, lgc_graph* gr) : ctx(c), g(gr) {}
   ~PushWork() {
@@ -625,6 +893,12 @@ struct PushWork {
     segv.release(ctx);
     segslot.release(ctx);
     total.release(ctx);
+    psh.release(ctx);
+    pq.release(ctx);
+    pcnt.release(ctx);
+    phacc.release(ctx);
+    phcnt.release(ctx);
+    phtouch.release(ctx);
   }
 
   int reset_counters() {
@@ -773,6 +1047,67 @@ struct PushWork {
     return read_counters(out);
   }
 
+  // Pull round into the dense table D.  The frontier's shares (share[], from
+  // the vertexMap) are scattered into the per-vertex array, every vertex
+  // gathers (in adjacency order in deterministic mode, heavy vertices by a
+  // tree reduction in atomic mode), the qualifying vertices are compacted in
+  // ascending id, and the per-vertex array is cleared again (O(|F|)).
+  int pull_phase(const Table& D, double c, int fmode, Counters* out, bool det) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n, words = (n + 31) / 32, nf = F.size;
+    if (!pull_ready) {
+      LGC_TRY(psh.reserve(ctx, n));
+      LGC_TRY(pq.reserve(ctx, words));
+      LGC_TRY(pcnt.reserve(ctx, words));
+      LGC_TRY(phacc.reserve(ctx, g->nheavy + 1));
+      LGC_TRY(phcnt.reserve(ctx, g->nheavy + 1));
+      LGC_TRY(phtouch.reserve(ctx, g->nheavy + 1));
+      LGC_CUDA_TRY(cudaMemsetAsync(psh.ptr, 0, 8 * n, s));
+      LGC_CUDA_TRY(cudaMemsetAsync(phacc.ptr, 0, 8 * (g->nheavy + 1), s));
+      LGC_CUDA_TRY(cudaMemsetAsync(phcnt.ptr, 0, 4 * (g->nheavy + 1), s));
+      LGC_CUDA_TRY(cudaMemsetAsync(phtouch.ptr, 0, 4 * (g->nheavy + 1), s));
+      pull_ready = true;
+    }
+    const int32_t ncap = (int32_t)G.v.cap;
+    pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
+    LGC_COUNT_LAUNCH(ctx);
+    {
+      ProfScope ps(ctx, det ? LGC_PROF_DET_EDGE : LGC_PROF_EDGEMAP,
+                   24.0 * (double)F.edges + 24.0 * nf);
+      int lg = grid_for(words * 32);
+      pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
+                                               ctx->d_counters);
+      LGC_COUNT_LAUNCH(ctx);
+      if (g->nheavy > 0 && det) {
+        int64_t hb = ceil_div(g->nheavy, kBlock / 32);
+        pull_heavy_det_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
+            g->off, g->col, g->heavy, g->nheavy, psh.ptr, D, c, fmode, pq.ptr, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      } else if (g->nheavy > 0) {
+        int64_t hb = ceil_div(g->nitems, kBlock / 32);
+        pull_heavy_tree_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
+            g->off, g->col, g->heavy, g->item_h, g->item_beg, g->items_of, g->nitems, psh.ptr, D,
+            c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+    }
+    if (fmode != kFmNone) {
+      bits_count_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_TRY(scan_i64(ctx, pcnt.ptr, pcnt.ptr, words, false, total.ptr));
+      bits_write_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg,
+                                                            G.v.ptr, G.s.ptr, ncap,
+                                                            ctx->d_counters);
+      LGC_COUNT_LAUNCH(ctx);
+      set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 1);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_CUDA_TRY(cudaGetLastError());
+    return read_counters(out);
+  }
+
   int scan_counts(int64_t* nrec_out) {
     LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, F.size, false, total.ptr));
     LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost,
@@ -805,6 +1140,23 @@ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 // more than a constant times the round's own work.
 bool use_bulk(bool det, const Table& D, int64_t round_edges, int64_t n) {
   return !det && D.dense && round_edges >= n / 32;
+}
+
+// Pull rounds: when the frontier's edges are at least 1/16 of the graph's,
+// gathering over every vertex costs no more than a constant times the push
+// it replaces, and it needs neither atomics nor (deterministic mode) records
+// and a sort.  The destination must be (made) dense.
+bool use_pull(const lgc_ctx* ctx, const lgc_graph* g, int64_t round_edges) {
+  if (ctx->table_form == 1 || ctx->pull_policy == 1) return false;
+  if (ctx->pull_policy == 2) return true;
+  return g->n >= 1024 && round_edges >= g->nnz / 16;
+}
+
+// An empty dense table over n vertices (reusing the allocation if it is one).
+int fresh_dense(lgc_ctx* ctx, Table* T, int64_t n) {
+  if (T->dense && T->cap == n && !T->p) return table_clear(ctx, T);
+  table_destroy(ctx, T);
+  return table_create_dense(ctx, T, n, false);
 }
 
 // Before a round that may add up to `add` keys to a persistent table holding
@@ -875,6 +1227,10 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
                                     W.F.size)) != LGC_OK)
         break;
       const int64_t nf = W.F.size;
+      const bool pull = use_pull(ctx, g, W.F.edges);
+      if (pull && !T.dense &&
+          (status = table_to_dense(ctx, &T, g->n, W.F.v.ptr, W.F.s.ptr, nf)) != LGC_OK)
+        break;
       const bool bulk = use_bulk(det, T, W.F.edges, g->n);
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) break;
@@ -883,22 +1239,27 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
         vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
-            (!det && !bulk) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap,
-            ctx->d_counters);
+            (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr,
+            (int32_t)W.G.v.cap, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
       if (cudaGetLastError() != cudaSuccess) {
         status = LGC_ECUDA;
         break;
       }
-      int64_t nrec = W.F.edges;
-      if (det) {
-        if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
-      } else {
-        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
-      }
       Counters C;
-      status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C, bulk);
+      if (pull) {
+        status = W.pull_phase(T, eps, kFmThreshold, &C, det);
+      } else {
+        int64_t nrec = W.F.edges;
+        if (det) {
+          if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+        } else {
+          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+            break;
+        }
+        status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C, bulk);
+      }
       if (status != LGC_OK) break;
       st.rounds++;
       st.pushes += nf;
@@ -957,7 +1318,9 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
       W.record_trace();
       const int64_t nf = W.F.size;
       const int64_t need = min64(g->n, nf + W.F.edges);
-      if ((status = table_fresh(ctx, &Pn, need, g->n, false)) != LGC_OK) break;  // p' = {}
+      const bool pull = use_pull(ctx, g, W.F.edges);
+      status = pull ? fresh_dense(ctx, &Pn, g->n) : table_fresh(ctx, &Pn, need, g->n, false);
+      if (status != LGC_OK) break;  // p' = {}
       const bool bulk = use_bulk(det, Pn, W.F.edges, g->n);
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reserve_next(need)) != LGC_OK) break;
@@ -966,7 +1329,7 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
         vmap_nibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, Pc, Pn, g->off, eps, fmode, det ? 1 : 0,
-            (!det && !bulk) ? 1 : 0, W.share.ptr,
+            (!det && !bulk && !pull) ? 1 : 0, W.share.ptr,
             W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
@@ -974,14 +1337,19 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
         status = LGC_ECUDA;
         break;
       }
-      int64_t nrec = W.F.edges;
-      if (det) {
-        if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
-      } else {
-        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
-      }
       Counters C;
-      status = W.edge_phase(Pn, eps, fmode, det, true, nrec, &C, bulk);
+      if (pull) {
+        status = W.pull_phase(Pn, eps, fmode, &C, det);
+      } else {
+        int64_t nrec = W.F.edges;
+        if (det) {
+          if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+        } else {
+          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+            break;
+        }
+        status = W.edge_phase(Pn, eps, fmode, det, true, nrec, &C, bulk);
+      }
       if (status != LGC_OK) break;
       st.rounds++;
       st.pushes += nf;
@@ -1042,6 +1410,10 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       if ((status = ensure_capacity(ctx, &P, pcount, nf + (last ? W.F.edges : 0), g->n, nullptr,
                                     nullptr, 0)) != LGC_OK)
         break;
+      const bool pull = use_pull(ctx, g, W.F.edges);
+      if (pull && last && !P.dense &&
+          (status = table_to_dense(ctx, &P, g->n, nullptr, nullptr, 0)) != LGC_OK)
+        break;
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
       {
@@ -1055,15 +1427,22 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
         status = LGC_ECUDA;
         break;
       }
-      if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK) break;
+      if (!pull &&
+          (status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+        break;
       Counters C;
       if (!last) {
         const int64_t need = min64(g->n, W.F.edges);
-        if ((status = table_fresh(ctx, &Rn, need, g->n, false)) != LGC_OK) break;  // r' = {}
+        status = pull ? fresh_dense(ctx, &Rn, g->n) : table_fresh(ctx, &Rn, need, g->n, false);
+        if (status != LGC_OK) break;  // r' = {}
         if ((status = W.reserve_next(need)) != LGC_OK) break;
         const double cj = c[j + 1];
-        status = W.edge_phase(Rn, cj, cj > 0.0 ? kFmThreshold : kFmInserted, det, false,
-                              W.F.edges, &C, use_bulk(det, Rn, W.F.edges, g->n));
+        const int fm = cj > 0.0 ? kFmThreshold : kFmInserted;
+        if (pull)
+          status = W.pull_phase(Rn, cj, fm, &C, det);
+        else
+          status = W.edge_phase(Rn, cj, fm, det, false, W.F.edges, &C,
+                                use_bulk(det, Rn, W.F.edges, g->n));
         if (status != LGC_OK) break;
         pcount += C.aux;
         st.rounds++;
@@ -1077,7 +1456,10 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       } else {
         if ((status = W.reserve_next(1)) != LGC_OK) break;
         // no frontier after the last level: fire-and-forget adds in either form
-        status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C, !det);
+        if (pull)
+          status = W.pull_phase(P, 0.0, kFmNone, &C, det);
+        else
+          status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C, !det);
         if (status != LGC_OK) break;
         pcount += C.aux + C.inserted;
         st.rounds++;

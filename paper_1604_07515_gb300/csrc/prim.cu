@@ -263,6 +263,10 @@ int radix_sort_u32_f64(lgc_ctx* ctx, uint32_t* keys, double* vals, uint32_t* key
                        double* vals_tmp, int64_t n, int bits) {
   return radix_sort_impl<uint32_t, double>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
 }
+int radix_sort_u64_f64(lgc_ctx* ctx, uint64_t* keys, double* vals, uint64_t* keys_tmp,
+                       double* vals_tmp, int64_t n, int bits) {
+  return radix_sort_impl<uint64_t, double>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
+}
 int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                        int32_t* vals_tmp, int64_t n, int bits) {
   return radix_sort_impl<uint64_t, int32_t>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);

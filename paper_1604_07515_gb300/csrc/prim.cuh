@@ -17,6 +17,8 @@ int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool incl
 // (the tmp buffers are scratch of the same length).
 int radix_sort_u32_f64(lgc_ctx* ctx, uint32_t* keys, double* vals, uint32_t* keys_tmp,
                        double* vals_tmp, int64_t n, int bits);
+int radix_sort_u64_f64(lgc_ctx* ctx, uint64_t* keys, double* vals, uint64_t* keys_tmp,
+                       double* vals_tmp, int64_t n, int bits);
 int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                        int32_t* vals_tmp, int64_t n, int bits);
 int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,

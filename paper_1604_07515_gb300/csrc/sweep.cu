@@ -55,17 +55,34 @@ __global__ void sweep_keys_kernel(const int32_t* __restrict__ idx, const double*
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(npos, c);
 }
 
+// The rank set: a dense int32 array indexed by vertex id (0 = not in S_N)
+// when the support is a sizeable part of the graph, else a hash table.
 __global__ void rank_insert_kernel(const int32_t* __restrict__ order, int64_t N, Table T,
+                                   int32_t* __restrict__ dense_rank,
                                    const int32_t* __restrict__ deg, int64_t* __restrict__ d_i,
                                    int* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ins = 0;
     const int32_t v = order[i];
-    const int64_t s = ht_find_or_insert(T, v, &ins, err);
-    if (s >= 0) T.s[s].aux = (int32_t)(i + 1);
+    if (dense_rank) {
+      dense_rank[v] = (int32_t)(i + 1);
+    } else {
+      int ins = 0;
+      const int64_t s = ht_find_or_insert(T, v, &ins, err);
+      if (s >= 0) T.s[s].aux = (int32_t)(i + 1);
+    }
     d_i[i] = deg[v];
   }
+}
+
+__device__ inline int64_t rank_of(const Table& T, const int32_t* dense_rank, int32_t w,
+                                  int64_t N) {
+  if (dense_rank) {
+    const int32_t r = dense_rank[w];
+    return r ? r : N + 1;
+  }
+  const int64_t s = ht_find(T, w);
+  return s >= 0 ? T.s[s].aux : N + 1;
 }
 
 __device__ inline int64_t upper_bound_excl(const int64_t* a, int64_t n, int64_t x) {
@@ -84,7 +101,8 @@ __device__ inline int64_t upper_bound_excl(const int64_t* a, int64_t n, int64_t 
 __global__ void __launch_bounds__(kBlock)
     sweep_cross_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                        const int32_t* __restrict__ order, const int64_t* __restrict__ vol,
-                       int64_t N, int64_t V, Table T, int32_t* __restrict__ before) {
+                       int64_t N, int64_t V, Table T, const int32_t* __restrict__ dense_rank,
+                       int32_t* __restrict__ before) {
   __shared__ int64_t s_vol[kTile];  // inclusive vol of the tile's sources
   __shared__ int64_t s_off[kTile];
   __shared__ int32_t s_cnt[kTile];
@@ -117,9 +135,7 @@ __global__ void __launch_bounds__(kBlock)
         if (j >= cnt) continue;
         const int64_t first = j > 0 ? s_vol[j - 1] : (i0 > 0 ? vol[i0 - 1] : 0);
         const int32_t w = col[s_off[j] + (e - first)];
-        const int64_t s = ht_find(T, w);
-        const int64_t rw = s >= 0 ? T.s[s].aux : N + 1;
-        if (rw < i0 + j + 1) atomicAdd(&s_cnt[j], 1);
+        if (rank_of(T, dense_rank, w, N) < i0 + j + 1) atomicAdd(&s_cnt[j], 1);
       }
     }
     __syncthreads();
@@ -222,6 +238,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
   int32_t *id = nullptr, *id2 = nullptr, *before = nullptr;
   int64_t *d_i = nullptr, *vol = nullptr, *delta = nullptr, *misc = nullptr;
   Best *parts = nullptr, *best = nullptr;
+  int32_t* drank = nullptr;
   Table T;
   int status = LGC_OK;
   Best hb{0, 0, -1};
@@ -261,15 +278,22 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
     }
     N = ctx->h_scratch[0];
     if (N == 0) break;
-    // S3, S4
-    if ((status = table_create(ctx, &T, 2 * N, false)) != LGC_OK) break;
+    // S3, S4: ranks in a dense array when the support is a sizeable part of
+    // the graph (one 4-byte read per edge in S5), else in a hash table
+    const bool dense_rank = N >= g->n / 64 && g->n >= 1024;
+    if (dense_rank) {
+      if ((status = dalloc_t(ctx, &drank, g->n)) != LGC_OK) break;
+      LGC_CUDA_TRY(cudaMemsetAsync(drank, 0, 4 * g->n, s));
+    } else if ((status = table_create(ctx, &T, 2 * N, false)) != LGC_OK) {
+      break;
+    }
     if ((status = dalloc_t(ctx, &d_i, N)) != LGC_OK) break;
     if ((status = dalloc_t(ctx, &vol, N)) != LGC_OK) break;
     if ((status = dalloc_t(ctx, &delta, N)) != LGC_OK) break;
     if ((status = dalloc_t(ctx, &before, N)) != LGC_OK) break;
     LGC_CUDA_TRY(cudaMemsetAsync(before, 0, 4 * N, s));
     LGC_CUDA_TRY(cudaMemsetAsync(&ctx->d_counters->err, 0, sizeof(int), s));
-    rank_insert_kernel<<<grid_for(N), kBlock, 0, s>>>(id, N, T, g->deg, d_i,
+    rank_insert_kernel<<<grid_for(N), kBlock, 0, s>>>(id, N, T, drank, g->deg, d_i,
                                                        &ctx->d_counters->err);
     LGC_COUNT_LAUNCH(ctx);
     if ((status = scan_i64(ctx, d_i, vol, N, true, misc + 1)) != LGC_OK) break;
@@ -282,7 +306,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
       int eg = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
       // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
       ProfScope ps(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
-      sweep_cross_kernel<<<eg, kBlock, 0, s>>>(g->off, g->col, id, vol, N, V, T, before);
+      sweep_cross_kernel<<<eg, kBlock, 0, s>>>(g->off, g->col, id, vol, N, V, T, drank, before);
       LGC_COUNT_LAUNCH(ctx);
     }
     sweep_delta_kernel<<<grid_for(N), kBlock, 0, s>>>(d_i, before, N, delta);
@@ -352,6 +376,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
   dfree(ctx, misc);
   dfree(ctx, parts);
   dfree(ctx, best);
+  dfree(ctx, drank);
   table_destroy(ctx, &T);
   return status;
 }

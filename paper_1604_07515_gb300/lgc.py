@@ -118,6 +118,7 @@ SIGNATURES = {
     "lgc_result_free": (None, [POINTER(Result)]),
     "lgc_strerror": (ctypes.c_char_p, [c_int]),
     "lgc_sweep_noalloc": (c_int, [_P, c_int64, _P, _P, _P, POINTER(Cluster)]),
+    "lgc_prnibble_batch": (c_int, [_P, c_int64, _P, _P, _P, _P]),
     "lgc_launch_count": (c_int64, [_P]),
     "lgc_profile_read": (c_int, [_P, c_int, _P]),
     "lgc_profile_reset": (c_int, [_P]),
@@ -454,3 +455,23 @@ def poll(ctx: Context, ticket: int):
                                   if c.size else np.zeros(0, np.int32))}
     load().lgc_result_free(out)
     return res
+
+
+def prnibble_batch(g: Graph, seeds, alpha, eps, rule="opt", mode="atomic", max_rounds=0):
+    """PR-Nibble for many seeds in one batch (lgc_prnibble_batch).  alpha and
+    eps may be scalars or one value per seed.  Returns (list of SparseVec,
+    list of Stats)."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    B = len(seeds)
+    alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (B,))
+    eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (B,))
+    prm = (PRNibbleParams * B)()
+    for b in range(B):
+        prm[b] = PRNibbleParams(float(alpha[b]), float(eps[b]), _RULES[rule], _MODES[mode],
+                                max_rounds)
+    outs = (POINTER(Svec) * B)()
+    sts = (Stats * B)()
+    _check(load().lgc_prnibble_batch(g.handle, B, seeds.ctypes.data, ctypes.addressof(prm),
+                                     ctypes.addressof(outs), ctypes.addressof(sts)),
+           "lgc_prnibble_batch")
+    return [SparseVec(outs[b], g.ctx) for b in range(B)], [sts[b] for b in range(B)]

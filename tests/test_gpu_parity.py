@@ -301,3 +301,60 @@ def test_graph_validation_rejects_bad_csr(ctx):
     for off, col in bad:
         with pytest.raises(lgc.LgcError):
             lgc.Graph(ctx, off, col, validate=True)
+
+
+# ---------------------------------------------------------------------------
+# deterministic pull rounds (every vertex gathers from its in-frontier
+# neighbours in ascending id): forced on every round, they must still be
+# bit-identical to the oracle
+# ---------------------------------------------------------------------------
+OPT_PULL = 7
+
+
+@pytest.mark.parametrize("name", ["paper", "star40", "grid6", "rand500", "rmat10", "rmat13"])
+def test_det_pull_rounds_bitexact(ctx, name):
+    off, col, g = gpu_graph(ctx, name)
+    ctx.set_option(OPT_PULL, 2)
+    try:
+        for x in seeds_for(off, col, 2, salt=3):
+            for rule in ("opt", "orig"):
+                ref = oracle.prnibble(off, col, x, 0.05, 1e-5, rule=1 if rule == "orig" else 0,
+                                      trace=True)
+                p, st = lgc.prnibble(g, x, 0.05, 1e-5, rule=rule, mode="det")
+                assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+                r = ctx.residual()
+                assert np.array_equal(r.idx, ref.idx2) and np.array_equal(r.val, ref.val2)
+                assert_trace_equal(ctx.trace(), ref.trace)
+            ref = oracle.nibble(off, col, x, 10, 1e-4, trace=True)
+            p, st = lgc.nibble(g, x, 10, 1e-4, mode="det")
+            assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+            assert_trace_equal(ctx.trace(), ref.trace)
+            for t, N, eps in [(5.0, 12, 1e-4), (3.0, 5, 0.0)]:
+                ref = oracle.hkpr(off, col, x, t, N, eps, trace=True)
+                p, st = lgc.hkpr(g, x, t, N, eps, mode="det")
+                assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+                assert_trace_equal(ctx.trace(), ref.trace)
+    finally:
+        ctx.set_option(OPT_PULL, 0)
+
+
+@pytest.mark.parametrize("name", ["paper", "star40", "grid6", "rand500", "rmat10", "rmat13"])
+def test_atomic_pull_rounds_within_tolerance(ctx, name):
+    """Atomic mode with every round gathering (heavy vertices reduced by a
+    warp butterfly, so the order of additions differs from the oracle's)."""
+    off, col, g = gpu_graph(ctx, name)
+    ctx.set_option(OPT_PULL, 2)
+    try:
+        for x in seeds_for(off, col, 2, salt=4):
+            ref = oracle.prnibble(off, col, x, 0.05, 1e-5, trace=True)
+            p, st = lgc.prnibble(g, x, 0.05, 1e-5, mode="atomic")
+            assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+            assert [f.tolist() for f in ctx.trace()] == [f.tolist() for f in ref.trace]
+            ref = oracle.nibble(off, col, x, 10, 1e-4)
+            p, st = lgc.nibble(g, x, 10, 1e-4, mode="atomic")
+            assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+            ref = oracle.hkpr(off, col, x, 5.0, 12, 1e-4)
+            p, st = lgc.hkpr(g, x, 5.0, 12, 1e-4, mode="atomic")
+            assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        ctx.set_option(OPT_PULL, 0)
