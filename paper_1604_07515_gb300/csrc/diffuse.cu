@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "fx128.cuh"
 #include "prim.cuh"
 
 namespace lgc {
@@ -548,74 +549,239 @@ __device__ inline void pull_finish(const Table& D, int32_t w, int64_t d, double 
   if (pull_qualifies(acc, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
 }
 
-// Deterministic mode: one warp per heavy vertex; after each batch, lane 0
-// folds the in-frontier shares from shared memory in adjacency order
-// (= ascending source id), starting from the vertex's current value.
+// ---------------------------------------------------------------------------
+// Deterministic mode, heavy vertices: the left fold acc <- RN(acc + s_k) over
+// the in-frontier shares in adjacency order, computed by a warp without a
+// chain of dependent FP64 adds.
+//
+// While acc stays in one binade [2^(bu-1023), 2^(bu-1022)) (bu >= 1; bu = 1
+// also covers zero and the subnormals), acc = A * u with the integer A below
+// 2^53 and u = 2^(bu-1075).  For s >= 0 with s / u = Q + f (0 <= f < 1),
+// RN(acc + s) = (A + Q + [f > 1/2]) * u, except that at f = 1/2 (a tie) the
+// result is the even one of A + Q and A + Q + 1 -- as long as the result is
+// below 2^53 * u.  So each share is a step A -> A + g[A & 1] (g[0] = g[1]
+// unless it is a tie), steps compose into steps of the same form, and a warp
+// scan of the compositions gives every partial fold.  The first position
+// whose value reaches 2^53 leaves the binade: that one add is done in FP64
+// (the rounding of the next binade applies), and the scan restarts after it
+// with the new binade.  Every result equals the sequential fold's bit for
+// bit; the number of FP64 adds per vertex is the number of binades acc
+// passes through.
+// ---------------------------------------------------------------------------
+// Folds the 32 * 8 shares v (lane l holds positions 8l .. 8l+7, in list
+// order) into acc, lane-uniformly.
+__device__ inline double fold_batch(double acc, const double v[8], int lane) {
+  int start = 0;
+  while (start < 256) {
+    const int bu = fold_binade(acc);
+    const int64_t A0 = fold_int(acc);
+    FoldStep st[8];
+    FoldStep F = {0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      st[j] = 8 * lane + j >= start ? fold_step(v[j], bu) : FoldStep{0, 0};
+      F = fold_compose(F, st[j]);
+    }
+    // inclusive scan over lanes, then shift to exclusive
+    FoldStep P = F;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      FoldStep q;
+      q.g0 = __shfl_up_sync(0xffffffffu, P.g0, o);
+      q.g1 = __shfl_up_sync(0xffffffffu, P.g1, o);
+      if (lane >= o) P = fold_compose(q, P);
+    }
+    FoldStep E;
+    E.g0 = __shfl_up_sync(0xffffffffu, P.g0, 1);
+    E.g1 = __shfl_up_sync(0xffffffffu, P.g1, 1);
+    if (lane == 0) E = {0, 0};
+    int64_t A = fold_apply(E, A0);
+    int cj = -1;
+    int64_t before = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int64_t nx = fold_apply(st[j], A);
+      if (cj < 0 && nx >= kFoldTop) {
+        cj = j;
+        before = A;
+      }
+      A = nx;
+    }
+    const unsigned crossed = __ballot_sync(0xffffffffu, cj >= 0);
+    if (!crossed) {
+      const int64_t Aend = __shfl_sync(0xffffffffu, A, 31);
+      return fold_double(Aend, bu);
+    }
+    const int lc = __ffs(crossed) - 1;
+    double nacc = 0.0;
+    if (lane == lc) {
+      double sj = 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        if (j == cj) sj = v[j];
+      nacc = fold_double(before, bu) + sj;  // the add that leaves the binade
+    }
+    acc = __shfl_sync(0xffffffffu, nacc, lc);
+    start = 8 * lc + __shfl_sync(0xffffffffu, cj, lc) + 1;
+  }
+  return acc;
+}
+
 __global__ void __launch_bounds__(kBlock)
     pull_heavy_det_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                           const int32_t* __restrict__ heavy, int64_t nheavy,
                           const double* __restrict__ sh, Table D, double c, int fmode,
                           uint32_t* __restrict__ qbits, Counters* C) {
-  __shared__ double s_val[kBlock / 32][32 * kPullBatch];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t h = warp0; h < nheavy; h += nwarps) {
     const int32_t w = heavy[h];
     const int64_t o0 = off[w], d = off[w + 1] - o0;
     const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
-    double acc = present ? D.dval[w] : 0.0;  // lane 0's running value, >= +0
+    double acc = present ? D.dval[w] : 0.0;  // >= +0
     bool touched = present;
-    for (int64_t k0 = 0; k0 < d; k0 += 32 * kPullBatch) {
-      double s[kPullBatch];
-      unsigned in[kPullBatch];
-      pull_batch(col, o0, k0, d, sh, lane, s, in);
-      int members = 0;
+    for (int64_t k0 = 0; k0 < d; k0 += 256) {
+      int32_t u[8];
 #pragma unroll
-      for (int j = 0; j < kPullBatch; j++) {
-        s_val[wib][32 * j + lane] = s[j];
-        touched = touched || in[j] != 0;
-        members += __popc(in[j]);
+      for (int j = 0; j < 8; j++) {
+        const int64_t k = k0 + 8 * lane + j;
+        u[j] = k < d ? col[o0 + k] : -1;
       }
-      __syncwarp();
-      if (lane == 0) {
-        if (members >= 64) {
-          // dense batch: add every slot in order; a non-member's +0.0 (or a
-          // member's -0.0) leaves a non-negative sum unchanged
-#pragma unroll 16
-          for (int t = 0; t < 32 * kPullBatch; t++) acc = acc + s_val[wib][t];
-        } else {
+      double v[8];
+      bool mem = false;
 #pragma unroll
-          for (int j = 0; j < kPullBatch; j++) {
-            unsigned mask = in[j];
-            while (mask) {
-              const int l = __ffs(mask) - 1;
-              mask &= mask - 1;
-              acc = acc + s_val[wib][32 * j + l];
-            }
-          }
-        }
+      for (int j = 0; j < 8; j++) {
+        v[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
+        mem = mem || pull_member(v[j]);
       }
-      __syncwarp();
+      const unsigned any = __ballot_sync(0xffffffffu, mem);
+      if (!any) continue;
+      touched = true;
+      acc = fold_batch(acc, v, lane);
     }
     if (lane == 0) pull_finish(D, w, d, acc, touched, present, c, fmode, qbits, C);
   }
 }
 
-// Atomic mode: one warp per work item (at most kPullItem edges of one heavy
-// vertex).  Lanes sum strided parts and the warp reduces by a butterfly.  A
-// vertex with one item is finished at once; otherwise the partial sums are
-// added into hacc[h] and the warp that completes the vertex's last item
-// finishes it (and resets the vertex's accumulators for the next round).
+// ---------------------------------------------------------------------------
+// Pull edgeMap, atomic mode.  The order of the adds is free, so the gather
+// sums in 128-bit fixed point (fx128.cuh) instead of FP64: per edge one
+// 16-byte load and four integer adds, and per vertex one rounding.  The
+// round's scale L comes from the range of the frontier's shares:
+// range[0] = max over nonzero shares of (2047 - biased exponent),
+// range[1] = max biased exponent (both 0 before the round).
+// shx[v] = {X, flag} for a frontier vertex v, {0, 0} otherwise.
+// ---------------------------------------------------------------------------
+__global__ void share_range_kernel(int64_t nf, const double* __restrict__ share,
+                                   int32_t* __restrict__ range) {
+  int emin = 0, emax = 0;  // emin holds 2047 - be
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(share[i]) & kFxMask;
+    if (b) {
+      const int be = fx_bexp(b);
+      emin = max(emin, 2047 - be);
+      emax = max(emax, be);
+    }
+  }
+  emin = __reduce_max_sync(0xffffffffu, emin);
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if ((threadIdx.x & 31) == 0 && (emin | emax)) {
+    atomicMax(&range[0], emin);
+    atomicMax(&range[1], emax);
+  }
+}
+
+__device__ inline int round_scale(const int32_t* range, int g) {
+  return fx_scale(2047 - range[0], range[1], g);
+}
+
+__global__ void pull_scatter_fx_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                       const double* __restrict__ share, Fx* __restrict__ shx,
+                                       const int32_t* __restrict__ range, int g, int clear) {
+  const int L = clear ? 0 : round_scale(range, g);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    Fx x = {0, 0};
+    if (!clear) {
+      x = fx_from_double(share[i], L);
+      x.hi |= kFxFlag;
+    }
+    shx[fv[i]] = x;
+  }
+}
+
+// Vertices of degree 1..kPullLight, one thread each, their edges read four
+// at a time (all column loads, then all share loads).  Every bitmap word of
+// qbits is written here (by ballot, heavy vertices' bits zero); the heavy
+// kernel, launched after this one, ORs its vertices in.
+__global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
+                                     const int32_t* __restrict__ col, int64_t n,
+                                     const Fx* __restrict__ shx,
+                                     const int32_t* __restrict__ range, int g, Table D, double c,
+                                     int fmode, uint32_t* __restrict__ qbits, Counters* C) {
+  const int L = round_scale(range, g);
+  const int64_t words = (n + 31) / 32;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words * 32;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    bool q = false;
+    int ins = 0;
+    if (w < n) {
+      const int64_t o0 = off[w], d = off[w + 1] - o0;
+      if (d >= 1 && d <= kPullLight) {
+        Fx acc = {0, 0};
+        uint64_t flag = 0;
+        for (int64_t k = 0; k < d; k += 4) {
+          int32_t u[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            if (u[j] >= 0) {
+              const Fx x = shx[u[j]];
+              flag |= x.hi;
+              fx_add(acc, x);
+            }
+          }
+        }
+        const uint32_t m = 1u << (w & 31);
+        const bool present = (D.bits[w >> 5] & m) != 0;
+        if (present || (flag & kFxFlag)) {
+          const double v = (present ? D.dval[w] : 0.0) + fx_to_double(acc, L);
+          D.dval[w] = v;
+          if (!present) {
+            atomicOr(&D.bits[w >> 5], m);
+            ins = 1;
+          }
+          q = pull_qualifies(v, d, c, fmode);
+        }
+      }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, q);
+    if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
+      qbits[(base + threadIdx.x) >> 5] = word;
+    count_inserted(ins, &C->inserted);
+  }
+}
+
+// Heavy vertices: one warp per work item (at most kPullItem edges of one
+// heavy vertex); lanes sum strided parts, then a butterfly.  A vertex with
+// one item is finished at once; otherwise the item's sum is added into
+// hacc[h] (two 64-bit atomic adds, the carry of the low word taken from its
+// returned old value) and the warp that completes the vertex's last item
+// finishes it and resets the accumulators for the next round.
 __global__ void __launch_bounds__(kBlock)
-    pull_heavy_tree_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ heavy, const int32_t* __restrict__ item_h,
-                           const int64_t* __restrict__ item_beg,
-                           const int32_t* __restrict__ items_of, int64_t nitems,
-                           const double* __restrict__ sh,
-                           Table D, double c, int fmode, uint32_t* __restrict__ qbits,
-                           double* __restrict__ hacc, int32_t* __restrict__ hcnt,
-                           int32_t* __restrict__ htouch, Counters* C) {
+    pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                         const int32_t* __restrict__ heavy, const int32_t* __restrict__ item_h,
+                         const int64_t* __restrict__ item_beg,
+                         const int32_t* __restrict__ items_of, int64_t nitems,
+                         const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
+                         Table D, double c, int fmode, uint32_t* __restrict__ qbits,
+                         Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
+                         int32_t* __restrict__ htouch, Counters* C) {
+  const int L = round_scale(range, g);
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -625,36 +791,64 @@ __global__ void __launch_bounds__(kBlock)
     const int64_t o0 = off[w], d = off[w + 1] - o0;
     const int64_t k_beg = item_beg[it] - o0;
     const int64_t k_end = min(d, k_beg + kPullItem);
-    double part = 0.0;
-    bool any = false;
+    Fx part = {0, 0};
+    uint64_t flag = 0;
     for (int64_t k0 = k_beg; k0 < k_end; k0 += 32 * kPullBatch) {
-      double s[kPullBatch];
-      unsigned in[kPullBatch];
-      pull_batch(col, o0, k0, k_end, sh, lane, s, in);
+      int32_t u[kPullBatch];
 #pragma unroll
       for (int j = 0; j < kPullBatch; j++) {
-        part = part + s[j];
-        any = any || in[j] != 0;
+        const int64_t k = k0 + 32 * j + lane;
+        u[j] = k < k_end ? col[o0 + k] : -1;
+      }
+      Fx x[kPullBatch];
+#pragma unroll
+      for (int j = 0; j < kPullBatch; j++) {
+        x[j].lo = 0;
+        x[j].hi = 0;
+        if (u[j] >= 0) x[j] = shx[u[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < kPullBatch; j++) {
+        flag |= x[j].hi;
+        fx_add(part, x[j]);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) part = part + __shfl_xor_sync(0xffffffffu, part, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      Fx t;
+      t.lo = __shfl_xor_sync(0xffffffffu, part.lo, o);
+      t.hi = __shfl_xor_sync(0xffffffffu, part.hi, o);
+      fx_add(part, t);
+    }
+    const bool any = __any_sync(0xffffffffu, (flag & kFxFlag) != 0);
     if (lane != 0) continue;
     const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
     if (items_of[h] == 1) {
-      const double base = present ? D.dval[w] : 0.0;
-      pull_finish(D, w, d, base + part, present || any, present, c, fmode, qbits, C);
+      if (present || any) {
+        const double base = present ? D.dval[w] : 0.0;
+        pull_finish(D, w, d, base + fx_to_double(part, L), true, present, c, fmode, qbits, C);
+      }
       continue;
     }
-    if (part != 0.0) atomicAdd(&hacc[h], part);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(&hacc[h]);
+    if (part.lo | part.hi) {
+      const unsigned long long old = atomicAdd(&acc[0], (unsigned long long)part.lo);
+      const unsigned long long carry = old + part.lo < old ? 1ull : 0ull;
+      atomicAdd(&acc[1], (unsigned long long)part.hi + carry);
+    }
     if (any) atomicOr(&htouch[h], 1);
     __threadfence();
     if (atomicAdd(&hcnt[h], 1) == items_of[h] - 1) {
       __threadfence();
-      const double total = atomicAdd(&hacc[h], 0.0);
-      const bool touched = present || atomicOr(&htouch[h], 0) != 0;
-      const double base = present ? D.dval[w] : 0.0;
-      pull_finish(D, w, d, base + total, touched, present, c, fmode, qbits, C);
-      hacc[h] = 0.0;
+      Fx total;
+      total.lo = atomicAdd(&acc[0], 0ull);
+      total.hi = atomicAdd(&acc[1], 0ull);
+      if (present || atomicOr(&htouch[h], 0) != 0) {
+        const double base = present ? D.dval[w] : 0.0;
+        pull_finish(D, w, d, base + fx_to_double(total, L), true, present, c, fmode, qbits,
+                    C);
+      }
+      acc[0] = 0;
+      acc[1] = 0;
       hcnt[h] = 0;
       htouch[h] = 0;
     }
@@ -869,7 +1063,9 @@ struct PushWork {
   DBuf<double> psh;
   DBuf<uint32_t> pq;
   DBuf<int64_t> pcnt;
-  DBuf<double> phacc;              // per heavy vertex: partial sums of its items
+  DBuf<Fx> pshx;                   // atomic mode: per-vertex fixed-point shares
+  DBuf<int32_t> prange;            // atomic mode: exponent range of the shares
+  DBuf<Fx> phacc;                  // per heavy vertex: partial sums of its items
   DBuf<int32_t> phcnt, phtouch;    // per heavy vertex: items done, any frontier neighbour
   bool pull_ready = false;
   lgc_stats st{};
@@ -894,6 +1090,8 @@ struct PushWork {
     segslot.release(ctx);
     total.release(ctx);
     psh.release(ctx);
+    pshx.release(ctx);
+    prange.release(ctx);
     pq.release(ctx);
     pcnt.release(ctx);
     phacc.release(ctx);
@@ -1056,27 +1254,51 @@ struct PushWork {
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n, words = (n + 31) / 32, nf = F.size;
     if (!pull_ready) {
-      LGC_TRY(psh.reserve(ctx, n));
       LGC_TRY(pq.reserve(ctx, words));
       LGC_TRY(pcnt.reserve(ctx, words));
+      pull_ready = true;
+    }
+    if (det && !psh.ptr) {
+      LGC_TRY(psh.reserve(ctx, n));
+      LGC_CUDA_TRY(cudaMemsetAsync(psh.ptr, 0, 8 * n, s));
+    }
+    if (!det && !pshx.ptr) {
+      LGC_TRY(pshx.reserve(ctx, n));
+      LGC_TRY(prange.reserve(ctx, 2));
       LGC_TRY(phacc.reserve(ctx, g->nheavy + 1));
       LGC_TRY(phcnt.reserve(ctx, g->nheavy + 1));
       LGC_TRY(phtouch.reserve(ctx, g->nheavy + 1));
-      LGC_CUDA_TRY(cudaMemsetAsync(psh.ptr, 0, 8 * n, s));
-      LGC_CUDA_TRY(cudaMemsetAsync(phacc.ptr, 0, 8 * (g->nheavy + 1), s));
+      LGC_CUDA_TRY(cudaMemsetAsync(pshx.ptr, 0, sizeof(Fx) * n, s));
+      LGC_CUDA_TRY(cudaMemsetAsync(phacc.ptr, 0, sizeof(Fx) * (g->nheavy + 1), s));
       LGC_CUDA_TRY(cudaMemsetAsync(phcnt.ptr, 0, 4 * (g->nheavy + 1), s));
       LGC_CUDA_TRY(cudaMemsetAsync(phtouch.ptr, 0, 4 * (g->nheavy + 1), s));
-      pull_ready = true;
     }
     const int32_t ncap = (int32_t)G.v.cap;
-    pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
-    LGC_COUNT_LAUNCH(ctx);
+    // sums of at most max_deg terms: max_deg < 2^gb
+    int gb = 1;
+    while (gb < 62 && (int64_t{1} << gb) <= g->max_deg) gb++;
+    if (det) {
+      pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
+      LGC_COUNT_LAUNCH(ctx);
+    } else {
+      LGC_CUDA_TRY(cudaMemsetAsync(prange.ptr, 0, 8, s));
+      share_range_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, share.ptr, prange.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
+                                                              prange.ptr, gb, 0);
+      LGC_COUNT_LAUNCH(ctx);
+    }
     {
       ProfScope ps(ctx, det ? LGC_PROF_DET_EDGE : LGC_PROF_EDGEMAP,
                    24.0 * (double)F.edges + 24.0 * nf);
       int lg = grid_for(words * 32);
-      pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
-                                               ctx->d_counters);
+      if (det) {
+        pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
+                                                 ctx->d_counters);
+      } else {
+        pull_light_fx_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, pshx.ptr, prange.ptr, gb,
+                                                    D, c, fmode, pq.ptr, ctx->d_counters);
+      }
       LGC_COUNT_LAUNCH(ctx);
       if (g->nheavy > 0 && det) {
         int64_t hb = ceil_div(g->nheavy, kBlock / 32);
@@ -1085,9 +1307,10 @@ struct PushWork {
         LGC_COUNT_LAUNCH(ctx);
       } else if (g->nheavy > 0) {
         int64_t hb = ceil_div(g->nitems, kBlock / 32);
-        pull_heavy_tree_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
-            g->off, g->col, g->heavy, g->item_h, g->item_beg, g->items_of, g->nitems, psh.ptr, D,
-            c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr, ctx->d_counters);
+        pull_heavy_fx_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
+            g->off, g->col, g->heavy, g->item_h, g->item_beg, g->items_of, g->nitems, pshx.ptr,
+            prange.ptr, gb, D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
+            ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
     }
@@ -1102,7 +1325,12 @@ struct PushWork {
       set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
       LGC_COUNT_LAUNCH(ctx);
     }
-    pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 1);
+    if (det) {
+      pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 1);
+    } else {
+      pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
+                                                              prange.ptr, gb, 1);
+    }
     LGC_COUNT_LAUNCH(ctx);
     LGC_CUDA_TRY(cudaGetLastError());
     return read_counters(out);
