@@ -123,30 +123,187 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def one_step(lgc, g, x):
-    """The hot path for one seed; returns (pushed_edges, clusters, d2h_bytes)."""
+ALGOS = ("prnibble", "nibble", "hkpr", "rand_hkpr")
+
+
+def run_algo(lgc, g, x, name):
+    if name == "prnibble":
+        return lgc.prnibble(g, x, PR["alpha"], PR["eps"], mode=MODE)
+    if name == "nibble":
+        return lgc.nibble(g, x, NB["T"], NB["eps"], mode=MODE)
+    if name == "hkpr":
+        return lgc.hkpr(g, x, HK["t"], HK["N"], HK["eps"], mode=MODE)
+    return lgc.rand_hkpr(g, x, RH["t"], RH["K"], RH["n_walks"], RH["rng_seed"])
+
+
+def one_step(lgc, g, x, events=None):
+    """The hot path for one seed; returns (pushed_edges, clusters, d2h_bytes).
+    With `events` (a list), records one CUDA event before each diffusion and
+    one at the end, for the per-diffusion split."""
+    import torch
     pushed, clusters, d2h = 0, 0, 0
-    p, st = lgc.prnibble(g, x, PR["alpha"], PR["eps"], mode=MODE)
-    c = lgc.sweep(g, p)
-    pushed += st.pushed_edges
-    clusters += 1
-    d2h += 0 if p.on_device else 12 * p.nnz + 4 * c.size
-    p, st = lgc.nibble(g, x, NB["T"], NB["eps"], mode=MODE)
-    c = lgc.sweep(g, p)
-    pushed += st.pushed_edges
-    clusters += 1
-    d2h += 0 if p.on_device else 12 * p.nnz + 4 * c.size
-    p, st = lgc.hkpr(g, x, HK["t"], HK["N"], HK["eps"], mode=MODE)
-    c = lgc.sweep(g, p)
-    pushed += st.pushed_edges
-    clusters += 1
-    d2h += 0 if p.on_device else 12 * p.nnz + 4 * c.size
-    p, st = lgc.rand_hkpr(g, x, RH["t"], RH["K"], RH["n_walks"], RH["rng_seed"])
-    c = lgc.sweep(g, p)
-    pushed += st.pushed_edges
-    clusters += 1
-    d2h += 0 if p.on_device else 12 * p.nnz + 4 * c.size
+    per = []
+    for name in STEP_ALGOS:
+        if events is not None:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(torch.cuda.current_stream())
+            events.append(ev)
+        p, st = run_algo(lgc, g, x, name)
+        c = lgc.sweep(g, p)
+        pushed += st.pushed_edges
+        per.append(st.pushed_edges)
+        clusters += 1
+        d2h += 0 if p.on_device else 12 * p.nnz + 4 * c.size
+    if events is not None:
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(torch.cuda.current_stream())
+        events.append(ev)
+        events.append(per)
     return pushed, clusters, d2h
+
+
+# ---------------------------------------------------------------------------
+# Batched vs one seed per call (PR-Nibble + sweep), and the request loop.
+# Both on R-MAT scale 24 (16.8M vertices, edge factor 16, seed 4) with seeds
+# drawn uniformly among degree >= 2 vertices; the serving mix follows the
+# paper's serving-style use (many local clusterings on one resident graph).
+# ---------------------------------------------------------------------------
+MANY = dict(scale=24, graph_seed=4, seeds=1024, seed_stream=4, alpha=0.01, eps_lo=-8.0,
+            eps_hi=-5.0, chunk=256)
+SERVE = dict(rates=(50, 100, 1000, 5000, 10000, 20000, 50000), requests=1000, offered_s=4.0,
+             arrival_seed=5,
+             hk_eps=1e-7, mem_budget=40 << 30, max_batch=32)
+
+
+def hk_terms(t, eps):
+    """Taylor degree N for serving HK-PR: the smallest N whose Poisson(t)
+    tail P(k > N) is at most eps, capped at ceil(2 t ln(1/eps))."""
+    import math
+    cap = math.ceil(2.0 * t * math.log(1.0 / eps))
+    term = math.exp(-t)
+    cdf = term
+    k = 0
+    while 1.0 - cdf > eps and k < cap:
+        k += 1
+        term *= t / k
+        cdf += term
+    return max(1, min(k, cap))
+
+
+def measure_many(lgc, inputs, torch, ctx, g, off):
+    """1024 PR-Nibble + sweep clusters, once through lgc_prnibble_batch (in
+    chunks) and once one seed per call; device-resident results."""
+    seeds = inputs.seeds_deg2(off, MANY["seeds"], MANY["seed_stream"])
+    eps = inputs.eps_loguniform(MANY["seeds"], MANY["seed_stream"], MANY["eps_lo"], MANY["eps_hi"])
+    a = MANY["alpha"]
+    ch = MANY["chunk"]
+    # warm-up of both paths
+    ps, _ = lgc.prnibble_batch(g, seeds[:8], a, eps[:8], mode=MODE)
+    for p in ps:
+        lgc.sweep(g, p)
+    p, _ = lgc.prnibble(g, int(seeds[0]), a, float(eps[0]), mode=MODE)
+    lgc.sweep(g, p)
+    torch.cuda.synchronize()
+
+    t0 = time.perf_counter()
+    e_b = 0
+    for i in range(0, len(seeds), ch):
+        ps, sts = lgc.prnibble_batch(g, seeds[i:i + ch], a, eps[i:i + ch], mode=MODE)
+        for p in ps:
+            lgc.sweep(g, p)
+        e_b += sum(st.pushed_edges for st in sts)
+        del ps
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    e_s = 0
+    for b in range(len(seeds)):
+        p, st = lgc.prnibble(g, int(seeds[b]), a, float(eps[b]), mode=MODE)
+        lgc.sweep(g, p)
+        e_s += st.pushed_edges
+        del p
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    B = len(seeds)
+    return {"workload": (f"R-MAT scale {MANY['scale']} (seed {MANY['graph_seed']}), {B} PR-Nibble "
+                         f"seeds (degree >= 2, stream {MANY['seed_stream']}), alpha {a}, eps "
+                         f"log-uniform [1e{int(MANY['eps_lo'])}, 1e{int(MANY['eps_hi'])}], + sweep "
+                         f"each; batched in chunks of {ch}"),
+            "clusters": B, "pushed_edges": e_b,
+            "batched": {"clusters_per_s": B / tb, "edges_per_s": e_b / tb, "s": tb},
+            "per_seed": {"clusters_per_s": B / ts, "edges_per_s": e_s / ts, "s": ts},
+            "speedup": ts / tb}
+
+
+def measure_serving(lgc, inputs, torch, ctx, g, off):
+    """Open-loop Poisson arrivals through lgc_submit / lgc_poll: 80% PR-Nibble
+    (alpha 0.01, eps log-uniform [1e-8, 1e-5]), 20% HK-PR (t log-uniform
+    [3, 30], eps 1e-7), each with its sweep; latency = completion - submission
+    (library clock)."""
+    import numpy as np
+    R = SERVE["requests"]
+    seeds = inputs.seeds_deg2(off, R, 5)
+    eps = inputs.eps_loguniform(R, 5, -8.0, -5.0)
+    ts = 10.0 ** (np.log10(3.0) + (np.log10(30.0) - np.log10(3.0)) * inputs.uniform(6, R))
+    kinds = inputs.uniform(7, R) < 0.8
+    reqs = []
+    for i in range(R):
+        if kinds[i]:
+            reqs.append(lgc.make_request(lgc.ALGO_PRNIBBLE, int(seeds[i]), True, alpha=0.01,
+                                         eps=float(eps[i]), mode=MODE))
+        else:
+            t = float(ts[i])
+            reqs.append(lgc.make_request(lgc.ALGO_HKPR, int(seeds[i]), True, t=t,
+                                         N=hk_terms(t, SERVE["hk_eps"]), eps=SERVE["hk_eps"],
+                                         mode=MODE))
+    ctx.set_option(lgc.OPT_SERVE_MEM_BUDGET, SERVE["mem_budget"])
+    ctx.set_option(lgc.OPT_SERVE_MAX_BATCH, SERVE["max_batch"])
+    # warm the workers
+    for tk in [lgc.submit(ctx, g, reqs[i]) for i in range(8)]:
+        while lgc.poll(ctx, tk) is None:
+            time.sleep(0.0005)
+    out = []
+    for rate in SERVE["rates"]:
+        # the first R requests of the mix; fewer at rates below capacity so
+        # that the offered load lasts about offered_s seconds
+        R = min(SERVE["requests"], max(50, int(SERVE["offered_s"] * rate)))
+        gaps = -np.log(1.0 - inputs.uniform(SERVE["arrival_seed"] + rate, R)) / rate
+        arrive = np.cumsum(gaps)
+        pending, lat, done_edges = [], [], 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < R or pending:
+            now = time.perf_counter() - t0
+            while i < R and arrive[i] <= now:
+                pending.append(lgc.submit(ctx, g, reqs[i]))
+                i += 1
+            still = []
+            for tk in pending:
+                r = lgc.poll(ctx, tk)
+                if r is None:
+                    still.append(tk)
+                else:
+                    lat.append(r["end_s"] - r["submit_s"])
+                    done_edges += r["stats"]["pushed_edges"]
+            pending = still
+            if i < R and not pending:
+                time.sleep(max(0.0, min(arrive[i] - (time.perf_counter() - t0), 0.001)))
+        wall = time.perf_counter() - t0
+        lat_ms = np.sort(np.asarray(lat)) * 1e3
+        out.append({"rate_per_s": rate, "requests": R, "clusters_per_s": R / wall,
+                    "edges_per_s": done_edges / wall,
+                    "p50_ms": float(np.percentile(lat_ms, 50)),
+                    "p99_ms": float(np.percentile(lat_ms, 99)),
+                    "offered_s": float(arrive[-1]), "wall_s": wall})
+    return {"workload": (f"R-MAT scale {MANY['scale']} (seed {MANY['graph_seed']}); Poisson "
+                         f"arrivals (seed {SERVE['arrival_seed']}), up to {SERVE['requests']} requests "
+                         f"per rate ({SERVE['offered_s']:.0f} s of offered load at low rates): 80% "
+                         "PR-Nibble alpha 0.01 eps log-uniform [1e-8, 1e-5], 20% HK-PR t "
+                         "log-uniform [3, 30] eps 1e-7 (N from the Poisson tail); sweep each; "
+                         f"memory budget {SERVE['mem_budget'] >> 30} GB, "
+                         f"{SERVE['max_batch']} resident"),
+            "rates": out}
 
 
 # bytes of the per-step inputs handed to the library (seed + parameter structs)
@@ -208,9 +365,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="atomic", choices=["atomic", "det"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-many", action="store_true",
+                    help="skip the batched-vs-per-seed and serving measurements")
+    ap.add_argument("--algos", default=",".join(ALGOS),
+                    help="comma-separated subset of the step (for profiling one diffusion)")
     args = ap.parse_args()
-    global MODE
+    global MODE, STEP_ALGOS
     MODE = args.mode
+    STEP_ALGOS = tuple(a for a in args.algos.split(",") if a)
+    if not STEP_ALGOS or any(a not in ALGOS for a in STEP_ALGOS):
+        ap.error(f"--algos takes a subset of {','.join(ALGOS)}")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -247,16 +411,21 @@ def main():
     clocks.start()
     launches0 = ctx.launch_count()
     step_ms, pushed, clusters = [], 0, 0
+    split = {a: {"ms": 0.0, "edges": 0} for a in STEP_ALGOS}
     for _ in range(args.steps):
         flush.fill_(1)  # evict L2 between timed steps (not timed)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        evs = []
         a.record(stream)
-        pe, cl, _ = one_step(lgc, g, x)
+        pe, cl, _ = one_step(lgc, g, x, evs)
         b.record(stream)
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
         pushed += pe
         clusters += cl
+        for i, name in enumerate(STEP_ALGOS):
+            split[name]["ms"] += evs[i].elapsed_time(evs[i + 1]) / args.steps
+            split[name]["edges"] += evs[-1][i] // args.steps
     barrier()
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
@@ -282,6 +451,20 @@ def main():
         d2h += db
     (e2e_s,), (e_pushed,) = reduce_ranks([e2e_s], [e_pushed], world, "cuda")
     e2e_value = e_pushed / e2e_s
+
+    # ---- batched vs per-seed, and serving (rank 0, one GPU) ----
+    many = serving = None
+    if rank == 0 and world == 1 and not args.no_many:
+        g.close()
+        del flush
+        offm, colm = inputs.rmat(MANY["scale"], seed=MANY["graph_seed"])
+        gm = lgc.Graph(ctx, offm, colm)
+        del colm
+        ctx.set_option(lgc.OPT_RESULT_ON_DEVICE, 1)
+        many = measure_many(lgc, inputs, torch, ctx, gm, offm)
+        ctx.set_option(lgc.OPT_RESULT_ON_DEVICE, 0)
+        serving = measure_serving(lgc, inputs, torch, ctx, gm, offm)
+        gm.close()
 
     # ---- roofline of the dominant kernel ----
     peaks = {}
@@ -321,17 +504,22 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": MODE,
+            "config": {"workload": WORKLOAD if STEP_ALGOS == ALGOS
+                       else WORKLOAD + f" (only: {','.join(STEP_ALGOS)})", "mode": MODE,
                        "l2": "inputs larger than L2 and L2 flushed between steps",
                        "parallelism": f"replicas{world}"},
             "clusters_per_s": clusters / (total_ms / 1e3),
             "pushed_edges_per_step": pushed / args.steps / max(1, world),
             "roofline": roofline, "kernels": prof,
+            "per_diffusion": {k: {"ms": v["ms"], "edges": v["edges"],
+                                  "edges_per_s": v["edges"] / (v["ms"] / 1e3) if v["ms"] else None}
+                              for k, v in split.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "edges/s",
                     "h2d_bytes_per_step": H2D_BYTES_PER_STEP,
                     "d2h_bytes_per_step": d2h // max(1, args.steps)},
             "clocks": clk, "gpu_launches": launches,
+            "many_seeds": many, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     g.close()
@@ -342,6 +530,7 @@ def main():
 
 
 MODE = "atomic"
+STEP_ALGOS = ALGOS
 
 if __name__ == "__main__":
     sys.exit(main())

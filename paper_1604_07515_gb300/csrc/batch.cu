@@ -392,6 +392,234 @@ __global__ void gather_degrees_kernel(int64_t B, const int32_t* __restrict__ see
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Table storage for the batch: the tables created or grown in one step share
+// one device allocation (a slab), cleared by one memset; a slab is freed when
+// none of its tables is in use any more.  Growing many seeds' tables is one
+// rehash launch over all their old slots; the results of all seeds are
+// extracted, sorted and copied out together.
+// ---------------------------------------------------------------------------
+struct Slabs {
+  std::vector<void*> ptr;
+  std::vector<int64_t> refs;
+  void release(lgc_ctx* ctx, int id) {
+    if (id >= 0 && --refs[id] == 0) {
+      dfree(ctx, ptr[id]);
+      ptr[id] = nullptr;
+    }
+  }
+  void release_all(lgc_ctx* ctx) {
+    for (size_t i = 0; i < ptr.size(); i++)
+      if (ptr[i]) dfree(ctx, ptr[i]);
+    ptr.clear();
+    refs.clear();
+  }
+};
+
+int64_t table_bytes(int64_t cap) { return ceil_div(cap * (int64_t)(sizeof(Slot) + 8), 256) * 256; }
+
+int64_t pow2_cap(int64_t min_cap) { return pow2_at_least(min_cap < 64 ? 64 : min_cap); }
+
+// Hashed tables (slots + p) of the given capacities (powers of two >= 64)
+// for seeds `which`, carved from one new cleared slab.
+int carve_tables(lgc_ctx* ctx, Slabs* S, const std::vector<int64_t>& which,
+                 const std::vector<int64_t>& caps, std::vector<Table>* tabs,
+                 std::vector<int>* slab_of) {
+  if (which.empty()) return LGC_OK;
+  int64_t bytes = 0;
+  for (int64_t c : caps) {
+    if (c > (int64_t{1} << 31)) return LGC_EINVAL;  // 32-bit slot hashes
+    bytes += table_bytes(c);
+  }
+  char* base = nullptr;
+  LGC_TRY(dalloc_t(ctx, &base, (size_t)bytes));
+  LGC_CUDA_TRY(cudaMemsetAsync(base, 0, (size_t)bytes, ctx->stream));
+  S->ptr.push_back(base);
+  S->refs.push_back((int64_t)which.size());
+  const int id = (int)S->ptr.size() - 1;
+  int64_t at = 0;
+  for (size_t k = 0; k < which.size(); k++) {
+    const int64_t cap = caps[k];
+    int lg = 0;
+    while (((int64_t)1 << lg) < cap) lg++;
+    Table T;
+    T.cap = cap;
+    T.shift = 32 - lg;
+    T.s = reinterpret_cast<Slot*>(base + at);
+    T.p = reinterpret_cast<double*>(base + at + cap * (int64_t)sizeof(Slot));
+    at += table_bytes(cap);
+    (*tabs)[which[k]] = T;
+    (*slab_of)[which[k]] = id;
+  }
+  return LGC_OK;
+}
+
+struct Regrow {
+  Table from, to;
+};
+
+// Re-inserts every key of the old tables rg[k].from into rg[k].to; old slot
+// i of table k is virtual slot beg[k] + i.
+__global__ void batch_rehash_kernel(const Regrow* __restrict__ rg,
+                                    const int64_t* __restrict__ beg, int64_t ng, int64_t total,
+                                    int* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = ub_i64(beg, ng, i) - 1;
+    const Table from = rg[k].from, to = rg[k].to;
+    const int64_t j = i - beg[k];
+    const Slot s = from.s[j];
+    if (s.key == 0) continue;
+    int ins = 0;
+    const int64_t q = ht_find_or_insert(to, s.key - 1, &ins, err);
+    if (q < 0) continue;
+    to.s[q].aux = s.aux;
+    to.s[q].val = s.val;
+    to.p[q] = from.p[j];
+  }
+}
+
+// Virtual slot i of the whole batch is slot i - capoff[b] of seed b's table.
+__global__ void batch_keep_kernel(const Table* __restrict__ tabs,
+                                  const int64_t* __restrict__ capoff, int64_t B, int64_t total,
+                                  int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = ub_i64(capoff, B, i) - 1;
+    const int64_t j = i - capoff[b];
+    const Table T = tabs[b];
+    flag[i] = (T.s[j].key != 0 && T.p[j] > 0.0) ? 1 : 0;
+  }
+}
+
+__global__ void batch_gather_kernel(const Table* __restrict__ tabs,
+                                    const int64_t* __restrict__ capoff, int64_t B, int64_t total,
+                                    const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                                    int vbits, uint64_t* __restrict__ key, double* __restrict__ val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    const int64_t b = ub_i64(capoff, B, i) - 1;
+    const int64_t j = i - capoff[b];
+    const Table T = tabs[b];
+    key[pos[i]] = ((uint64_t)b << vbits) | (uint64_t)(T.s[j].key - 1);
+    val[pos[i]] = T.p[j];
+  }
+}
+
+// Per-seed output ranges: start[b] = pos[capoff[b]] (start[B] = total kept),
+// and the vertex ids without the seed bits.
+__global__ void batch_bounds_kernel(const int64_t* __restrict__ capoff, int64_t B,
+                                    const int64_t* __restrict__ pos, const int64_t* __restrict__ kept,
+                                    int64_t* __restrict__ start) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
+       b += (int64_t)gridDim.x * blockDim.x)
+    start[b] = b == B ? *kept : pos[capoff[b]];
+}
+
+__global__ void batch_ids_kernel(const uint64_t* __restrict__ key, int64_t m, int vbits,
+                                 int32_t* __restrict__ idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    idx[i] = (int32_t)(key[i] & ((1ull << vbits) - 1));
+}
+
+int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector<Table>& tabs,
+                lgc_svec** p_out) {
+  cudaStream_t s = ctx->stream;
+  std::vector<int64_t> capoff(B + 1, 0);
+  for (int64_t b = 0; b < B; b++) capoff[b + 1] = capoff[b] + tabs[b].cap;
+  const int64_t total = capoff[B];
+  const int kbits = vbits + bits_for(B);
+  Table* d_tabs = nullptr;
+  int64_t *d_capoff = nullptr, *flag = nullptr, *pos = nullptr, *kept = nullptr, *start = nullptr;
+  uint64_t *key = nullptr, *key2 = nullptr;
+  double *val = nullptr, *val2 = nullptr;
+  int32_t* idx = nullptr;
+  std::vector<int64_t> hstart(B + 1);
+  std::vector<int32_t> hidx;
+  std::vector<double> hval;
+  int st = LGC_OK;
+  do {
+    if ((st = dalloc_t(ctx, &d_tabs, B)) || (st = dalloc_t(ctx, &d_capoff, B + 1)) ||
+        (st = dalloc_t(ctx, &flag, total)) || (st = dalloc_t(ctx, &pos, total)) ||
+        (st = dalloc_t(ctx, &kept, 1)) || (st = dalloc_t(ctx, &start, B + 1)))
+      break;
+    if (cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d_capoff, capoff.data(), 8 * (B + 1), cudaMemcpyHostToDevice, s)) {
+      st = LGC_ECUDA;
+      break;
+    }
+    const int grid = (int)std::min<int64_t>(ceil_div(total, kBlock), 152 * 16);
+    batch_keep_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag);
+    LGC_COUNT_LAUNCH(ctx);
+    if ((st = scan_i64(ctx, flag, pos, total, false, kept)) != LGC_OK) break;
+    batch_bounds_kernel<<<grid_for(B + 1), kBlock, 0, s>>>(d_capoff, B, pos, kept, start);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaMemcpyAsync(hstart.data(), start, 8 * (B + 1), cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s)) {
+      st = LGC_ECUDA;
+      break;
+    }
+    const int64_t m = hstart[B];
+    if ((st = dalloc_t(ctx, &key, m)) || (st = dalloc_t(ctx, &key2, m)) ||
+        (st = dalloc_t(ctx, &val, m)) || (st = dalloc_t(ctx, &val2, m)) ||
+        (st = dalloc_t(ctx, &idx, m)))
+      break;
+    batch_gather_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag, pos, vbits, key,
+                                                 val);
+    LGC_COUNT_LAUNCH(ctx);
+    if ((st = radix_sort_u64_f64(ctx, key, val, key2, val2, m, kbits)) != LGC_OK) break;
+    batch_ids_kernel<<<grid_for(m), kBlock, 0, s>>>(key, m, vbits, idx);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = LGC_ECUDA;
+      break;
+    }
+    if (ctx->result_on_device) {
+      for (int64_t b = 0; b < B && st == LGC_OK; b++)
+        st = make_svec(ctx, idx + hstart[b], val + hstart[b], hstart[b + 1] - hstart[b], true,
+                       &p_out[b]);
+      break;
+    }
+    hidx.resize(m ? m : 1);
+    hval.resize(m ? m : 1);
+    if ((m && (cudaMemcpyAsync(hidx.data(), idx, 4 * m, cudaMemcpyDeviceToHost, s) ||
+               cudaMemcpyAsync(hval.data(), val, 8 * m, cudaMemcpyDeviceToHost, s))) ||
+        cudaStreamSynchronize(s)) {
+      st = LGC_ECUDA;
+      break;
+    }
+    for (int64_t b = 0; b < B && st == LGC_OK; b++) {
+      const int64_t a = hstart[b], k = hstart[b + 1] - a;
+      SvecBox* box = new (std::nothrow) SvecBox();
+      if (!box) {
+        st = LGC_ENOMEM;
+        break;
+      }
+      box->ctx = ctx;
+      box->pub.nnz = k;
+      box->pub.on_device = 0;
+      box->pub.idx = (int32_t*)malloc(4 * (k ? k : 1));
+      box->pub.val = (double*)malloc(8 * (k ? k : 1));
+      if (!box->pub.idx || !box->pub.val) {
+        free(box->pub.idx);
+        free(box->pub.val);
+        delete box;
+        st = LGC_ENOMEM;
+        break;
+      }
+      memcpy(box->pub.idx, hidx.data() + a, 4 * k);
+      memcpy(box->pub.val, hval.data() + a, 8 * k);
+      p_out[b] = &box->pub;
+    }
+  } while (0);
+  for (void* q : {(void*)d_tabs, (void*)d_capoff, (void*)flag, (void*)pos, (void*)kept,
+                  (void*)start, (void*)key, (void*)key2, (void*)val, (void*)val2, (void*)idx})
+    dfree(ctx, q);
+  return st;
+}
+
 int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,
                        const lgc_prnibble_params* prm_h, lgc_svec** p_out, lgc_stats* st_out) {
   if (!g || B < 1 || B > (1 << 24) || !seeds_h || !prm_h || !p_out) return LGC_EINVAL;
@@ -414,6 +642,10 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       pushed(B, 0), max_rounds(B);
   std::vector<SeedParam> sp(B);
   std::vector<Table> tabs(B);
+  std::vector<int> slab_of(B, -1);
+  Slabs slabs;
+  DBuf<Regrow> d_rg;
+  DBuf<int64_t> d_rgbeg;
   std::vector<int32_t> grown(B, 0), alive(B, 1);
   std::vector<SeedCount> sc_h(B);
 
@@ -464,15 +696,22 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       sp[b].pad = 0;
       edges[b] = dseed[b];
       max_rounds[b] = P.max_rounds > 0 ? P.max_rounds : INT64_MAX;
-      if (fail(table_create(ctx, &tabs[b], 2 * (1 + dseed[b]), true)) != LGC_OK) break;
     }
-    if (status != LGC_OK) break;
+    {
+      std::vector<int64_t> all(B), caps(B);
+      for (int64_t b = 0; b < B; b++) {
+        all[b] = b;
+        caps[b] = pow2_cap(2 * (1 + dseed[b]));
+      }
+      if (fail(carve_tables(ctx, &slabs, all, caps, &tabs, &slab_of)) != LGC_OK) break;
+    }
     if (fail(dalloc_t(ctx, &d_tabs, B)) != LGC_OK) break;
     if (fail(dalloc_t(ctx, &d_prm, B)) != LGC_OK) break;
     if (fail(dalloc_t(ctx, &d_sc, B)) != LGC_OK) break;
     if (fail(dalloc_t(ctx, &d_grown, B)) != LGC_OK) break;
     if (fail(dalloc_t(ctx, &d_alive, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &gsize, 2)) != LGC_OK) break;
+    if (fail(dalloc_t(ctx, &gsize, 3)) != LGC_OK) break;  // size, overflow, rehash error
+    cudaMemsetAsync(gsize, 0, 12, s);
     cudaMemcpyAsync(d_prm, sp.data(), sizeof(SeedParam) * B, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(d_sc, 0, sizeof(SeedCount) * B, s);
@@ -513,23 +752,42 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
         }
         if (nf == 0) break;
       }
-      // grow each seed's table so its round's new keys fit at load 1/2
-      bool any_grown = false;
+      // grow the tables of the seeds whose round's new keys would not fit at
+      // load 1/2: one slab for all new tables, one rehash launch for all
+      std::vector<int64_t> gw, gcap;
       int64_t next_cap = 0, E = 0;
       for (int64_t b = 0; b < B; b++) {
         grown[b] = 0;
         if (nfs[b] == 0) continue;
         const int64_t need = std::min<int64_t>(count[b] + edges[b], n);
         if (2 * need > tabs[b].cap) {
-          if (fail(table_grow(ctx, &tabs[b], 2 * need, nullptr, nullptr, 0)) != LGC_OK) break;
+          gw.push_back(b);
+          gcap.push_back(pow2_cap(2 * need));
           grown[b] = 1;
-          any_grown = true;
         }
         next_cap += std::min<int64_t>(n, count[b] + edges[b] + nfs[b]);
         E += edges[b];
       }
-      if (status != LGC_OK) break;
-      if (any_grown) {
+      if (!gw.empty()) {
+        std::vector<Regrow> rg(gw.size());
+        std::vector<int64_t> rgbeg(gw.size() + 1, 0);
+        std::vector<int> old_slab(gw.size());
+        for (size_t k = 0; k < gw.size(); k++) {
+          rg[k].from = tabs[gw[k]];
+          old_slab[k] = slab_of[gw[k]];
+          rgbeg[k + 1] = rgbeg[k] + tabs[gw[k]].cap;
+        }
+        if (fail(carve_tables(ctx, &slabs, gw, gcap, &tabs, &slab_of)) != LGC_OK) break;
+        for (size_t k = 0; k < gw.size(); k++) rg[k].to = tabs[gw[k]];
+        if (fail(d_rg.reserve(ctx, gw.size())) || fail(d_rgbeg.reserve(ctx, gw.size() + 1)))
+          break;
+        cudaMemcpyAsync(d_rg.ptr, rg.data(), sizeof(Regrow) * gw.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_rgbeg.ptr, rgbeg.data(), 8 * (gw.size() + 1), cudaMemcpyHostToDevice, s);
+        const int64_t tot = rgbeg[gw.size()];
+        batch_rehash_kernel<<<(int)std::min<int64_t>(ceil_div(tot, kBlock), 152 * 16), kBlock, 0,
+                              s>>>(d_rg.ptr, d_rgbeg.ptr, (int64_t)gw.size(), tot, gsize + 2);
+        LGC_COUNT_LAUNCH(ctx);
+        for (size_t k = 0; k < gw.size(); k++) slabs.release(ctx, old_slab[k]);
         cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_grown, grown.data(), 4 * B, cudaMemcpyHostToDevice, s);
         batch_reresolve_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, Fv.ptr, Fslot.ptr,
@@ -612,13 +870,13 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       // one read-back per round for the whole batch
       if (cudaMemcpyAsync(sc_h.data(), d_sc, sizeof(SeedCount) * B, cudaMemcpyDeviceToHost, s) !=
               cudaSuccess ||
-          cudaMemcpyAsync(ctx->h_scratch, gsize, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(ctx->h_scratch, gsize, 12, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess) {
         fail(LGC_ECUDA);
         break;
       }
       const int32_t* gs = (const int32_t*)ctx->h_scratch;
-      if (gs[1] != 0) {
+      if (gs[1] != 0 || gs[2] != 0) {
         fail(LGC_ETABLEFULL);
         break;
       }
@@ -644,17 +902,12 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       nf = next;
     }
     if (status != LGC_OK) break;
-    // results
-    for (int64_t b = 0; b < B && status == LGC_OK; b++) {
-      int32_t* d_idx = nullptr;
-      double* d_val = nullptr;
-      int64_t nnz = 0;
-      status = table_extract_sorted(ctx, tabs[b], tabs[b].p, n, &d_idx, &d_val, &nnz);
-      if (status == LGC_OK) status = make_svec(ctx, d_idx, d_val, nnz, ctx->result_on_device,
-                                               &p_out[b]);
-      dfree(ctx, d_idx);
-      dfree(ctx, d_val);
-      if (st_out) {
+    // results of all seeds at once: keep {p > 0}, sort by (seed, vertex),
+    // one copy out, then one vector per seed
+    status = extract_all(ctx, B, n, vbits, tabs, p_out);
+    if (status != LGC_OK) break;
+    if (st_out) {
+      for (int64_t b = 0; b < B; b++) {
         st_out[b] = lgc_stats{};
         st_out[b].rounds = rounds[b];
         st_out[b].pushes = pushes[b];
@@ -665,7 +918,9 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       }
     }
   } while (0);
-  for (int64_t b = 0; b < B; b++) table_destroy(ctx, &tabs[b]);
+  slabs.release_all(ctx);
+  d_rg.release(ctx);
+  d_rgbeg.release(ctx);
   dfree(ctx, d_seeds);
   dfree(ctx, d_deg);
   dfree(ctx, d_tabs);

@@ -675,21 +675,35 @@ __global__ void __launch_bounds__(kBlock)
 // ---------------------------------------------------------------------------
 __global__ void share_range_kernel(int64_t nf, const double* __restrict__ share,
                                    int32_t* __restrict__ range) {
+  __shared__ int s_r[2][kBlock / 32];
   int emin = 0, emax = 0;  // emin holds 2047 - be
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = (uint64_t)__double_as_longlong(share[i]) & kFxMask;
+    const uint64_t b = fx_bits(share[i]) & kFxMask;
     if (b) {
       const int be = fx_bexp(b);
       emin = max(emin, 2047 - be);
       emax = max(emax, be);
     }
   }
+  // one atomic pair per block: same-address atomics serialise in L2
   emin = __reduce_max_sync(0xffffffffu, emin);
   emax = __reduce_max_sync(0xffffffffu, emax);
-  if ((threadIdx.x & 31) == 0 && (emin | emax)) {
-    atomicMax(&range[0], emin);
-    atomicMax(&range[1], emax);
+  const int wib = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_r[0][wib] = emin;
+    s_r[1][wib] = emax;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    emin = threadIdx.x < kBlock / 32 ? s_r[0][threadIdx.x] : 0;
+    emax = threadIdx.x < kBlock / 32 ? s_r[1][threadIdx.x] : 0;
+    emin = __reduce_max_sync(0xffffffffu, emin);
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (threadIdx.x == 0 && (emin | emax)) {
+      atomicMax(&range[0], emin);
+      atomicMax(&range[1], emax);
+    }
   }
 }
 
@@ -1282,7 +1296,9 @@ struct PushWork {
       LGC_COUNT_LAUNCH(ctx);
     } else {
       LGC_CUDA_TRY(cudaMemsetAsync(prange.ptr, 0, 8, s));
-      share_range_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, share.ptr, prange.ptr);
+      const int64_t rb = ceil_div(nf, kBlock);
+      share_range_kernel<<<(int)(rb < 1 ? 1 : rb > 152 * 4 ? 152 * 4 : rb), kBlock, 0, s>>>(
+          nf, share.ptr, prange.ptr);
       LGC_COUNT_LAUNCH(ctx);
       pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
                                                               prange.ptr, gb, 0);
