@@ -191,16 +191,16 @@ def hk_terms(t, eps):
 
 
 def measure_many(lgc, inputs, torch, ctx, g, off):
-    """1024 PR-Nibble + sweep clusters, once through lgc_prnibble_batch (in
-    chunks) and once one seed per call; device-resident results."""
+    """1024 PR-Nibble + sweep clusters, once through lgc_prnibble_batch and
+    lgc_sweep_batch (in chunks) and once one seed per call (lgc_prnibble,
+    lgc_sweep); device-resident results."""
     seeds = inputs.seeds_deg2(off, MANY["seeds"], MANY["seed_stream"])
     eps = inputs.eps_loguniform(MANY["seeds"], MANY["seed_stream"], MANY["eps_lo"], MANY["eps_hi"])
     a = MANY["alpha"]
     ch = MANY["chunk"]
     # warm-up of both paths
     ps, _ = lgc.prnibble_batch(g, seeds[:8], a, eps[:8], mode=MODE)
-    for p in ps:
-        lgc.sweep(g, p)
+    lgc.sweep_batch(g, ps)
     p, _ = lgc.prnibble(g, int(seeds[0]), a, float(eps[0]), mode=MODE)
     lgc.sweep(g, p)
     torch.cuda.synchronize()
@@ -209,8 +209,7 @@ def measure_many(lgc, inputs, torch, ctx, g, off):
     e_b = 0
     for i in range(0, len(seeds), ch):
         ps, sts = lgc.prnibble_batch(g, seeds[i:i + ch], a, eps[i:i + ch], mode=MODE)
-        for p in ps:
-            lgc.sweep(g, p)
+        lgc.sweep_batch(g, ps)
         e_b += sum(st.pushed_edges for st in sts)
         del ps
     torch.cuda.synchronize()

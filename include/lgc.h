@@ -200,6 +200,14 @@ int lgc_prnibble_batch(lgc_graph *g, int64_t B, const int32_t *seeds,
  * p may be on the host or the device (p->on_device). */
 int lgc_sweep(lgc_graph *g, const lgc_svec *p, lgc_cluster **out);
 
+/* Sweep cuts of B vectors in one pass: out[b] is lgc_sweep(g, p[b], ...) for
+ * every b (the same cluster, vol, cut and conductance), computed with one
+ * sort of all their entries (by key, then stably by vector), one rank table
+ * per vector and one edge-balanced crossing count over all of them.  The
+ * vectors may be on the host or the device, each its own.  Errors: as
+ * lgc_sweep, for the whole batch (no out[b] is set then). */
+int lgc_sweep_batch(lgc_graph *g, int64_t B, const lgc_svec *const *p, lgc_cluster **out);
+
 /* ---- sweep cut without device allocation ---- */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot let a library allocate device memory during a call: processes

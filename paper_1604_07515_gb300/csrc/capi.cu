@@ -81,26 +81,29 @@ __global__ void heavy_write_kernel(const int32_t* __restrict__ deg, int64_t n,
 }
 
 __global__ void items_count_kernel(const int32_t* __restrict__ heavy, int64_t nh,
-                                   const int32_t* __restrict__ deg, int64_t* __restrict__ cnt,
-                                   int32_t* __restrict__ items_of) {
+                                   const int32_t* __restrict__ deg, int64_t* __restrict__ cnt) {
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
-       h += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = ((int64_t)deg[heavy[h]] + kPullItem - 1) / kPullItem;
-    cnt[h] = c;
-    items_of[h] = (int32_t)c;
-  }
+       h += (int64_t)gridDim.x * blockDim.x)
+    cnt[h] = ((int64_t)deg[heavy[h]] + kPullItem - 1) / kPullItem;
 }
 
 __global__ void items_fill_kernel(const int32_t* __restrict__ heavy, int64_t nh,
                                   const int64_t* __restrict__ off, const int64_t* __restrict__ pos,
-                                  const int32_t* __restrict__ items_of, int32_t* __restrict__ ih,
-                                  int64_t* __restrict__ ibeg) {
+                                  PullItem* __restrict__ items) {
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
        h += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o0 = off[heavy[h]];
-    for (int k = 0; k < items_of[h]; k++) {
-      ih[pos[h] + k] = (int32_t)h;
-      ibeg[pos[h] + k] = o0 + (int64_t)k * kPullItem;
+    const int32_t w = heavy[h];
+    const int64_t o0 = off[w], d = off[w + 1] - o0;
+    const int32_t parts = (int32_t)((d + kPullItem - 1) / kPullItem);
+    for (int32_t k = 0; k < parts; k++) {
+      PullItem it;
+      it.beg = o0 + (int64_t)k * kPullItem;
+      it.w = w;
+      it.h = (int32_t)h;
+      it.len = (int32_t)min((int64_t)kPullItem, d - (int64_t)k * kPullItem);
+      it.nparts = parts;
+      it.pad = 0;
+      items[pos[h] + k] = it;
     }
   }
 }
@@ -135,9 +138,8 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
   }
   // work items of at most kPullItem edges over the heavy vertices' lists
   const int64_t nh = g->nheavy;
-  if (st == LGC_OK && nh > 0) st = dalloc_t(ctx, &g->items_of, nh);
   if (st == LGC_OK && nh > 0) {
-    items_count_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->deg, flag, g->items_of);
+    items_count_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->deg, flag);
     LGC_COUNT_LAUNCH(ctx);
     st = scan_i64(ctx, flag, flag, nh, false, tot);
   }
@@ -148,12 +150,10 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
   }
   if (st == LGC_OK && nh > 0) {
     g->nitems = ctx->h_scratch[0];
-    st = dalloc_t(ctx, &g->item_h, g->nitems);
-    if (st == LGC_OK) st = dalloc_t(ctx, &g->item_beg, g->nitems);
+    st = dalloc_t(ctx, &g->items, g->nitems);
   }
   if (st == LGC_OK && nh > 0) {
-    items_fill_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->off, flag, g->items_of,
-                                                       g->item_h, g->item_beg);
+    items_fill_kernel<<<grid_for(nh), kBlock, 0, s>>>(g->heavy, nh, g->off, flag, g->items);
     LGC_COUNT_LAUNCH(ctx);
     if (cudaGetLastError() != cudaSuccess) st = LGC_ECUDA;
   }
@@ -431,9 +431,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     dfree(ctx, g->col);
     dfree(ctx, g->deg);
     dfree(ctx, g->heavy);
-  dfree(ctx, g->item_h);
-  dfree(ctx, g->item_beg);
-  dfree(ctx, g->items_of);
+    dfree(ctx, g->items);
     cudaStreamSynchronize(s);
     delete g;
     return st;
@@ -459,9 +457,7 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->col);
   dfree(ctx, g->deg);
   dfree(ctx, g->heavy);
-  dfree(ctx, g->item_h);
-  dfree(ctx, g->item_beg);
-  dfree(ctx, g->items_of);
+  dfree(ctx, g->items);
   cudaStreamSynchronize(ctx->stream);
   delete g;
 }
@@ -520,6 +516,11 @@ int lgc_rand_hkpr_endpoints(lgc_ctx* ctx, int32_t* out, int64_t n_walks) {
 int lgc_sweep(lgc_graph* g, const lgc_svec* p, lgc_cluster** out) {
   if (!g || !p || !out) return LGC_EINVAL;
   return run_sweep(g->ctx, g, p, out);
+}
+
+int lgc_sweep_batch(lgc_graph* g, int64_t B, const lgc_svec* const* p, lgc_cluster** out) {
+  if (!g || !p || !out) return LGC_EINVAL;
+  return run_sweep_batch(g->ctx, g, B, p, out);
 }
 
 int lgc_get_trace(lgc_ctx* ctx, int64_t* rounds, int64_t* sizes, int64_t cap_rounds,

@@ -223,6 +223,14 @@ struct lgc_ctx {
   lgc_kernel_profile prof[LGC_PROF_COUNT] = {};
 };
 
+// Work item of a pull round: edges [beg, beg + len) of heavy vertex w, the
+// item's vertex being heavy[h] and having nparts items in all.
+struct __align__(32) PullItem {
+  int64_t beg;
+  int32_t w, h, len, nparts;
+  int64_t pad;
+};
+
 struct lgc_graph {
   lgc_ctx* ctx = nullptr;
   int64_t n = 0, nnz = 0;
@@ -233,12 +241,10 @@ struct lgc_graph {
   // vertices of degree > kPullLight in ascending id, for the pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;
-  // their adjacency cut into work items of at most kPullItem edges:
-  // item i covers edges [item_beg[i], item_beg[i] + len) of heavy vertex
-  // item_h[i] (an index into heavy), len = min(kPullItem, rest of the list)
-  int32_t* item_h = nullptr;
-  int64_t* item_beg = nullptr;
-  int32_t* items_of = nullptr;  // per heavy vertex: number of items
+  // their adjacency cut into work items of at most kPullItem edges (one
+  // 32-byte record each, so a warp learns everything about its item from one
+  // load)
+  PullItem* items = nullptr;
   int64_t nitems = 0;
 };
 
@@ -340,6 +346,8 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
 int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_params* prm,
                   lgc_svec** p, lgc_stats* st);
 int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out);
+int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const* ps,
+                    lgc_cluster** out);
 // d(x) of a seed, checked: LGC_EINVAL unless 0 <= x < n and d(x) >= 1.
 int validate_seed(lgc_ctx* ctx, lgc_graph* g, int32_t x, int64_t* dx);
 int ctx_init(lgc_ctx* ctx, int device, cudaStream_t stream);

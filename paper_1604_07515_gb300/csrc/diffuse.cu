@@ -781,16 +781,17 @@ __global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
 }
 
 // Heavy vertices: one warp per work item (at most kPullItem edges of one
-// heavy vertex); lanes sum strided parts, then a butterfly.  A vertex with
-// one item is finished at once; otherwise the item's sum is added into
-// hacc[h] (two 64-bit atomic adds, the carry of the low word taken from its
-// returned old value) and the warp that completes the vertex's last item
-// finishes it and resets the accumulators for the next round.
+// heavy vertex); lanes sum strided parts, then a butterfly.  The item's
+// record and the vertex's current state are loaded first and the latter is
+// not waited for until the end, so an item costs three dependent memory
+// trips (record, columns, shares).  A vertex with one item is finished at
+// once; otherwise the item's sum is added into hacc[h] (two 64-bit atomic
+// adds, the low word's carry taken from its returned old value) and the warp
+// that completes the vertex's last item finishes it and resets the
+// accumulators for the next round.
 __global__ void __launch_bounds__(kBlock)
     pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                         const int32_t* __restrict__ heavy, const int32_t* __restrict__ item_h,
-                         const int64_t* __restrict__ item_beg,
-                         const int32_t* __restrict__ items_of, int64_t nitems,
+                         const PullItem* __restrict__ items, int64_t nitems,
                          const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
                          Table D, double c, int fmode, uint32_t* __restrict__ qbits,
                          Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
@@ -800,19 +801,25 @@ __global__ void __launch_bounds__(kBlock)
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = warp0; it < nitems; it += nwarps) {
-    const int32_t h = item_h[it];
-    const int32_t w = heavy[h];
-    const int64_t o0 = off[w], d = off[w + 1] - o0;
-    const int64_t k_beg = item_beg[it] - o0;
-    const int64_t k_end = min(d, k_beg + kPullItem);
+    const PullItem I = items[it];
+    const int32_t w = I.w;
+    // the vertex's state, needed only by lane 0 at the end
+    uint32_t bword = 0;
+    double cur = 0.0;
+    int64_t d = 0;
+    if (lane == 0) {
+      bword = D.bits[w >> 5];
+      cur = D.dval[w];
+      d = off[w + 1] - off[w];
+    }
     Fx part = {0, 0};
     uint64_t flag = 0;
-    for (int64_t k0 = k_beg; k0 < k_end; k0 += 32 * kPullBatch) {
+    for (int k0 = 0; k0 < I.len; k0 += 32 * kPullBatch) {
       int32_t u[kPullBatch];
 #pragma unroll
       for (int j = 0; j < kPullBatch; j++) {
-        const int64_t k = k0 + 32 * j + lane;
-        u[j] = k < k_end ? col[o0 + k] : -1;
+        const int k = k0 + 32 * j + lane;
+        u[j] = k < I.len ? col[I.beg + k] : -1;
       }
       Fx x[kPullBatch];
 #pragma unroll
@@ -835,14 +842,14 @@ __global__ void __launch_bounds__(kBlock)
     }
     const bool any = __any_sync(0xffffffffu, (flag & kFxFlag) != 0);
     if (lane != 0) continue;
-    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
-    if (items_of[h] == 1) {
-      if (present || any) {
-        const double base = present ? D.dval[w] : 0.0;
-        pull_finish(D, w, d, base + fx_to_double(part, L), true, present, c, fmode, qbits, C);
-      }
+    const bool present = (bword >> (w & 31)) & 1u;
+    if (I.nparts == 1) {
+      if (present || any)
+        pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(part, L), true, present, c,
+                    fmode, qbits, C);
       continue;
     }
+    const int32_t h = I.h;
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(&hacc[h]);
     if (part.lo | part.hi) {
       const unsigned long long old = atomicAdd(&acc[0], (unsigned long long)part.lo);
@@ -851,16 +858,14 @@ __global__ void __launch_bounds__(kBlock)
     }
     if (any) atomicOr(&htouch[h], 1);
     __threadfence();
-    if (atomicAdd(&hcnt[h], 1) == items_of[h] - 1) {
+    if (atomicAdd(&hcnt[h], 1) == I.nparts - 1) {
       __threadfence();
       Fx total;
       total.lo = atomicAdd(&acc[0], 0ull);
       total.hi = atomicAdd(&acc[1], 0ull);
-      if (present || atomicOr(&htouch[h], 0) != 0) {
-        const double base = present ? D.dval[w] : 0.0;
-        pull_finish(D, w, d, base + fx_to_double(total, L), true, present, c, fmode, qbits,
-                    C);
-      }
+      if (present || atomicOr(&htouch[h], 0) != 0)
+        pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(total, L), true, present, c,
+                    fmode, qbits, C);
       acc[0] = 0;
       acc[1] = 0;
       hcnt[h] = 0;
@@ -1324,8 +1329,8 @@ struct PushWork {
       } else if (g->nheavy > 0) {
         int64_t hb = ceil_div(g->nitems, kBlock / 32);
         pull_heavy_fx_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
-            g->off, g->col, g->heavy, g->item_h, g->item_beg, g->items_of, g->nitems, pshx.ptr,
-            prange.ptr, gb, D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
+            g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr, gb, D, c, fmode, pq.ptr,
+            phacc.ptr, phcnt.ptr, phtouch.ptr,
             ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }

@@ -16,6 +16,10 @@
 //      cut_i * den_j < cut_j * den_i on 128-bit products, first index on
 //      ties, zero denominators skipped
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "prim.cuh"
@@ -225,6 +229,186 @@ __global__ void argmin_final_kernel(const Best* __restrict__ parts, int nparts,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched sweep: the vectors of B seeds in one pass.  Element i of the
+// concatenation belongs to seed b with inoff[b] <= i < inoff[b + 1].  After
+// the positive entries are kept (seed-major, ids ascending within a seed),
+// one sort by key and a stable sort by seed give every seed's sweep order in
+// its own segment [nbeg[b], nbeg[b + 1]); vol and cut are prefix sums over
+// the whole concatenation, read per seed relative to the segment's start.
+// ---------------------------------------------------------------------------
+struct SweepIn {
+  const int32_t* idx;
+  const double* val;
+};
+
+__device__ inline int64_t seg_of(const int64_t* __restrict__ beg, int64_t B, int64_t i) {
+  int64_t lo = 0, hi = B;  // last b with beg[b] <= i
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (beg[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void bsweep_keys_kernel(const SweepIn* __restrict__ in, const int64_t* __restrict__ inoff,
+                                   int64_t B, int64_t M, const int32_t* __restrict__ deg, int64_t n,
+                                   uint64_t* __restrict__ key, int32_t* __restrict__ id,
+                                   int32_t* __restrict__ seg, int64_t* __restrict__ keep,
+                                   int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = seg_of(inoff, B - 1, i);
+    const int64_t j = i - inoff[b];
+    int32_t v = in[b].idx[j];
+    double pv = in[b].val[j];
+    if (v < 0 || v >= n || deg[v] < 1) {
+      atomicOr(bad, 1);
+      v = 0;
+      pv = 0.0;
+    }
+    const bool pos = pv > 0.0;
+    key[i] = pos ? 0x7FFFFFFFFFFFFFFFull -
+                       (uint64_t)__double_as_longlong(pv / (double)deg[v])
+                 : ~0ull;
+    id[i] = v;
+    seg[i] = (int32_t)b;
+    keep[i] = pos ? 1 : 0;
+  }
+}
+
+// Compaction of the kept entries (order preserved); cnt[b] boundaries from
+// the exclusive positions: nbeg[b] = pos[inoff[b]], nbeg[B] = total.
+__global__ void bsweep_compact_kernel(const int64_t* __restrict__ keep,
+                                      const int64_t* __restrict__ pos, int64_t M,
+                                      const uint64_t* __restrict__ key,
+                                      const int32_t* __restrict__ id,
+                                      const int32_t* __restrict__ seg, uint64_t* __restrict__ ko,
+                                      int32_t* __restrict__ eo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[i]) continue;
+    ko[pos[i]] = key[i];
+    eo[pos[i]] = (int32_t)i;  // element index: id[i], seg[i]
+  }
+}
+
+__global__ void bsweep_bounds_kernel(const int64_t* __restrict__ inoff, int64_t B, int64_t M,
+                                     const int64_t* __restrict__ pos,
+                                     const int64_t* __restrict__ total, int64_t* __restrict__ nbeg) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
+       b += (int64_t)gridDim.x * blockDim.x)
+    nbeg[b] = (b == B || inoff[b] >= M) ? *total : pos[inoff[b]];
+}
+
+__global__ void bsweep_segkey_kernel(const int32_t* __restrict__ elem, int64_t N,
+                                     const int32_t* __restrict__ seg, uint32_t* __restrict__ sk) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sk[i] = (uint32_t)seg[elem[i]];
+}
+
+// Sorted position i (seed b = sk[i], local rank i - nbeg[b] + 1): vertex id,
+// its rank in seed b's table, its degree.
+__global__ void bsweep_rank_kernel(const int32_t* __restrict__ elem, int64_t N,
+                                   const uint32_t* __restrict__ sk,
+                                   const int32_t* __restrict__ id, const int64_t* __restrict__ nbeg,
+                                   const Table* __restrict__ tabs,
+                                   const int32_t* __restrict__ deg, int32_t* __restrict__ order,
+                                   int64_t* __restrict__ d_i, int* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = id[elem[i]];
+    const uint32_t b = sk[i];
+    order[i] = v;
+    d_i[i] = deg[v];
+    int ins = 0;
+    const Table T = tabs[b];
+    const int64_t s = ht_find_or_insert(T, v, &ins, err);
+    if (s >= 0) T.s[s].aux = (int32_t)(i - nbeg[b] + 1);
+  }
+}
+
+// Edge-balanced over all seeds' vol(S_N) edges: per sorted position i, the
+// neighbours ranked before it in its own seed's order.
+__global__ void __launch_bounds__(kBlock)
+    bsweep_cross_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                        const int32_t* __restrict__ order, const uint32_t* __restrict__ sk,
+                        const int64_t* __restrict__ nbeg, const int64_t* __restrict__ vol,
+                        int64_t N, int64_t V, const Table* __restrict__ tabs,
+                        int32_t* __restrict__ before) {
+  __shared__ int64_t s_vol[kTile];
+  __shared__ int64_t s_off[kTile];
+  __shared__ int32_t s_cnt[kTile];
+  __shared__ int64_t s_i0, s_i1;
+  const int64_t ntiles = (V + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * kTile, e1 = min(V, e0 + kTile);
+    if (threadIdx.x == 0) s_i0 = upper_bound_excl(vol, N, e0);
+    if (threadIdx.x == 32) s_i1 = upper_bound_excl(vol, N, e1 - 1);
+    __syncthreads();
+    const int64_t i0 = s_i0;
+    int cnt = (int)(s_i1 - i0 + 1);
+    if (cnt > kTile) cnt = kTile;  // unreachable: every swept vertex has d >= 1
+    for (int j = threadIdx.x; j < cnt; j += kBlock) {
+      s_vol[j] = vol[i0 + j];
+      s_off[j] = off[order[i0 + j]];
+      s_cnt[j] = 0;
+    }
+    __syncthreads();
+    for (int k = 0; k < kTileItems; k++) {
+      const int64_t e = e0 + (int64_t)k * kBlock + threadIdx.x;
+      if (e < e1) {
+        int lo = 0, hi = cnt;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (s_vol[mid] <= e) lo = mid + 1;
+          else hi = mid;
+        }
+        const int j = lo;
+        if (j >= cnt) continue;
+        const int64_t first = j > 0 ? s_vol[j - 1] : (i0 > 0 ? vol[i0 - 1] : 0);
+        const int32_t w = col[s_off[j] + (e - first)];
+        const uint32_t b = sk[i0 + j];
+        const int64_t s = ht_find(tabs[b], w);
+        if (s >= 0 && tabs[b].s[s].aux < i0 + j - nbeg[b] + 1) atomicAdd(&s_cnt[j], 1);
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kBlock)
+      if (s_cnt[j]) atomicAdd(&before[i0 + j], s_cnt[j]);
+    __syncthreads();
+  }
+}
+
+// One CTA per seed: argmin over its segment of cut / min(vol, 2m - vol),
+// with vol and cut taken relative to the segment's start.
+__global__ void bsweep_argmin_kernel(const int64_t* __restrict__ cut,
+                                     const int64_t* __restrict__ vol,
+                                     const int64_t* __restrict__ nbeg, int64_t B, int64_t two_m,
+                                     Best* __restrict__ best, int64_t* __restrict__ best_vol) {
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    const int64_t s0 = nbeg[b], s1 = nbeg[b + 1];
+    const int64_t vb = s0 > 0 ? vol[s0 - 1] : 0, cb = s0 > 0 ? cut[s0 - 1] : 0;
+    Best x{0, 0, -1};
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      const int64_t v = vol[i] - vb;
+      const int64_t den = v < two_m - v ? v : two_m - v;
+      if (den > 0) {
+        Best c{cut[i] - cb, den, i - s0};
+        if (better(c, x)) x = c;
+      }
+    }
+    x = block_best(x);
+    if (threadIdx.x == 0) {
+      best[b] = x;
+      best_vol[b] = x.i >= 0 ? vol[s0 + x.i] - vb : 0;
+    }
+    __syncthreads();  // block_best's shared array is reused by the next seed
+  }
+}
+
 }  // namespace
 
 int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) {
@@ -379,6 +563,235 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
   dfree(ctx, drank);
   table_destroy(ctx, &T);
   return status;
+}
+
+// Sweep cuts of B vectors in one pass (see the batched kernels above).
+int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const* ps,
+                    lgc_cluster** out) {
+  if (B < 1 || B > (1 << 24) || !ps || !out) return LGC_EINVAL;
+  for (int64_t b = 0; b < B; b++) {
+    out[b] = nullptr;
+    if (!ps[b] || ps[b]->nnz < 0) return LGC_EINVAL;
+  }
+  cudaStream_t s = ctx->stream;
+  std::vector<int64_t> inoff(B + 1, 0);
+  for (int64_t b = 0; b < B; b++) inoff[b + 1] = inoff[b] + ps[b]->nnz;
+  const int64_t M = inoff[B];
+  std::vector<SweepIn> hin(B);
+  std::vector<int64_t> nbeg(B + 1, 0);
+  std::vector<Best> hbest(B, Best{0, 0, -1});
+  std::vector<int64_t> hbvol(B, 0);
+  std::vector<int32_t> hord;
+  int32_t* cidx = nullptr;  // host vectors, concatenated on the device
+  double* cval = nullptr;
+  SweepIn* d_in = nullptr;
+  int64_t *d_inoff = nullptr, *keep = nullptr, *pos = nullptr, *tot = nullptr, *d_nbeg = nullptr;
+  uint64_t *key = nullptr, *ko = nullptr, *ko2 = nullptr;
+  int32_t *id = nullptr, *seg = nullptr, *eo = nullptr, *eo2 = nullptr, *order = nullptr,
+          *before = nullptr;
+  uint32_t *sk = nullptr, *sk2 = nullptr;
+  int64_t *d_i = nullptr, *vol = nullptr, *cut = nullptr, *d_bvol = nullptr;
+  Best* d_best = nullptr;
+  Table* d_tabs = nullptr;
+  char* slab = nullptr;
+  int* d_err = nullptr;
+  int st = LGC_OK;
+  int64_t N = 0;
+  do {
+    if ((st = dalloc_t(ctx, &d_err, 2)) != LGC_OK) break;
+    if (cudaMemsetAsync(d_err, 0, 8, s) != cudaSuccess) { st = LGC_ECUDA; break; }
+    if (M > 0) {
+      // inputs: device vectors are read in place, host ones copied once
+      int64_t host_nnz = 0;
+      for (int64_t b = 0; b < B; b++)
+        if (!ps[b]->on_device) host_nnz += ps[b]->nnz;
+      if (host_nnz > 0) {
+        if ((st = dalloc_t(ctx, &cidx, host_nnz)) || (st = dalloc_t(ctx, &cval, host_nnz))) break;
+      }
+      int64_t at = 0;
+      for (int64_t b = 0; b < B && st == LGC_OK; b++) {
+        const lgc_svec* p = ps[b];
+        if (p->on_device || p->nnz == 0) {
+          hin[b] = SweepIn{p->idx, p->val};
+        } else {
+          if (cudaMemcpyAsync(cidx + at, p->idx, 4 * p->nnz, cudaMemcpyHostToDevice, s) ||
+              cudaMemcpyAsync(cval + at, p->val, 8 * p->nnz, cudaMemcpyHostToDevice, s))
+            st = LGC_ECUDA;
+          hin[b] = SweepIn{cidx + at, cval + at};
+          at += p->nnz;
+        }
+      }
+      if (st != LGC_OK) break;
+      if ((st = dalloc_t(ctx, &d_in, B)) || (st = dalloc_t(ctx, &d_inoff, B + 1)) ||
+          (st = dalloc_t(ctx, &key, M)) || (st = dalloc_t(ctx, &id, M)) ||
+          (st = dalloc_t(ctx, &seg, M)) || (st = dalloc_t(ctx, &keep, M)) ||
+          (st = dalloc_t(ctx, &pos, M)) || (st = dalloc_t(ctx, &tot, 1)) ||
+          (st = dalloc_t(ctx, &d_nbeg, B + 1)))
+        break;
+      if (cudaMemcpyAsync(d_in, hin.data(), sizeof(SweepIn) * B, cudaMemcpyHostToDevice, s) ||
+          cudaMemcpyAsync(d_inoff, inoff.data(), 8 * (B + 1), cudaMemcpyHostToDevice, s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), 152 * 32);
+      // S1: keys of the positive entries, seed-major, ids ascending per seed
+      bsweep_keys_kernel<<<grid, kBlock, 0, s>>>(d_in, d_inoff, B, M, g->deg, g->n, key, id, seg,
+                                                 keep, d_err);
+      LGC_COUNT_LAUNCH(ctx);
+      if ((st = scan_i64(ctx, keep, pos, M, false, tot)) != LGC_OK) break;
+      bsweep_bounds_kernel<<<grid_for(B + 1), kBlock, 0, s>>>(d_inoff, B, M, pos, tot, d_nbeg);
+      LGC_COUNT_LAUNCH(ctx);
+      if (cudaMemcpyAsync(nbeg.data(), d_nbeg, 8 * (B + 1), cudaMemcpyDeviceToHost, s) ||
+          cudaMemcpyAsync(ctx->h_scratch, d_err, 4, cudaMemcpyDeviceToHost, s) ||
+          cudaStreamSynchronize(s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      if (*(int*)ctx->h_scratch) {
+        st = LGC_EINVAL;  // an entry is not a vertex of degree >= 1
+        break;
+      }
+      N = nbeg[B];
+    }
+    if (N > 0) {
+      if ((st = dalloc_t(ctx, &ko, N)) || (st = dalloc_t(ctx, &ko2, N)) ||
+          (st = dalloc_t(ctx, &eo, N)) || (st = dalloc_t(ctx, &eo2, N)) ||
+          (st = dalloc_t(ctx, &sk, N)) || (st = dalloc_t(ctx, &sk2, N)) ||
+          (st = dalloc_t(ctx, &order, N)) || (st = dalloc_t(ctx, &d_i, N)) ||
+          (st = dalloc_t(ctx, &vol, N)) || (st = dalloc_t(ctx, &cut, N)) ||
+          (st = dalloc_t(ctx, &before, N)))
+        break;
+      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), 152 * 32);
+      bsweep_compact_kernel<<<grid, kBlock, 0, s>>>(keep, pos, M, key, id, seg, ko, eo);
+      LGC_COUNT_LAUNCH(ctx);
+      // S2: by key, then stably by seed
+      if ((st = radix_sort_u64_i32(ctx, ko, eo, ko2, eo2, N, 64)) != LGC_OK) break;
+      bsweep_segkey_kernel<<<grid_for(N), kBlock, 0, s>>>(eo, N, seg, sk);
+      LGC_COUNT_LAUNCH(ctx);
+      if ((st = radix_sort_u32_i32(ctx, sk, eo, sk2, eo2, N, bits_for(B))) != LGC_OK) break;
+      // S3: one rank table per seed, all in one cleared slab
+      std::vector<Table> tabs(B);
+      std::vector<int64_t> toff(B + 1, 0);
+      for (int64_t b = 0; b < B; b++) {
+        int64_t cap = 64;
+        while (cap < 2 * (nbeg[b + 1] - nbeg[b])) cap <<= 1;
+        toff[b + 1] = toff[b] + cap;
+      }
+      if ((st = dalloc_t(ctx, &slab, (size_t)(toff[B] * (int64_t)sizeof(Slot)))) != LGC_OK) break;
+      if (cudaMemsetAsync(slab, 0, (size_t)(toff[B] * (int64_t)sizeof(Slot)), s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      for (int64_t b = 0; b < B; b++) {
+        const int64_t cap = toff[b + 1] - toff[b];
+        int lg = 0;
+        while (((int64_t)1 << lg) < cap) lg++;
+        tabs[b] = Table();
+        tabs[b].cap = cap;
+        tabs[b].shift = 32 - lg;
+        tabs[b].s = reinterpret_cast<Slot*>(slab) + toff[b];
+      }
+      if ((st = dalloc_t(ctx, &d_tabs, B)) != LGC_OK) break;
+      if (cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s) ||
+          cudaMemsetAsync(before, 0, 4 * N, s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      bsweep_rank_kernel<<<grid_for(N), kBlock, 0, s>>>(eo, N, sk, id, d_nbeg, d_tabs, g->deg,
+                                                         order, d_i, d_err + 1);
+      LGC_COUNT_LAUNCH(ctx);
+      // S4: volumes over the whole concatenation
+      if ((st = scan_i64(ctx, d_i, vol, N, true, tot)) != LGC_OK) break;
+      if (cudaMemcpyAsync(ctx->h_scratch, tot, 8, cudaMemcpyDeviceToHost, s) ||
+          cudaStreamSynchronize(s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      const int64_t V = ctx->h_scratch[0];
+      // S5
+      if (V > 0) {
+        const int64_t tiles = ceil_div(V, kTile);
+        ProfScope ps_(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
+        bsweep_cross_kernel<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), kBlock, 0, s>>>(
+            g->off, g->col, order, sk, d_nbeg, vol, N, V, d_tabs, before);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      sweep_delta_kernel<<<grid_for(N), kBlock, 0, s>>>(d_i, before, N, cut);
+      LGC_COUNT_LAUNCH(ctx);
+      // S6
+      if ((st = scan_i64(ctx, cut, cut, N, true, nullptr)) != LGC_OK) break;
+    }
+    // S7, per seed
+    if ((st = dalloc_t(ctx, &d_best, B)) || (st = dalloc_t(ctx, &d_bvol, B))) break;
+    if (N > 0) {
+      bsweep_argmin_kernel<<<(int)std::min<int64_t>(B, 152 * 8), kBlock, 0, s>>>(
+          cut, vol, d_nbeg, B, g->nnz, d_best, d_bvol);
+      LGC_COUNT_LAUNCH(ctx);
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpyAsync(hbest.data(), d_best, sizeof(Best) * B, cudaMemcpyDeviceToHost, s) ||
+          cudaMemcpyAsync(hbvol.data(), d_bvol, 8 * B, cudaMemcpyDeviceToHost, s) ||
+          cudaMemcpyAsync(ctx->h_scratch, d_err + 1, 4, cudaMemcpyDeviceToHost, s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      if (!ctx->result_on_device) {
+        hord.resize(N);
+        if (cudaMemcpyAsync(hord.data(), order, 4 * N, cudaMemcpyDeviceToHost, s)) {
+          st = LGC_ECUDA;
+          break;
+        }
+      }
+      if (cudaStreamSynchronize(s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      if (*(int*)ctx->h_scratch & kErrTableFull) {
+        st = LGC_ETABLEFULL;
+        break;
+      }
+    }
+    for (int64_t b = 0; b < B && st == LGC_OK; b++) {
+      const Best& hb = hbest[b];
+      ClusterBox* box = new (std::nothrow) ClusterBox();
+      if (!box) {
+        st = LGC_ENOMEM;
+        break;
+      }
+      box->ctx = ctx;
+      const int64_t size = hb.i >= 0 ? hb.i + 1 : 0;
+      box->pub.size = size;
+      box->pub.vol = hb.i >= 0 ? hbvol[b] : 0;
+      box->pub.cut = hb.i >= 0 ? hb.cut : 0;
+      box->pub.conductance = hb.i >= 0 ? (double)hb.cut / (double)hb.den : INFINITY;
+      box->pub.on_device = ctx->result_on_device ? 1 : 0;
+      box->pub.ids = nullptr;
+      if (ctx->result_on_device) {
+        st = dalloc_t(ctx, &box->pub.ids, size);
+        if (st == LGC_OK && size &&
+            cudaMemcpyAsync(box->pub.ids, order + nbeg[b], 4 * size, cudaMemcpyDeviceToDevice, s))
+          st = LGC_ECUDA;
+      } else {
+        box->pub.ids = (int32_t*)malloc(4 * (size ? size : 1));
+        if (!box->pub.ids) st = LGC_ENOMEM;
+        else if (size) memcpy(box->pub.ids, hord.data() + nbeg[b], 4 * size);
+      }
+      if (st == LGC_OK) out[b] = &box->pub;
+      else lgc_cluster_free(&box->pub);
+    }
+  } while (0);
+  if (st != LGC_OK) {
+    for (int64_t b = 0; b < B; b++) {
+      lgc_cluster_free(out[b]);
+      out[b] = nullptr;
+    }
+  }
+  for (void* q : {(void*)cidx, (void*)cval, (void*)d_in, (void*)d_inoff, (void*)keep, (void*)pos,
+                  (void*)tot, (void*)d_nbeg, (void*)key, (void*)ko, (void*)ko2, (void*)id,
+                  (void*)seg, (void*)eo, (void*)eo2, (void*)order, (void*)before, (void*)sk,
+                  (void*)sk2, (void*)d_i, (void*)vol, (void*)cut, (void*)d_bvol, (void*)d_best,
+                  (void*)d_tabs, (void*)slab, (void*)d_err})
+    dfree(ctx, q);
+  return st;
 }
 
 }  // namespace lgc

@@ -109,6 +109,7 @@ SIGNATURES = {
                               POINTER(Stats)]),
     "lgc_rand_hkpr_endpoints": (c_int, [_P, _P, c_int64]),
     "lgc_sweep": (c_int, [_P, POINTER(Svec), POINTER(POINTER(Cluster))]),
+    "lgc_sweep_batch": (c_int, [_P, c_int64, _P, _P]),
     "lgc_get_trace": (c_int, [_P, POINTER(c_int64), _P, c_int64, _P, c_int64]),
     "lgc_prnibble_residual": (c_int, [_P, POINTER(POINTER(Svec))]),
     "lgc_submit": (c_int, [_P, _P, POINTER(Request), POINTER(c_uint64)]),
@@ -310,6 +311,7 @@ class SparseVec:
             load().lgc_svec_free(ptr)
             self._ptr = None
         elif ctx is not None:
+            self._ctx = ctx  # keeps the context alive while this result is
             ctx._own(self)
 
     def c_struct(self):
@@ -321,7 +323,9 @@ class SparseVec:
 
     def close(self):
         if getattr(self, "_ptr", None) is not None:
-            load().lgc_svec_free(self._ptr)
+            ctx = getattr(self, "_ctx", None)
+            if ctx is None or getattr(ctx, "handle", None):  # never after the context
+                load().lgc_svec_free(self._ptr)
             self._ptr = None
 
     def __del__(self):
@@ -359,11 +363,14 @@ class ClusterResult:
             load().lgc_cluster_free(ptr)
             self._ptr = None
         elif ctx is not None:
+            self._ctx = ctx
             ctx._own(self)
 
     def close(self):
         if getattr(self, "_ptr", None) is not None:
-            load().lgc_cluster_free(self._ptr)
+            ctx = getattr(self, "_ctx", None)
+            if ctx is None or getattr(ctx, "handle", None):
+                load().lgc_cluster_free(self._ptr)
             self._ptr = None
 
     def __del__(self):
@@ -408,6 +415,20 @@ def sweep(g: Graph, p: SparseVec) -> ClusterResult:
     out = POINTER(Cluster)()
     _check(load().lgc_sweep(g.handle, p.c_struct(), byref(out)), "lgc_sweep")
     return ClusterResult(out, g.ctx)
+
+
+def sweep_batch(g: Graph, ps) -> list:
+    """Sweep cuts of many vectors in one pass (lgc_sweep_batch); the same
+    clusters as sweep() on each."""
+    ps = list(ps)
+    B = len(ps)
+    if B == 0:
+        return []
+    ptrs = (POINTER(Svec) * B)(*[p.c_struct() for p in ps])
+    outs = (POINTER(Cluster) * B)()
+    _check(load().lgc_sweep_batch(g.handle, B, ctypes.addressof(ptrs), ctypes.addressof(outs)),
+           "lgc_sweep_batch")
+    return [ClusterResult(outs[b], g.ctx) for b in range(B)]
 
 
 def make_request(algo: int, seed: int, want_sweep: bool = True, **kw) -> Request:

@@ -73,3 +73,66 @@ def test_batch_duplicate_seeds_and_errors(setup):
         lgc.prnibble_batch(g, [x, iso], 0.01, 1e-5)
     with pytest.raises(lgc.LgcError):
         lgc.prnibble_batch(g, [x, x], [0.01, 1.5], 1e-5)
+
+
+def same_cluster(c, ref):
+    assert c.size == ref.best and c.vol == ref.best_vol and c.cut == ref.best_cut
+    assert np.array_equal(c.ids, ref.cluster)
+    assert c.conductance == ref.conductance or (np.isinf(c.conductance)
+                                                and np.isinf(ref.conductance))
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_sweep_batch_equals_oracle(setup, on_device):
+    """lgc_sweep_batch over PR-Nibble vectors and hand-made ones (empty, all
+    zero, ties in p/d, the whole support) gives each vector's own sweep."""
+    ctx, graphs = setup
+    off, col, g = graphs["rmat16"]
+    d = np.diff(off)
+    seeds = inputs.seeds_deg2(off, 24, 31)
+    eps = inputs.eps_loguniform(24, 32, -6.0, -4.0)
+    ctx.set_option(lgc.OPT_RESULT_ON_DEVICE, 1 if on_device else 0)
+    try:
+        ps, _ = lgc.prnibble_batch(g, seeds, 0.05, eps, mode="det")
+        vecs = list(ps)
+        host = []
+        for p in ps:
+            r = oracle.prnibble(off, col, int(seeds[len(host)]), 0.05, float(eps[len(host)]))
+            host.append((r.idx, r.val))
+        rng = np.random.default_rng(3)
+        sup = np.flatnonzero(d > 0).astype(np.int32)
+        extra = [(np.zeros(0, np.int32), np.zeros(0)), (sup[:5], np.zeros(5)),
+                 (sup[:300], (rng.integers(0, 4, 300) * 0.25 * d[sup[:300]])),
+                 (sup, np.ones(len(sup)))]
+        for idx, val in extra:
+            vecs.insert(int(rng.integers(0, len(vecs) + 1)), lgc.host_svec(idx, val))
+        cs = lgc.sweep_batch(g, vecs)
+        assert len(cs) == len(vecs)
+        for v, c in zip(vecs, cs):
+            c1 = lgc.sweep(g, v)
+            assert (c.size, c.vol, c.cut) == (c1.size, c1.vol, c1.cut)
+            assert c.conductance == c1.conductance or (np.isinf(c.conductance)
+                                                       and np.isinf(c1.conductance))
+            if not on_device:
+                assert np.array_equal(c.ids, c1.ids)
+        if not on_device:
+            for k, (idx, val) in enumerate(host):
+                same_cluster(cs[vecs.index(ps[k])], oracle.sweep(off, col, idx, val))
+            for idx, val in extra:
+                c = [c for v, c in zip(vecs, cs) if v.nnz == len(idx) and not v.on_device
+                     and np.array_equal(v.idx, idx) and np.array_equal(v.val, val)][0]
+                same_cluster(c, oracle.sweep(off, col, idx, val))
+    finally:
+        ctx.set_option(lgc.OPT_RESULT_ON_DEVICE, 0)
+
+
+def test_sweep_batch_rejects_bad_entries(setup):
+    ctx, graphs = setup
+    off, col, g = graphs["rmat13"]
+    iso = int(np.flatnonzero(np.diff(off) == 0)[0])
+    good = lgc.host_svec([int(np.flatnonzero(np.diff(off) > 0)[0])], [1.0])
+    with pytest.raises(lgc.LgcError):
+        lgc.sweep_batch(g, [good, lgc.host_svec([iso], [0.5])])
+    with pytest.raises(lgc.LgcError):
+        lgc.sweep_batch(g, [good, lgc.host_svec([len(off) + 5], [0.5])])
+    assert lgc.sweep_batch(g, []) == []
