@@ -135,9 +135,13 @@ enum {
   LGC_OPT_SERVE_MAX_BATCH = 4,  /* requests resident on the device at once */
   LGC_OPT_TABLE_FORM = 6,       /* sparse sets: 0 automatic (dense once a set may reach
                                    n/8 keys), 1 always hashed, 2 always dense */
-  LGC_OPT_PULL = 7              /* deterministic rounds gather from the frontier instead of
+  LGC_OPT_PULL = 7,             /* deterministic rounds gather from the frontier instead of
                                    sorting pushed records: 0 automatic (rounds of >= 2m/16
                                    edges), 1 never, 2 always; same results either way */
+  LGC_OPT_DEVICE_ROUNDS = 8     /* 1 (default): consecutive small rounds of atomic-mode
+                                   PR-Nibble run in one cooperative launch without returning
+                                   to the host in between; 0: one launch per step.  Request-
+                                   loop workers never use it.  Same results either way */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */

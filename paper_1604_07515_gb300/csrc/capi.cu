@@ -350,6 +350,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value < 0 || value > 2) return LGC_EINVAL;
       ctx->pull_policy = (int)value;
       return LGC_OK;
+    case LGC_OPT_DEVICE_ROUNDS:
+      if (value < 0 || value > 1) return LGC_EINVAL;
+      ctx->device_rounds = value != 0;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -572,6 +576,7 @@ int lgc_submit(lgc_ctx* ctx, lgc_graph* g, const lgc_request* req, uint64_t* tic
         }
         break;
       }
+      w->device_rounds = false;  // cooperative launches are never run side by side
       S->wctx.push_back(w);
     }
     if (S->wctx.empty()) {

@@ -195,6 +195,7 @@ struct lgc_ctx {
   bool trace = false;
   int table_form = 0;   // LGC_OPT_TABLE_FORM
   int pull_policy = 0;  // LGC_OPT_PULL: 0 automatic, 1 never, 2 every deterministic round
+  bool device_rounds = true;  // LGC_OPT_DEVICE_ROUNDS
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back

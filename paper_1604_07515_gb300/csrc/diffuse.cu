@@ -27,9 +27,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "fx128.cuh"
 #include "prim.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lgc {
 
@@ -55,7 +59,7 @@ __device__ inline int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t x
 // the end of the last staged source) and returns cnt <= kEdgeTile.  All
 // threads of the block must call it; the caller synchronizes after staging
 // its own per-source arrays.
-__device__ inline int stage_sources(const int64_t* __restrict__ epos, int64_t nf, int64_t total,
+__device__ inline int stage_sources(const int64_t* epos, int64_t nf, int64_t total,
                                     int64_t e0, int64_t e1, int64_t* s_i0, int64_t* s_i1,
                                     int64_t* s_epos) {
   if (threadIdx.x == 0) *s_i0 = upper_bound_i64(epos, nf, e0) - 1;
@@ -105,13 +109,12 @@ __device__ inline void count_inserted(int ins, int64_t* counter) {
 // PR-Nibble, Fig. alg:pr-nibble (rule 1) / alg:pr-nibble2 (rule 0).  T holds
 // r in slot.val and p in T.p[slot]; r' is updated in place (every read of r
 // in the round is of a frontier vertex, done here before the edgeMap).
-__global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
-                                     const int32_t* __restrict__ fs, Table T,
-                                     const int64_t* __restrict__ off, double alpha, double cs,
-                                     double cn, double eps, int rule, int det, int self_append,
-                                     double* __restrict__ share, int64_t* __restrict__ cnt,
-                                     int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
-                                     int32_t ncap, Counters* C) {
+__device__ inline void prnibble_vmap_body(int64_t nf, const int32_t* fv, const int32_t* fs,
+                                          Table T, const int64_t* __restrict__ off,
+                                          double alpha, double cs, double cn, double eps,
+                                          int rule, int det, int self_append, double* share,
+                                          int64_t* cnt, int64_t* foff, int32_t* nfv,
+                                          int32_t* nfs, int32_t ncap, Counters* C) {
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -143,6 +146,17 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
     }
     frontier_append(pred, v, s, d, nfv, nfs, C, ncap);
   }
+}
+
+__global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                     const int32_t* __restrict__ fs, Table T,
+                                     const int64_t* __restrict__ off, double alpha, double cs,
+                                     double cn, double eps, int rule, int det, int self_append,
+                                     double* __restrict__ share, int64_t* __restrict__ cnt,
+                                     int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
+                                     int32_t ncap, Counters* C) {
+  prnibble_vmap_body(nf, fv, fs, T, off, alpha, cs, cn, eps, rule, det, self_append, share, cnt,
+                     foff, nfv, nfs, ncap, C);
 }
 
 // Nibble, Fig. alg:nibble: p'[v] = p[v]/2 on the frontier (S = p, D = p',
@@ -214,18 +228,16 @@ __global__ void vmap_hkpr_kernel(int64_t nf, const int32_t* __restrict__ fv,
 // thread then finds its edge's source there.  Consecutive threads read
 // consecutive col[] entries.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock)
-    emap_atomic_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
-                       const double* __restrict__ share, const int64_t* __restrict__ epos,
-                       const int64_t* __restrict__ foff, int64_t nf, int64_t E_host,
-                       const int64_t* __restrict__ E_dev, Table D, double c, int fmode,
-                       int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
+// The tiles [first tile, ntiles) of the edge push with the given stride.
+__device__ inline void emap_atomic_body(const int32_t* __restrict__ col,
+                                        const int32_t* __restrict__ deg, const double* share,
+                                        const int64_t* epos, const int64_t* foff, int64_t nf,
+                                        int64_t E, Table D, double c, int fmode, int32_t* nfv,
+                                        int32_t* nfs, int32_t ncap, Counters* C) {
   __shared__ int64_t s_epos[kEdgeTile + 1];
   __shared__ int64_t s_off[kEdgeTile];
   __shared__ double s_share[kEdgeTile];
   __shared__ int64_t s_i0, s_i1;
-  // the device-computed total bounds every edge index, whatever the host passed
-  const int64_t E = min(E_host, *E_dev);
   const int64_t ntiles = (E + kEdgeTile - 1) / kEdgeTile;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kEdgeTile;
@@ -311,6 +323,17 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+__global__ void __launch_bounds__(kBlock)
+    emap_atomic_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+                       const double* __restrict__ share, const int64_t* __restrict__ epos,
+                       const int64_t* __restrict__ foff, int64_t nf, int64_t E_host,
+                       const int64_t* __restrict__ E_dev, Table D, double c, int fmode,
+                       int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
+  // the device-computed total bounds every edge index, whatever the host passed
+  emap_atomic_body(col, deg, share, epos, foff, nf, min(E_host, *E_dev), D, c, fmode, nfv, nfs,
+                   ncap, C);
+}
+
 // ---------------------------------------------------------------------------
 // edgeMap for bulk rounds (atomic mode, dense destination): the adds are
 // fire-and-forget reductions (no returned value, so nothing waits on them)
@@ -379,6 +402,148 @@ __global__ void __launch_bounds__(kBlock)
     for (int k = 0; k < kEdgeItems; k++) count_inserted(ins[k], &C->inserted);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Consecutive small PR-Nibble rounds (atomic mode) in one cooperative launch:
+// vertexMap, prefix sum of the frontier degrees, edge push with the
+// threshold-crossing append, and the frontier swap, separated by grid-wide
+// barriers, with no return to the host between rounds.  The kernel stops
+// (leaving the state for the host, which continues with the same rounds
+// one launch per step) when the frontier is empty, the round limit is
+// reached, or the next round is not small: more than e_max edges, a next
+// frontier that might not fit the buffers, or a table that might pass its
+// load limit.  Each round computes exactly what the host-driven round does.
+// ---------------------------------------------------------------------------
+struct RoundsState {
+  int32_t cur;   // frontier buffer of the current round (0 or 1)
+  int32_t stop;  // 1 empty frontier, 2 round limit, 3 round not small, 4 error flagged
+  int64_t count, rounds, pushes, pushed_edges;
+};
+
+__device__ inline int64_t block_sum_i64(int64_t x, int64_t* s_red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  int64_t t = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_red[k];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kBlock)
+    rounds_prnibble_kernel(Table T, const int64_t* __restrict__ off,
+                           const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+                           double alpha, double cs, double cn, double eps, int rule,
+                           int32_t* fv0, int32_t* fs0, int32_t* fv1, int32_t* fs1, int32_t fcap,
+                           double* share, int64_t* cnt, int64_t* epos, int64_t* foff,
+                           int64_t* bsum, Counters* Cn, RoundsState* S, int64_t max_rounds,
+                           int64_t e_max, int64_t key_limit) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ int64_t s_red[kBlock / 32];
+  __shared__ int64_t s_scan[kBlock / 32];
+  const int G = gridDim.x;
+  for (;;) {
+    const int cur = __ldcg(&S->cur), nxt = cur ^ 1;
+    const int64_t nf = __ldcg(&Cn[cur].next_size);
+    const int64_t E = __ldcg(&Cn[cur].next_edges);
+    const int64_t count = __ldcg(&S->count);
+    const int err = __ldcg(&Cn[cur].err) | __ldcg(&Cn[nxt].err);
+    int stop = 0;
+    if (err) stop = 4;
+    else if (nf == 0) stop = 1;
+    else if (__ldcg(&S->rounds) >= max_rounds) stop = 2;
+    else if (E > e_max || nf + E > fcap || count + E > key_limit) stop = 3;
+    if (stop) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) S->stop = stop;
+      return;  // the same decision in every thread: no barrier is left waiting
+    }
+    int32_t* fv = cur ? fv1 : fv0;
+    int32_t* fs = cur ? fs1 : fs0;
+    int32_t* nfv = cur ? fv0 : fv1;
+    int32_t* nfs = cur ? fs0 : fs1;
+    // vertexMap (the original rule keeps a vertex whose reduced residual
+    // still reaches the threshold)
+    prnibble_vmap_body(nf, fv, fs, T, off, alpha, cs, cn, eps, rule, 0, 1, share, cnt, foff, nfv,
+                       nfs, fcap, &Cn[nxt]);
+    grid.sync();
+    // exclusive prefix sum of the degrees: block b scans its chunk after
+    // adding the sums of the chunks before it
+    const int64_t chunk = (nf + G - 1) / G;
+    const int64_t c0 = min(nf, (int64_t)blockIdx.x * chunk), c1 = min(nf, c0 + chunk);
+    int64_t part = 0;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) part += cnt[i];
+    part = block_sum_i64(part, s_red);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = part;
+    grid.sync();
+    int64_t pre = 0, tot = 0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+      const int64_t x = __ldcg(&bsum[b]);
+      tot += x;
+      if (b < (int)blockIdx.x) pre += x;
+    }
+    pre = block_sum_i64(pre, s_red);
+    tot = block_sum_i64(tot, s_red);
+    for (int64_t base = c0; base < c1; base += blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      const int64_t x = i < c1 ? cnt[i] : 0;
+      int64_t inc = x;  // inclusive scan within the warp, then across warps
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((threadIdx.x & 31) >= o) inc += y;
+      }
+      if ((threadIdx.x & 31) == 31) s_scan[threadIdx.x >> 5] = inc;
+      __syncthreads();
+      int64_t wpre = 0, btot = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+        if (k < (int)(threadIdx.x >> 5)) wpre += s_scan[k];
+        btot += s_scan[k];
+      }
+      if (i < c1) epos[i] = pre + wpre + inc - x;
+      pre += btot;
+      __syncthreads();
+    }
+    grid.sync();
+    // edge push into the same table, appending crossings to the next frontier
+    const int64_t Er = min(E, tot);
+    emap_atomic_body(col, deg, share, epos, foff, nf, Er, T, eps, kFmThreshold, nfv, nfs, fcap,
+                     &Cn[nxt]);
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->rounds += 1;
+      S->pushes += nf;
+      S->pushed_edges += E;
+      S->count += Cn[nxt].inserted;
+      Cn[nxt].inserted = 0;
+      Cn[cur] = Counters{};
+      S->cur = nxt;
+    }
+    grid.sync();
+  }
+}
+
+__global__ void rounds_init_kernel(Counters* Cn, RoundsState* S, int64_t nf, int64_t E,
+                                   int64_t count) {
+  Cn[0] = Counters{};
+  Cn[1] = Counters{};
+  Cn[0].next_size = (int32_t)nf;
+  Cn[0].next_edges = E;
+  *S = RoundsState{};
+  S->count = count;
+}
+
+// out: stop | err << 8, cur, frontier size, its edges, keys, rounds, pushes,
+// pushed edges
+__global__ void rounds_pack_kernel(const Counters* Cn, const RoundsState* S, int64_t* out) {
+  const int cur = S->cur;
+  out[0] = (int64_t)S->stop | ((int64_t)(Cn[0].err | Cn[1].err) << 8);
+  out[1] = cur;
+  out[2] = Cn[cur].next_size;
+  out[3] = Cn[cur].next_edges;
+  out[4] = S->count;
+  out[5] = S->rounds;
+  out[6] = S->pushes;
+  out[7] = S->pushed_edges;
 }
 
 // Filter of a dense set, in ascending vertex order: vertex v qualifies when it
@@ -1087,11 +1252,21 @@ struct PushWork {
   DBuf<Fx> phacc;                  // per heavy vertex: partial sums of its items
   DBuf<int32_t> phcnt, phtouch;    // per heavy vertex: items done, any frontier neighbour
   bool pull_ready = false;
+  // device-driven rounds: two frontier buffers, block sums, counters, state
+  Frontier X[2];
+  DBuf<int64_t> xbsum;
+  DBuf<Counters> xcn;
+  DBuf<RoundsState> xst;
   lgc_stats st{};
   explicit PushWork(lgc_ctx* c, lgc_graph* gr) : ctx(c), g(gr) {}
   ~PushWork() {
     F.release(ctx);
     G.release(ctx);
+    X[0].release(ctx);
+    X[1].release(ctx);
+    xbsum.release(ctx);
+    xcn.release(ctx);
+    xst.release(ctx);
     share.release(ctx);
     cnt.release(ctx);
     epos.release(ctx);
@@ -1357,6 +1532,88 @@ struct PushWork {
     return read_counters(out);
   }
 
+  // Consecutive small rounds of atomic PR-Nibble on the device (see
+  // rounds_prnibble_kernel).  Runs at least one round when small_round()
+  // holds for the current one; afterwards F, T's key count and st describe
+  // the state reached, and the host continues from there.
+  static constexpr int64_t kRoundsEmax = int64_t{1} << 20;
+  static constexpr int64_t kRoundsPerLaunch = 1024;
+  int64_t rounds_emax() const { return std::min<int64_t>(kRoundsEmax, g->nnz / 16); }
+  int64_t rounds_fcap() const { return std::min<int64_t>(g->n, 2 * kRoundsEmax); }
+  static int64_t key_limit(const Table& T) { return T.dense ? INT64_MAX : T.cap / 2; }
+  bool small_round(const Table& T, int64_t count) const {
+    return ctx->device_rounds && !ctx->trace && F.size > 0 && F.edges <= rounds_emax() &&
+           F.size + F.edges <= rounds_fcap() && count + F.edges <= key_limit(T);
+  }
+  int device_rounds_prnibble(Table& T, int64_t* count, double alpha, double cs, double cn,
+                             double eps, int rule, int64_t rounds_left) {
+    cudaStream_t s = ctx->stream;
+    static int blocks_per_sm = -1;  // the same for every device of this build
+    if (blocks_per_sm < 0) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rounds_prnibble_kernel, kBlock, 0) !=
+          cudaSuccess)
+        nb = 0;
+      blocks_per_sm = nb;
+    }
+    int sms = 0;
+    LGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int G = sms * std::min(blocks_per_sm, 2);
+    if (G < 1) {  // no co-resident grid possible: rounds stay on the host
+      ctx->device_rounds = false;
+      return LGC_OK;
+    }
+    const int64_t fcap = rounds_fcap();
+    for (int k = 0; k < 2; k++) {
+      LGC_TRY(X[k].v.reserve(ctx, fcap));
+      LGC_TRY(X[k].s.reserve(ctx, fcap));
+    }
+    LGC_TRY(reserve_frontier_scratch(fcap));
+    LGC_TRY(xbsum.reserve(ctx, G));
+    LGC_TRY(xcn.reserve(ctx, 2));
+    LGC_TRY(xst.reserve(ctx, 1));
+    LGC_TRY(total.reserve(ctx, 8));
+    LGC_CUDA_TRY(cudaMemcpyAsync(X[0].v.ptr, F.v.ptr, 4 * F.size, cudaMemcpyDeviceToDevice, s));
+    LGC_CUDA_TRY(cudaMemcpyAsync(X[0].s.ptr, F.s.ptr, 4 * F.size, cudaMemcpyDeviceToDevice, s));
+    rounds_init_kernel<<<1, 1, 0, s>>>(xcn.ptr, xst.ptr, F.size, F.edges, *count);
+    LGC_COUNT_LAUNCH(ctx);
+    int32_t fc = (int32_t)fcap;
+    // at most kRoundsPerLaunch rounds per launch: the host regains control
+    // at least that often
+    int64_t mr = std::min<int64_t>(rounds_left, kRoundsPerLaunch), em = rounds_emax(),
+            kl = key_limit(T);
+    void* args[] = {&T, &g->off, &g->col, &g->deg, &alpha, &cs, &cn, &eps, &rule,
+                    &X[0].v.ptr, &X[0].s.ptr, &X[1].v.ptr, &X[1].s.ptr, &fc, &share.ptr, &cnt.ptr,
+                    &epos.ptr, &foff.ptr, &xbsum.ptr, &xcn.ptr, &xst.ptr, &mr, &em, &kl};
+    {
+      ProfScope ps(ctx, LGC_PROF_EDGEMAP, 0.0);
+      LGC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)rounds_prnibble_kernel, G, kBlock,
+                                               args, 0, s));
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    rounds_pack_kernel<<<1, 1, 0, s>>>(xcn.ptr, xst.ptr, total.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, total.ptr, 64, cudaMemcpyDeviceToHost, s));
+    LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t* o = ctx->h_scratch;
+    const int64_t cur = o[1], nf = o[2], E = o[3], rounds = o[5];
+    if (ctx->profile && !ctx->prof_pending.empty())
+      ctx->prof_pending.back().bytes += 24.0 * (double)o[7] + 88.0 * (double)o[6];
+    if ((o[0] >> 8) != 0) return LGC_ETABLEFULL;
+    if (rounds < 1) return LGC_ECUDA;  // the host checked that the first round is small
+    LGC_TRY(F.v.reserve(ctx, std::max<int64_t>(nf, 1024)));
+    LGC_TRY(F.s.reserve(ctx, std::max<int64_t>(nf, 1024)));
+    LGC_CUDA_TRY(cudaMemcpyAsync(F.v.ptr, X[cur].v.ptr, 4 * nf, cudaMemcpyDeviceToDevice, s));
+    LGC_CUDA_TRY(cudaMemcpyAsync(F.s.ptr, X[cur].s.ptr, 4 * nf, cudaMemcpyDeviceToDevice, s));
+    F.size = nf;
+    F.edges = E;
+    *count = o[4];
+    st.rounds += rounds;
+    st.pushes += o[6];
+    st.pushed_edges += o[7];
+    return LGC_OK;
+  }
+
   int scan_counts(int64_t* nrec_out) {
     LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, F.size, false, total.ptr));
     LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost,
@@ -1469,6 +1726,12 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
       if (st.rounds >= max_rounds) {
         status = LGC_EMAXROUNDS;
         break;
+      }
+      if (!det && W.small_round(T, count)) {
+        status = W.device_rounds_prnibble(T, &count, alpha, cs, cn, eps, prm->rule,
+                                          max_rounds - st.rounds);
+        if (status != LGC_OK) break;
+        continue;
       }
       W.record_trace();
       // room for the round's new keys (at most the frontier's edges)

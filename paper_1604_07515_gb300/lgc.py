@@ -127,6 +127,8 @@ SIGNATURES = {
 
 OPT_PROFILE = 5
 OPT_TABLE_FORM = 6
+OPT_PULL = 7
+OPT_DEVICE_ROUNDS = 8
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}

@@ -358,3 +358,60 @@ def test_atomic_pull_rounds_within_tolerance(ctx, name):
             assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
     finally:
         ctx.set_option(OPT_PULL, 0)
+
+
+# ---------------------------------------------------------------------------
+# Device-driven rounds (consecutive small atomic PR-Nibble rounds in one
+# cooperative launch): same rounds, pushes and p as the host-driven rounds
+# and the oracle.  Tracing is off here (it keeps rounds on the host).
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def ctx_notrace():
+    c = lgc.Context(0)
+    yield c
+    c.close()
+
+
+DEV_CASES = [("paper", 0.1, 1e-4), ("star40", 0.05, 1e-4), ("grid6", 0.05, 1e-5),
+             ("rand500", 0.01, 1e-6), ("rmat10", 0.01, 1e-6), ("rmat13", 0.05, 1e-7),
+             ("rmat16", 0.01, 1e-7), ("rmat16", 0.01, 1e-5)]
+
+
+@pytest.mark.parametrize("rule", ["opt", "orig"])
+@pytest.mark.parametrize("form_", [0, 1, 2], ids=["auto", "hashed", "dense"])
+@pytest.mark.parametrize("name,alpha,eps", DEV_CASES)
+def test_prnibble_device_rounds(ctx_notrace, name, alpha, eps, form_, rule):
+    c = ctx_notrace
+    off, col = GRAPHS[name]()
+    g = lgc.Graph(c, off, col)
+    c.set_option(lgc.OPT_TABLE_FORM, form_)
+    try:
+        for x in seeds_for(off, col, 3, salt=7):
+            ref = oracle.prnibble(off, col, x, alpha, eps, rule=0 if rule == "opt" else 1)
+            c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
+            p1, s1 = lgc.prnibble(g, x, alpha, eps, rule=rule, mode="atomic")
+            c.set_option(lgc.OPT_DEVICE_ROUNDS, 0)
+            p0, s0 = lgc.prnibble(g, x, alpha, eps, rule=rule, mode="atomic")
+            for p, s in ((p1, s1), (p0, s0)):
+                assert (s.rounds, s.pushes, s.pushed_edges) == (ref.rounds, ref.pushes,
+                                                                 ref.pushed_edges)
+                assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
+        c.set_option(lgc.OPT_TABLE_FORM, 0)
+        g.close()
+
+
+def test_prnibble_device_rounds_round_limit(ctx_notrace):
+    c = ctx_notrace
+    off, col = GRAPHS["rmat13"]()
+    g = lgc.Graph(c, off, col)
+    try:
+        x = inputs.config1_seed(off, col)
+        for k in (1, 2, 5):
+            ref = oracle.prnibble(off, col, x, 0.01, 1e-6, max_rounds=k)
+            p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic", max_rounds=k)
+            assert st.rounds == k and st.pushed_edges == ref.pushed_edges
+            assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        g.close()
