@@ -138,10 +138,13 @@ enum {
   LGC_OPT_PULL = 7,             /* deterministic rounds gather from the frontier instead of
                                    sorting pushed records: 0 automatic (rounds of >= 2m/16
                                    edges), 1 never, 2 always; same results either way */
-  LGC_OPT_DEVICE_ROUNDS = 8     /* 1 (default): consecutive small rounds of atomic-mode
+  LGC_OPT_DEVICE_ROUNDS = 8,    /* 1 (default): consecutive small rounds of atomic-mode
                                    PR-Nibble run in one cooperative launch without returning
                                    to the host in between; 0: one launch per step.  Request-
                                    loop workers never use it.  Same results either way */
+  LGC_OPT_PULL_BATCH = 9        /* edges per lane per batch in the heavy-vertex pull gather:
+                                   0 (default) the graph's tuned value (see
+                                   lgc_graph_autotune), or 4, 8, 16 */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */
@@ -155,6 +158,13 @@ int lgc_ctx_synchronize(lgc_ctx *ctx);
 int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *cols,
                      int flags, lgc_graph **out);
 void lgc_graph_destroy(lgc_graph *g);
+/* Tunes the graph's launch shapes by timing them on the graph itself (the
+ * paper has no counterpart; it affects speed only): the number of edges each
+ * lane loads per batch in the heavy-vertex pull gather, from {4, 8, 16}, on
+ * a frontier of all vertices.  Takes a few launches of that gather; the
+ * chosen value is written to *pull_batch (nullable).  Until it is called
+ * the graph uses 8. */
+int lgc_graph_autotune(lgc_graph *g, int *pull_batch);
 int64_t lgc_graph_num_vertices(const lgc_graph *g);
 int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
 

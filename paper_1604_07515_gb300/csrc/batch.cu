@@ -381,14 +381,6 @@ __global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ 
     }
 }
 
-__global__ void gather_degrees_kernel(int64_t B, const int32_t* __restrict__ seeds, int64_t n,
-                                      const int32_t* __restrict__ deg, int64_t* __restrict__ out) {
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = seeds[b];
-    out[b] = (x >= 0 && x < n) ? deg[x] : -1;
-  }
-}
 
 }  // namespace
 
@@ -650,7 +642,6 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   std::vector<SeedCount> sc_h(B);
 
   int32_t *d_seeds = nullptr, *d_grown = nullptr, *d_alive = nullptr, *gsize = nullptr;
-  int64_t* d_deg = nullptr;
   Table* d_tabs = nullptr;
   SeedParam* d_prm = nullptr;
   SeedCount* d_sc = nullptr;
@@ -668,18 +659,13 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   };
   do {
     if (fail(dalloc_t(ctx, &d_seeds, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &d_deg, B)) != LGC_OK) break;
     if (cudaMemcpyAsync(d_seeds, seeds_h, 4 * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
       fail(LGC_ECUDA);
       break;
     }
-    gather_degrees_kernel<<<grid_for(B), kBlock, 0, s>>>(B, d_seeds, n, g->deg, d_deg);
-    LGC_COUNT_LAUNCH(ctx);
-    if (cudaMemcpyAsync(dseed.data(), d_deg, 8 * B, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      fail(LGC_ECUDA);
-      break;
-    }
+    // seed degrees from the graph's host copy (out-of-range seeds read 0)
+    for (int64_t b = 0; b < B; b++)
+      dseed[b] = (seeds_h[b] >= 0 && seeds_h[b] < n) ? g->hdeg[seeds_h[b]] : 0;
     bool bad = false;
     for (int64_t b = 0; b < B; b++) bad = bad || dseed[b] < 1;
     if (bad) {
@@ -922,7 +908,6 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   d_rg.release(ctx);
   d_rgbeg.release(ctx);
   dfree(ctx, d_seeds);
-  dfree(ctx, d_deg);
   dfree(ctx, d_tabs);
   dfree(ctx, d_prm);
   dfree(ctx, d_sc);

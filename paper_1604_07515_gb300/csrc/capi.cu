@@ -354,6 +354,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value < 0 || value > 1) return LGC_EINVAL;
       ctx->device_rounds = value != 0;
       return LGC_OK;
+    case LGC_OPT_PULL_BATCH:
+      if (value != 0 && value != 4 && value != 8 && value != 16) return LGC_EINVAL;
+      ctx->pull_batch = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -428,6 +432,18 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
       break;
     }
     g->max_deg = hf[1];
+    try {
+      g->hdeg.resize(n);
+    } catch (...) {
+      st = LGC_ENOMEM;
+      break;
+    }
+    if (n && (cudaMemcpyAsync(g->hdeg.data(), g->deg, 4 * n, cudaMemcpyDeviceToHost, s) !=
+                  cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess)) {
+      st = LGC_ECUDA;
+      break;
+    }
     st = build_heavy_list(ctx, g);
   } while (0);
   if (st != LGC_OK) {
@@ -464,6 +480,13 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->items);
   cudaStreamSynchronize(ctx->stream);
   delete g;
+}
+
+int lgc_graph_autotune(lgc_graph* g, int* pull_batch) {
+  if (!g) return LGC_EINVAL;
+  LGC_TRY(autotune_pull(g->ctx, g));
+  if (pull_batch) *pull_batch = g->pull_batch;
+  return LGC_OK;
 }
 
 int64_t lgc_graph_num_vertices(const lgc_graph* g) { return g ? g->n : -1; }

@@ -25,6 +25,8 @@
 // All arithmetic is IEEE binary64 with FMA contraction disabled (--fmad=false),
 // each expression evaluated in the order written.
 #include <math.h>
+
+#include <algorithm>
 #include <string.h>
 
 #include <cooperative_groups.h>
@@ -678,29 +680,11 @@ __global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t
   }
 }
 
-// Heavy vertices read their lists in batches of 32 * kPullBatch edges: every
-// lane issues the loads of kPullBatch edges (column, then share) before any
-// of them is used, so one batch costs two memory round trips.
+// Heavy vertices are read in batches of 32 * BATCH edges: every lane issues
+// the loads of BATCH edges (column, then share) before any of them is used,
+// so one batch costs two memory round trips; BATCH is the graph's tuned value
+// (kPullBatch until tuned).
 constexpr int kPullBatch = 8;
-
-// Loads batch [k0, k0 + 256) of a list: lane l holds edge k0 + 32 j + l in
-// slot j (adjacency order is j-major, then lane).  s[j] is +0.0 for an edge
-// whose source is not in the frontier.
-__device__ inline void pull_batch(const int32_t* __restrict__ col, int64_t o0, int64_t k0,
-                                  int64_t kend, const double* __restrict__ sh, int lane,
-                                  double s[kPullBatch], unsigned in[kPullBatch]) {
-  int32_t u[kPullBatch];
-#pragma unroll
-  for (int j = 0; j < kPullBatch; j++) {
-    const int64_t k = k0 + 32 * j + lane;
-    u[j] = k < kend ? col[o0 + k] : -1;
-  }
-#pragma unroll
-  for (int j = 0; j < kPullBatch; j++) {
-    s[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
-    in[j] = __ballot_sync(0xffffffffu, pull_member(s[j]));
-  }
-}
 
 // Writes a heavy vertex's gathered value (lane 0 calls it).
 __device__ inline void pull_finish(const Table& D, int32_t w, int64_t d, double acc, bool touched,
@@ -891,6 +875,21 @@ __global__ void pull_scatter_fx_kernel(int64_t nf, const int32_t* __restrict__ f
   }
 }
 
+// Autotuning input: every vertex in the frontier with share 1 (X = 1 at
+// the scale the range {1023, 1023} gives).
+__global__ void tune_fill_kernel(Fx* __restrict__ shx, int64_t n, int32_t* __restrict__ range,
+                                 int g) {
+  const int L = fx_scale(1023, 1023, g);
+  const Fx one = fx_from_double(1.0, L);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    shx[v] = Fx{one.lo, one.hi | kFxFlag};
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    range[0] = 2047 - 1023;
+    range[1] = 1023;
+  }
+}
+
 // Vertices of degree 1..kPullLight, one thread each, their edges read four
 // at a time (all column loads, then all share loads).  Every bitmap word of
 // qbits is written here (by ballot, heavy vertices' bits zero); the heavy
@@ -954,6 +953,7 @@ __global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
 // adds, the low word's carry taken from its returned old value) and the warp
 // that completes the vertex's last item finishes it and resets the
 // accumulators for the next round.
+template <int BATCH>
 __global__ void __launch_bounds__(kBlock)
     pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                          const PullItem* __restrict__ items, int64_t nitems,
@@ -979,22 +979,22 @@ __global__ void __launch_bounds__(kBlock)
     }
     Fx part = {0, 0};
     uint64_t flag = 0;
-    for (int k0 = 0; k0 < I.len; k0 += 32 * kPullBatch) {
-      int32_t u[kPullBatch];
+    for (int k0 = 0; k0 < I.len; k0 += 32 * BATCH) {
+      int32_t u[BATCH];
 #pragma unroll
-      for (int j = 0; j < kPullBatch; j++) {
+      for (int j = 0; j < BATCH; j++) {
         const int k = k0 + 32 * j + lane;
         u[j] = k < I.len ? col[I.beg + k] : -1;
       }
-      Fx x[kPullBatch];
+      Fx x[BATCH];
 #pragma unroll
-      for (int j = 0; j < kPullBatch; j++) {
+      for (int j = 0; j < BATCH; j++) {
         x[j].lo = 0;
         x[j].hi = 0;
         if (u[j] >= 0) x[j] = shx[u[j]];
       }
 #pragma unroll
-      for (int j = 0; j < kPullBatch; j++) {
+      for (int j = 0; j < BATCH; j++) {
         flag |= x[j].hi;
         fx_add(part, x[j]);
       }
@@ -1503,10 +1503,14 @@ struct PushWork {
         LGC_COUNT_LAUNCH(ctx);
       } else if (g->nheavy > 0) {
         int64_t hb = ceil_div(g->nitems, kBlock / 32);
-        pull_heavy_fx_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
-            g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr, gb, D, c, fmode, pq.ptr,
-            phacc.ptr, phcnt.ptr, phtouch.ptr,
-            ctx->d_counters);
+        const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+        const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
+        auto heavy = batch == 16 ? pull_heavy_fx_kernel<16>
+                     : batch == 4 ? pull_heavy_fx_kernel<4>
+                                  : pull_heavy_fx_kernel<kPullBatch>;
+        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr, gb,
+                                    D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
+                                    ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
       }
     }
@@ -1692,6 +1696,75 @@ int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, 
 }
 
 }  // namespace
+
+// Picks the batch depth of the heavy-vertex pull gather for this graph: each
+// candidate gathers a frontier of all vertices into a scratch dense set
+// three times (after one untimed launch), and the fastest median wins.  The
+// gathered sums are exact, so every candidate gives the same values.
+int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
+  if (g->nheavy == 0 || g->nitems == 0) return LGC_OK;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = g->n, words = (n + 31) / 32;
+  Table D;
+  Fx *shx = nullptr, *hacc = nullptr;
+  int32_t *range = nullptr, *hcnt = nullptr, *htouch = nullptr;
+  uint32_t* q = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = LGC_OK;
+  int gb = 1;
+  while (gb < 62 && (int64_t{1} << gb) <= g->max_deg) gb++;
+  do {
+    if ((st = table_create_dense(ctx, &D, n, false)) || (st = dalloc_t(ctx, &shx, n)) ||
+        (st = dalloc_t(ctx, &range, 2)) || (st = dalloc_t(ctx, &q, words)) ||
+        (st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
+        (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
+      break;
+    if (cudaMemsetAsync(q, 0, 4 * words, s) || cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
+        cudaMemsetAsync(hcnt, 0, 4 * (g->nheavy + 1), s) ||
+        cudaMemsetAsync(htouch, 0, 4 * (g->nheavy + 1), s) ||
+        cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+      st = LGC_ECUDA;
+      break;
+    }
+    tune_fill_kernel<<<grid_for(n), kBlock, 0, s>>>(shx, n, range, gb);
+    LGC_COUNT_LAUNCH(ctx);
+    const int64_t hb = ceil_div(g->nitems, kBlock / 32);
+    const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+    const int cand[3] = {4, 8, 16};
+    float best_ms = 0.f;
+    int best = kPullBatch;
+    for (int c : cand) {
+      auto heavy = c == 16 ? pull_heavy_fx_kernel<16>
+                   : c == 4 ? pull_heavy_fx_kernel<4>
+                            : pull_heavy_fx_kernel<kPullBatch>;
+      float t[3];
+      for (int r = -1; r < 3; r++) {
+        if (cudaEventRecord(e0, s)) st = LGC_ECUDA;
+        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shx, range, gb, D, 1.0,
+                                    kFmThreshold, q, hacc, hcnt, htouch, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        if (cudaEventRecord(e1, s) || cudaEventSynchronize(e1)) st = LGC_ECUDA;
+        if (st != LGC_OK) break;
+        if (r >= 0 && cudaEventElapsedTime(&t[r], e0, e1)) st = LGC_ECUDA;
+      }
+      if (st != LGC_OK) break;
+      std::sort(t, t + 3);
+      if (c == cand[0] || t[1] < best_ms) {
+        best_ms = t[1];
+        best = c;
+      }
+    }
+    if (st == LGC_OK) g->pull_batch = best;
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  table_destroy(ctx, &D);
+  for (void* p : {(void*)shx, (void*)range, (void*)q, (void*)hacc, (void*)hcnt, (void*)htouch})
+    dfree(ctx, p);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(Counters), s);
+  if (cudaGetLastError() != cudaSuccess && st == LGC_OK) st = LGC_ECUDA;
+  return st;
+}
 
 int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm, lgc_svec** p,
                  lgc_stats* st_out, lgc_svec** r_out) {

@@ -219,11 +219,69 @@ __global__ void radix_scatter_kernel(const K* __restrict__ keys_in, const V* __r
   }
 }
 
+// Short arrays: one CTA sorts (key masked to its low bits, original index)
+// pairs in shared memory with a bitonic network; ordering by the index among
+// equal keys makes it stable, so the result is the LSD radix sort's.
+constexpr int kSmallSort = 1024;
+
+template <class K, class V>
+__global__ void __launch_bounds__(kSmallSort)
+    small_sort_kernel(K* keys, V* vals, int n, K mask, int has_vals) {
+  __shared__ K sk[kSmallSort];   // sort keys, permuted by the network
+  __shared__ uint16_t si[kSmallSort];
+  __shared__ K kf[kSmallSort];   // full keys, in input order
+  __shared__ V sv[kSmallSort];   // values, in input order
+  const int t = threadIdx.x;
+  int N = 1;
+  while (N < n) N <<= 1;
+  if (t < N) {
+    if (t < n) {
+      const K k = keys[t];
+      kf[t] = k;
+      sk[t] = k & mask;
+      if (has_vals) sv[t] = vals[t];
+    } else {
+      sk[t] = ~(K)0;  // padding sorts after every real key (larger index on ties)
+    }
+    si[t] = (uint16_t)t;
+  }
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      __syncthreads();
+      const int q = t ^ j;
+      if (t < N && q > t) {
+        const bool up = (t & k) == 0;
+        const K a = sk[t], b = sk[q];
+        const uint16_t ia = si[t], ib = si[q];
+        const bool gt = a > b || (a == b && ia > ib);
+        if (gt == up) {
+          sk[t] = b;
+          sk[q] = a;
+          si[t] = ib;
+          si[q] = ia;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (t < n) {
+    keys[t] = kf[si[t]];
+    if (has_vals) vals[t] = sv[si[t]];
+  }
+}
+
 template <class K, class V>
 int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
                     int bits) {
   if (n <= 1) return LGC_OK;
   cudaStream_t st = ctx->stream;
+  if (n <= kSmallSort) {
+    const K mask = bits >= (int)(8 * sizeof(K)) ? ~(K)0 : (K)((((K)1) << bits) - 1);
+    small_sort_kernel<K, V><<<1, kSmallSort, 0, st>>>(keys, vals, (int)n, mask,
+                                                       vals != nullptr);
+    LGC_COUNT_LAUNCH(ctx);
+    return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
+  }
   const int64_t ntiles = ceil_div(n, kTile);
   int64_t* hist = nullptr;
   LGC_TRY(dalloc_t(ctx, &hist, (size_t)kRadix * ntiles));

@@ -61,12 +61,20 @@ __global__ void sweep_keys_kernel(const int32_t* __restrict__ idx, const double*
 
 // The rank set: a dense int32 array indexed by vertex id (0 = not in S_N)
 // when the support is a sizeable part of the graph, else a hash table.
-__global__ void rank_insert_kernel(const int32_t* __restrict__ order, int64_t N, Table T,
+// Entries n0 > i >= N (not in the support, sorted last) get d_i = 0, so the
+// prefix sums over all n0 entries equal those over the N swept ones.
+__global__ void rank_insert_kernel(const int32_t* __restrict__ order, int64_t n0,
+                                   const unsigned long long* __restrict__ dN, Table T,
                                    int32_t* __restrict__ dense_rank,
                                    const int32_t* __restrict__ deg, int64_t* __restrict__ d_i,
                                    int* err) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+  const int64_t N = (int64_t)*dN;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n0;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (i >= N) {
+      d_i[i] = 0;
+      continue;
+    }
     const int32_t v = order[i];
     if (dense_rank) {
       dense_rank[v] = (int32_t)(i + 1);
@@ -105,12 +113,14 @@ __device__ inline int64_t upper_bound_excl(const int64_t* a, int64_t n, int64_t 
 __global__ void __launch_bounds__(kBlock)
     sweep_cross_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                        const int32_t* __restrict__ order, const int64_t* __restrict__ vol,
-                       int64_t N, int64_t V, Table T, const int32_t* __restrict__ dense_rank,
-                       int32_t* __restrict__ before) {
+                       const unsigned long long* __restrict__ dN,
+                       const int64_t* __restrict__ dV, Table T,
+                       const int32_t* __restrict__ dense_rank, int32_t* __restrict__ before) {
   __shared__ int64_t s_vol[kTile];  // inclusive vol of the tile's sources
   __shared__ int64_t s_off[kTile];
   __shared__ int32_t s_cnt[kTile];
   __shared__ int64_t s_i0, s_i1;
+  const int64_t N = (int64_t)*dN, V = *dV;
   const int64_t ntiles = (V + kTile - 1) / kTile;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTile, e1 = min(V, e0 + kTile);
@@ -201,7 +211,9 @@ __device__ inline Best block_best(Best b) {
 }
 
 __global__ void argmin_kernel(const int64_t* __restrict__ cut, const int64_t* __restrict__ vol,
-                              int64_t N, int64_t two_m, Best* __restrict__ out) {
+                              const unsigned long long* __restrict__ dN, int64_t two_m,
+                              Best* __restrict__ out) {
+  const int64_t N = (int64_t)*dN;
   Best b{0, 0, -1};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -454,66 +466,65 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
     LGC_CUDA_TRY(cudaGetLastError());
     // S2
     if ((status = radix_sort_u64_i32(ctx, key, id, key2, id2, n0, 64)) != LGC_OK) break;
-    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, misc, 32, cudaMemcpyDeviceToHost, s));
-    LGC_CUDA_TRY(cudaStreamSynchronize(s));
-    if (*(int*)(ctx->h_scratch + 3) != 0) {
-      status = LGC_EINVAL;  // an entry is not a vertex of degree >= 1
-      break;
-    }
-    N = ctx->h_scratch[0];
-    if (N == 0) break;
-    // S3, S4: ranks in a dense array when the support is a sizeable part of
-    // the graph (one 4-byte read per edge in S5), else in a hash table
-    const bool dense_rank = N >= g->n / 64 && g->n >= 1024;
+    // S3, S4 over all n0 entries: the N = misc[0] positive ones come first
+    // and the rest weigh nothing, so no count is read back mid-call.  Ranks
+    // in a dense array when the input is a sizeable part of the graph (one
+    // 4-byte read per edge in S5), else in a hash table.
+    const bool dense_rank = n0 >= g->n / 64 && g->n >= 1024;
     if (dense_rank) {
       if ((status = dalloc_t(ctx, &drank, g->n)) != LGC_OK) break;
       LGC_CUDA_TRY(cudaMemsetAsync(drank, 0, 4 * g->n, s));
-    } else if ((status = table_create(ctx, &T, 2 * N, false)) != LGC_OK) {
+    } else if ((status = table_create(ctx, &T, 2 * n0, false)) != LGC_OK) {
       break;
     }
-    if ((status = dalloc_t(ctx, &d_i, N)) != LGC_OK) break;
-    if ((status = dalloc_t(ctx, &vol, N)) != LGC_OK) break;
-    if ((status = dalloc_t(ctx, &delta, N)) != LGC_OK) break;
-    if ((status = dalloc_t(ctx, &before, N)) != LGC_OK) break;
-    LGC_CUDA_TRY(cudaMemsetAsync(before, 0, 4 * N, s));
+    if ((status = dalloc_t(ctx, &d_i, n0)) != LGC_OK) break;
+    if ((status = dalloc_t(ctx, &vol, n0)) != LGC_OK) break;
+    if ((status = dalloc_t(ctx, &delta, n0)) != LGC_OK) break;
+    if ((status = dalloc_t(ctx, &before, n0)) != LGC_OK) break;
+    LGC_CUDA_TRY(cudaMemsetAsync(before, 0, 4 * n0, s));
     LGC_CUDA_TRY(cudaMemsetAsync(&ctx->d_counters->err, 0, sizeof(int), s));
-    rank_insert_kernel<<<grid_for(N), kBlock, 0, s>>>(id, N, T, drank, g->deg, d_i,
-                                                       &ctx->d_counters->err);
+    const unsigned long long* dN = (const unsigned long long*)misc;
+    rank_insert_kernel<<<grid, kBlock, 0, s>>>(id, n0, dN, T, drank, g->deg, d_i,
+                                                &ctx->d_counters->err);
     LGC_COUNT_LAUNCH(ctx);
-    if ((status = scan_i64(ctx, d_i, vol, N, true, misc + 1)) != LGC_OK) break;
-    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, misc + 1, 8, cudaMemcpyDeviceToHost, s));
-    LGC_CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t V = ctx->h_scratch[0];
-    // S5
-    if (V > 0) {
-      int64_t tiles = ceil_div(V, kTile);
-      int eg = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+    if ((status = scan_i64(ctx, d_i, vol, n0, true, misc + 1)) != LGC_OK) break;
+    // S5, edge-balanced over V = misc[1] edges with a grid sized for the
+    // largest possible V (the kernel loops over the tiles that exist)
+    {
       // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
-      ProfScope ps(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
-      sweep_cross_kernel<<<eg, kBlock, 0, s>>>(g->off, g->col, id, vol, N, V, T, drank, before);
+      ProfScope ps(ctx, LGC_PROF_SWEEP, 0.0);
+      sweep_cross_kernel<<<152 * 16, kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1, T,
+                                                      drank, before);
       LGC_COUNT_LAUNCH(ctx);
     }
-    sweep_delta_kernel<<<grid_for(N), kBlock, 0, s>>>(d_i, before, N, delta);
+    sweep_delta_kernel<<<grid, kBlock, 0, s>>>(d_i, before, n0, delta);
     LGC_COUNT_LAUNCH(ctx);
     // S6
-    if ((status = scan_i64(ctx, delta, delta, N, true, nullptr)) != LGC_OK) break;
+    if ((status = scan_i64(ctx, delta, delta, n0, true, nullptr)) != LGC_OK) break;
     // S7
-    int ag = grid_for(N);
+    int ag = grid;
     if (ag > 1024) ag = 1024;
     if ((status = dalloc_t(ctx, &parts, ag)) != LGC_OK) break;
     if ((status = dalloc_t(ctx, &best, 1)) != LGC_OK) break;
-    argmin_kernel<<<ag, kBlock, 0, s>>>(delta, vol, N, g->nnz, parts);
+    argmin_kernel<<<ag, kBlock, 0, s>>>(delta, vol, dN, g->nnz, parts);
     LGC_COUNT_LAUNCH(ctx);
     argmin_final_kernel<<<1, kBlock, 0, s>>>(parts, ag, vol, best, misc + 2);
     LGC_COUNT_LAUNCH(ctx);
     LGC_CUDA_TRY(cudaGetLastError());
     LGC_CUDA_TRY(cudaMemcpyAsync(&hb, best, sizeof(Best), cudaMemcpyDeviceToHost, s));
-    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch + 2, misc + 2, 8, cudaMemcpyDeviceToHost, s));
-    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch + 3, &ctx->d_counters->err, 4,
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, misc, 32, cudaMemcpyDeviceToHost, s));
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch + 4, &ctx->d_counters->err, 4,
                                  cudaMemcpyDeviceToHost, s));
     LGC_CUDA_TRY(cudaStreamSynchronize(s));
-    if (*(int32_t*)(ctx->h_scratch + 3) & kErrTableFull) status = LGC_ETABLEFULL;
+    if (*(int*)(ctx->h_scratch + 3) != 0) {
+      status = LGC_EINVAL;  // an entry is not a vertex of degree >= 1
+      break;
+    }
+    if (*(int32_t*)(ctx->h_scratch + 4) & kErrTableFull) status = LGC_ETABLEFULL;
+    N = ctx->h_scratch[0];
     best_vol = ctx->h_scratch[2];
+    if (ctx->profile && !ctx->prof_pending.empty())
+      ctx->prof_pending.back().bytes = 12.0 * (double)ctx->h_scratch[1] + 24.0 * (double)N;
   } while (0);
   if (status == LGC_OK) {
     ClusterBox* b = new (std::nothrow) ClusterBox();

@@ -110,6 +110,7 @@ SIGNATURES = {
     "lgc_rand_hkpr_endpoints": (c_int, [_P, _P, c_int64]),
     "lgc_sweep": (c_int, [_P, POINTER(Svec), POINTER(POINTER(Cluster))]),
     "lgc_sweep_batch": (c_int, [_P, c_int64, _P, _P]),
+    "lgc_graph_autotune": (c_int, [_P, POINTER(c_int)]),
     "lgc_get_trace": (c_int, [_P, POINTER(c_int64), _P, c_int64, _P, c_int64]),
     "lgc_prnibble_residual": (c_int, [_P, POINTER(POINTER(Svec))]),
     "lgc_submit": (c_int, [_P, _P, POINTER(Request), POINTER(c_uint64)]),
@@ -129,6 +130,7 @@ OPT_PROFILE = 5
 OPT_TABLE_FORM = 6
 OPT_PULL = 7
 OPT_DEVICE_ROUNDS = 8
+OPT_PULL_BATCH = 9
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}
@@ -282,6 +284,13 @@ class Graph:
         self.n = n
         self.nnz = lib.lgc_graph_num_entries(h)
         ctx._own(self)
+
+    def autotune(self) -> int:
+        """lgc_graph_autotune: times the heavy-vertex pull gather's batch depths
+        on this graph and keeps the fastest; returns it."""
+        b = c_int()
+        _check(load().lgc_graph_autotune(self.handle, byref(b)), "lgc_graph_autotune")
+        return b.value
 
     def close(self):
         if getattr(self, "handle", None):

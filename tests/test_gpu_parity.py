@@ -415,3 +415,36 @@ def test_prnibble_device_rounds_round_limit(ctx_notrace):
             assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
     finally:
         g.close()
+
+
+# ---------------------------------------------------------------------------
+# Heavy-vertex pull gather: every batch depth gives the same (exact) sums, and
+# the autotuner picks one of them.
+# ---------------------------------------------------------------------------
+def test_pull_batch_depths_bit_identical(ctx_notrace):
+    c = ctx_notrace
+    off, col = GRAPHS["rmat16"]()
+    g = lgc.Graph(c, off, col)
+    c.set_option(lgc.OPT_DEVICE_ROUNDS, 0)
+    c.set_option(lgc.OPT_PULL, 2)  # every round a pull round: no atomics decide the order
+    try:
+        x = inputs.config1_seed(off, col)
+        ref = oracle.prnibble(off, col, x, 0.01, 1e-6)
+        res = []
+        for b in (4, 8, 16):
+            c.set_option(lgc.OPT_PULL_BATCH, b)
+            p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
+            assert (st.rounds, st.pushed_edges) == (ref.rounds, ref.pushed_edges)
+            assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+            res.append(p)
+        for p in res[1:]:
+            assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
+        c.set_option(lgc.OPT_PULL_BATCH, 0)
+        assert g.autotune() in (4, 8, 16)
+        p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
+        assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
+    finally:
+        c.set_option(lgc.OPT_PULL_BATCH, 0)
+        c.set_option(lgc.OPT_PULL, 0)
+        c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
+        g.close()
