@@ -14,7 +14,10 @@
  *    lgc_poll also returns LGC_PENDING (1).  Nothing aborts the process.
  *  - Inputs are copied; the library keeps no caller pointer after a call
  *    returns.  Outputs (lgc_svec, lgc_cluster, lgc_result) are owned by the
- *    library and released with the matching *_free function.
+ *    library and released with the matching *_free function.  Host outputs
+ *    live in page-locked memory from a process-wide pool and stay valid after
+ *    their context is destroyed; device outputs must be released before
+ *    their context.
  *  - Graphs are undirected and unweighted: CSR with int64 offsets[n+1] and
  *    int32 cols[offsets[n]], every edge stored in both directions, each
  *    adjacency list sorted ascending, no self loops, no duplicate edges

@@ -529,8 +529,8 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
   double *val = nullptr, *val2 = nullptr;
   int32_t* idx = nullptr;
   std::vector<int64_t> hstart(B + 1);
-  std::vector<int32_t> hidx;
-  std::vector<double> hval;
+  int32_t* hidx = nullptr;
+  double* hval = nullptr;
   int st = LGC_OK;
   do {
     if ((st = dalloc_t(ctx, &d_tabs, B)) || (st = dalloc_t(ctx, &d_capoff, B + 1)) ||
@@ -574,10 +574,15 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
                        &p_out[b]);
       break;
     }
-    hidx.resize(m ? m : 1);
-    hval.resize(m ? m : 1);
-    if ((m && (cudaMemcpyAsync(hidx.data(), idx, 4 * m, cudaMemcpyDeviceToHost, s) ||
-               cudaMemcpyAsync(hval.data(), val, 8 * m, cudaMemcpyDeviceToHost, s))) ||
+    // page-locked staging: the copies run at the link's speed
+    hidx = (int32_t*)host_alloc(4 * (m ? m : 1));
+    hval = (double*)host_alloc(8 * (m ? m : 1));
+    if (!hidx || !hval) {
+      st = LGC_ENOMEM;
+      break;
+    }
+    if ((m && (cudaMemcpyAsync(hidx, idx, 4 * m, cudaMemcpyDeviceToHost, s) ||
+               cudaMemcpyAsync(hval, val, 8 * m, cudaMemcpyDeviceToHost, s))) ||
         cudaStreamSynchronize(s)) {
       st = LGC_ECUDA;
       break;
@@ -592,23 +597,25 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
       box->ctx = ctx;
       box->pub.nnz = k;
       box->pub.on_device = 0;
-      box->pub.idx = (int32_t*)malloc(4 * (k ? k : 1));
-      box->pub.val = (double*)malloc(8 * (k ? k : 1));
+      box->pub.idx = (int32_t*)host_alloc(4 * (k ? k : 1));
+      box->pub.val = (double*)host_alloc(8 * (k ? k : 1));
       if (!box->pub.idx || !box->pub.val) {
-        free(box->pub.idx);
-        free(box->pub.val);
+        host_free(box->pub.idx);
+        host_free(box->pub.val);
         delete box;
         st = LGC_ENOMEM;
         break;
       }
-      memcpy(box->pub.idx, hidx.data() + a, 4 * k);
-      memcpy(box->pub.val, hval.data() + a, 8 * k);
+      memcpy(box->pub.idx, hidx + a, 4 * k);
+      memcpy(box->pub.val, hval + a, 8 * k);
       p_out[b] = &box->pub;
     }
   } while (0);
   for (void* q : {(void*)d_tabs, (void*)d_capoff, (void*)flag, (void*)pos, (void*)kept,
                   (void*)start, (void*)key, (void*)key2, (void*)val, (void*)val2, (void*)idx})
     dfree(ctx, q);
+  host_free(hidx);
+  host_free(hval);
   return st;
 }
 

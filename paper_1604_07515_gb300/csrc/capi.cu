@@ -650,8 +650,8 @@ void lgc_svec_free(lgc_svec* p) {
     dfree(b->ctx, p->idx);
     dfree(b->ctx, p->val);
   } else {
-    free(p->idx);
-    free(p->val);
+    host_free(p->idx);
+    host_free(p->val);
   }
   delete b;
 }
@@ -660,7 +660,7 @@ void lgc_cluster_free(lgc_cluster* c) {
   if (!c) return;
   ClusterBox* b = (ClusterBox*)c;
   if (c->on_device) dfree(b->ctx, c->ids);
-  else free(c->ids);
+  else host_free(c->ids);
   delete b;
 }
 

@@ -5,6 +5,8 @@
 
 #include <new>
 
+#include <unordered_map>
+
 #include "common.cuh"
 #include "prim.cuh"
 
@@ -27,6 +29,7 @@ int validate_seed(lgc_ctx* ctx, lgc_graph* g, int32_t x, int64_t* dx) {
 int ctx_init(lgc_ctx* ctx, int device, cudaStream_t stream) {
   ctx->device = device;
   LGC_CUDA_TRY(cudaSetDevice(device));
+  LGC_CUDA_TRY(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device));
   if (stream) {
     ctx->stream = stream;
     ctx->own_stream = false;
@@ -417,6 +420,67 @@ int table_extract_sorted(lgc_ctx* ctx, const Table& T, const double* vals, int64
   return LGC_OK;
 }
 
+namespace {
+struct HostPool {
+  std::mutex mu;
+  std::unordered_map<void*, std::pair<size_t, bool>> info;  // block -> (size class, pinned)
+  std::map<size_t, std::vector<void*>> spare;
+  size_t spare_bytes = 0;
+};
+// never destroyed: host results may be freed while the process exits
+HostPool& host_pool() {
+  static HostPool* p = new HostPool();
+  return *p;
+}
+constexpr size_t kHostSpareMax = size_t{4} << 30;
+}  // namespace
+
+void* host_alloc(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  HostPool& P = host_pool();
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    auto it = P.spare.find(c);
+    if (it != P.spare.end() && !it->second.empty()) {
+      void* q = it->second.back();
+      it->second.pop_back();
+      P.spare_bytes -= c;
+      return q;
+    }
+  }
+  void* q = nullptr;
+  bool pinned = true;
+  if (cudaHostAlloc(&q, c, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    q = malloc(c);
+    pinned = false;
+    if (!q) return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.info[q] = {c, pinned};
+  return q;
+}
+
+void host_free(void* q) {
+  if (!q) return;
+  HostPool& P = host_pool();
+  std::unique_lock<std::mutex> lk(P.mu);
+  auto it = P.info.find(q);
+  if (it == P.info.end()) return;  // not ours
+  const size_t c = it->second.first;
+  const bool pinned = it->second.second;
+  if (pinned && P.spare_bytes + c <= kHostSpareMax) {
+    P.spare[c].push_back(q);
+    P.spare_bytes += c;
+    return;
+  }
+  P.info.erase(it);
+  lk.unlock();
+  if (pinned) cudaFreeHost(q);
+  else free(q);
+}
+
 int make_svec(lgc_ctx* ctx, const int32_t* d_idx, const double* d_val, int64_t nnz,
               bool on_device, lgc_svec** out) {
   *out = nullptr;
@@ -440,11 +504,11 @@ int make_svec(lgc_ctx* ctx, const int32_t* d_idx, const double* d_val, int64_t n
                                    ctx->stream));
     }
   } else {
-    b->pub.idx = (int32_t*)malloc(4 * (nnz ? nnz : 1));
-    b->pub.val = (double*)malloc(8 * (nnz ? nnz : 1));
+    b->pub.idx = (int32_t*)host_alloc(4 * (nnz ? nnz : 1));
+    b->pub.val = (double*)host_alloc(8 * (nnz ? nnz : 1));
     if (!b->pub.idx || !b->pub.val) {
-      free(b->pub.idx);
-      free(b->pub.val);
+      host_free(b->pub.idx);
+      host_free(b->pub.val);
       delete b;
       return LGC_ENOMEM;
     }

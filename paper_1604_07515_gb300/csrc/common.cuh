@@ -195,6 +195,7 @@ struct lgc_ctx {
   bool trace = false;
   int table_form = 0;   // LGC_OPT_TABLE_FORM
   int pull_policy = 0;  // LGC_OPT_PULL: 0 automatic, 1 never, 2 every deterministic round
+  int sms = 152;              // multiprocessors of the device
   bool device_rounds = true;  // LGC_OPT_DEVICE_ROUNDS
   int pull_batch = 0;          // LGC_OPT_PULL_BATCH: 0 = the graph's tuned value
   int64_t serve_mem_budget = 40ll << 30;
@@ -320,6 +321,13 @@ int table_grow(lgc_ctx* ctx, Table* T, int64_t new_cap, const int32_t* fv, int32
 int64_t pow2_at_least(int64_t x);
 
 // Library-owned outputs carry their context for release.
+// Host memory for results: page-locked blocks from a process-wide pool (so
+// device-to-host copies run at the link's full speed and a host result does
+// not depend on the context that made it), ordinary heap memory if
+// page-locking fails.  Freed blocks are kept for reuse, up to 4 GB.
+void* host_alloc(size_t bytes);
+void host_free(void* p);
+
 struct SvecBox {
   lgc_svec pub;
   lgc_ctx* ctx;

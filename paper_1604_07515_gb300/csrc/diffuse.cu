@@ -894,15 +894,16 @@ __global__ void tune_fill_kernel(Fx* __restrict__ shx, int64_t n, int32_t* __res
 // at a time (all column loads, then all share loads).  Every bitmap word of
 // qbits is written here (by ballot, heavy vertices' bits zero); the heavy
 // kernel, launched after this one, ORs its vertices in.
-__global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
-                                     const int32_t* __restrict__ col, int64_t n,
-                                     const Fx* __restrict__ shx,
-                                     const int32_t* __restrict__ range, int g, Table D, double c,
-                                     int fmode, uint32_t* __restrict__ qbits, Counters* C) {
+__device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
+                                          const int64_t* __restrict__ off,
+                                          const int32_t* __restrict__ col, int64_t n,
+                                          const Fx* __restrict__ shx,
+                                          const int32_t* __restrict__ range, int g, Table D,
+                                          double c, int fmode, uint32_t* __restrict__ qbits,
+                                          Counters* C) {
   const int L = round_scale(range, g);
   const int64_t words = (n + 31) / 32;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words * 32;
-       base += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = bid * blockDim.x; base < words * 32; base += nblk * blockDim.x) {
     const int64_t w = base + threadIdx.x;
     bool q = false;
     int ins = 0;
@@ -937,6 +938,8 @@ __global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
         }
       }
     }
+    // every bitmap word is written whole here (the heavy vertices' bits
+    // zero); the heavy gather, launched after this one, ORs its vertices in
     const unsigned word = __ballot_sync(0xffffffffu, q);
     if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
       qbits[(base + threadIdx.x) >> 5] = word;
@@ -954,8 +957,9 @@ __global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
 // that completes the vertex's last item finishes it and resets the
 // accumulators for the next round.
 template <int BATCH>
-__global__ void __launch_bounds__(kBlock)
-    pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+__device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
+                                          const int64_t* __restrict__ off,
+                                          const int32_t* __restrict__ col,
                          const PullItem* __restrict__ items, int64_t nitems,
                          const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
                          Table D, double c, int fmode, uint32_t* __restrict__ qbits,
@@ -963,8 +967,8 @@ __global__ void __launch_bounds__(kBlock)
                          int32_t* __restrict__ htouch, Counters* C) {
   const int L = round_scale(range, g);
   const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp0 = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (nblk * blockDim.x) >> 5;
   for (int64_t it = warp0; it < nitems; it += nwarps) {
     const PullItem I = items[it];
     const int32_t w = I.w;
@@ -1037,6 +1041,26 @@ __global__ void __launch_bounds__(kBlock)
       htouch[h] = 0;
     }
   }
+}
+
+template <int BATCH>
+__global__ void __launch_bounds__(kBlock)
+    pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                         const PullItem* __restrict__ items, int64_t nitems,
+                         const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
+                         Table D, double c, int fmode, uint32_t* __restrict__ qbits,
+                         Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
+                         int32_t* __restrict__ htouch, Counters* C) {
+  pull_heavy_fx_body<BATCH>(blockIdx.x, gridDim.x, off, col, items, nitems, shx, range, g, D, c,
+                            fmode, qbits, hacc, hcnt, htouch, C);
+}
+
+__global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
+                                     const int32_t* __restrict__ col, int64_t n,
+                                     const Fx* __restrict__ shx,
+                                     const int32_t* __restrict__ range, int g, Table D, double c,
+                                     int fmode, uint32_t* __restrict__ qbits, Counters* C) {
+  pull_light_fx_body(blockIdx.x, gridDim.x, off, col, n, shx, range, g, D, c, fmode, qbits, C);
 }
 
 // Ordered compaction of a vertex bitmap into a frontier (ascending id), with
@@ -1491,27 +1515,32 @@ struct PushWork {
       if (det) {
         pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
                                                  ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+        if (g->nheavy > 0) {
+          int64_t hb = ceil_div(g->nheavy, kBlock / 32);
+          pull_heavy_det_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
+              g->off, g->col, g->heavy, g->nheavy, psh.ptr, D, c, fmode, pq.ptr,
+              ctx->d_counters);
+          LGC_COUNT_LAUNCH(ctx);
+        }
       } else {
+        // light vertices (writing every bitmap word), then the heavy items
+        // (ORing their vertices in); the two in one grid measured slower
         pull_light_fx_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, pshx.ptr, prange.ptr, gb,
                                                     D, c, fmode, pq.ptr, ctx->d_counters);
-      }
-      LGC_COUNT_LAUNCH(ctx);
-      if (g->nheavy > 0 && det) {
-        int64_t hb = ceil_div(g->nheavy, kBlock / 32);
-        pull_heavy_det_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
-            g->off, g->col, g->heavy, g->nheavy, psh.ptr, D, c, fmode, pq.ptr, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
-      } else if (g->nheavy > 0) {
-        int64_t hb = ceil_div(g->nitems, kBlock / 32);
-        const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
-        const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
-        auto heavy = batch == 16 ? pull_heavy_fx_kernel<16>
-                     : batch == 4 ? pull_heavy_fx_kernel<4>
-                                  : pull_heavy_fx_kernel<kPullBatch>;
-        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr, gb,
-                                    D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
-                                    ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
+        if (g->nitems > 0) {
+          const int64_t hb = ceil_div(g->nitems, kBlock / 32);
+          const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+          const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
+          auto heavy = batch == 16 ? pull_heavy_fx_kernel<16>
+                       : batch == 4 ? pull_heavy_fx_kernel<4>
+                                    : pull_heavy_fx_kernel<kPullBatch>;
+          heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr,
+                                      gb, D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
+                                      ctx->d_counters);
+          LGC_COUNT_LAUNCH(ctx);
+        }
       }
     }
     if (fmode != kFmNone) {

@@ -545,7 +545,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
               cudaSuccess)
             status = LGC_ECUDA;
       } else {
-        b->pub.ids = (int32_t*)malloc(4 * (size ? size : 1));
+        b->pub.ids = (int32_t*)host_alloc(4 * (size ? size : 1));
         if (!b->pub.ids) status = LGC_ENOMEM;
         else if (size) {
           if (cudaMemcpyAsync(b->pub.ids, id, 4 * size, cudaMemcpyDeviceToHost, s) !=
@@ -592,7 +592,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
   std::vector<int64_t> nbeg(B + 1, 0);
   std::vector<Best> hbest(B, Best{0, 0, -1});
   std::vector<int64_t> hbvol(B, 0);
-  std::vector<int32_t> hord;
+  int32_t* hord = nullptr;
   int32_t* cidx = nullptr;  // host vectors, concatenated on the device
   double* cval = nullptr;
   SweepIn* d_in = nullptr;
@@ -746,8 +746,12 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
         break;
       }
       if (!ctx->result_on_device) {
-        hord.resize(N);
-        if (cudaMemcpyAsync(hord.data(), order, 4 * N, cudaMemcpyDeviceToHost, s)) {
+        hord = (int32_t*)host_alloc(4 * N);
+        if (!hord) {
+          st = LGC_ENOMEM;
+          break;
+        }
+        if (cudaMemcpyAsync(hord, order, 4 * N, cudaMemcpyDeviceToHost, s)) {
           st = LGC_ECUDA;
           break;
         }
@@ -782,9 +786,9 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
             cudaMemcpyAsync(box->pub.ids, order + nbeg[b], 4 * size, cudaMemcpyDeviceToDevice, s))
           st = LGC_ECUDA;
       } else {
-        box->pub.ids = (int32_t*)malloc(4 * (size ? size : 1));
+        box->pub.ids = (int32_t*)host_alloc(4 * (size ? size : 1));
         if (!box->pub.ids) st = LGC_ENOMEM;
-        else if (size) memcpy(box->pub.ids, hord.data() + nbeg[b], 4 * size);
+        else if (size) memcpy(box->pub.ids, hord + nbeg[b], 4 * size);
       }
       if (st == LGC_OK) out[b] = &box->pub;
       else lgc_cluster_free(&box->pub);
@@ -802,6 +806,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
                   (void*)sk2, (void*)d_i, (void*)vol, (void*)cut, (void*)d_bvol, (void*)d_best,
                   (void*)d_tabs, (void*)slab, (void*)d_err})
     dfree(ctx, q);
+  host_free(hord);
   return st;
 }
 

@@ -305,9 +305,43 @@ class Graph:
             pass
 
 
+class _HostResult:
+    """Owns a library host result (page-locked memory from the library's
+    pool); the numpy views of its arrays keep it alive and the last one to go
+    releases it."""
+
+    def __init__(self, ptr, free_name: str):
+        self._ptr = ptr
+        self._free = free_name
+
+    def __del__(self):
+        try:
+            if self._ptr is not None:
+                getattr(load(), self._free)(self._ptr)
+                self._ptr = None
+        except Exception:
+            pass
+
+
+class _View:
+    """Array interface over library memory; numpy keeps it as the array's base."""
+
+    def __init__(self, addr: int, n: int, typestr: str, owner: _HostResult):
+        self.__array_interface__ = {"shape": (n,), "typestr": typestr,
+                                    "data": (addr, False), "version": 3}
+        self.owner = owner
+
+
+def _host_array(addr, n: int, dtype, owner: _HostResult) -> np.ndarray:
+    if n == 0:
+        return np.zeros(0, dtype)
+    return np.asarray(_View(addr, n, np.dtype(dtype).str, owner))
+
+
 class SparseVec:
-    """A library sparse vector.  Host results are copied to numpy (idx, val)
-    and released at once; device results keep the library handle."""
+    """A library sparse vector.  Host results are numpy views (idx, val) of
+    the library's page-locked result memory, released when the last view
+    goes; device results keep the library handle."""
 
     def __init__(self, ptr, ctx: Context | None = None):
         self._ptr = ptr
@@ -315,11 +349,9 @@ class SparseVec:
         self.nnz = s.nnz
         self.on_device = bool(s.on_device)
         if not self.on_device:
-            self.idx = (np.ctypeslib.as_array((c_int32 * s.nnz).from_address(s.idx)).copy()
-                        if s.nnz else np.zeros(0, np.int32))
-            self.val = (np.ctypeslib.as_array((c_double * s.nnz).from_address(s.val)).copy()
-                        if s.nnz else np.zeros(0))
-            load().lgc_svec_free(ptr)
+            owner = _HostResult(ptr, "lgc_svec_free")
+            self.idx = _host_array(s.idx, s.nnz, np.int32, owner)
+            self.val = _host_array(s.val, s.nnz, np.float64, owner)
             self._ptr = None
         elif ctx is not None:
             self._ctx = ctx  # keeps the context alive while this result is
@@ -369,9 +401,7 @@ class ClusterResult:
         self.on_device = bool(c.on_device)
         self._ptr = ptr
         if not self.on_device:
-            self.ids = (np.ctypeslib.as_array((c_int32 * c.size).from_address(c.ids)).copy()
-                        if c.size else np.zeros(0, np.int32))
-            load().lgc_cluster_free(ptr)
+            self.ids = _host_array(c.ids, c.size, np.int32, _HostResult(ptr, "lgc_cluster_free"))
             self._ptr = None
         elif ctx is not None:
             self._ctx = ctx
