@@ -108,6 +108,57 @@ __global__ void items_fill_kernel(const int32_t* __restrict__ heavy, int64_t nh,
   }
 }
 
+__global__ void gather_off_kernel(const int32_t* __restrict__ ids, int64_t k,
+                                  const int64_t* __restrict__ off, int64_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = off[ids[i]];
+}
+
+// The vertices of degree > kDetBig and their 256-edge segments (built on the
+// host from the degree copy; only their list starts are read back).
+int build_big_segments(lgc_ctx* ctx, lgc_graph* g) {
+  cudaStream_t s = ctx->stream;
+  std::vector<int32_t> bw;
+  for (int64_t v = 0; v < g->n; v++)
+    if (g->hdeg[v] > kDetBig) bw.push_back((int32_t)v);
+  g->nbig = (int64_t)bw.size();
+  if (g->nbig == 0) return LGC_OK;
+  std::vector<int64_t> starts(g->nbig), seg0(g->nbig + 1, 0);
+  int64_t* d_starts = nullptr;
+  LGC_TRY(dalloc_t(ctx, &g->big_w, g->nbig));
+  LGC_TRY(dalloc_t(ctx, &d_starts, g->nbig));
+  LGC_CUDA_TRY(cudaMemcpyAsync(g->big_w, bw.data(), 4 * g->nbig, cudaMemcpyHostToDevice, s));
+  gather_off_kernel<<<grid_for(g->nbig), kBlock, 0, s>>>(g->big_w, g->nbig, g->off, d_starts);
+  LGC_COUNT_LAUNCH(ctx);
+  LGC_CUDA_TRY(cudaMemcpyAsync(starts.data(), d_starts, 8 * g->nbig, cudaMemcpyDeviceToHost, s));
+  LGC_CUDA_TRY(cudaStreamSynchronize(s));
+  dfree(ctx, d_starts);
+  for (int64_t b = 0; b < g->nbig; b++)
+    seg0[b + 1] = seg0[b] + (g->hdeg[bw[b]] + kDetSeg - 1) / kDetSeg;
+  g->nsegs = seg0[g->nbig];
+  std::vector<DetSeg> segs(g->nsegs);
+  for (int64_t b = 0; b < g->nbig; b++) {
+    const int64_t d = g->hdeg[bw[b]];
+    for (int64_t k = 0; k < seg0[b + 1] - seg0[b]; k++) {
+      DetSeg& S = segs[seg0[b] + k];
+      S = DetSeg{};
+      S.beg = starts[b] + k * kDetSeg;
+      S.w = bw[b];
+      S.len = (int32_t)std::min<int64_t>(kDetSeg, d - k * kDetSeg);
+      S.big = (int32_t)b;
+    }
+  }
+  LGC_TRY(dalloc_t(ctx, &g->big_seg0, g->nbig + 1));
+  LGC_TRY(dalloc_t(ctx, &g->segs, g->nsegs));
+  LGC_CUDA_TRY(cudaMemcpyAsync(g->big_seg0, seg0.data(), 8 * (g->nbig + 1),
+                               cudaMemcpyHostToDevice, s));
+  LGC_CUDA_TRY(cudaMemcpyAsync(g->segs, segs.data(), sizeof(DetSeg) * g->nsegs,
+                               cudaMemcpyHostToDevice, s));
+  LGC_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  return LGC_OK;
+}
+
 // The vertices of degree > kPullLight, ascending, for pull rounds, and their
 // adjacency cut into work items.
 int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
@@ -445,6 +496,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
       break;
     }
     st = build_heavy_list(ctx, g);
+    if (st == LGC_OK) st = build_big_segments(ctx, g);
   } while (0);
   if (st != LGC_OK) {
     dfree(ctx, g->off);
@@ -452,6 +504,9 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     dfree(ctx, g->deg);
     dfree(ctx, g->heavy);
     dfree(ctx, g->items);
+    dfree(ctx, g->big_w);
+    dfree(ctx, g->big_seg0);
+    dfree(ctx, g->segs);
     cudaStreamSynchronize(s);
     delete g;
     return st;
@@ -478,6 +533,9 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->deg);
   dfree(ctx, g->heavy);
   dfree(ctx, g->items);
+  dfree(ctx, g->big_w);
+  dfree(ctx, g->big_seg0);
+  dfree(ctx, g->segs);
   cudaStreamSynchronize(ctx->stream);
   delete g;
 }

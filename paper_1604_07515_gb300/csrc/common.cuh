@@ -234,6 +234,14 @@ struct __align__(32) PullItem {
   int64_t pad;
 };
 
+// A 256-edge segment of a big vertex's list (deterministic pull rounds):
+// edges [beg, beg + len) of vertex w, the big vertex's index `big`.
+struct __align__(32) DetSeg {
+  int64_t beg;
+  int32_t w, len, big, pad0;
+  int64_t pad1;
+};
+
 struct lgc_graph {
   lgc_ctx* ctx = nullptr;
   int64_t n = 0, nnz = 0;
@@ -251,12 +259,22 @@ struct lgc_graph {
   // load)
   PullItem* items = nullptr;
   int64_t nitems = 0;
+  // vertices of degree > kDetBig, whose deterministic fold runs segment-
+  // parallel: their ids, the first of their segments (nbig + 1 prefix), and
+  // the 256-edge segments
+  int32_t* big_w = nullptr;
+  int64_t* big_seg0 = nullptr;
+  int64_t nbig = 0;
+  DetSeg* segs = nullptr;
+  int64_t nsegs = 0;
 };
 
 namespace lgc {
 // A pull round handles vertices of degree <= kPullLight with one thread each
 // and the rest in work items of at most kPullItem edges.
 constexpr int kPullLight = 32;
+constexpr int kDetBig = 4096;  // longer lists fold segment-parallel in deterministic mode
+constexpr int kDetSeg = 256;
 constexpr int kPullItem = 4096;
 }  // namespace lgc
 

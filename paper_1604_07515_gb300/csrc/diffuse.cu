@@ -787,6 +787,7 @@ __global__ void __launch_bounds__(kBlock)
   for (int64_t h = warp0; h < nheavy; h += nwarps) {
     const int32_t w = heavy[h];
     const int64_t o0 = off[w], d = off[w + 1] - o0;
+    if (d > kDetBig) continue;  // folded segment-parallel (det_seg_* kernels)
     const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
     double acc = present ? D.dval[w] : 0.0;  // >= +0
     bool touched = present;
@@ -810,6 +811,152 @@ __global__ void __launch_bounds__(kBlock)
       acc = fold_batch(acc, v, lane);
     }
     if (lane == 0) pull_finish(D, w, d, acc, touched, present, c, fmode, qbits, C);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic mode, vertices of degree > kDetBig: the fold of the whole
+// list is split into 256-edge segments that are worked on in parallel.
+//  1. det_seg_sum: each segment's plain sum and whether it holds a member.
+//  2. det_seg_predict: per vertex, a running sum of the segment sums
+//     predicts the binade the fold is in at each segment's start (the fold
+//     differs from the exact prefix sum by rounding only, so the prediction
+//     misses only next to a power of two).
+//  3. det_seg_step: each segment's composed integer step (see fold_step) for
+//     its predicted binade.
+//  4. det_seg_verify: one warp per vertex walks its segments in order: when
+//     the fold's actual binade is the predicted one and the composed step
+//     keeps the value below 2^53, the step is the exact fold of the segment
+//     (the value only grows, so no intermediate value left the binade);
+//     otherwise the segment is folded element by element (fold_batch).
+// The result is the sequential fold, bit for bit.
+// ---------------------------------------------------------------------------
+__global__ void det_seg_sum_kernel(const int32_t* __restrict__ col,
+                                   const DetSeg* __restrict__ segs, int64_t nsegs,
+                                   const double* __restrict__ sh, double* __restrict__ segsum,
+                                   int32_t* __restrict__ segany) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = warp0; k < nsegs; k += nwarps) {
+    const DetSeg S = segs[k];
+    int32_t u[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) u[j] = 32 * j + lane < S.len ? col[S.beg + 32 * j + lane] : -1;
+    double x = 0.0;
+    bool mem = false;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const double v = u[j] >= 0 ? sh[u[j]] : 0.0;
+      x += v;
+      mem = mem || pull_member(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const bool any = __any_sync(0xffffffffu, mem);
+    if (lane == 0) {
+      segsum[k] = x;
+      segany[k] = any ? 1 : 0;
+    }
+  }
+}
+
+__global__ void det_seg_predict_kernel(const int32_t* __restrict__ big_w,
+                                       const int64_t* __restrict__ seg0, int64_t nbig, Table D,
+                                       const double* __restrict__ segsum,
+                                       int32_t* __restrict__ pred) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbig;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = big_w[b];
+    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
+    double acc = present ? D.dval[w] : 0.0;
+    for (int64_t k = seg0[b]; k < seg0[b + 1]; k++) {
+      pred[k] = fold_binade(acc);
+      acc += segsum[k];
+    }
+  }
+}
+
+__global__ void det_seg_step_kernel(const int32_t* __restrict__ col,
+                                    const DetSeg* __restrict__ segs, int64_t nsegs,
+                                    const double* __restrict__ sh,
+                                    const int32_t* __restrict__ pred,
+                                    FoldStep* __restrict__ step) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = warp0; k < nsegs; k += nwarps) {
+    const DetSeg S = segs[k];
+    const int bu = pred[k];
+    int32_t u[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) u[j] = 8 * lane + j < S.len ? col[S.beg + 8 * lane + j] : -1;
+    FoldStep F = {0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+      F = fold_compose(F, fold_step(u[j] >= 0 ? sh[u[j]] : 0.0, bu));
+    // ordered reduction: lane l's steps come before lane l+1's
+    for (int o = 1; o < 32; o <<= 1) {
+      FoldStep q;
+      q.g0 = __shfl_down_sync(0xffffffffu, F.g0, o);
+      q.g1 = __shfl_down_sync(0xffffffffu, F.g1, o);
+      if ((lane & (2 * o - 1)) == 0) F = fold_compose(F, q);
+    }
+    if (lane == 0) step[k] = F;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    det_seg_verify_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                          const DetSeg* __restrict__ segs, const int32_t* __restrict__ big_w,
+                          const int64_t* __restrict__ seg0, int64_t nbig,
+                          const double* __restrict__ sh, const int32_t* __restrict__ pred,
+                          const FoldStep* __restrict__ step, const int32_t* __restrict__ segany,
+                          Table D, double c, int fmode, uint32_t* __restrict__ qbits,
+                          Counters* C) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = warp0; b < nbig; b += nwarps) {
+    const int32_t w = big_w[b];
+    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
+    double acc = present ? D.dval[w] : 0.0;  // >= +0, the same in every lane
+    bool touched = present;
+    const int64_t k1 = seg0[b + 1];
+    for (int64_t k0 = seg0[b]; k0 < k1; k0 += 32) {
+      // 32 segments' predictions and steps, one per lane, walked in order
+      const int64_t kl = k0 + lane;
+      const bool ok = kl < k1;
+      const int pl = ok ? pred[kl] : 0;
+      const FoldStep sl = ok ? step[kl] : FoldStep{0, 0};
+      touched = touched || __any_sync(0xffffffffu, ok && segany[kl] != 0);
+      const int cnt = (int)min((int64_t)32, k1 - k0);
+      for (int j = 0; j < cnt; j++) {
+        const int pj = __shfl_sync(0xffffffffu, pl, j);
+        FoldStep sj;
+        sj.g0 = __shfl_sync(0xffffffffu, sl.g0, j);
+        sj.g1 = __shfl_sync(0xffffffffu, sl.g1, j);
+        const int bu = fold_binade(acc);
+        if (bu == pj) {
+          const int64_t A = fold_apply(sj, fold_int(acc));
+          if (A < kFoldTop) {
+            acc = fold_double(A, bu);
+            continue;
+          }
+        }
+        // the prediction missed or the segment leaves the binade: fold it
+        // element by element
+        const DetSeg S = segs[k0 + j];
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int pos = 8 * lane + q;
+          v[q] = pos < S.len ? sh[col[S.beg + pos]] : 0.0;
+        }
+        acc = fold_batch(acc, v, lane);
+      }
+    }
+    if (lane == 0)
+      pull_finish(D, w, off[w + 1] - off[w], acc, touched, present, c, fmode, qbits, C);
   }
 }
 
@@ -1275,6 +1422,11 @@ struct PushWork {
   DBuf<int32_t> prange;            // atomic mode: exponent range of the shares
   DBuf<Fx> phacc;                  // per heavy vertex: partial sums of its items
   DBuf<int32_t> phcnt, phtouch;    // per heavy vertex: items done, any frontier neighbour
+  // deterministic pull of big vertices: per segment sum, member flag,
+  // predicted binade, composed step
+  DBuf<double> dsum;
+  DBuf<int32_t> dany, dpred;
+  DBuf<FoldStep> dstep;
   bool pull_ready = false;
   // device-driven rounds: two frontier buffers, block sums, counters, state
   Frontier X[2];
@@ -1288,6 +1440,10 @@ struct PushWork {
     G.release(ctx);
     X[0].release(ctx);
     X[1].release(ctx);
+    dsum.release(ctx);
+    dany.release(ctx);
+    dpred.release(ctx);
+    dstep.release(ctx);
     xbsum.release(ctx);
     xcn.release(ctx);
     xst.release(ctx);
@@ -1521,6 +1677,28 @@ struct PushWork {
           pull_heavy_det_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
               g->off, g->col, g->heavy, g->nheavy, psh.ptr, D, c, fmode, pq.ptr,
               ctx->d_counters);
+          LGC_COUNT_LAUNCH(ctx);
+        }
+        if (g->nbig > 0) {  // lists longer than kDetBig, folded segment-parallel
+          LGC_TRY(dsum.reserve(ctx, g->nsegs));
+          LGC_TRY(dany.reserve(ctx, g->nsegs));
+          LGC_TRY(dpred.reserve(ctx, g->nsegs));
+          LGC_TRY(dstep.reserve(ctx, g->nsegs));
+          const int sg = (int)std::min<int64_t>(ceil_div(g->nsegs, kBlock / 32), 152 * 16);
+          det_seg_sum_kernel<<<sg, kBlock, 0, s>>>(g->col, g->segs, g->nsegs, psh.ptr, dsum.ptr,
+                                                   dany.ptr);
+          LGC_COUNT_LAUNCH(ctx);
+          det_seg_predict_kernel<<<grid_for(g->nbig), kBlock, 0, s>>>(
+              g->big_w, g->big_seg0, g->nbig, D, dsum.ptr, dpred.ptr);
+          LGC_COUNT_LAUNCH(ctx);
+          det_seg_step_kernel<<<sg, kBlock, 0, s>>>(g->col, g->segs, g->nsegs, psh.ptr, dpred.ptr,
+                                                    dstep.ptr);
+          LGC_COUNT_LAUNCH(ctx);
+          const int vg = (int)std::min<int64_t>(ceil_div(g->nbig, kBlock / 32), 152 * 16);
+          det_seg_verify_kernel<<<vg, kBlock, 0, s>>>(g->off, g->col, g->segs, g->big_w,
+                                                      g->big_seg0, g->nbig, psh.ptr, dpred.ptr,
+                                                      dstep.ptr, dany.ptr, D, c, fmode, pq.ptr,
+                                                      ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
         }
       } else {

@@ -87,3 +87,49 @@ double fxh_fold(double acc, const double* v, int n, double* seq) {
   return acc;
 }
 }
+
+extern "C" {
+// The deterministic gather's segment-parallel fold for long lists, emulated:
+// per 256-share segment a plain sum, a running sum of them predicting the
+// binade at each segment start, the segment's composed step for that
+// binade, then the in-order walk that takes the step when the binade
+// matches and the value stays below 2^53, and folds the segment element by
+// element otherwise.  *redone counts the segments folded element by element.
+double fxh_fold_segmented(double acc, const double* v, int n, int* redone) {
+  using namespace lgc;
+  const int nseg = (n + 255) / 256;
+  double buf[256];
+  double pacc = acc;
+  int* pred = new int[nseg];
+  FoldStep* st = new FoldStep[nseg];
+  for (int k = 0; k < nseg; k++) {
+    pred[k] = fold_binade(pacc);
+    double s = 0.0;
+    for (int i = 256 * k; i < n && i < 256 * k + 256; i++) s += v[i];
+    pacc += s;
+  }
+  for (int k = 0; k < nseg; k++) {
+    FoldStep F = {0, 0};
+    for (int i = 256 * k; i < n && i < 256 * k + 256; i++)
+      F = fold_compose(F, fold_step(v[i], pred[k]));
+    st[k] = F;
+  }
+  *redone = 0;
+  for (int k = 0; k < nseg; k++) {
+    const int bu = fold_binade(acc);
+    if (bu == pred[k]) {
+      const int64_t A = fold_apply(st[k], fold_int(acc));
+      if (A < kFoldTop) {
+        acc = fold_double(A, bu);
+        continue;
+      }
+    }
+    (*redone)++;
+    for (int i = 0; i < 256; i++) buf[i] = 256 * k + i < n ? v[256 * k + i] : 0.0;
+    acc = fold_batch_host(acc, buf);
+  }
+  delete[] pred;
+  delete[] st;
+  return acc;
+}
+}

@@ -171,3 +171,40 @@ def test_binade_fold_equals_sequential_fold(fx, kind):
                 xs[i] = -0.0
         got, seq = fold(fx, acc, xs)
         assert bits(got) == bits(seq), (kind, trial, got, seq)
+
+
+@pytest.mark.parametrize("kind", ["hub", "growing", "ties", "wide"])
+def test_segmented_fold_equals_sequential_fold(fx, kind):
+    """The segment-parallel fold of long lists (predicted binades, composed
+    segment steps, element-wise refold where the prediction misses or the
+    value leaves the binade) reproduces the sequential FP64 fold bit for
+    bit, and refolds only a few segments."""
+    fx.fxh_fold_segmented.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    fx.fxh_fold_segmented.restype = ctypes.c_double
+    rng = random.Random(hash(kind) & 0xFFFF)
+    for trial in range(12):
+        n = rng.choice([257, 4097, 20000, 60000])
+        acc = rng.choice([0.0, rng.random() * 1e-6])
+        if kind == "hub":
+            xs = [math.ldexp(1 + rng.random(), -30) if rng.random() < 0.7 else 0.0
+                  for _ in range(n)]
+        elif kind == "growing":
+            xs = [math.ldexp(rng.random(), -50 + i // 500) for i in range(n)]
+        elif kind == "ties":
+            acc = 1.0
+            xs = [math.ldexp(rng.choice([1, 3]), -53) for _ in range(n)]
+        else:
+            xs = [math.ldexp(rng.random(), rng.randint(-70, -20)) for _ in range(n)]
+        arr = (ctypes.c_double * n)(*xs)
+        red = ctypes.c_int()
+        got = fx.fxh_fold_segmented(acc, arr, n, ctypes.byref(red))
+        seq = acc
+        for x in xs:
+            seq = seq + x
+        assert bits(got) == bits(seq), (kind, trial)
+        # refolds happen where the sum enters a new binade (plus a rare
+        # missed prediction next to a power of two)
+        first = next((x for x in [acc] + xs if x > 0), 0.0)
+        crossings = (bexp(seq) - bexp(first) + 1) if first > 0 else 0
+        assert red.value <= crossings + 2, (kind, red.value, crossings)
