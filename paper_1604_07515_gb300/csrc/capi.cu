@@ -119,6 +119,20 @@ __global__ void gather_off_kernel(const int32_t* __restrict__ ids, int64_t k,
 // host from the degree copy; only their list starts are read back).
 int build_big_segments(lgc_ctx* ctx, lgc_graph* g) {
   cudaStream_t s = ctx->stream;
+  {
+    std::vector<int32_t> mid;
+    for (int64_t v = 0; v < g->n; v++)
+      if (g->hdeg[v] > kPullLight && g->hdeg[v] <= kDetBig) mid.push_back((int32_t)v);
+    std::stable_sort(mid.begin(), mid.end(),
+                     [&](int32_t a, int32_t b) { return g->hdeg[a] > g->hdeg[b]; });
+    g->ndet_mid = (int64_t)mid.size();
+    if (g->ndet_mid > 0) {
+      LGC_TRY(dalloc_t(ctx, &g->det_mid, g->ndet_mid));
+      LGC_CUDA_TRY(cudaMemcpyAsync(g->det_mid, mid.data(), 4 * g->ndet_mid,
+                                   cudaMemcpyHostToDevice, s));
+      LGC_CUDA_TRY(cudaStreamSynchronize(s));  // mid goes out of scope
+    }
+  }
   std::vector<int32_t> bw;
   for (int64_t v = 0; v < g->n; v++)
     if (g->hdeg[v] > kDetBig) bw.push_back((int32_t)v);
@@ -507,6 +521,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     dfree(ctx, g->big_w);
     dfree(ctx, g->big_seg0);
     dfree(ctx, g->segs);
+    dfree(ctx, g->det_mid);
     cudaStreamSynchronize(s);
     delete g;
     return st;
@@ -536,6 +551,7 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->big_w);
   dfree(ctx, g->big_seg0);
   dfree(ctx, g->segs);
+  dfree(ctx, g->det_mid);
   cudaStreamSynchronize(ctx->stream);
   delete g;
 }

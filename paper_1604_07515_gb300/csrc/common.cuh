@@ -259,6 +259,10 @@ struct lgc_graph {
   // load)
   PullItem* items = nullptr;
   int64_t nitems = 0;
+  // vertices of degree in (kPullLight, kDetBig], longest lists first (one
+  // lane each folds its list in the deterministic pull)
+  int32_t* det_mid = nullptr;
+  int64_t ndet_mid = 0;
   // vertices of degree > kDetBig, whose deterministic fold runs segment-
   // parallel: their ids, the first of their segments (nbig + 1 prefix), and
   // the 256-edge segments
@@ -273,7 +277,7 @@ namespace lgc {
 // A pull round handles vertices of degree <= kPullLight with one thread each
 // and the rest in work items of at most kPullItem edges.
 constexpr int kPullLight = 32;
-constexpr int kDetBig = 4096;  // longer lists fold segment-parallel in deterministic mode
+constexpr int kDetBig = 1024;  // longer lists fold segment-parallel in deterministic mode
 constexpr int kDetSeg = 256;
 constexpr int kPullItem = 4096;
 }  // namespace lgc

@@ -699,23 +699,17 @@ __device__ inline void pull_finish(const Table& D, int32_t w, int64_t d, double 
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic mode, heavy vertices: the left fold acc <- RN(acc + s_k) over
-// the in-frontier shares in adjacency order, computed by a warp without a
-// chain of dependent FP64 adds.
+// The ordered fold acc <- RN(acc + s_k) of 256 shares by a warp, without a
+// chain of dependent FP64 adds (the segment-parallel fold of long lists
+// refolds a segment with it where its composed step does not apply).
 //
-// While acc stays in one binade [2^(bu-1023), 2^(bu-1022)) (bu >= 1; bu = 1
-// also covers zero and the subnormals), acc = A * u with the integer A below
-// 2^53 and u = 2^(bu-1075).  For s >= 0 with s / u = Q + f (0 <= f < 1),
-// RN(acc + s) = (A + Q + [f > 1/2]) * u, except that at f = 1/2 (a tie) the
-// result is the even one of A + Q and A + Q + 1 -- as long as the result is
-// below 2^53 * u.  So each share is a step A -> A + g[A & 1] (g[0] = g[1]
-// unless it is a tie), steps compose into steps of the same form, and a warp
-// scan of the compositions gives every partial fold.  The first position
-// whose value reaches 2^53 leaves the binade: that one add is done in FP64
-// (the rounding of the next binade applies), and the scan restarts after it
-// with the new binade.  Every result equals the sequential fold's bit for
-// bit; the number of FP64 adds per vertex is the number of binades acc
-// passes through.
+// While acc stays in one binade it is A * u with the integer A below 2^53,
+// and each share is an integer step A -> A + g[A & 1] (fold_step in
+// fx128.cuh); steps compose, so a warp scan of the compositions gives every
+// partial fold.  The first position whose value reaches 2^53 leaves the
+// binade: that one add is done in FP64 (the rounding of the next binade
+// applies), and the scan restarts after it with the new binade.  Every
+// result equals the sequential fold's bit for bit.
 // ---------------------------------------------------------------------------
 // Folds the 32 * 8 shares v (lane l holds positions 8l .. 8l+7, in list
 // order) into acc, lane-uniformly.
@@ -776,41 +770,50 @@ __device__ inline double fold_batch(double acc, const double v[8], int lane) {
   return acc;
 }
 
+// Deterministic mode, vertices of degree (kPullLight, kDetBig]: one lane per
+// vertex folds its in-frontier shares in adjacency order with FP64 adds --
+// the fold's definition, so bit-identical by construction.  The vertices are
+// taken longest list first and a warp's lanes have lists of similar length,
+// so every add is issued for (nearly) all 32 lanes; each lane loads eight
+// columns, then their eight shares, before folding them.
 __global__ void __launch_bounds__(kBlock)
-    pull_heavy_det_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                          const int32_t* __restrict__ heavy, int64_t nheavy,
-                          const double* __restrict__ sh, Table D, double c, int fmode,
-                          uint32_t* __restrict__ qbits, Counters* C) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t h = warp0; h < nheavy; h += nwarps) {
-    const int32_t w = heavy[h];
-    const int64_t o0 = off[w], d = off[w + 1] - o0;
-    if (d > kDetBig) continue;  // folded segment-parallel (det_seg_* kernels)
-    const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
-    double acc = present ? D.dval[w] : 0.0;  // >= +0
-    bool touched = present;
-    for (int64_t k0 = 0; k0 < d; k0 += 256) {
-      int32_t u[8];
+    pull_mid_det_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                        const int32_t* __restrict__ mid, int64_t nmid,
+                        const double* __restrict__ sh, Table D, double c, int fmode,
+                        uint32_t* __restrict__ qbits, Counters* C) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nmid;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int ins = 0;
+    if (i < nmid) {
+      const int32_t w = mid[i];
+      const int64_t o0 = off[w], d = off[w + 1] - o0;
+      const uint32_t m = 1u << (w & 31);
+      const bool present = (D.bits[w >> 5] & m) != 0;
+      double acc = present ? D.dval[w] : 0.0;
+      bool touched = present;
+      for (int64_t k = 0; k < d; k += 8) {
+        int32_t u[8];
 #pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const int64_t k = k0 + 8 * lane + j;
-        u[j] = k < d ? col[o0 + k] : -1;
-      }
-      double v[8];
-      bool mem = false;
+        for (int j = 0; j < 8; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
+        double x[8];
 #pragma unroll
-      for (int j = 0; j < 8; j++) {
-        v[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
-        mem = mem || pull_member(v[j]);
+        for (int j = 0; j < 8; j++) x[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          if (pull_member(x[j])) {  // in order: j ascending is adjacency order
+            acc = acc + x[j];
+            touched = true;
+          }
+        }
       }
-      const unsigned any = __ballot_sync(0xffffffffu, mem);
-      if (!any) continue;
-      touched = true;
-      acc = fold_batch(acc, v, lane);
+      if (touched) {
+        D.dval[w] = acc;
+        if (!present && !(atomicOr(&D.bits[w >> 5], m) & m)) ins = 1;
+        if (pull_qualifies(acc, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
+      }
     }
-    if (lane == 0) pull_finish(D, w, d, acc, touched, present, c, fmode, qbits, C);
+    count_inserted(ins, &C->inserted);
   }
 }
 
@@ -1672,11 +1675,11 @@ struct PushWork {
         pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
                                                  ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
-        if (g->nheavy > 0) {
-          int64_t hb = ceil_div(g->nheavy, kBlock / 32);
-          pull_heavy_det_kernel<<<(int)(hb < 152 * 16 ? hb : 152 * 16), kBlock, 0, s>>>(
-              g->off, g->col, g->heavy, g->nheavy, psh.ptr, D, c, fmode, pq.ptr,
-              ctx->d_counters);
+        if (g->ndet_mid > 0) {
+          const int mg = (int)std::min<int64_t>(ceil_div(g->ndet_mid, kBlock), 152 * 32);
+          pull_mid_det_kernel<<<mg, kBlock, 0, s>>>(g->off, g->col, g->det_mid, g->ndet_mid,
+                                                    psh.ptr, D, c, fmode, pq.ptr,
+                                                    ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
         }
         if (g->nbig > 0) {  // lists longer than kDetBig, folded segment-parallel
