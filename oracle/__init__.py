@@ -82,6 +82,7 @@ def _load():
         for name, extra in [
             ("orc_prnibble", [i32, f64, f64, ci, i64, ci]),
             ("orc_prnibble_queue", [i32, f64, f64, ci]),
+            ("orc_prnibble_set", [i64, P, P, f64, f64, ci, f64, i64, ci]),
             ("orc_nibble", [i32, ci, f64, ci]),
             ("orc_hkpr", [i32, f64, ci, f64, ci]),
             ("orc_hkpr_queue", [i32, f64, ci, f64]),
@@ -176,6 +177,21 @@ def prnibble(off, col, seed, alpha, eps, rule=0, max_rounds=1 << 40, trace=False
     off, col, n = _g(off, col)
     h = _load().orc_prnibble(n, off.ctypes.data, col.ctypes.data, int(seed), float(alpha),
                              float(eps), int(rule), int(max_rounds), int(bool(trace)))
+    return _collect(h)
+
+
+def prnibble_set(off, col, seeds, weights, alpha, eps, rule=0, beta=1.0,
+                 max_rounds=1 << 40, trace=False) -> Result:
+    """PR-Nibble from a weighted seed set with beta-fraction rounds
+    (orc_prnibble_set)."""
+    off, col, n = _g(off, col)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    weights = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64),
+                                                   seeds.shape))
+    h = _load().orc_prnibble_set(n, off.ctypes.data, col.ctypes.data, len(seeds),
+                                 seeds.ctypes.data, weights.ctypes.data, float(alpha),
+                                 float(eps), int(rule), float(beta), int(max_rounds),
+                                 int(bool(trace)))
     return _collect(h)
 
 

@@ -269,6 +269,113 @@ orc_result* orc_prnibble(int64_t n, const int64_t* off, const int32_t* col, int3
 }
 
 // ---------------------------------------------------------------------------
+// Synchronous PR-Nibble from a seed set, with the beta-fraction rounds of
+// Sec. 3.3 (the variant that, each iteration, processes only the top
+// beta-fraction of {v : r[v] >= d(v) eps} by r[v]/d(v)).  Readings:
+//  * seed set (Sec. 3: the algorithms extend to seed sets): r starts as the
+//    distribution w_i / W on the k distinct seeds, W the sum of the weights
+//    added left to right; every seed is on the first frontier;
+//  * selection: the candidates are sorted by r[v]/d(v) (binary64, r as at the
+//    start of the round) descending, ties by ascending id, and the first
+//    ceil(beta * |F|) of them (at least one) push; the others stay in the
+//    frontier, which is again every v with r[v] >= d(v) eps after the round;
+//  * the selected vertices push exactly as in orc_prnibble, in ascending id.
+// With one seed of weight 1 and beta = 1 this is orc_prnibble.
+// ---------------------------------------------------------------------------
+orc_result* orc_prnibble_set(int64_t n, const int64_t* off, const int32_t* col, int64_t k,
+                             const int32_t* seeds, const double* weights, double alpha,
+                             double eps, int rule, double beta, int64_t max_rounds, int trace) {
+  orc_result* res = new orc_result();
+  Graph g{n, off, col};
+  bool bad = k < 1 || !(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0) || !(beta > 0.0 && beta <= 1.0);
+  double W = 0.0;
+  std::vector<int32_t> F;
+  for (int64_t i = 0; i < k && !bad; i++) {
+    const int32_t x = seeds[i];
+    if (x < 0 || x >= n || g.deg(x) < 1 || !(weights[i] > 0.0)) bad = true;
+    else {
+      W = W + weights[i];
+      F.push_back(x);
+    }
+  }
+  std::sort(F.begin(), F.end());
+  if (!bad && std::adjacent_find(F.begin(), F.end()) != F.end()) bad = true;
+  if (bad) {
+    res->stats[ORC_ST_STATUS] = -1;
+    return res;
+  }
+  SparseSet p(n), r(n);
+  for (int64_t i = 0; i < k; i++) r.at(seeds[i]) = weights[i] / W;
+  const double cs = (2.0 * alpha) / (1.0 + alpha);
+  const double cn = (1.0 - alpha) / (1.0 + alpha);
+  int64_t rounds = 0, pushes = 0, pushed_edges = 0;
+  while (!F.empty()) {
+    if (rounds == max_rounds) {
+      res->stats[ORC_ST_STATUS] = -4;
+      break;
+    }
+    // the pushing set S: the top ceil(beta |F|) by r/d, then in ascending id
+    std::vector<int32_t> S = F;
+    if (beta < 1.0) {
+      int64_t m = (int64_t)std::ceil(beta * (double)F.size());
+      if (m < 1) m = 1;
+      if (m > (int64_t)F.size()) m = (int64_t)F.size();
+      std::vector<std::pair<double, int32_t>> byk;
+      for (int32_t v : F) byk.push_back({r.get(v) / (double)g.deg(v), v});
+      std::stable_sort(byk.begin(), byk.end(), [](const std::pair<double, int32_t>& a,
+                                                    const std::pair<double, int32_t>& b) {
+        return a.first > b.first || (a.first == b.first && a.second < b.second);
+      });
+      S.clear();
+      for (int64_t i = 0; i < m; i++) S.push_back(byk[i].second);
+      std::sort(S.begin(), S.end());
+    }
+    if (trace) {
+      res->i32[ORC_TRACE].insert(res->i32[ORC_TRACE].end(), S.begin(), S.end());
+      res->i64[ORC_TRACE_N].push_back((int64_t)S.size());
+    }
+    std::vector<double> rv(S.size());
+    for (size_t i = 0; i < S.size(); i++) rv[i] = r.get(S[i]);
+    for (size_t i = 0; i < S.size(); i++) {
+      int32_t v = S[i];
+      if (rule == 0) {
+        p.at(v) = p.get(v) + cs * rv[i];
+        r.at(v) = 0.0;
+      } else {
+        p.at(v) = p.get(v) + alpha * rv[i];
+        r.at(v) = ((1.0 - alpha) * rv[i]) / 2.0;
+      }
+    }
+    int64_t round_edges = 0;
+    for (size_t i = 0; i < S.size(); i++) {
+      int32_t v = S[i];
+      int64_t d = g.deg(v);
+      double share = (rule == 0) ? (cn * rv[i]) / (double)d
+                                 : ((1.0 - alpha) * rv[i]) / (2.0 * (double)d);
+      for (int64_t e = off[v]; e < off[v + 1]; e++) {
+        int32_t w = col[e];
+        r.at(w) = r.get(w) + share;
+      }
+      round_edges += d;
+    }
+    rounds++;
+    pushes += (int64_t)S.size();
+    pushed_edges += round_edges;
+    std::vector<int32_t> next;
+    for (int32_t kk : r.sorted_keys())
+      if (r.val[kk] >= eps * (double)g.deg(kk)) next.push_back(kk);
+    F.swap(next);
+  }
+  res->stats[ORC_ST_ROUNDS] = rounds;
+  res->stats[ORC_ST_PUSHES] = pushes;
+  res->stats[ORC_ST_PUSHED_EDGES] = pushed_edges;
+  res->stats[ORC_ST_TOUCHED] = (int64_t)r.keys.size();
+  emit_sorted(p, res->i32[ORC_IDX], res->f64[ORC_VAL], true);
+  emit_sorted(r, res->i32[ORC_IDX2], res->f64[ORC_VAL2], false);
+  return res;
+}
+
+// ---------------------------------------------------------------------------
 // Sequential PR-Nibble with a FIFO queue, Sec. 3.3 (following Andersen,
 // Chung, Lang): push one vertex at a time using the latest r, append a
 // neighbour to the queue when it reaches eps*d, and keep pushing the popped

@@ -211,6 +211,76 @@ def test_prnibble_both_rules_same_system():
         assert np.abs(to_dense(n, res.idx, res.val) - pstar).max() < 1e-7
 
 
+# PR-Nibble from a seed set, beta-fraction rounds (Sec. 3 seed sets; Sec. 3.3
+# beta variant).  Pins: the dense PPR invariant with the seed distribution
+# after every round, the terminal guarantee, the work bound, and the
+# hand-worked order of a star.
+@pytest.mark.parametrize("beta", [1.0, 0.5, 0.2, 1e-9])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_prnibble_set_invariant_every_round(beta, rule):
+    off, col = inputs.random_graph(60, 200, seed=4)
+    n = len(off) - 1
+    _, W, d = walk_matrix(off, col)
+    cand = np.flatnonzero(d > 0)
+    seeds = cand[[0, 5, 9]].astype(np.int32)
+    w = np.array([1.0, 2.0, 0.5])
+    s = np.zeros(n)
+    Wsum = (1.0 + 2.0) + 0.5
+    s[seeds] = w / Wsum
+    pstar = ppr(W, 0.1, s)
+    eps = 1e-4
+    full = oracle.prnibble_set(off, col, seeds, w, 0.1, eps, rule=rule, beta=beta, trace=True)
+    assert full.status == 0
+    for k in range(1, min(full.rounds, 40) + 1):
+        res = oracle.prnibble_set(off, col, seeds, w, 0.1, eps, rule=rule, beta=beta, max_rounds=k)
+        p = to_dense(n, res.idx, res.val)
+        r = to_dense(n, res.idx2, res.val2)
+        assert np.abs(p + ppr(W, 0.1, r) - pstar).max() < 1e-13
+        assert abs(p.sum() + r.sum() - 1.0) < 1e-14
+    p = to_dense(n, full.idx, full.val)
+    r = to_dense(n, full.idx2, full.val2)
+    gap = pstar - p
+    assert gap.min() > -1e-14 and np.all(gap <= eps * d + 1e-14)
+    assert np.all(r < eps * d)
+    assert full.pushed_edges <= 1.0 / (0.1 * eps)
+    if beta == 1e-9:  # one vertex per round
+        assert all(len(f) == 1 for f in full.trace) and full.pushes == full.rounds
+
+
+def test_prnibble_set_one_seed_is_prnibble():
+    off, col = inputs.rmat(10, seed=5)
+    x = inputs.config1_seed(off, col)
+    a = oracle.prnibble(off, col, x, 0.05, 1e-5)
+    b = oracle.prnibble_set(off, col, [x], [1.0], 0.05, 1e-5)
+    assert np.array_equal(a.idx, b.idx) and np.array_equal(a.val, b.val)
+    assert (a.rounds, a.pushes, a.pushed_edges) == (b.rounds, b.pushes, b.pushed_edges)
+
+
+def test_prnibble_set_beta_hand_worked_star():
+    """Star, centre 0 and leaves 1..4, seeds {1, 2} with weights 3 and 1
+    (r = 3/4, 1/4), alpha = 1/2 (optimized rule: 2a/(1+a) = 2/3,
+    (1-a)/(1+a) = 1/3), eps = 0.01, beta = 0.5: both seeds qualify
+    (r/d = 3/4 and 1/4); ceil(0.5 * 2) = 1 pushes, the larger r/d: leaf 1.
+    Round 1: p1 = 1/2, r1 = 0, r0 = 1/4; frontier {0, 2} (1/4 >= 0.04)."""
+    off, col = inputs.star(4)
+    res = oracle.prnibble_set(off, col, [1, 2], [3.0, 1.0], 0.5, 0.01, beta=0.5,
+                              max_rounds=1, trace=True)
+    assert [f.tolist() for f in res.trace] == [[1]]
+    assert res.idx.tolist() == [1] and res.val.tolist() == [0.5]
+    assert res.idx2.tolist() == [0, 1, 2] and res.val2.tolist() == [0.25, 0.0, 0.25]
+    # round 2: r/d of 0 is (1/4)/4 = 1/16, of leaf 2 is 1/4: leaf 2 pushes
+    res = oracle.prnibble_set(off, col, [1, 2], [3.0, 1.0], 0.5, 0.01, beta=0.5,
+                              max_rounds=2, trace=True)
+    assert [f.tolist() for f in res.trace] == [[1], [2]]
+
+
+def test_prnibble_set_rejects_bad_sets():
+    off, col = inputs.star(4)
+    for seeds, w, beta in [([1, 1], [1.0, 1.0], 1.0), ([1], [0.0], 1.0), ([1], [1.0], 0.0),
+                           ([1], [1.0], 1.5), ([9], [1.0], 1.0)]:
+        assert oracle.prnibble_set(off, col, seeds, w, 0.1, 1e-3, beta=beta).status == -1
+
+
 def test_prnibble_queue_vs_synchronous():
     """The sequential queue version reaches the same accuracy guarantee; the
     synchronous version does at least roughly as many pushes (Table
