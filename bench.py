@@ -392,7 +392,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = lgc.Context(dev, stream)
     g = lgc.Graph(ctx, off, col)
-    pull_batch = g.autotune()  # launch-shape tuning on this graph, before any timing
+    pull_shape = g.autotune()  # launch-shape tuning on this graph, before any timing
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -508,7 +508,7 @@ def main():
             "config": {"workload": WORKLOAD if STEP_ALGOS == ALGOS
                        else WORKLOAD + f" (only: {','.join(STEP_ALGOS)})", "mode": MODE,
                        "l2": "inputs larger than L2 and L2 flushed between steps",
-                       "parallelism": f"replicas{world}", "pull_batch": pull_batch},
+                       "parallelism": f"replicas{world}", "pull_shape": list(pull_shape)},
             "clusters_per_s": clusters / (total_ms / 1e3),
             "pushed_edges_per_step": pushed / args.steps / max(1, world),
             "roofline": roofline, "kernels": prof,

@@ -145,9 +145,13 @@ enum {
                                    PR-Nibble run in one cooperative launch without returning
                                    to the host in between; 0: one launch per step.  Request-
                                    loop workers never use it.  Same results either way */
-  LGC_OPT_PULL_BATCH = 9        /* edges per lane per batch in the heavy-vertex pull gather:
+  LGC_OPT_PULL_BATCH = 9,       /* edges per lane per batch in the heavy-vertex pull gather:
                                    0 (default) the graph's tuned value (see
                                    lgc_graph_autotune), or 4, 8, 16 */
+  LGC_OPT_PULL_GROUP = 10       /* lanes per work item in the heavy-vertex pull gather: 0
+                                   (default) the graph's tuned value, or 8, 16, 32 (only
+                                   the pairs lgc_graph_autotune tries are compiled: 4 with
+                                   32; 8 and 16 with 8, 16, 32) */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */
@@ -162,12 +166,13 @@ int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int3
                      int flags, lgc_graph **out);
 void lgc_graph_destroy(lgc_graph *g);
 /* Tunes the graph's launch shapes by timing them on the graph itself (the
- * paper has no counterpart; it affects speed only): the number of edges each
- * lane loads per batch in the heavy-vertex pull gather, from {4, 8, 16}, on
- * a frontier of all vertices.  Takes a few launches of that gather; the
- * chosen value is written to *pull_batch (nullable).  Until it is called
- * the graph uses 8. */
-int lgc_graph_autotune(lgc_graph *g, int *pull_batch);
+ * paper has no counterpart; it affects speed only): for the heavy-vertex
+ * pull gather, the edges each lane loads per batch and the lanes per work
+ * item, from (4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8),
+ * on a frontier of all vertices.  Takes a few launches of that gather per
+ * candidate; the chosen pair is written to *pull_batch and *pull_group
+ * (both nullable).  Until it is called the graph uses (8, 32). */
+int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group);
 int64_t lgc_graph_num_vertices(const lgc_graph *g);
 int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
 
@@ -177,6 +182,19 @@ int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
  * the round; returns p.  st may be NULL. */
 int lgc_prnibble(lgc_graph *g, int32_t seed, const lgc_prnibble_params *prm, lgc_svec **p,
                  lgc_stats *st);
+/* PR-Nibble from a seed set with beta-fraction rounds.  Sec. 3 notes that the
+ * algorithms extend to seed sets and Sec. 3.3 describes the variant that
+ * processes, each iteration, only the top beta-fraction of
+ * {v : r[v] >= eps d(v)} by r[v]/d(v).  Here r starts as the distribution
+ * w_i / W over the k distinct seeds (W = the weights summed left to right;
+ * weights NULL: all 1), all seeds on the first frontier; each round the first
+ * ceil(beta |F|) (at least one) candidates by r/d descending, ties by
+ * ascending id, push as in lgc_prnibble and the others stay candidates.
+ * beta in (0, 1]; k = 1 with beta = 1 is lgc_prnibble.  Errors: LGC_EINVAL
+ * for a repeated or invalid seed, a weight <= 0, beta outside (0, 1]. */
+int lgc_prnibble_set(lgc_graph *g, int64_t k, const int32_t *seeds, const double *weights,
+                     double beta, const lgc_prnibble_params *prm, lgc_svec **p,
+                     lgc_stats *st);
 /* Parallel Nibble (Sec. 3.2, Fig. alg:nibble); returns p_T, or p_{i-1} when
  * the frontier of step i is empty. */
 int lgc_nibble(lgc_graph *g, int32_t seed, const lgc_nibble_params *prm, lgc_svec **p,

@@ -423,6 +423,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 4 && value != 8 && value != 16) return LGC_EINVAL;
       ctx->pull_batch = (int)value;
       return LGC_OK;
+    case LGC_OPT_PULL_GROUP:
+      if (value != 0 && value != 8 && value != 16 && value != 32) return LGC_EINVAL;
+      ctx->pull_group = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -556,10 +560,11 @@ void lgc_graph_destroy(lgc_graph* g) {
   delete g;
 }
 
-int lgc_graph_autotune(lgc_graph* g, int* pull_batch) {
+int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group) {
   if (!g) return LGC_EINVAL;
   LGC_TRY(autotune_pull(g->ctx, g));
   if (pull_batch) *pull_batch = g->pull_batch;
+  if (pull_group) *pull_group = g->pull_group;
   return LGC_OK;
 }
 
@@ -584,6 +589,18 @@ int lgc_prnibble_residual(lgc_ctx* ctx, lgc_svec** r) {
   *r = ctx->last_residual;
   ctx->last_residual = nullptr;
   return LGC_OK;
+}
+
+int lgc_prnibble_set(lgc_graph* g, int64_t k, const int32_t* seeds, const double* weights,
+                     double beta, const lgc_prnibble_params* prm, lgc_svec** p, lgc_stats* st) {
+  if (!g || !prm || !p) return LGC_EINVAL;
+  lgc_ctx* ctx = g->ctx;
+  if (ctx->last_residual) {
+    lgc_svec_free(ctx->last_residual);
+    ctx->last_residual = nullptr;
+  }
+  return run_prnibble_set(ctx, g, k, seeds, weights, beta, prm, p, st,
+                          ctx->trace ? &ctx->last_residual : nullptr);
 }
 
 int lgc_nibble(lgc_graph* g, int32_t seed, const lgc_nibble_params* prm, lgc_svec** p,

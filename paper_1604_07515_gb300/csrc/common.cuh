@@ -198,6 +198,7 @@ struct lgc_ctx {
   int sms = 152;              // multiprocessors of the device
   bool device_rounds = true;  // LGC_OPT_DEVICE_ROUNDS
   int pull_batch = 0;          // LGC_OPT_PULL_BATCH: 0 = the graph's tuned value
+  int pull_group = 0;          // LGC_OPT_PULL_GROUP: 0 = the graph's tuned value
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back
@@ -251,6 +252,7 @@ struct lgc_graph {
   int32_t max_deg = 0;
   std::vector<int32_t> hdeg;  // host copy of deg (seeds are checked without a device read)
   int pull_batch = 8;          // edges per lane per batch in heavy pull gathers (tuned)
+  int pull_group = 32;         // lanes per work item in heavy pull gathers (tuned)
   // vertices of degree > kPullLight in ascending id, for the pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;
@@ -380,6 +382,9 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
 int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_params* prm,
                   lgc_svec** p, lgc_stats* st);
 int autotune_pull(lgc_ctx* ctx, lgc_graph* g);
+int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds,
+                     const double* weights, double beta, const lgc_prnibble_params* prm,
+                     lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out);
 int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out);
 int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const* ps,
                     lgc_cluster** out);

@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 #include <string.h>
 
 #include <cooperative_groups.h>
@@ -1106,38 +1107,55 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
 // adds, the low word's carry taken from its returned old value) and the warp
 // that completes the vertex's last item finishes it and resets the
 // accumulators for the next round.
-template <int BATCH>
+// GL lanes (8, 16 or 32) work on one item; a warp's 32 / GL groups take
+// consecutive items.  The loop over items runs the same number of times in
+// every lane of the warp (a group past the end works on nothing), so the
+// group-wide shuffles always find all their lanes.
+template <int BATCH, int GL>
 __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
                                           const int64_t* __restrict__ off,
                                           const int32_t* __restrict__ col,
-                         const PullItem* __restrict__ items, int64_t nitems,
-                         const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
-                         Table D, double c, int fmode, uint32_t* __restrict__ qbits,
-                         Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
-                         int32_t* __restrict__ htouch, Counters* C) {
+                                          const PullItem* __restrict__ items, int64_t nitems,
+                                          const Fx* __restrict__ shx,
+                                          const int32_t* __restrict__ range, int g, Table D,
+                                          double c, int fmode, uint32_t* __restrict__ qbits,
+                                          Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
+                                          int32_t* __restrict__ htouch, Counters* C) {
+  constexpr int kGroups = 32 / GL;
   const int L = round_scale(range, g);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, gl = lane % GL, gid = lane / GL;
   const int64_t warp0 = (bid * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (nblk * blockDim.x) >> 5;
-  for (int64_t it = warp0; it < nitems; it += nwarps) {
-    const PullItem I = items[it];
+  for (int64_t base = warp0 * kGroups; base < nitems; base += nwarps * kGroups) {
+    const int64_t it = base + gid;
+    const bool valid = it < nitems;
+    PullItem I;
+    if (valid) {
+      I = items[it];
+    } else {
+      I.beg = 0;
+      I.w = 0;
+      I.h = 0;
+      I.len = 0;
+      I.nparts = 1;
+    }
     const int32_t w = I.w;
-    // the vertex's state, needed only by lane 0 at the end
+    // the vertex's state, needed only by the group's first lane at the end
     uint32_t bword = 0;
     double cur = 0.0;
     int64_t d = 0;
-    if (lane == 0) {
+    if (gl == 0 && valid) {
       bword = D.bits[w >> 5];
       cur = D.dval[w];
       d = off[w + 1] - off[w];
     }
     Fx part = {0, 0};
     uint64_t flag = 0;
-    for (int k0 = 0; k0 < I.len; k0 += 32 * BATCH) {
+    for (int k0 = 0; k0 < I.len; k0 += GL * BATCH) {
       int32_t u[BATCH];
 #pragma unroll
       for (int j = 0; j < BATCH; j++) {
-        const int k = k0 + 32 * j + lane;
+        const int k = k0 + GL * j + gl;
         u[j] = k < I.len ? col[I.beg + k] : -1;
       }
       Fx x[BATCH];
@@ -1153,14 +1171,16 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
         fx_add(part, x[j]);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
+    uint32_t mem = (flag & kFxFlag) ? 1u : 0u;
+    for (int o = GL / 2; o > 0; o >>= 1) {  // within the group
       Fx t;
       t.lo = __shfl_xor_sync(0xffffffffu, part.lo, o);
       t.hi = __shfl_xor_sync(0xffffffffu, part.hi, o);
       fx_add(part, t);
+      mem |= __shfl_xor_sync(0xffffffffu, mem, o);
     }
-    const bool any = __any_sync(0xffffffffu, (flag & kFxFlag) != 0);
-    if (lane != 0) continue;
+    const bool any = mem != 0;
+    if (gl != 0 || !valid) continue;
     const bool present = (bword >> (w & 31)) & 1u;
     if (I.nparts == 1) {
       if (present || any)
@@ -1193,7 +1213,7 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
   }
 }
 
-template <int BATCH>
+template <int BATCH, int GL>
 __global__ void __launch_bounds__(kBlock)
     pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                          const PullItem* __restrict__ items, int64_t nitems,
@@ -1201,7 +1221,8 @@ __global__ void __launch_bounds__(kBlock)
                          Table D, double c, int fmode, uint32_t* __restrict__ qbits,
                          Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
                          int32_t* __restrict__ htouch, Counters* C) {
-  pull_heavy_fx_body<BATCH>(blockIdx.x, gridDim.x, off, col, items, nitems, shx, range, g, D, c,
+  pull_heavy_fx_body<BATCH, GL>(blockIdx.x, gridDim.x, off, col, items, nitems, shx, range, g, D,
+                                c,
                             fmode, qbits, hacc, hcnt, htouch, C);
 }
 
@@ -1390,7 +1411,138 @@ __global__ void init_seed_kernel(Table T, int32_t x, double r0, int32_t* fv, int
   fs[0] = (int32_t)s;
 }
 
+// Seed set: seeds (ascending, distinct) with their initial residuals.
+__global__ void init_seeds_kernel(Table T, const int32_t* __restrict__ x,
+                                  const double* __restrict__ r0, int64_t k, int32_t* fv,
+                                  int32_t* fs, Counters* C) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ins = 0;
+    const int64_t s = tb_find_or_insert(T, x[i], &ins, &C->err);
+    if (s >= 0) *tb_val(T, s) = r0[i];
+    fv[i] = x[i];
+    fs[i] = (int32_t)s;
+  }
+}
+
+// beta-fraction rounds: order the frontier by r/d descending, ties by
+// ascending id (sort by id, then stably by the key 0x7FF...F - bits(r/d)).
+__global__ void sel_ids_kernel(const int32_t* __restrict__ fv, int64_t nf,
+                               uint32_t* __restrict__ key, int32_t* __restrict__ pos) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    key[i] = (uint32_t)fv[i];
+    pos[i] = (int32_t)i;
+  }
+}
+
+__global__ void sel_keys_kernel(const int32_t* __restrict__ fv, const int32_t* __restrict__ fs,
+                                const int32_t* __restrict__ pos, int64_t nf, Table T,
+                                const int32_t* __restrict__ deg, uint64_t* __restrict__ key) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = pos[i];
+    const double r = fs[j] >= 0 ? *tb_val(T, fs[j]) : 0.0;
+    const double kv = r / (double)deg[fv[j]];
+    key[i] = 0x7FFFFFFFFFFFFFFFull - ((uint64_t)__double_as_longlong(kv) & 0x7FFFFFFFFFFFFFFFull);
+  }
+}
+
+// The first m in the order push (written with their ids as keys, to be
+// sorted ascending), the rest stay (rv/rs).
+__global__ void sel_split_kernel(const int32_t* __restrict__ fv, const int32_t* __restrict__ fs,
+                                 const int32_t* __restrict__ pos, int64_t nf, int64_t m,
+                                 uint32_t* __restrict__ sv, int32_t* __restrict__ ss,
+                                 int32_t* __restrict__ rv, int32_t* __restrict__ rs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = pos[i];
+    if (i < m) {
+      sv[i] = (uint32_t)fv[j];
+      ss[i] = fs[j];
+    } else {
+      rv[i - m] = fv[j];
+      rs[i - m] = fs[j];
+    }
+  }
+}
+
+__global__ void copy_frontier_kernel(const uint32_t* __restrict__ sv, const int32_t* __restrict__ ss,
+                                     int64_t m, const int32_t* __restrict__ deg, int32_t* fv,
+                                     int32_t* fs, unsigned long long* edges) {
+  unsigned long long e = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    fv[i] = (int32_t)sv[i];
+    fs[i] = ss[i];
+    e += (unsigned long long)deg[sv[i]];
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e) atomicAdd(edges, e);
+}
+
+// Next frontier = the round's qualifying vertices together with the
+// candidates that did not push and still have r >= eps d (a seed is on the
+// first frontier whatever its residual; afterwards only the threshold
+// counts): concatenated, sorted by id, duplicates dropped (a waiting
+// candidate that was pushed to may be in both).  A dropped one gets the key
+// 0xFFFFFFFF (no vertex id), which sorts last.
+__global__ void cat_frontier_kernel(const int32_t* __restrict__ av, const int32_t* __restrict__ as,
+                                    int64_t na, const int32_t* __restrict__ bv,
+                                    const int32_t* __restrict__ bs, int64_t nb, Table T,
+                                    const int32_t* __restrict__ deg, double eps,
+                                    uint32_t* __restrict__ kv, int32_t* __restrict__ ks) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < na) {
+      kv[i] = (uint32_t)av[i];
+      ks[i] = as[i];
+    } else {
+      const int32_t v = bv[i - na], s = bs[i - na];
+      const bool keep = s >= 0 && *tb_val(T, s) >= eps * (double)deg[v];
+      kv[i] = keep ? (uint32_t)v : 0xFFFFFFFFu;
+      ks[i] = s;
+    }
+  }
+}
+
+__global__ void uniq_flags_kernel(const uint32_t* __restrict__ kv, int64_t n,
+                                  int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (kv[i] != 0xFFFFFFFFu && (i == 0 || kv[i] != kv[i - 1])) ? 1 : 0;
+}
+
+__global__ void uniq_write_kernel(const uint32_t* __restrict__ kv, const int32_t* __restrict__ ks,
+                                  const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                                  int64_t n, const int32_t* __restrict__ deg, int32_t* fv,
+                                  int32_t* fs, unsigned long long* edges) {
+  unsigned long long e = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    fv[pos[i]] = (int32_t)kv[i];
+    fs[pos[i]] = ks[i];
+    e += (unsigned long long)deg[kv[i]];
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e) atomicAdd(edges, e);
+}
+
 }  // namespace
+
+using HeavyKernel = void (*)(const int64_t*, const int32_t*, const PullItem*, int64_t, const Fx*,
+                             const int32_t*, int, Table, double, int, uint32_t*, Fx*, int32_t*,
+                             int32_t*, Counters*);
+
+// The heavy-vertex gather compiled for a (batch depth, lanes per item) shape.
+HeavyKernel heavy_kernel(int batch, int group) {
+  if (group == 8) return batch == 16 ? pull_heavy_fx_kernel<16, 8> : pull_heavy_fx_kernel<8, 8>;
+  if (group == 16) return batch == 16 ? pull_heavy_fx_kernel<16, 16> : pull_heavy_fx_kernel<8, 16>;
+  return batch == 16 ? pull_heavy_fx_kernel<16, 32>
+         : batch == 4 ? pull_heavy_fx_kernel<4, 32>
+                      : pull_heavy_fx_kernel<kPullBatch, 32>;
+}
 
 // ---------------------------------------------------------------------------
 // Host driver
@@ -1431,6 +1583,12 @@ struct PushWork {
   DBuf<int32_t> dany, dpred;
   DBuf<FoldStep> dstep;
   bool pull_ready = false;
+  // beta-fraction rounds: the candidates that did not push, sort scratch
+  Frontier U;
+  DBuf<uint64_t> selk, selk2;
+  DBuf<uint32_t> selv, selv2;
+  DBuf<int32_t> seli, seli2;
+  DBuf<unsigned long long> selcnt;
   // device-driven rounds: two frontier buffers, block sums, counters, state
   Frontier X[2];
   DBuf<int64_t> xbsum;
@@ -1443,6 +1601,14 @@ struct PushWork {
     G.release(ctx);
     X[0].release(ctx);
     X[1].release(ctx);
+    U.release(ctx);
+    selk.release(ctx);
+    selk2.release(ctx);
+    selv.release(ctx);
+    selv2.release(ctx);
+    seli.release(ctx);
+    seli2.release(ctx);
+    selcnt.release(ctx);
     dsum.release(ctx);
     dany.release(ctx);
     dpred.release(ctx);
@@ -1711,12 +1877,12 @@ struct PushWork {
                                                     D, c, fmode, pq.ptr, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
         if (g->nitems > 0) {
-          const int64_t hb = ceil_div(g->nitems, kBlock / 32);
+          const int gw = ctx->pull_group ? ctx->pull_group : g->pull_group;
+          const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / gw));
           const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
           const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
-          auto heavy = batch == 16 ? pull_heavy_fx_kernel<16>
-                       : batch == 4 ? pull_heavy_fx_kernel<4>
-                                    : pull_heavy_fx_kernel<kPullBatch>;
+          const int group = ctx->pull_group ? ctx->pull_group : g->pull_group;
+          HeavyKernel heavy = heavy_kernel(batch, group);
           heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr,
                                       gb, D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
                                       ctx->d_counters);
@@ -1828,6 +1994,82 @@ struct PushWork {
     return LGC_OK;
   }
 
+  // beta-fraction rounds: keeps in F the first m candidates by r/d
+  // descending (ties by ascending id), in ascending id, and moves the others
+  // to U (they stay candidates).
+  int select_top(const Table& T, int64_t m) {
+    cudaStream_t s = ctx->stream;
+    const int64_t nf = F.size, E0 = F.edges;
+    const int vb = bits_for(g->n);
+    LGC_TRY(selv.reserve(ctx, nf));
+    LGC_TRY(selv2.reserve(ctx, nf));
+    LGC_TRY(seli.reserve(ctx, nf));
+    LGC_TRY(seli2.reserve(ctx, nf));
+    LGC_TRY(selk.reserve(ctx, nf));
+    LGC_TRY(selk2.reserve(ctx, nf));
+    LGC_TRY(selcnt.reserve(ctx, 2));
+    LGC_TRY(U.v.reserve(ctx, nf));
+    LGC_TRY(U.s.reserve(ctx, nf));
+    sel_ids_kernel<<<grid_for(nf), kBlock, 0, s>>>(F.v.ptr, nf, selv.ptr, seli.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(radix_sort_u32_i32(ctx, selv.ptr, seli.ptr, selv2.ptr, seli2.ptr, nf, vb));
+    sel_keys_kernel<<<grid_for(nf), kBlock, 0, s>>>(F.v.ptr, F.s.ptr, seli.ptr, nf, T, g->deg,
+                                                     selk.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(radix_sort_u64_i32(ctx, selk.ptr, seli.ptr, selk2.ptr, seli2.ptr, nf, 64));
+    sel_split_kernel<<<grid_for(nf), kBlock, 0, s>>>(F.v.ptr, F.s.ptr, seli.ptr, nf, m, selv.ptr,
+                                                      seli2.ptr, U.v.ptr, U.s.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(radix_sort_u32_i32(ctx, selv.ptr, seli2.ptr, selv2.ptr, seli.ptr, m, vb));
+    LGC_CUDA_TRY(cudaMemsetAsync(selcnt.ptr, 0, 8, s));
+    copy_frontier_kernel<<<grid_for(m), kBlock, 0, s>>>(selv.ptr, seli2.ptr, m, g->deg, F.v.ptr,
+                                                         F.s.ptr, selcnt.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, selcnt.ptr, 8, cudaMemcpyDeviceToHost, s));
+    LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    F.size = m;
+    F.edges = ctx->h_scratch[0];
+    U.size = nf - m;
+    U.edges = E0 - F.edges;
+    return LGC_OK;
+  }
+
+  // G (the round's next frontier) united with U: sorted by id, duplicates
+  // dropped.
+  int merge_rest(const Table& T, double eps) {
+    if (U.size == 0) return LGC_OK;
+    cudaStream_t s = ctx->stream;
+    const int64_t na = G.size, nb = U.size, tot = na + nb;
+    LGC_TRY(selv.reserve(ctx, tot));
+    LGC_TRY(selv2.reserve(ctx, tot));
+    LGC_TRY(seli.reserve(ctx, tot));
+    LGC_TRY(seli2.reserve(ctx, tot));
+    LGC_TRY(flag.reserve(ctx, tot));
+    LGC_TRY(qpos.reserve(ctx, tot));
+    LGC_TRY(selcnt.reserve(ctx, 2));
+    cat_frontier_kernel<<<grid_for(tot), kBlock, 0, s>>>(G.v.ptr, G.s.ptr, na, U.v.ptr, U.s.ptr,
+                                                          nb, T, g->deg, eps, selv.ptr, seli.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(radix_sort_u32_i32(ctx, selv.ptr, seli.ptr, selv2.ptr, seli2.ptr, tot, 32));
+    uniq_flags_kernel<<<grid_for(tot), kBlock, 0, s>>>(selv.ptr, tot, flag.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(scan_i64(ctx, flag.ptr, qpos.ptr, tot, false, (int64_t*)selcnt.ptr + 1));
+    // G's entries are in selv/seli now: its buffers may be replaced
+    LGC_TRY(G.v.reserve(ctx, tot));
+    LGC_TRY(G.s.reserve(ctx, tot));
+    LGC_CUDA_TRY(cudaMemsetAsync(selcnt.ptr, 0, 8, s));
+    uniq_write_kernel<<<grid_for(tot), kBlock, 0, s>>>(selv.ptr, seli.ptr, flag.ptr, qpos.ptr, tot,
+                                                        g->deg, G.v.ptr, G.s.ptr, selcnt.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, selcnt.ptr, 16, cudaMemcpyDeviceToHost, s));
+    LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    G.edges = ctx->h_scratch[0];
+    G.size = ctx->h_scratch[1];
+    U.size = 0;
+    U.edges = 0;
+    return LGC_OK;
+  }
+
   int scan_counts(int64_t* nrec_out) {
     LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, F.size, false, total.ptr));
     LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost,
@@ -1907,10 +2149,11 @@ int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, 
 
 }  // namespace
 
-// Picks the batch depth of the heavy-vertex pull gather for this graph: each
-// candidate gathers a frontier of all vertices into a scratch dense set
-// three times (after one untimed launch), and the fastest median wins.  The
-// gathered sums are exact, so every candidate gives the same values.
+// Picks the shape of the heavy-vertex pull gather for this graph (edges per
+// lane per batch, lanes per work item): each candidate gathers a frontier of
+// all vertices into a scratch dense set three times (after one untimed
+// launch), and the fastest median wins.  The gathered sums are exact, so
+// every candidate gives the same values.
 int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   if (g->nheavy == 0 || g->nitems == 0) return LGC_OK;
   cudaStream_t s = ctx->stream;
@@ -1938,15 +2181,15 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
     }
     tune_fill_kernel<<<grid_for(n), kBlock, 0, s>>>(shx, n, range, gb);
     LGC_COUNT_LAUNCH(ctx);
-    const int64_t hb = ceil_div(g->nitems, kBlock / 32);
-    const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
-    const int cand[3] = {4, 8, 16};
+    // (batch depth, lanes per item)
+    const int cand[7][2] = {{4, 32}, {8, 32}, {16, 32}, {8, 16}, {16, 16}, {8, 8}, {16, 8}};
     float best_ms = 0.f;
-    int best = kPullBatch;
-    for (int c : cand) {
-      auto heavy = c == 16 ? pull_heavy_fx_kernel<16>
-                   : c == 4 ? pull_heavy_fx_kernel<4>
-                            : pull_heavy_fx_kernel<kPullBatch>;
+    int best = kPullBatch, best_group = 32;
+    for (int ci = 0; ci < 7; ci++) {
+      const int cb = cand[ci][0], cg = cand[ci][1];
+      HeavyKernel heavy = heavy_kernel(cb, cg);
+      const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / cg));
+      const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
       float t[3];
       for (int r = -1; r < 3; r++) {
         if (cudaEventRecord(e0, s)) st = LGC_ECUDA;
@@ -1959,12 +2202,16 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
       }
       if (st != LGC_OK) break;
       std::sort(t, t + 3);
-      if (c == cand[0] || t[1] < best_ms) {
+      if (ci == 0 || t[1] < best_ms) {
         best_ms = t[1];
-        best = c;
+        best = cb;
+        best_group = cg;
       }
     }
-    if (st == LGC_OK) g->pull_batch = best;
+    if (st == LGC_OK) {
+      g->pull_batch = best;
+      g->pull_group = best_group;
+    }
   } while (0);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -1976,14 +2223,37 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   return st;
 }
 
-int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm, lgc_svec** p,
-                 lgc_stats* st_out, lgc_svec** r_out) {
-  int64_t dx = 0;
-  LGC_TRY(validate_seed(ctx, g, x, &dx));
+// PR-Nibble from the seed set seeds[0..k) with weights (null: all 1) and
+// beta-fraction rounds (beta = 1: every candidate pushes).  One seed of
+// weight 1 with beta = 1 is Fig. alg:pr-nibble2 / alg:pr-nibble exactly.
+int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds,
+                     const double* weights, double beta, const lgc_prnibble_params* prm,
+                     lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out) {
+  if (!g || k < 1 || !seeds || !prm || !(beta > 0.0 && beta <= 1.0)) return LGC_EINVAL;
   const double alpha = prm->alpha, eps = prm->eps;
   if (!(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0) || (prm->rule != 0 && prm->rule != 1) ||
       (prm->mode != 0 && prm->mode != 1))
     return LGC_EINVAL;
+  // r starts as w_i / W (W summed left to right), the seeds in ascending id
+  std::vector<std::pair<int32_t, double>> init((size_t)k);
+  double Wsum = 0.0;
+  int64_t dsum = 0;
+  for (int64_t i = 0; i < k; i++) {
+    int64_t dx = 0;
+    LGC_TRY(validate_seed(ctx, g, seeds[i], &dx));
+    const double w = weights ? weights[i] : 1.0;
+    if (!(w > 0.0) || !std::isfinite(w)) return LGC_EINVAL;
+    Wsum = Wsum + w;
+    dsum += dx;
+    init[i] = {seeds[i], w};
+  }
+  for (auto& e : init) e.second = e.second / Wsum;
+  std::sort(init.begin(), init.end(),
+            [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+              return a.first < b.first;
+            });
+  for (int64_t i = 1; i < k; i++)
+    if (init[i].first == init[i - 1].first) return LGC_EINVAL;  // seeds must be distinct
   const bool det = prm->mode == LGC_MODE_DET;
   const double cs = (2.0 * alpha) / (1.0 + alpha);
   const double cn = (1.0 - alpha) / (1.0 + alpha);
@@ -1993,40 +2263,69 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
 
   PushWork W(ctx, g);
   Table T;
-  LGC_TRY(table_create(ctx, &T, 2 * (1 + dx), true));
-  int64_t count = 1;  // keys in T
+  LGC_TRY(table_create(ctx, &T, 2 * (k + dsum), true));
+  int64_t count = k;  // keys in T
   int status = LGC_OK;
+  int32_t* d_x = nullptr;
+  double* d_r = nullptr;
   do {
-    if ((status = W.F.v.reserve(ctx, 1024)) != LGC_OK) break;
-    if ((status = W.F.s.reserve(ctx, 1024)) != LGC_OK) break;
+    if ((status = W.F.v.reserve(ctx, std::max<int64_t>(k, 1024))) != LGC_OK) break;
+    if ((status = W.F.s.reserve(ctx, std::max<int64_t>(k, 1024))) != LGC_OK) break;
     if ((status = W.reset_counters()) != LGC_OK) break;
-    init_seed_kernel<<<1, 1, 0, ctx->stream>>>(T, x, 1.0, W.F.v.ptr, W.F.s.ptr, ctx->d_counters);
+    if (k == 1) {
+      init_seed_kernel<<<1, 1, 0, ctx->stream>>>(T, init[0].first, init[0].second, W.F.v.ptr,
+                                                  W.F.s.ptr, ctx->d_counters);
+    } else {
+      std::vector<int32_t> xs((size_t)k);
+      std::vector<double> rs((size_t)k);
+      for (int64_t i = 0; i < k; i++) {
+        xs[i] = init[i].first;
+        rs[i] = init[i].second;
+      }
+      if ((status = dalloc_t(ctx, &d_x, k)) != LGC_OK) break;
+      if ((status = dalloc_t(ctx, &d_r, k)) != LGC_OK) break;
+      if (cudaMemcpyAsync(d_x, xs.data(), 4 * k, cudaMemcpyHostToDevice, ctx->stream) ||
+          cudaMemcpyAsync(d_r, rs.data(), 8 * k, cudaMemcpyHostToDevice, ctx->stream) ||
+          cudaStreamSynchronize(ctx->stream)) {  // xs, rs go out of scope
+        status = LGC_ECUDA;
+        break;
+      }
+      init_seeds_kernel<<<grid_for(k), kBlock, 0, ctx->stream>>>(T, d_x, d_r, k, W.F.v.ptr,
+                                                                  W.F.s.ptr, ctx->d_counters);
+    }
     LGC_COUNT_LAUNCH(ctx);
-    W.F.size = 1;
-    W.F.edges = dx;
+    W.F.size = k;
+    W.F.edges = dsum;
     lgc_stats& st = W.st;
     while (W.F.size > 0) {
       if (st.rounds >= max_rounds) {
         status = LGC_EMAXROUNDS;
         break;
       }
-      if (!det && W.small_round(T, count)) {
+      if (!det && beta >= 1.0 && W.small_round(T, count)) {
         status = W.device_rounds_prnibble(T, &count, alpha, cs, cn, eps, prm->rule,
                                           max_rounds - st.rounds);
         if (status != LGC_OK) break;
         continue;
       }
-      W.record_trace();
       // room for the round's new keys (at most the frontier's edges)
       if ((status = ensure_capacity(ctx, &T, count, W.F.edges, g->n, W.F.v.ptr, W.F.s.ptr,
                                     W.F.size)) != LGC_OK)
         break;
-      const int64_t nf = W.F.size;
       const bool pull = use_pull(ctx, g, W.F.edges);
       if (pull && !T.dense &&
-          (status = table_to_dense(ctx, &T, g->n, W.F.v.ptr, W.F.s.ptr, nf)) != LGC_OK)
+          (status = table_to_dense(ctx, &T, g->n, W.F.v.ptr, W.F.s.ptr, W.F.size)) != LGC_OK)
         break;
       const bool bulk = use_bulk(det, T, W.F.edges, g->n);
+      // beta-fraction rounds: the top ceil(beta |F|) candidates push, the
+      // others wait in W.U (after every change of the table's slots)
+      if (beta < 1.0 && W.F.size > 1) {
+        int64_t m = (int64_t)std::ceil(beta * (double)W.F.size);
+        m = std::max<int64_t>(1, std::min<int64_t>(m, W.F.size));
+        if (m < W.F.size && (status = W.select_top(T, m)) != LGC_OK) break;
+      }
+      W.record_trace();
+      const int64_t nf = W.F.size;
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
@@ -2062,6 +2361,7 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
       count += C.inserted;
       W.G.size = C.next_size;
       W.G.edges = C.next_edges;
+      if ((status = W.merge_rest(T, eps)) != LGC_OK) break;  // candidates that waited
       W.swap_frontiers();
     }
     st.touched = count;
@@ -2081,7 +2381,14 @@ int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_param
     if (s2 != LGC_OK) status = s2;
   }
   table_destroy(ctx, &T);
+  dfree(ctx, d_x);
+  dfree(ctx, d_r);
   return status;
+}
+
+int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm,
+                 lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out) {
+  return run_prnibble_set(ctx, g, 1, &x, nullptr, 1.0, prm, p, st_out, r_out);
 }
 
 int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* prm, lgc_svec** p,

@@ -110,7 +110,7 @@ SIGNATURES = {
     "lgc_rand_hkpr_endpoints": (c_int, [_P, _P, c_int64]),
     "lgc_sweep": (c_int, [_P, POINTER(Svec), POINTER(POINTER(Cluster))]),
     "lgc_sweep_batch": (c_int, [_P, c_int64, _P, _P]),
-    "lgc_graph_autotune": (c_int, [_P, POINTER(c_int)]),
+    "lgc_graph_autotune": (c_int, [_P, POINTER(c_int), POINTER(c_int)]),
     "lgc_get_trace": (c_int, [_P, POINTER(c_int64), _P, c_int64, _P, c_int64]),
     "lgc_prnibble_residual": (c_int, [_P, POINTER(POINTER(Svec))]),
     "lgc_submit": (c_int, [_P, _P, POINTER(Request), POINTER(c_uint64)]),
@@ -121,6 +121,8 @@ SIGNATURES = {
     "lgc_strerror": (ctypes.c_char_p, [c_int]),
     "lgc_sweep_noalloc": (c_int, [_P, c_int64, _P, _P, _P, POINTER(Cluster)]),
     "lgc_prnibble_batch": (c_int, [_P, c_int64, _P, _P, _P, _P]),
+    "lgc_prnibble_set": (c_int, [_P, c_int64, _P, _P, c_double, POINTER(PRNibbleParams),
+                                 POINTER(POINTER(Svec)), POINTER(Stats)]),
     "lgc_launch_count": (c_int64, [_P]),
     "lgc_profile_read": (c_int, [_P, c_int, _P]),
     "lgc_profile_reset": (c_int, [_P]),
@@ -131,6 +133,7 @@ OPT_TABLE_FORM = 6
 OPT_PULL = 7
 OPT_DEVICE_ROUNDS = 8
 OPT_PULL_BATCH = 9
+OPT_PULL_GROUP = 10
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}
@@ -285,12 +288,12 @@ class Graph:
         self.nnz = lib.lgc_graph_num_entries(h)
         ctx._own(self)
 
-    def autotune(self) -> int:
-        """lgc_graph_autotune: times the heavy-vertex pull gather's batch depths
-        on this graph and keeps the fastest; returns it."""
-        b = c_int()
-        _check(load().lgc_graph_autotune(self.handle, byref(b)), "lgc_graph_autotune")
-        return b.value
+    def autotune(self) -> tuple:
+        """lgc_graph_autotune: times the heavy-vertex pull gather's shapes on
+        this graph and keeps the fastest; returns (batch depth, lanes per item)."""
+        b, gr = c_int(), c_int()
+        _check(load().lgc_graph_autotune(self.handle, byref(b), byref(gr)), "lgc_graph_autotune")
+        return b.value, gr.value
 
     def close(self):
         if getattr(self, "handle", None):
@@ -427,6 +430,22 @@ def prnibble(g: Graph, seed: int, alpha: float, eps: float, rule="opt", mode="at
     out, st = POINTER(Svec)(), Stats()
     s = load().lgc_prnibble(g.handle, seed, byref(prm), byref(out), byref(st))
     _check(s, "lgc_prnibble", ok=(LGC_OK, LGC_EMAXROUNDS))
+    return SparseVec(out, g.ctx), st
+
+
+def prnibble_set(g: Graph, seeds, alpha: float, eps: float, weights=None, beta: float = 1.0,
+                 rule="opt", mode="atomic", max_rounds: int = 0):
+    """PR-Nibble from a seed set (weights: None for all 1) with beta-fraction
+    rounds (lgc_prnibble_set)."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(weights, dtype=np.float64), seeds.shape))
+    prm = PRNibbleParams(alpha, eps, _RULES[rule], _MODES[mode], max_rounds)
+    out, st = POINTER(Svec)(), Stats()
+    s = load().lgc_prnibble_set(g.handle, len(seeds), seeds.ctypes.data,
+                                None if w is None else w.ctypes.data, float(beta), byref(prm),
+                                byref(out), byref(st))
+    _check(s, "lgc_prnibble_set", ok=(LGC_OK, LGC_EMAXROUNDS))
     return SparseVec(out, g.ctx), st
 
 

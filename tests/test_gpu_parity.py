@@ -431,8 +431,9 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         x = inputs.config1_seed(off, col)
         ref = oracle.prnibble(off, col, x, 0.01, 1e-6)
         res = []
-        for b in (4, 8, 16):
+        for b, gw in ((4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8)):
             c.set_option(lgc.OPT_PULL_BATCH, b)
+            c.set_option(lgc.OPT_PULL_GROUP, gw)
             p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
             assert (st.rounds, st.pushed_edges) == (ref.rounds, ref.pushed_edges)
             assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
@@ -440,11 +441,14 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         for p in res[1:]:
             assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
         c.set_option(lgc.OPT_PULL_BATCH, 0)
-        assert g.autotune() in (4, 8, 16)
+        c.set_option(lgc.OPT_PULL_GROUP, 0)
+        b, gw = g.autotune()
+        assert (b, gw) in ((4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8))
         p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
         assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
     finally:
         c.set_option(lgc.OPT_PULL_BATCH, 0)
+        c.set_option(lgc.OPT_PULL_GROUP, 0)
         c.set_option(lgc.OPT_PULL, 0)
         c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
         g.close()
