@@ -191,9 +191,10 @@ def hk_terms(t, eps):
 
 
 def measure_many(lgc, inputs, torch, ctx, g, off):
-    """1024 PR-Nibble + sweep clusters, once through lgc_prnibble_batch and
-    lgc_sweep_batch (in chunks) and once one seed per call (lgc_prnibble,
-    lgc_sweep); device-resident results."""
+    """1024 PR-Nibble + sweep clusters three ways: lgc_prnibble_batch and
+    lgc_sweep_batch (in chunks), one seed per call (lgc_prnibble, lgc_sweep),
+    and all at once through the request loop (lgc_submit / lgc_poll, host
+    results); device-resident results for the first two."""
     seeds = inputs.seeds_deg2(off, MANY["seeds"], MANY["seed_stream"])
     eps = inputs.eps_loguniform(MANY["seeds"], MANY["seed_stream"], MANY["eps_lo"], MANY["eps_hi"])
     a = MANY["alpha"]
@@ -224,6 +225,33 @@ def measure_many(lgc, inputs, torch, ctx, g, off):
         del p
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
+    # all requests at once through the request loop (worker contexts run the
+    # single-seed diffusions side by side on their own streams)
+    ctx.set_option(lgc.OPT_SERVE_MEM_BUDGET, SERVE["mem_budget"])
+    try:
+        ctx.set_option(lgc.OPT_SERVE_MAX_BATCH, SERVE["max_batch"])
+    except lgc.LgcError:
+        pass  # the loop is already running
+    reqs = [lgc.make_request(lgc.ALGO_PRNIBBLE, int(seeds[b]), True, alpha=a, eps=float(eps[b]),
+                             mode=MODE) for b in range(len(seeds))]
+    for tk in [lgc.submit(ctx, g, reqs[b]) for b in range(8)]:  # warm the workers
+        while lgc.poll(ctx, tk) is None:
+            time.sleep(0.0005)
+    t0 = time.perf_counter()
+    pending = [lgc.submit(ctx, g, r) for r in reqs]
+    e_q = 0
+    while pending:
+        still = []
+        for tk in pending:
+            r = lgc.poll(ctx, tk)
+            if r is None:
+                still.append(tk)
+            else:
+                e_q += r["stats"]["pushed_edges"]
+        pending = still
+        if pending:
+            time.sleep(0.0002)
+    tq = time.perf_counter() - t0
     B = len(seeds)
     return {"workload": (f"R-MAT scale {MANY['scale']} (seed {MANY['graph_seed']}), {B} PR-Nibble "
                          f"seeds (degree >= 2, stream {MANY['seed_stream']}), alpha {a}, eps "
@@ -232,6 +260,8 @@ def measure_many(lgc, inputs, torch, ctx, g, off):
             "clusters": B, "pushed_edges": e_b,
             "batched": {"clusters_per_s": B / tb, "edges_per_s": e_b / tb, "s": tb},
             "per_seed": {"clusters_per_s": B / ts, "edges_per_s": e_s / ts, "s": ts},
+            "request_loop": {"clusters_per_s": B / tq, "edges_per_s": e_q / tq, "s": tq,
+                             "resident": SERVE["max_batch"]},
             "speedup": ts / tb}
 
 
@@ -257,7 +287,10 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
                                          N=hk_terms(t, SERVE["hk_eps"]), eps=SERVE["hk_eps"],
                                          mode=MODE))
     ctx.set_option(lgc.OPT_SERVE_MEM_BUDGET, SERVE["mem_budget"])
-    ctx.set_option(lgc.OPT_SERVE_MAX_BATCH, SERVE["max_batch"])
+    try:
+        ctx.set_option(lgc.OPT_SERVE_MAX_BATCH, SERVE["max_batch"])
+    except lgc.LgcError:
+        pass  # the loop is already running with it (set by measure_many)
     # warm the workers
     for tk in [lgc.submit(ctx, g, reqs[i]) for i in range(8)]:
         while lgc.poll(ctx, tk) is None:

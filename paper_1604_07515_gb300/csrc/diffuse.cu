@@ -1338,33 +1338,90 @@ __global__ void head_starts_kernel(const uint32_t* __restrict__ rkey, int64_t R,
 
 // One thread per destination run: left fold from the current table value,
 // in ascending source order (the order of the run after the stable sort).
+// Runs longer than kFoldLong records (a hub destination) are not folded by
+// one thread: fold_kernel resolves their slot and lists them, and
+// fold_long_kernel folds each with a warp, 256 records at a time, with the
+// binade scan of fold_batch (same bits as the sequential fold).
+constexpr int64_t kFoldLong = 64;
+
 __global__ void fold_kernel(const uint32_t* __restrict__ rkey, const double* __restrict__ rval,
                             int64_t R, const int64_t* __restrict__ segstart, int64_t nseg,
                             Table D, const int32_t* __restrict__ deg, double c, int fmode,
                             int64_t* __restrict__ qflag, int32_t* __restrict__ segv,
-                            int32_t* __restrict__ segslot, Counters* C) {
+                            int32_t* __restrict__ segslot, int64_t* __restrict__ longs,
+                            int32_t* __restrict__ nlong, Counters* C) {
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nseg;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sg = base + threadIdx.x;
     int ins = 0;
+    bool is_long = false;
     if (sg < nseg) {
       const int64_t b = segstart[sg];
       const int64_t e = sg + 1 < nseg ? segstart[sg + 1] : R;
       const int32_t w = (int32_t)rkey[b];
       const int64_t slot = tb_find_or_insert(D, w, &ins, &C->err);
       int64_t q = 0;
-      if (slot >= 0) {
+      if (slot >= 0 && e - b > kFoldLong) {
+        is_long = true;  // folded by fold_long_kernel, which also sets qflag
+      } else if (slot >= 0) {
         double acc = *tb_val(D, slot);
         for (int64_t k = b; k < e; k++) acc = acc + rval[k];
         *tb_val(D, slot) = acc;
         if (fmode == kFmThreshold) q = acc >= c * (double)deg[w] ? 1 : 0;
         else if (fmode == kFmInserted) q = 1;
       }
-      qflag[sg] = q;
+      if (!is_long) qflag[sg] = q;
       segv[sg] = w;
       segslot[sg] = (int32_t)slot;
     }
+    // warp-aggregated append of the long runs
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, is_long);
+    if (m) {
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      int at = 0;
+      if (lane == leader) at = atomicAdd(nlong, __popc(m));
+      at = __shfl_sync(active, at, leader);
+      if (is_long) longs[at + __popc(m & ((1u << lane) - 1))] = sg;
+    }
     count_inserted(ins, &C->inserted);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    fold_long_kernel(const double* __restrict__ rval, int64_t R,
+                     const int64_t* __restrict__ segstart, int64_t nseg,
+                     const int64_t* __restrict__ longs, const int32_t* __restrict__ nlong,
+                     Table D, const int32_t* __restrict__ deg, double c, int fmode,
+                     int64_t* __restrict__ qflag, const int32_t* __restrict__ segv,
+                     const int32_t* __restrict__ segslot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nl = *nlong;
+  for (int64_t i = warp0; i < nl; i += nwarps) {
+    const int64_t sg = longs[i];
+    const int64_t b = segstart[sg];
+    const int64_t e = sg + 1 < nseg ? segstart[sg + 1] : R;
+    const int32_t w = segv[sg];
+    const int64_t slot = segslot[sg];
+    double acc = *tb_val(D, slot);  // the same in every lane
+    for (int64_t k0 = b; k0 < e; k0 += 256) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int64_t k = k0 + 8 * lane + j;
+        v[j] = k < e ? rval[k] : 0.0;  // +0.0 past the run adds nothing
+      }
+      acc = fold_batch(acc, v, lane);
+    }
+    if (lane == 0) {
+      *tb_val(D, slot) = acc;
+      int64_t q = 0;
+      if (fmode == kFmThreshold) q = acc >= c * (double)deg[w] ? 1 : 0;
+      else if (fmode == kFmInserted) q = 1;
+      qflag[sg] = q;
+    }
   }
 }
 
@@ -1568,6 +1625,8 @@ struct PushWork {
   DBuf<double> rv, rv2;
   DBuf<int64_t> flag, segid, segstart, qflag, qpos;
   DBuf<int32_t> segv, segslot;
+  DBuf<int64_t> longs;  // runs folded by a warp
+  DBuf<int32_t> nlong;
   DBuf<int64_t> total;  // one device int64
   // pull rounds: per-vertex frontier share (membership encoded), qualify bitmap
   DBuf<double> psh;
@@ -1631,6 +1690,8 @@ struct PushWork {
     qpos.release(ctx);
     segv.release(ctx);
     segslot.release(ctx);
+    longs.release(ctx);
+    nlong.release(ctx);
     total.release(ctx);
     psh.release(ctx);
     pshx.release(ctx);
@@ -1769,9 +1830,17 @@ struct PushWork {
       ProfScope ps(ctx, LGC_PROF_DET_EDGE, 0.0);
       head_starts_kernel<<<grid_for(nrec), kBlock, 0, s>>>(rk.ptr, nrec, segid.ptr, segstart.ptr);
       LGC_COUNT_LAUNCH(ctx);
+      LGC_TRY(longs.reserve(ctx, nseg));
+      LGC_TRY(nlong.reserve(ctx, 1));
+      LGC_CUDA_TRY(cudaMemsetAsync(nlong.ptr, 0, 4, s));
       fold_kernel<<<grid_for(nseg), kBlock, 0, s>>>(rk.ptr, rv.ptr, nrec, segstart.ptr, nseg, D,
                                                      g->deg, c, fmode, qflag.ptr, segv.ptr,
-                                                     segslot.ptr, ctx->d_counters);
+                                                     segslot.ptr, longs.ptr, nlong.ptr,
+                                                     ctx->d_counters);
+      LGC_COUNT_LAUNCH(ctx);
+      fold_long_kernel<<<152 * 4, kBlock, 0, s>>>(rv.ptr, nrec, segstart.ptr, nseg, longs.ptr,
+                                                   nlong.ptr, D, g->deg, c, fmode, qflag.ptr,
+                                                   segv.ptr, segslot.ptr);
       LGC_COUNT_LAUNCH(ctx);
       LGC_CUDA_TRY(cudaGetLastError());
       if (fmode != kFmNone) {
@@ -2070,14 +2139,6 @@ struct PushWork {
     return LGC_OK;
   }
 
-  int scan_counts(int64_t* nrec_out) {
-    LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, F.size, false, total.ptr));
-    LGC_CUDA_TRY(cudaMemcpyAsync(&ctx->h_counters->aux, total.ptr, 8, cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-    LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    *nrec_out = ctx->h_counters->aux;
-    return LGC_OK;
-  }
 
   void swap_frontiers() {
     std::swap(F.v, G.v);
@@ -2347,7 +2408,11 @@ int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds
       } else {
         int64_t nrec = W.F.edges;
         if (det) {
-          if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+          // one record per edge and one self record per frontier vertex
+          // (cnt[i] = d + 1): the total is known without reading it back
+          nrec = W.F.edges + nf;
+          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+            break;
         } else {
           if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
             break;
@@ -2445,7 +2510,11 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
       } else {
         int64_t nrec = W.F.edges;
         if (det) {
-          if ((status = W.scan_counts(&nrec)) != LGC_OK) break;
+          // one record per edge and one self record per frontier vertex
+          // (cnt[i] = d + 1): the total is known without reading it back
+          nrec = W.F.edges + nf;
+          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+            break;
         } else {
           if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
             break;
