@@ -148,10 +148,14 @@ enum {
   LGC_OPT_PULL_BATCH = 9,       /* edges per lane per batch in the heavy-vertex pull gather:
                                    0 (default) the graph's tuned value (see
                                    lgc_graph_autotune), or 4, 8, 16 */
-  LGC_OPT_PULL_GROUP = 10       /* lanes per work item in the heavy-vertex pull gather: 0
+  LGC_OPT_PULL_GROUP = 10,      /* lanes per work item in the heavy-vertex pull gather: 0
                                    (default) the graph's tuned value, or 8, 16, 32 (only
                                    the pairs lgc_graph_autotune tries are compiled: 4 with
                                    32; 8 and 16 with 8, 16, 32) */
+  LGC_OPT_PULL_SHARE = 11       /* bytes per gathered share in atomic pull rounds: 0
+                                   (default) the graph's tuned value, 16 (fixed-point
+                                   records) or 8 (doubles, converted per edge); same
+                                   results either way */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */
@@ -167,12 +171,13 @@ int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int3
 void lgc_graph_destroy(lgc_graph *g);
 /* Tunes the graph's launch shapes by timing them on the graph itself (the
  * paper has no counterpart; it affects speed only): for the heavy-vertex
- * pull gather, the edges each lane loads per batch and the lanes per work
- * item, from (4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8),
- * on a frontier of all vertices.  Takes a few launches of that gather per
- * candidate; the chosen pair is written to *pull_batch and *pull_group
- * (both nullable).  Until it is called the graph uses (8, 32). */
-int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group);
+ * pull gather of atomic rounds, the edges each lane loads per batch and the
+ * lanes per work item, from (4, 32), (8, 32), (16, 32), (8, 16), (16, 16),
+ * (8, 8), (16, 8), each with 16- and 8-byte gathered shares, on a frontier
+ * of all vertices.  Takes a few launches of that gather per candidate; the
+ * choice is written to *pull_batch, *pull_group, *pull_share (nullable).
+ * Until it is called the graph uses (8, 32, 16). */
+int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group, int *pull_share);
 int64_t lgc_graph_num_vertices(const lgc_graph *g);
 int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
 

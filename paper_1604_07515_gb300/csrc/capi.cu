@@ -427,6 +427,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 8 && value != 16 && value != 32) return LGC_EINVAL;
       ctx->pull_group = (int)value;
       return LGC_OK;
+    case LGC_OPT_PULL_SHARE:
+      if (value != 0 && value != 8 && value != 16) return LGC_EINVAL;
+      ctx->pull_share = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -560,11 +564,12 @@ void lgc_graph_destroy(lgc_graph* g) {
   delete g;
 }
 
-int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group) {
+int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group, int* pull_share) {
   if (!g) return LGC_EINVAL;
   LGC_TRY(autotune_pull(g->ctx, g));
   if (pull_batch) *pull_batch = g->pull_batch;
   if (pull_group) *pull_group = g->pull_group;
+  if (pull_share) *pull_share = g->pull_share;
   return LGC_OK;
 }
 

@@ -199,6 +199,7 @@ struct lgc_ctx {
   bool device_rounds = true;  // LGC_OPT_DEVICE_ROUNDS
   int pull_batch = 0;          // LGC_OPT_PULL_BATCH: 0 = the graph's tuned value
   int pull_group = 0;          // LGC_OPT_PULL_GROUP: 0 = the graph's tuned value
+  int pull_share = 0;          // LGC_OPT_PULL_SHARE: 0 = the graph's tuned value
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back
@@ -253,6 +254,7 @@ struct lgc_graph {
   std::vector<int32_t> hdeg;  // host copy of deg (seeds are checked without a device read)
   int pull_batch = 8;          // edges per lane per batch in heavy pull gathers (tuned)
   int pull_group = 32;         // lanes per work item in heavy pull gathers (tuned)
+  int pull_share = 16;         // bytes per gathered share in atomic pull gathers (tuned)
   // vertices of degree > kPullLight in ascending id, for the pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;

@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 #include <string.h>
 
@@ -1011,6 +1012,28 @@ __device__ inline int round_scale(const int32_t* range, int g) {
   return fx_scale(2047 - range[0], range[1], g);
 }
 
+// The gathered frontier share as a fixed-point record: either stored so
+// (16 bytes per vertex), or stored as the double share with the membership
+// encoding of the deterministic pull (+0.0 outside the frontier, -0.0 for a
+// zero share) and converted here (8 bytes per vertex, a few integer
+// operations per edge).  Same value either way.
+__device__ inline Fx to_fx(const Fx& x, int) { return x; }
+__device__ inline Fx to_fx(double s, int L) {
+  Fx x = fx_from_double(s, L);  // -0.0 -> 0
+  if (fx_bits(s) != 0) x.hi |= kFxFlag;
+  return x;
+}
+template <typename SH>
+__device__ inline SH no_share();
+template <>
+__device__ inline Fx no_share<Fx>() {
+  return Fx{0, 0};
+}
+template <>
+__device__ inline double no_share<double>() {
+  return 0.0;
+}
+
 __global__ void pull_scatter_fx_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                        const double* __restrict__ share, Fx* __restrict__ shx,
                                        const int32_t* __restrict__ range, int g, int clear) {
@@ -1028,13 +1051,19 @@ __global__ void pull_scatter_fx_kernel(int64_t nf, const int32_t* __restrict__ f
 
 // Autotuning input: every vertex in the frontier with share 1 (X = 1 at
 // the scale the range {1023, 1023} gives).
-__global__ void tune_fill_kernel(Fx* __restrict__ shx, int64_t n, int32_t* __restrict__ range,
+template <typename SH>
+__global__ void tune_fill_kernel(SH* __restrict__ shx, int64_t n, int32_t* __restrict__ range,
                                  int g) {
   const int L = fx_scale(1023, 1023, g);
   const Fx one = fx_from_double(1.0, L);
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    shx[v] = Fx{one.lo, one.hi | kFxFlag};
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(SH) == sizeof(Fx)) {
+      shx[v] = Fx{one.lo, one.hi | kFxFlag};
+    } else {
+      shx[v] = 1.0;
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     range[0] = 2047 - 1023;
     range[1] = 1023;
@@ -1045,10 +1074,11 @@ __global__ void tune_fill_kernel(Fx* __restrict__ shx, int64_t n, int32_t* __res
 // at a time (all column loads, then all share loads).  Every bitmap word of
 // qbits is written here (by ballot, heavy vertices' bits zero); the heavy
 // kernel, launched after this one, ORs its vertices in.
+template <typename SH>
 __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
                                           const int64_t* __restrict__ off,
                                           const int32_t* __restrict__ col, int64_t n,
-                                          const Fx* __restrict__ shx,
+                                          const SH* __restrict__ shx,
                                           const int32_t* __restrict__ range, int g, Table D,
                                           double c, int fmode, uint32_t* __restrict__ qbits,
                                           Counters* C) {
@@ -1068,12 +1098,14 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
 #pragma unroll
           for (int j = 0; j < 4; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
 #pragma unroll
+          SH raw[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) raw[j] = u[j] >= 0 ? shx[u[j]] : no_share<SH>();
+#pragma unroll
           for (int j = 0; j < 4; j++) {
-            if (u[j] >= 0) {
-              const Fx x = shx[u[j]];
-              flag |= x.hi;
-              fx_add(acc, x);
-            }
+            const Fx x = to_fx(raw[j], L);
+            flag |= x.hi;
+            fx_add(acc, x);
           }
         }
         const uint32_t m = 1u << (w & 31);
@@ -1111,12 +1143,12 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
 // consecutive items.  The loop over items runs the same number of times in
 // every lane of the warp (a group past the end works on nothing), so the
 // group-wide shuffles always find all their lanes.
-template <int BATCH, int GL>
+template <int BATCH, int GL, typename SH>
 __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
                                           const int64_t* __restrict__ off,
                                           const int32_t* __restrict__ col,
                                           const PullItem* __restrict__ items, int64_t nitems,
-                                          const Fx* __restrict__ shx,
+                                          const SH* __restrict__ shx,
                                           const int32_t* __restrict__ range, int g, Table D,
                                           double c, int fmode, uint32_t* __restrict__ qbits,
                                           Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
@@ -1158,17 +1190,14 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
         const int k = k0 + GL * j + gl;
         u[j] = k < I.len ? col[I.beg + k] : -1;
       }
-      Fx x[BATCH];
+      SH raw[BATCH];
+#pragma unroll
+      for (int j = 0; j < BATCH; j++) raw[j] = u[j] >= 0 ? shx[u[j]] : no_share<SH>();
 #pragma unroll
       for (int j = 0; j < BATCH; j++) {
-        x[j].lo = 0;
-        x[j].hi = 0;
-        if (u[j] >= 0) x[j] = shx[u[j]];
-      }
-#pragma unroll
-      for (int j = 0; j < BATCH; j++) {
-        flag |= x[j].hi;
-        fx_add(part, x[j]);
+        const Fx x = to_fx(raw[j], L);
+        flag |= x.hi;
+        fx_add(part, x);
       }
     }
     uint32_t mem = (flag & kFxFlag) ? 1u : 0u;
@@ -1213,25 +1242,26 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
   }
 }
 
-template <int BATCH, int GL>
+template <int BATCH, int GL, typename SH>
 __global__ void __launch_bounds__(kBlock)
     pull_heavy_fx_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                          const PullItem* __restrict__ items, int64_t nitems,
-                         const Fx* __restrict__ shx, const int32_t* __restrict__ range, int g,
+                         const SH* __restrict__ shx, const int32_t* __restrict__ range, int g,
                          Table D, double c, int fmode, uint32_t* __restrict__ qbits,
                          Fx* __restrict__ hacc, int32_t* __restrict__ hcnt,
                          int32_t* __restrict__ htouch, Counters* C) {
-  pull_heavy_fx_body<BATCH, GL>(blockIdx.x, gridDim.x, off, col, items, nitems, shx, range, g, D,
-                                c,
-                            fmode, qbits, hacc, hcnt, htouch, C);
+  pull_heavy_fx_body<BATCH, GL, SH>(blockIdx.x, gridDim.x, off, col, items, nitems, shx, range, g,
+                                    D, c, fmode, qbits, hacc, hcnt, htouch, C);
 }
 
+template <typename SH>
 __global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
                                      const int32_t* __restrict__ col, int64_t n,
-                                     const Fx* __restrict__ shx,
+                                     const SH* __restrict__ shx,
                                      const int32_t* __restrict__ range, int g, Table D, double c,
                                      int fmode, uint32_t* __restrict__ qbits, Counters* C) {
-  pull_light_fx_body(blockIdx.x, gridDim.x, off, col, n, shx, range, g, D, c, fmode, qbits, C);
+  pull_light_fx_body<SH>(blockIdx.x, gridDim.x, off, col, n, shx, range, g, D, c, fmode, qbits,
+                         C);
 }
 
 // Ordered compaction of a vertex bitmap into a frontier (ascending id), with
@@ -1588,17 +1618,21 @@ __global__ void uniq_write_kernel(const uint32_t* __restrict__ kv, const int32_t
 
 }  // namespace
 
-using HeavyKernel = void (*)(const int64_t*, const int32_t*, const PullItem*, int64_t, const Fx*,
+template <typename SH>
+using HeavyKernel = void (*)(const int64_t*, const int32_t*, const PullItem*, int64_t, const SH*,
                              const int32_t*, int, Table, double, int, uint32_t*, Fx*, int32_t*,
                              int32_t*, Counters*);
 
 // The heavy-vertex gather compiled for a (batch depth, lanes per item) shape.
-HeavyKernel heavy_kernel(int batch, int group) {
-  if (group == 8) return batch == 16 ? pull_heavy_fx_kernel<16, 8> : pull_heavy_fx_kernel<8, 8>;
-  if (group == 16) return batch == 16 ? pull_heavy_fx_kernel<16, 16> : pull_heavy_fx_kernel<8, 16>;
-  return batch == 16 ? pull_heavy_fx_kernel<16, 32>
-         : batch == 4 ? pull_heavy_fx_kernel<4, 32>
-                      : pull_heavy_fx_kernel<kPullBatch, 32>;
+template <typename SH>
+HeavyKernel<SH> heavy_kernel(int batch, int group) {
+  if (group == 8)
+    return batch == 16 ? pull_heavy_fx_kernel<16, 8, SH> : pull_heavy_fx_kernel<8, 8, SH>;
+  if (group == 16)
+    return batch == 16 ? pull_heavy_fx_kernel<16, 16, SH> : pull_heavy_fx_kernel<8, 16, SH>;
+  return batch == 16 ? pull_heavy_fx_kernel<16, 32, SH>
+         : batch == 4 ? pull_heavy_fx_kernel<4, 32, SH>
+                      : pull_heavy_fx_kernel<kPullBatch, 32, SH>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1870,17 +1904,22 @@ struct PushWork {
       LGC_TRY(pcnt.reserve(ctx, words));
       pull_ready = true;
     }
-    if (det && !psh.ptr) {
+    // atomic mode gathers 16-byte fixed-point records or 8-byte doubles
+    // (the graph's tuned choice); deterministic mode always doubles
+    const int sb = det ? 8 : (ctx->pull_share ? ctx->pull_share : g->pull_share);
+    if (sb == 8 && !psh.ptr) {
       LGC_TRY(psh.reserve(ctx, n));
       LGC_CUDA_TRY(cudaMemsetAsync(psh.ptr, 0, 8 * n, s));
     }
-    if (!det && !pshx.ptr) {
+    if (!det && sb == 16 && !pshx.ptr) {
       LGC_TRY(pshx.reserve(ctx, n));
+      LGC_CUDA_TRY(cudaMemsetAsync(pshx.ptr, 0, sizeof(Fx) * n, s));
+    }
+    if (!det && !prange.ptr) {
       LGC_TRY(prange.reserve(ctx, 2));
       LGC_TRY(phacc.reserve(ctx, g->nheavy + 1));
       LGC_TRY(phcnt.reserve(ctx, g->nheavy + 1));
       LGC_TRY(phtouch.reserve(ctx, g->nheavy + 1));
-      LGC_CUDA_TRY(cudaMemsetAsync(pshx.ptr, 0, sizeof(Fx) * n, s));
       LGC_CUDA_TRY(cudaMemsetAsync(phacc.ptr, 0, sizeof(Fx) * (g->nheavy + 1), s));
       LGC_CUDA_TRY(cudaMemsetAsync(phcnt.ptr, 0, 4 * (g->nheavy + 1), s));
       LGC_CUDA_TRY(cudaMemsetAsync(phtouch.ptr, 0, 4 * (g->nheavy + 1), s));
@@ -1898,8 +1937,12 @@ struct PushWork {
       share_range_kernel<<<(int)(rb < 1 ? 1 : rb > 152 * 4 ? 152 * 4 : rb), kBlock, 0, s>>>(
           nf, share.ptr, prange.ptr);
       LGC_COUNT_LAUNCH(ctx);
-      pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
-                                                              prange.ptr, gb, 0);
+      if (sb == 8) {
+        pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
+      } else {
+        pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
+                                                                prange.ptr, gb, 0);
+      }
       LGC_COUNT_LAUNCH(ctx);
     }
     {
@@ -1942,21 +1985,25 @@ struct PushWork {
       } else {
         // light vertices (writing every bitmap word), then the heavy items
         // (ORing their vertices in); the two in one grid measured slower
-        pull_light_fx_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, pshx.ptr, prange.ptr, gb,
-                                                    D, c, fmode, pq.ptr, ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
-        if (g->nitems > 0) {
-          const int gw = ctx->pull_group ? ctx->pull_group : g->pull_group;
-          const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / gw));
-          const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
-          const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
-          const int group = ctx->pull_group ? ctx->pull_group : g->pull_group;
-          HeavyKernel heavy = heavy_kernel(batch, group);
-          heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, pshx.ptr, prange.ptr,
-                                      gb, D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
-                                      ctx->d_counters);
+        auto gather = [&](auto* shv) {
+          using SH = std::remove_const_t<std::remove_pointer_t<decltype(shv)>>;
+          pull_light_fx_kernel<SH><<<lg, kBlock, 0, s>>>(g->off, g->col, n, shv, prange.ptr, gb,
+                                                          D, c, fmode, pq.ptr, ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
-        }
+          if (g->nitems > 0) {
+            const int gw = ctx->pull_group ? ctx->pull_group : g->pull_group;
+            const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / gw));
+            const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+            const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
+            HeavyKernel<SH> heavy = heavy_kernel<SH>(batch, gw);
+            heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shv, prange.ptr, gb,
+                                        D, c, fmode, pq.ptr, phacc.ptr, phcnt.ptr, phtouch.ptr,
+                                        ctx->d_counters);
+            LGC_COUNT_LAUNCH(ctx);
+          }
+        };
+        if (sb == 8) gather(psh.ptr);
+        else gather(pshx.ptr);
       }
     }
     if (fmode != kFmNone) {
@@ -1970,7 +2017,7 @@ struct PushWork {
       set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
       LGC_COUNT_LAUNCH(ctx);
     }
-    if (det) {
+    if (sb == 8) {
       pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 1);
     } else {
       pull_scatter_fx_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, pshx.ptr,
@@ -2211,16 +2258,17 @@ int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, 
 }  // namespace
 
 // Picks the shape of the heavy-vertex pull gather for this graph (edges per
-// lane per batch, lanes per work item): each candidate gathers a frontier of
-// all vertices into a scratch dense set three times (after one untimed
-// launch), and the fastest median wins.  The gathered sums are exact, so
-// every candidate gives the same values.
+// lane per batch, lanes per work item, bytes per gathered share): each
+// candidate gathers a frontier of all vertices into a scratch dense set three
+// times (after one untimed launch), and the fastest median wins.  The
+// gathered sums are exact, so every candidate gives the same values.
 int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   if (g->nheavy == 0 || g->nitems == 0) return LGC_OK;
   cudaStream_t s = ctx->stream;
   const int64_t n = g->n, words = (n + 31) / 32;
   Table D;
   Fx *shx = nullptr, *hacc = nullptr;
+  double* shd = nullptr;
   int32_t *range = nullptr, *hcnt = nullptr, *htouch = nullptr;
   uint32_t* q = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2229,6 +2277,7 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   while (gb < 62 && (int64_t{1} << gb) <= g->max_deg) gb++;
   do {
     if ((st = table_create_dense(ctx, &D, n, false)) || (st = dalloc_t(ctx, &shx, n)) ||
+        (st = dalloc_t(ctx, &shd, n)) ||
         (st = dalloc_t(ctx, &range, 2)) || (st = dalloc_t(ctx, &q, words)) ||
         (st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
         (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
@@ -2240,44 +2289,59 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
       st = LGC_ECUDA;
       break;
     }
-    tune_fill_kernel<<<grid_for(n), kBlock, 0, s>>>(shx, n, range, gb);
+    tune_fill_kernel<Fx><<<grid_for(n), kBlock, 0, s>>>(shx, n, range, gb);
     LGC_COUNT_LAUNCH(ctx);
-    // (batch depth, lanes per item)
+    tune_fill_kernel<double><<<grid_for(n), kBlock, 0, s>>>(shd, n, range, gb);
+    LGC_COUNT_LAUNCH(ctx);
+    // (batch depth, lanes per item) x (16- or 8-byte shares)
     const int cand[7][2] = {{4, 32}, {8, 32}, {16, 32}, {8, 16}, {16, 16}, {8, 8}, {16, 8}};
     float best_ms = 0.f;
-    int best = kPullBatch, best_group = 32;
-    for (int ci = 0; ci < 7; ci++) {
-      const int cb = cand[ci][0], cg = cand[ci][1];
-      HeavyKernel heavy = heavy_kernel(cb, cg);
+    int best = kPullBatch, best_group = 32, best_share = 16;
+    bool first = true;
+    auto time_shape = [&](auto* shv, int cb, int cg, float* med) {
+      using SH = std::remove_pointer_t<decltype(shv)>;
+      HeavyKernel<SH> heavy = heavy_kernel<SH>(cb, cg);
       const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / cg));
       const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
-      float t[3];
+      float t[3] = {0.f, 0.f, 0.f};
       for (int r = -1; r < 3; r++) {
         if (cudaEventRecord(e0, s)) st = LGC_ECUDA;
-        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shx, range, gb, D, 1.0,
+        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shv, range, gb, D, 1.0,
                                     kFmThreshold, q, hacc, hcnt, htouch, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
         if (cudaEventRecord(e1, s) || cudaEventSynchronize(e1)) st = LGC_ECUDA;
-        if (st != LGC_OK) break;
+        if (st != LGC_OK) return;
         if (r >= 0 && cudaEventElapsedTime(&t[r], e0, e1)) st = LGC_ECUDA;
       }
-      if (st != LGC_OK) break;
       std::sort(t, t + 3);
-      if (ci == 0 || t[1] < best_ms) {
-        best_ms = t[1];
-        best = cb;
-        best_group = cg;
+      *med = t[1];
+    };
+    for (int sb : {16, 8}) {
+      for (int ci = 0; ci < 7 && st == LGC_OK; ci++) {
+        const int cb = cand[ci][0], cg = cand[ci][1];
+        float med = 0.f;
+        if (sb == 16) time_shape(shx, cb, cg, &med);
+        else time_shape(shd, cb, cg, &med);
+        if (st != LGC_OK) break;
+        if (first || med < best_ms) {
+          first = false;
+          best_ms = med;
+          best = cb;
+          best_group = cg;
+          best_share = sb;
+        }
       }
     }
     if (st == LGC_OK) {
       g->pull_batch = best;
       g->pull_group = best_group;
+      g->pull_share = best_share;
     }
   } while (0);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   table_destroy(ctx, &D);
-  for (void* p : {(void*)shx, (void*)range, (void*)q, (void*)hacc, (void*)hcnt, (void*)htouch})
+  for (void* p : {(void*)shx, (void*)shd, (void*)range, (void*)q, (void*)hacc, (void*)hcnt, (void*)htouch})
     dfree(ctx, p);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(Counters), s);
   if (cudaGetLastError() != cudaSuccess && st == LGC_OK) st = LGC_ECUDA;

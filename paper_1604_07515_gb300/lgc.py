@@ -110,7 +110,7 @@ SIGNATURES = {
     "lgc_rand_hkpr_endpoints": (c_int, [_P, _P, c_int64]),
     "lgc_sweep": (c_int, [_P, POINTER(Svec), POINTER(POINTER(Cluster))]),
     "lgc_sweep_batch": (c_int, [_P, c_int64, _P, _P]),
-    "lgc_graph_autotune": (c_int, [_P, POINTER(c_int), POINTER(c_int)]),
+    "lgc_graph_autotune": (c_int, [_P, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "lgc_get_trace": (c_int, [_P, POINTER(c_int64), _P, c_int64, _P, c_int64]),
     "lgc_prnibble_residual": (c_int, [_P, POINTER(POINTER(Svec))]),
     "lgc_submit": (c_int, [_P, _P, POINTER(Request), POINTER(c_uint64)]),
@@ -134,6 +134,7 @@ OPT_PULL = 7
 OPT_DEVICE_ROUNDS = 8
 OPT_PULL_BATCH = 9
 OPT_PULL_GROUP = 10
+OPT_PULL_SHARE = 11
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}
@@ -290,10 +291,12 @@ class Graph:
 
     def autotune(self) -> tuple:
         """lgc_graph_autotune: times the heavy-vertex pull gather's shapes on
-        this graph and keeps the fastest; returns (batch depth, lanes per item)."""
-        b, gr = c_int(), c_int()
-        _check(load().lgc_graph_autotune(self.handle, byref(b), byref(gr)), "lgc_graph_autotune")
-        return b.value, gr.value
+        this graph and keeps the fastest; returns (batch depth, lanes per item,
+        bytes per gathered share)."""
+        b, gr, sb = c_int(), c_int(), c_int()
+        _check(load().lgc_graph_autotune(self.handle, byref(b), byref(gr), byref(sb)),
+               "lgc_graph_autotune")
+        return b.value, gr.value, sb.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -431,9 +431,12 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         x = inputs.config1_seed(off, col)
         ref = oracle.prnibble(off, col, x, 0.01, 1e-6)
         res = []
-        for b, gw in ((4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8)):
+        shapes = [(b, gw, sb) for sb in (16, 8)
+                  for b, gw in ((4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8))]
+        for b, gw, sb in shapes:
             c.set_option(lgc.OPT_PULL_BATCH, b)
             c.set_option(lgc.OPT_PULL_GROUP, gw)
+            c.set_option(lgc.OPT_PULL_SHARE, sb)
             p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
             assert (st.rounds, st.pushed_edges) == (ref.rounds, ref.pushed_edges)
             assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
@@ -442,13 +445,14 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
             assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
         c.set_option(lgc.OPT_PULL_BATCH, 0)
         c.set_option(lgc.OPT_PULL_GROUP, 0)
-        b, gw = g.autotune()
-        assert (b, gw) in ((4, 32), (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8))
+        c.set_option(lgc.OPT_PULL_SHARE, 0)
+        assert g.autotune() in shapes
         p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
         assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
     finally:
         c.set_option(lgc.OPT_PULL_BATCH, 0)
         c.set_option(lgc.OPT_PULL_GROUP, 0)
+        c.set_option(lgc.OPT_PULL_SHARE, 0)
         c.set_option(lgc.OPT_PULL, 0)
         c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
         g.close()
