@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -193,7 +194,7 @@ def hk_terms(t, eps):
 def measure_many(lgc, inputs, torch, ctx, g, off):
     """1024 PR-Nibble + sweep clusters three ways: lgc_prnibble_batch and
     lgc_sweep_batch (in chunks), one seed per call (lgc_prnibble, lgc_sweep),
-    and all at once through the request loop (lgc_submit / lgc_poll, host
+    and all at once through the request loop (lgc_submit / lgc_wait, host
     results); device-resident results for the first two."""
     seeds = inputs.seeds_deg2(off, MANY["seeds"], MANY["seed_stream"])
     eps = inputs.eps_loguniform(MANY["seeds"], MANY["seed_stream"], MANY["eps_lo"], MANY["eps_hi"])
@@ -235,22 +236,10 @@ def measure_many(lgc, inputs, torch, ctx, g, off):
     reqs = [lgc.make_request(lgc.ALGO_PRNIBBLE, int(seeds[b]), True, alpha=a, eps=float(eps[b]),
                              mode=MODE) for b in range(len(seeds))]
     for tk in [lgc.submit(ctx, g, reqs[b]) for b in range(8)]:  # warm the workers
-        while lgc.poll(ctx, tk) is None:
-            time.sleep(0.0005)
+        lgc.wait(ctx, tk)
     t0 = time.perf_counter()
     pending = [lgc.submit(ctx, g, r) for r in reqs]
-    e_q = 0
-    while pending:
-        still = []
-        for tk in pending:
-            r = lgc.poll(ctx, tk)
-            if r is None:
-                still.append(tk)
-            else:
-                e_q += r["stats"]["pushed_edges"]
-        pending = still
-        if pending:
-            time.sleep(0.0002)
+    e_q = sum(lgc.wait(ctx, tk)["stats"]["pushed_edges"] for tk in pending)
     tq = time.perf_counter() - t0
     B = len(seeds)
     return {"workload": (f"R-MAT scale {MANY['scale']} (seed {MANY['graph_seed']}), {B} PR-Nibble "
@@ -266,7 +255,7 @@ def measure_many(lgc, inputs, torch, ctx, g, off):
 
 
 def measure_serving(lgc, inputs, torch, ctx, g, off):
-    """Open-loop Poisson arrivals through lgc_submit / lgc_poll: 80% PR-Nibble
+    """Open-loop Poisson arrivals through lgc_submit / lgc_wait: 80% PR-Nibble
     (alpha 0.01, eps log-uniform [1e-8, 1e-5]), 20% HK-PR (t log-uniform
     [3, 30], eps 1e-7), each with its sweep; latency = completion - submission
     (library clock)."""
@@ -293,8 +282,7 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
         pass  # the loop is already running with it (set by measure_many)
     # warm the workers
     for tk in [lgc.submit(ctx, g, reqs[i]) for i in range(8)]:
-        while lgc.poll(ctx, tk) is None:
-            time.sleep(0.0005)
+        lgc.wait(ctx, tk)
     out = []
     for rate in SERVE["rates"]:
         # the first R requests of the mix; fewer at rates below capacity so
@@ -302,26 +290,29 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
         R = min(SERVE["requests"], max(50, int(SERVE["offered_s"] * rate)))
         gaps = -np.log(1.0 - inputs.uniform(SERVE["arrival_seed"] + rate, R)) / rate
         arrive = np.cumsum(gaps)
-        pending, lat, done_edges = [], [], 0
+        # this thread submits at the arrival times; a collector thread takes
+        # the results with the blocking lgc_wait (latency is measured on the
+        # library's clock, so the order of collection does not matter)
+        tickets = queue.Queue()
+        lat, done_edges = [], [0]
+
+        def collect():
+            for _ in range(R):
+                r = lgc.wait(ctx, tickets.get())
+                lat.append(r["end_s"] - r["submit_s"])
+                done_edges[0] += r["stats"]["pushed_edges"]
+
+        th = threading.Thread(target=collect)
         t0 = time.perf_counter()
-        i = 0
-        while i < R or pending:
-            now = time.perf_counter() - t0
-            while i < R and arrive[i] <= now:
-                pending.append(lgc.submit(ctx, g, reqs[i]))
-                i += 1
-            still = []
-            for tk in pending:
-                r = lgc.poll(ctx, tk)
-                if r is None:
-                    still.append(tk)
-                else:
-                    lat.append(r["end_s"] - r["submit_s"])
-                    done_edges += r["stats"]["pushed_edges"]
-            pending = still
-            if i < R and not pending:
-                time.sleep(max(0.0, min(arrive[i] - (time.perf_counter() - t0), 0.001)))
+        th.start()
+        for i in range(R):
+            dt = arrive[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.put(lgc.submit(ctx, g, reqs[i]))
+        th.join()
         wall = time.perf_counter() - t0
+        done_edges = done_edges[0]
         lat_ms = np.sort(np.asarray(lat)) * 1e3
         out.append({"rate_per_s": rate, "requests": R, "clusters_per_s": R / wall,
                     "edges_per_s": done_edges / wall,

@@ -24,7 +24,7 @@
  *    (Sec. 2, "Graph Notation"; Sec. 4, "Input Graphs").
  *  - A seed x must satisfy 0 <= x < n and d(x) >= 1, else LGC_EINVAL.
  *  - Calls on one context are serialised by the caller (one stream per
- *    context); lgc_submit / lgc_poll are thread-safe.
+ *    context); lgc_submit / lgc_poll / lgc_wait are thread-safe.
  */
 #ifndef LGC_H_
 #define LGC_H_
@@ -345,6 +345,12 @@ int lgc_submit(lgc_ctx *ctx, lgc_graph *g, const lgc_request *req, uint64_t *tic
 /* LGC_PENDING while the request runs; LGC_OK and *out when done (the ticket
  * is then released); LGC_ENOTFOUND for an unknown ticket. */
 int lgc_poll(lgc_ctx *ctx, uint64_t ticket, lgc_result **out);
+/* As lgc_poll, but blocks (without spinning: it sleeps on the loop's
+ * condition variable) until the request is done: LGC_OK and *out, or
+ * LGC_ENOTFOUND for an unknown or already taken ticket, or when the context
+ * is being destroyed.  Thread-safe like lgc_poll; it must not overlap
+ * lgc_ctx_destroy of its context. */
+int lgc_wait(lgc_ctx *ctx, uint64_t ticket, lgc_result **out);
 
 /* ---- release ---- */
 void lgc_svec_free(lgc_svec *p);

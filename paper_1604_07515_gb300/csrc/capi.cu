@@ -739,6 +739,22 @@ int lgc_poll(lgc_ctx* ctx, uint64_t ticket, lgc_result** out) {
   return S->known.count(ticket) ? LGC_PENDING : LGC_ENOTFOUND;
 }
 
+int lgc_wait(lgc_ctx* ctx, uint64_t ticket, lgc_result** out) {
+  if (!ctx || !out) return LGC_EINVAL;
+  *out = nullptr;
+  Serve* S = ctx->serve;
+  if (!S) return LGC_ENOTFOUND;
+  std::unique_lock<std::mutex> lk(S->mu);
+  // woken by every finished request (the workers notify all after storing)
+  S->cv.wait(lk, [&] { return S->stop || S->done.count(ticket) || !S->known.count(ticket); });
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) return LGC_ENOTFOUND;
+  *out = it->second;
+  S->done.erase(it);
+  S->known.erase(ticket);
+  return LGC_OK;
+}
+
 void lgc_svec_free(lgc_svec* p) {
   if (!p) return;
   SvecBox* b = (SvecBox*)p;

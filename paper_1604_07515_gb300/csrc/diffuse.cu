@@ -1097,7 +1097,6 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
           int32_t u[4];
 #pragma unroll
           for (int j = 0; j < 4; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
-#pragma unroll
           SH raw[4];
 #pragma unroll
           for (int j = 0; j < 4; j++) raw[j] = u[j] >= 0 ? shx[u[j]] : no_share<SH>();

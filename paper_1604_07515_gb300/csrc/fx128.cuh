@@ -137,26 +137,22 @@ LGC_HD double fx_to_double(Fx X, int L) {
     mant = lo << (-r);  // here p - r <= 52, so the value sits in lo
   } else {
     // q = X >> r, round bit = bit r-1, sticky = bits below it
-    uint64_t qlo, qhi, rbit, sticky;
+    uint64_t qlo, rbit, sticky;
     if (r >= 128) {
       qlo = 0;
-      qhi = 0;
       rbit = 0;
       sticky = (hi | lo) != 0;
     } else if (r >= 64) {
       const int s = r - 64;
       qlo = hi >> s;
-      qhi = 0;
       rbit = s ? (hi >> (s - 1)) & 1 : lo >> 63;
       sticky = s ? ((hi & ((1ull << (s - 1)) - 1)) | lo) != 0
                  : (lo & ((1ull << 63) - 1)) != 0;
     } else {
-      qlo = (lo >> r) | (r ? hi << (64 - r) : 0);
-      qhi = hi >> r;
+      qlo = (lo >> r) | (r ? hi << (64 - r) : 0);  // at most 53 bits remain: hi >> r is zero
       rbit = (lo >> (r - 1)) & 1;
       sticky = r > 1 ? (lo & ((1ull << (r - 1)) - 1)) != 0 : 0;
     }
-    (void)qhi;  // zero: at most 53 bits remain
     mant = qlo;
     if (rbit && (sticky || (mant & 1))) mant++;
   }

@@ -115,6 +115,7 @@ SIGNATURES = {
     "lgc_prnibble_residual": (c_int, [_P, POINTER(POINTER(Svec))]),
     "lgc_submit": (c_int, [_P, _P, POINTER(Request), POINTER(c_uint64)]),
     "lgc_poll": (c_int, [_P, c_uint64, POINTER(POINTER(Result))]),
+    "lgc_wait": (c_int, [_P, c_uint64, POINTER(POINTER(Result))]),
     "lgc_svec_free": (None, [POINTER(Svec)]),
     "lgc_cluster_free": (None, [POINTER(Cluster)]),
     "lgc_result_free": (None, [POINTER(Result)]),
@@ -522,6 +523,17 @@ def poll(ctx: Context, ticket: int):
     if s == LGC_PENDING:
         return None
     _check(s, "lgc_poll")
+    return _take_result(out)
+
+
+def wait(ctx: Context, ticket: int):
+    """Block until the request is done (lgc_wait); the same dict as poll."""
+    out = POINTER(Result)()
+    _check(load().lgc_wait(ctx.handle, ticket, byref(out)), "lgc_wait")
+    return _take_result(out)
+
+
+def _take_result(out):
     r = out.contents
     res = {"status": r.status, "stats": r.stats.as_dict(), "submit_s": r.submit_s,
            "start_s": r.start_s, "end_s": r.end_s, "idx": None, "val": None, "cluster": None}

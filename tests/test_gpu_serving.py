@@ -1,4 +1,4 @@
-"""Request loop (lgc_submit / lgc_poll): requests that arrive while others run
+"""Request loop (lgc_submit / lgc_poll / lgc_wait): requests that arrive while others run
 are admitted as slots and memory free up, run concurrently on worker
 streams, and each result is the same alone and in the mix (bit-identical in
 deterministic mode, within 1e-12 relative L1 in atomic mode)."""
@@ -48,7 +48,7 @@ def alone(g, kind, kw, seed):
     return p, c
 
 
-def submit_all(ctx, g, reqs):
+def submit_all(ctx, g, reqs, collect="poll"):
     tickets = []
     for kind, kw, seed in reqs:
         if kind == "pr":
@@ -58,6 +58,8 @@ def submit_all(ctx, g, reqs):
         else:
             r = lgc.make_request(lgc.ALGO_RAND_HKPR, seed, True, **kw)
         tickets.append(lgc.submit(ctx, g, r))
+    if collect == "wait":
+        return [lgc.wait(ctx, t) for t in tickets]
     results = {}
     deadline = time.time() + 300
     while len(results) < len(tickets) and time.time() < deadline:
@@ -105,4 +107,57 @@ def test_poll_unknown_ticket(setup):
     ctx, g, off, col = setup
     with pytest.raises(lgc.LgcError) as e:
         lgc.poll(ctx, 10 ** 12)
+    assert e.value.status == lgc.LGC_ENOTFOUND
+
+
+def test_wait_matches_poll(setup):
+    """lgc_wait returns the same results as polling and releases the ticket."""
+    ctx, g, off, col = setup
+    reqs = requests(off, 16, "det")
+    polled = submit_all(ctx, g, reqs)
+    waited = submit_all(ctx, g, reqs, collect="wait")
+    for a, b in zip(polled, waited):
+        assert a["status"] == b["status"] == 0
+        assert np.array_equal(a["idx"], b["idx"]) and np.array_equal(a["val"], b["val"])
+        assert np.array_equal(a["cluster"]["ids"], b["cluster"]["ids"])
+
+
+def test_wait_in_completion_threads(setup):
+    """Several threads each wait on their own tickets while the main thread
+    keeps submitting (lgc_wait sleeps with the interpreter lock released)."""
+    import threading
+    ctx, g, off, col = setup
+    reqs = requests(off, 32, "atomic")
+    got, errs = {}, []
+
+    def waiter(tks):
+        try:
+            for t in tks:
+                got[t] = lgc.wait(ctx, t)
+        except Exception as e:  # surfaced by the assert below
+            errs.append(e)
+
+    tickets = []
+    threads = []
+    for k in range(4):
+        part = [lgc.submit(ctx, g, lgc.make_request(
+            lgc.ALGO_PRNIBBLE if kind == "pr" else lgc.ALGO_HKPR if kind == "hkpr"
+            else lgc.ALGO_RAND_HKPR, seed, True, **kw)) for kind, kw, seed in reqs[k::4]]
+        tickets += part
+        th = threading.Thread(target=waiter, args=(part,))
+        th.start()
+        threads.append(th)
+    for th in threads:
+        th.join(timeout=300)
+    assert not errs and len(got) == len(tickets)
+    assert all(r["status"] == 0 for r in got.values())
+    with pytest.raises(lgc.LgcError) as e:
+        lgc.wait(ctx, tickets[0])  # already taken
+    assert e.value.status == lgc.LGC_ENOTFOUND
+
+
+def test_wait_unknown_ticket(setup):
+    ctx, g, off, col = setup
+    with pytest.raises(lgc.LgcError) as e:
+        lgc.wait(ctx, 10 ** 12)
     assert e.value.status == lgc.LGC_ENOTFOUND
