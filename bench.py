@@ -329,6 +329,15 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
             "rates": out}
 
 
+# DRAM read + write bytes of the edge-phase kernels over one step of the
+# default workload, by heavy pull shape (batch, lanes, share bytes): ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of emap_atomic_kernel,
+# emap_red_kernel, pull_light_fx_kernel, pull_heavy_fx_kernel and
+# rounds_prnibble_kernel, summed over one step.  Re-capture when any of
+# these kernels changes.
+EDGE_TRAFFIC_PER_STEP = {(8, 32, 8): 8.452e9, (8, 32, 16): 10.095e9}
+TRAFFIC_SOURCE = "profiles/traffic_edge_phase_rmat22.md"
+
 # bytes of the per-step inputs handed to the library (seed + parameter structs)
 H2D_BYTES_PER_STEP = 4 * 4 + 32 + 24 + 24 + 32
 
@@ -390,6 +399,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-many", action="store_true",
                     help="skip the batched-vs-per-seed and serving measurements")
+    ap.add_argument("--pull-shape", default="",
+                    help="heavy pull gather shape 'batch,lanes,share_bytes' instead of the "
+                         "graph's autotuned one (e.g. 8,32,8)")
     ap.add_argument("--algos", default=",".join(ALGOS),
                     help="comma-separated subset of the step (for profiling one diffusion)")
     args = ap.parse_args()
@@ -416,7 +428,13 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = lgc.Context(dev, stream)
     g = lgc.Graph(ctx, off, col)
-    pull_shape = g.autotune()  # launch-shape tuning on this graph, before any timing
+    if args.pull_shape:
+        pull_shape = tuple(int(v) for v in args.pull_shape.split(","))
+        for opt, v in zip((lgc.OPT_PULL_BATCH, lgc.OPT_PULL_GROUP, lgc.OPT_PULL_SHARE),
+                          pull_shape):
+            ctx.set_option(opt, v)
+    else:
+        pull_shape = g.autotune()  # launch-shape tuning on this graph, before any timing
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -503,9 +521,18 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     achieved = (d["bytes"] / (d["ms"] / 1e3)) / 1e9 if d["ms"] > 0 else 0.0
+    # DRAM bytes of the edge phase per launch, from the ncu capture of this
+    # workload and pull shape (null for any other workload or shape)
+    traffic = None
+    shape_key = tuple(pull_shape)
+    if (dname == "edgemap_atomic" and MODE == "atomic" and STEP_ALGOS == ALGOS
+            and shape_key in EDGE_TRAFFIC_PER_STEP and d["launches"] > 0):
+        per_step = d["launches"] / args.steps
+        traffic = EDGE_TRAFFIC_PER_STEP[shape_key] / per_step
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": None, "launches": d["launches"],
+                "traffic": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else None,
+                "launches": d["launches"],
                 "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
                 "alg_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                 "share_of_step": d["ms"] / total_ms if total_ms else None}
