@@ -1019,8 +1019,9 @@ __device__ inline int round_scale(const int32_t* range, int g) {
 // operations per edge).  Same value either way.
 __device__ inline Fx to_fx(const Fx& x, int) { return x; }
 __device__ inline Fx to_fx(double s, int L) {
-  Fx x = fx_from_double(s, L);  // -0.0 -> 0
-  if (fx_bits(s) != 0) x.hi |= kFxFlag;
+  const uint64_t b = fx_bits(s);
+  Fx x = fx_from_bits(b, L);  // -0.0 -> 0
+  x.hi |= (uint64_t)(b != 0) << 63;
   return x;
 }
 template <typename SH>

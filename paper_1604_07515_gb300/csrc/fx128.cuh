@@ -116,6 +116,45 @@ LGC_HD Fx fx_from_double(double x, int L) {
   return r;
 }
 
+// x << s and x >> s for every s < 2^32, zero once s >= 64: the PTX shifts
+// clamp the shift amount to the register width; host code says so.
+LGC_HD uint64_t fx_shl(uint64_t x, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  uint64_t r;
+  asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+#else
+  return s >= 64 ? 0 : x << s;
+#endif
+}
+LGC_HD uint64_t fx_shr(uint64_t x, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  uint64_t r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+#else
+  return s >= 64 ? 0 : x >> s;
+#endif
+}
+
+// fx_from_double of a share's bits without branches (the pull gathers
+// convert one 8-byte share per edge).  With m the significand and
+// sh = lsb - L, X = m * 2^sh: for 0 <= sh the low word is m << sh and the
+// high word m >> (64 - sh) or m << (sh - 64); for sh < 0 the low word is
+// m >> -sh.  Every out-of-range shift gives zero, so the four terms combine
+// by OR (at sh = 0 and sh = 64 the two terms of a word are equal), and the
+// result equals fx_from_double's for every input, sh >= 128 included.
+LGC_HD Fx fx_from_bits(uint64_t bits, int L) {
+  bits &= kFxMask;  // -0.0 -> +0.0
+  const int be = fx_bexp(bits);
+  const uint64_t m = (bits & ((1ull << 52) - 1)) | ((uint64_t)(be != 0) << 52);
+  const int sh = fx_lsb(be) - L;
+  Fx r;
+  r.lo = fx_shl(m, (uint32_t)sh) | fx_shr(m, (uint32_t)(-sh));
+  r.hi = fx_shr(m, (uint32_t)(64 - sh)) | fx_shl(m, (uint32_t)(sh - 64));
+  return r;
+}
+
 // a += b over the 127 value bits (b's flag is dropped).
 LGC_HD void fx_add(Fx& a, const Fx& b) {
   const uint64_t lo = a.lo + b.lo;

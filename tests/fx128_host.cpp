@@ -10,6 +10,11 @@ void fxh_from_double(double x, int L, uint64_t* lo, uint64_t* hi) {
   *lo = r.lo;
   *hi = r.hi;
 }
+void fxh_from_bits(double x, int L, uint64_t* lo, uint64_t* hi) {
+  lgc::Fx r = lgc::fx_from_bits(lgc::fx_bits(x), L);
+  *lo = r.lo;
+  *hi = r.hi;
+}
 double fxh_to_double(uint64_t lo, uint64_t hi, int L) { return lgc::fx_to_double({lo, hi}, L); }
 // Sum of n shares at the scale their range gives, rounded once.
 double fxh_sum(const double* x, int n, int g, int* L_out) {

@@ -25,6 +25,7 @@ def fx():
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.fxh_scale.argtypes = [ctypes.c_int] * 3
     lib.fxh_from_double.argtypes = [ctypes.c_double, ctypes.c_int, u64p, u64p]
+    lib.fxh_from_bits.argtypes = [ctypes.c_double, ctypes.c_int, u64p, u64p]
     lib.fxh_to_double.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
     lib.fxh_to_double.restype = ctypes.c_double
     lib.fxh_sum.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
@@ -96,6 +97,34 @@ def test_from_double_exact_and_truncating(fx):
         assert X == math.floor(q), (x, L)
     fx.fxh_from_double(-0.0, 3, ctypes.byref(lo), ctypes.byref(hi))
     assert lo.value == 0 and hi.value == 0
+
+
+def test_branch_free_conversion_matches(fx):
+    """fx_from_bits (no branches, shifts that clamp) gives fx_from_double's
+    words for every input: shifts at and around 0, 64 and 128 bits, below
+    the scale, subnormals, zeros; and the exact floor wherever it fits."""
+    rng = random.Random(7)
+    a, b = (ctypes.c_uint64(), ctypes.c_uint64()), (ctypes.c_uint64(), ctypes.c_uint64())
+    cases = []
+    for sh in list(range(-70, 140)) + [-2000, -129, -128, 200, 1000]:
+        for _ in range(4):
+            be = rng.randint(1, 2046)
+            x = math.ldexp(1.0 + rng.getrandbits(52) / 2**52, be - 1023)
+            cases.append((x, (be - 1075) - sh))  # lsb(x) - L = sh
+    for _ in range(2000):
+        x = math.ldexp(rng.random() + 0.5, rng.randint(-1070, 1000))
+        cases.append((x, rng.randint(-1100, 1000)))
+    for _ in range(200):
+        cases.append((math.ldexp(rng.getrandbits(52), -1074), rng.randint(-1200, -1000)))
+    cases += [(0.0, 5), (-0.0, -7), (5e-324, -1074), (5e-324, -1080), (1.0, 0)]
+    for x, L in cases:
+        fx.fxh_from_double(x, L, ctypes.byref(a[0]), ctypes.byref(a[1]))
+        fx.fxh_from_bits(x, L, ctypes.byref(b[0]), ctypes.byref(b[1]))
+        assert (a[0].value, a[1].value) == (b[0].value, b[1].value), (x, L)
+        X = b[0].value | (b[1].value << 64)
+        q = Fraction(x) / Fraction(2) ** L
+        if q < 2**127:
+            assert X == math.floor(q), (x, L)
 
 
 @pytest.mark.parametrize("spread", [0, 10, 40, 56, 80, 300])
