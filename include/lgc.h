@@ -237,7 +237,8 @@ int lgc_prnibble_batch(lgc_graph *g, int64_t B, const int32_t *seeds,
  * ascending id), computes vol and boundary of every prefix by prefix sums,
  * and returns the prefix of smallest conductance (exact rational comparison,
  * first index on ties; prefixes with min(vol, 2m - vol) = 0 are skipped).
- * p may be on the host or the device (p->on_device). */
+ * p may be on the host or the device (p->on_device).  Errors: LGC_EINVAL if
+ * an entry is not a vertex of degree >= 1 or names a vertex a second time. */
 int lgc_sweep(lgc_graph *g, const lgc_svec *p, lgc_cluster **out);
 
 /* Sweep cuts of B vectors in one pass: out[b] is lgc_sweep(g, p[b], ...) for

@@ -42,6 +42,7 @@ constexpr uint32_t kMaxProbe = 1u << 20;
 // Device-side error flags (bit mask in Counters::err).
 constexpr int kErrTableFull = 1;
 constexpr int kErrFrontierOverflow = 2;
+constexpr int kErrDuplicate = 4;  // a sweep input names a vertex twice
 
 // ---------------------------------------------------------------------------
 // Hash table slot: key = vertex + 1 (0 = empty, so a zero memset clears the

@@ -67,7 +67,7 @@ __global__ void rank_insert_kernel(const int32_t* __restrict__ order, int64_t n0
                                    const unsigned long long* __restrict__ dN, Table T,
                                    int32_t* __restrict__ dense_rank,
                                    const int32_t* __restrict__ deg, int64_t* __restrict__ d_i,
-                                   int* err) {
+                                   int* err, int* bad) {
   const int64_t N = (int64_t)*dN;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n0;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -77,11 +77,14 @@ __global__ void rank_insert_kernel(const int32_t* __restrict__ order, int64_t n0
     }
     const int32_t v = order[i];
     if (dense_rank) {
-      dense_rank[v] = (int32_t)(i + 1);
+      if (atomicExch(&dense_rank[v], (int32_t)(i + 1)) != 0) atomicOr(bad, 1);  // named twice
     } else {
       int ins = 0;
       const int64_t s = ht_find_or_insert(T, v, &ins, err);
-      if (s >= 0) T.s[s].aux = (int32_t)(i + 1);
+      if (s >= 0) {
+        T.s[s].aux = (int32_t)(i + 1);
+        if (!ins) atomicOr(bad, 1);  // named twice
+      }
     }
     d_i[i] = deg[v];
   }
@@ -97,15 +100,37 @@ __device__ inline int64_t rank_of(const Table& T, const int32_t* dense_rank, int
   return s >= 0 ? T.s[s].aux : N + 1;
 }
 
-__device__ inline int64_t upper_bound_excl(const int64_t* a, int64_t n, int64_t x) {
-  // a = inclusive prefix sums; the source of edge x is the first i with a[i] > x
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (a[mid] <= x) lo = mid + 1;
-    else hi = mid;
+// The first sorted vertex of every kTile-edge tile of the vol(S_N) edges:
+// vertex i's edges are [vol[i-1], vol[i]), and the tiles starting in that
+// range get i (every swept vertex has d >= 1, so each tile start has exactly
+// one writer).  N from dN when it is given, else the argument.
+// At most cap tiles are written (more only for an invalid input, which ORs
+// flag into *bad).
+__global__ void tile_first_kernel(const int64_t* __restrict__ vol,
+                                  const unsigned long long* __restrict__ dN, int64_t n_arg,
+                                  int32_t* __restrict__ tile0, int64_t cap, int* bad, int flag) {
+  const int64_t N = dN ? (int64_t)*dN : n_arg;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = i > 0 ? vol[i - 1] : 0, b = vol[i];
+    for (int64_t t = (a + kTile - 1) / kTile; t * kTile < b; t++) {
+      if (t >= cap) {
+        atomicOr(bad, flag);
+        break;
+      }
+      tile0[t] = (int32_t)i;
+    }
   }
-  return lo;
+}
+
+// A tile's sorted vertices: from its first one through the next tile's first
+// (or the last vertex), at most kTile of them.
+__device__ inline int tile_sources(const int32_t* tile0, int64_t tile, int64_t ntiles, int64_t N,
+                                   int64_t* i0) {
+  *i0 = tile0[tile];
+  const int64_t last = tile + 1 < ntiles ? tile0[tile + 1] : N - 1;
+  const int64_t cnt = last - *i0 + 1;
+  return (int)(cnt < kTile ? cnt : kTile);
 }
 
 // Edge-balanced over the vol(S_N) edges of the sorted vertices; counts, per
@@ -114,22 +139,18 @@ __global__ void __launch_bounds__(kBlock)
     sweep_cross_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                        const int32_t* __restrict__ order, const int64_t* __restrict__ vol,
                        const unsigned long long* __restrict__ dN,
-                       const int64_t* __restrict__ dV, Table T,
-                       const int32_t* __restrict__ dense_rank, int32_t* __restrict__ before) {
+                       const int64_t* __restrict__ dV, const int32_t* __restrict__ tile0,
+                       int64_t cap, Table T, const int32_t* __restrict__ dense_rank,
+                       int32_t* __restrict__ before) {
   __shared__ int64_t s_vol[kTile];  // inclusive vol of the tile's sources
   __shared__ int64_t s_off[kTile];
   __shared__ int32_t s_cnt[kTile];
-  __shared__ int64_t s_i0, s_i1;
   const int64_t N = (int64_t)*dN, V = *dV;
-  const int64_t ntiles = (V + kTile - 1) / kTile;
+  const int64_t ntiles = min((V + kTile - 1) / kTile, cap);  // cap: invalid input, flagged
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTile, e1 = min(V, e0 + kTile);
-    if (threadIdx.x == 0) s_i0 = upper_bound_excl(vol, N, e0);
-    if (threadIdx.x == 32) s_i1 = upper_bound_excl(vol, N, e1 - 1);
-    __syncthreads();
-    const int64_t i0 = s_i0;
-    int cnt = (int)(s_i1 - i0 + 1);
-    if (cnt > kTile) cnt = kTile;  // unreachable: every swept vertex has d >= 1
+    int64_t i0;
+    const int cnt = tile_sources(tile0, tile, ntiles, N, &i0);
     for (int j = threadIdx.x; j < cnt; j += kBlock) {
       s_vol[j] = vol[i0 + j];
       s_off[j] = off[order[i0 + j]];
@@ -338,7 +359,10 @@ __global__ void bsweep_rank_kernel(const int32_t* __restrict__ elem, int64_t N,
     int ins = 0;
     const Table T = tabs[b];
     const int64_t s = ht_find_or_insert(T, v, &ins, err);
-    if (s >= 0) T.s[s].aux = (int32_t)(i - nbeg[b] + 1);
+    if (s >= 0) {
+      T.s[s].aux = (int32_t)(i - nbeg[b] + 1);
+      if (!ins) atomicOr(err, kErrDuplicate);  // a vector names v twice
+    }
   }
 }
 
@@ -348,21 +372,16 @@ __global__ void __launch_bounds__(kBlock)
     bsweep_cross_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                         const int32_t* __restrict__ order, const uint32_t* __restrict__ sk,
                         const int64_t* __restrict__ nbeg, const int64_t* __restrict__ vol,
-                        int64_t N, int64_t V, const Table* __restrict__ tabs,
-                        int32_t* __restrict__ before) {
+                        int64_t N, int64_t V, const int32_t* __restrict__ tile0,
+                        const Table* __restrict__ tabs, int32_t* __restrict__ before) {
   __shared__ int64_t s_vol[kTile];
   __shared__ int64_t s_off[kTile];
   __shared__ int32_t s_cnt[kTile];
-  __shared__ int64_t s_i0, s_i1;
   const int64_t ntiles = (V + kTile - 1) / kTile;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTile, e1 = min(V, e0 + kTile);
-    if (threadIdx.x == 0) s_i0 = upper_bound_excl(vol, N, e0);
-    if (threadIdx.x == 32) s_i1 = upper_bound_excl(vol, N, e1 - 1);
-    __syncthreads();
-    const int64_t i0 = s_i0;
-    int cnt = (int)(s_i1 - i0 + 1);
-    if (cnt > kTile) cnt = kTile;  // unreachable: every swept vertex has d >= 1
+    int64_t i0;
+    const int cnt = tile_sources(tile0, tile, ntiles, N, &i0);
     for (int j = threadIdx.x; j < cnt; j += kBlock) {
       s_vol[j] = vol[i0 + j];
       s_off[j] = off[order[i0 + j]];
@@ -434,7 +453,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
   int32_t *id = nullptr, *id2 = nullptr, *before = nullptr;
   int64_t *d_i = nullptr, *vol = nullptr, *delta = nullptr, *misc = nullptr;
   Best *parts = nullptr, *best = nullptr;
-  int32_t* drank = nullptr;
+  int32_t *drank = nullptr, *tile0 = nullptr;
   Table T;
   int status = LGC_OK;
   Best hb{0, 0, -1};
@@ -485,16 +504,23 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
     LGC_CUDA_TRY(cudaMemsetAsync(&ctx->d_counters->err, 0, sizeof(int), s));
     const unsigned long long* dN = (const unsigned long long*)misc;
     rank_insert_kernel<<<grid, kBlock, 0, s>>>(id, n0, dN, T, drank, g->deg, d_i,
-                                                &ctx->d_counters->err);
+                                                &ctx->d_counters->err, (int*)(misc + 3));
     LGC_COUNT_LAUNCH(ctx);
     if ((status = scan_i64(ctx, d_i, vol, n0, true, misc + 1)) != LGC_OK) break;
     // S5, edge-balanced over V = misc[1] edges with a grid sized for the
-    // largest possible V (the kernel loops over the tiles that exist)
+    // largest possible V (the kernel loops over the tiles that exist); the
+    // tiles' first vertices first, for at most min(2m, n0 * max degree)
+    // edges
     {
+      const int64_t vmax = std::min<int64_t>(g->nnz, n0 * (int64_t)g->max_deg);
+      const int64_t cap = vmax / kTile + 1;
+      if ((status = dalloc_t(ctx, &tile0, cap)) != LGC_OK) break;
+      tile_first_kernel<<<grid, kBlock, 0, s>>>(vol, dN, 0, tile0, cap, (int*)(misc + 3), 1);
+      LGC_COUNT_LAUNCH(ctx);
       // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
       ProfScope ps(ctx, LGC_PROF_SWEEP, 0.0);
-      sweep_cross_kernel<<<152 * 16, kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1, T,
-                                                      drank, before);
+      sweep_cross_kernel<<<152 * 16, kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1,
+                                                      tile0, cap, T, drank, before);
       LGC_COUNT_LAUNCH(ctx);
     }
     sweep_delta_kernel<<<grid, kBlock, 0, s>>>(d_i, before, n0, delta);
@@ -517,7 +543,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
                                  cudaMemcpyDeviceToHost, s));
     LGC_CUDA_TRY(cudaStreamSynchronize(s));
     if (*(int*)(ctx->h_scratch + 3) != 0) {
-      status = LGC_EINVAL;  // an entry is not a vertex of degree >= 1
+      status = LGC_EINVAL;  // an entry is not a vertex of degree >= 1, or one is named twice
       break;
     }
     if (*(int32_t*)(ctx->h_scratch + 4) & kErrTableFull) status = LGC_ETABLEFULL;
@@ -572,6 +598,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
   dfree(ctx, parts);
   dfree(ctx, best);
   dfree(ctx, drank);
+  dfree(ctx, tile0);
   table_destroy(ctx, &T);
   return status;
 }
@@ -599,7 +626,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
   int64_t *d_inoff = nullptr, *keep = nullptr, *pos = nullptr, *tot = nullptr, *d_nbeg = nullptr;
   uint64_t *key = nullptr, *ko = nullptr, *ko2 = nullptr;
   int32_t *id = nullptr, *seg = nullptr, *eo = nullptr, *eo2 = nullptr, *order = nullptr,
-          *before = nullptr;
+          *before = nullptr, *tile0 = nullptr;
   uint32_t *sk = nullptr, *sk2 = nullptr;
   int64_t *d_i = nullptr, *vol = nullptr, *cut = nullptr, *d_bvol = nullptr;
   Best* d_best = nullptr;
@@ -722,9 +749,13 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
       // S5
       if (V > 0) {
         const int64_t tiles = ceil_div(V, kTile);
+        if ((st = dalloc_t(ctx, &tile0, tiles)) != LGC_OK) break;
+        tile_first_kernel<<<grid_for(N), kBlock, 0, s>>>(vol, nullptr, N, tile0, tiles,
+                                                          d_err + 1, kErrDuplicate);
+        LGC_COUNT_LAUNCH(ctx);
         ProfScope ps_(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
         bsweep_cross_kernel<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), kBlock, 0, s>>>(
-            g->off, g->col, order, sk, d_nbeg, vol, N, V, d_tabs, before);
+            g->off, g->col, order, sk, d_nbeg, vol, N, V, tile0, d_tabs, before);
         LGC_COUNT_LAUNCH(ctx);
       }
       sweep_delta_kernel<<<grid_for(N), kBlock, 0, s>>>(d_i, before, N, cut);
@@ -758,6 +789,10 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
       }
       if (cudaStreamSynchronize(s)) {
         st = LGC_ECUDA;
+        break;
+      }
+      if (*(int*)ctx->h_scratch & kErrDuplicate) {
+        st = LGC_EINVAL;
         break;
       }
       if (*(int*)ctx->h_scratch & kErrTableFull) {
@@ -804,7 +839,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
                   (void*)tot, (void*)d_nbeg, (void*)key, (void*)ko, (void*)ko2, (void*)id,
                   (void*)seg, (void*)eo, (void*)eo2, (void*)order, (void*)before, (void*)sk,
                   (void*)sk2, (void*)d_i, (void*)vol, (void*)cut, (void*)d_bvol, (void*)d_best,
-                  (void*)d_tabs, (void*)slab, (void*)d_err})
+                  (void*)d_tabs, (void*)slab, (void*)d_err, (void*)tile0})
     dfree(ctx, q);
   host_free(hord);
   return st;

@@ -124,6 +124,32 @@ def test_sweep_edge_cases(ctx):
     assert c.size == ref.best and c.cut == ref.best_cut and c.vol == ref.best_vol
 
 
+def test_sweep_rejects_invalid_entries(ctx):
+    """A vertex named twice is LGC_EINVAL, single and batched, with the rank
+    hash table (small input) and the dense rank array (input over n/64,
+    whose volume then exceeds 2m); the context stays usable."""
+    off, col, g = gpu_graph(ctx, "rmat13")
+    d = np.diff(off)
+    v = np.flatnonzero(d > 0).astype(np.int32)
+    small = lgc.host_svec(np.array([v[0], v[1], v[0]], np.int32), [0.3, 0.2, 0.1])
+    big_idx = np.concatenate([v, v[:5]]).astype(np.int32)
+    big = lgc.host_svec(big_idx, np.ones(len(big_idx)))
+    ok = lgc.host_svec(v[2:3], [1.0])
+    for p in (small, big):
+        with pytest.raises(lgc.LgcError) as e:
+            lgc.sweep(g, p)
+        assert e.value.status == lgc.LGC_EINVAL
+        with pytest.raises(lgc.LgcError) as e:
+            lgc.sweep_batch(g, [ok, p])
+        assert e.value.status == lgc.LGC_EINVAL
+    with pytest.raises(lgc.LgcError) as e:
+        lgc.sweep(g, lgc.host_svec(np.array([len(off) - 1], np.int32), [1.0]))  # not a vertex
+    assert e.value.status == lgc.LGC_EINVAL
+    ref = oracle.sweep(off, col, v, np.ones(len(v)))
+    c = lgc.sweep(g, lgc.host_svec(v, np.ones(len(v))))
+    assert c.size == ref.best and c.cut == ref.best_cut and c.vol == ref.best_vol
+
+
 # ---------------------------------------------------------------------------
 # PR-Nibble
 # ---------------------------------------------------------------------------
