@@ -29,6 +29,7 @@
 #ifndef LGC_H_
 #define LGC_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -130,6 +131,27 @@ typedef struct {
  * ordered on that stream. */
 int lgc_ctx_create(int device, void *cuda_stream, lgc_ctx **out);
 void lgc_ctx_destroy(lgc_ctx *ctx);
+
+/* Device memory from the caller's allocator instead of the device's
+ * stream-ordered pool (for example PyTorch's caching allocator, so that the
+ * library's graphs and temporaries come out of the same memory as the
+ * caller's tensors).  alloc(bytes, stream, user) returns device memory for
+ * work ordered on `stream` (the context's stream), or NULL (the call then
+ * fails with LGC_ENOMEM); free(ptr, stream, user) may be called while work
+ * that reads ptr is still queued on that stream, so the allocator must not
+ * hand the block to another stream before that work is done (a stream-ordered
+ * pool keyed by stream, as PyTorch's is, satisfies this).  Both are called
+ * only from the thread that calls into the context.  The request loop's
+ * worker contexts (lgc_submit) keep the device pool. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, void *stream, void *user);
+  void *user;
+} lgc_alloc_fns;
+/* lgc_ctx_create with the allocator `fns` (copied; NULL: the device pool).
+ * LGC_EINVAL if fns has a NULL alloc or free. */
+int lgc_ctx_create_with_alloc(int device, const lgc_alloc_fns *fns, void *cuda_stream,
+                              lgc_ctx **out);
 
 enum {
   LGC_OPT_RESULT_ON_DEVICE = 1, /* 1: outputs stay in device memory (default 0: host) */

@@ -373,7 +373,13 @@ const char* lgc_strerror(int s) {
 }
 
 int lgc_ctx_create(int device, void* cuda_stream, lgc_ctx** out) {
+  return lgc_ctx_create_with_alloc(device, nullptr, cuda_stream, out);
+}
+
+int lgc_ctx_create_with_alloc(int device, const lgc_alloc_fns* fns, void* cuda_stream,
+                              lgc_ctx** out) {
   if (!out) return LGC_EINVAL;
+  if (fns && (!fns->alloc || !fns->free)) return LGC_EINVAL;
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -383,6 +389,7 @@ int lgc_ctx_create(int device, void* cuda_stream, lgc_ctx** out) {
   if (device < 0 || device >= ndev) return LGC_EINVAL;
   lgc_ctx* ctx = new (std::nothrow) lgc_ctx();
   if (!ctx) return LGC_ENOMEM;
+  if (fns) ctx->alloc_fns = *fns;
   int s = ctx_init(ctx, device, (cudaStream_t)cuda_stream);
   if (s != LGC_OK) {
     ctx_fini(ctx);

@@ -123,6 +123,10 @@ double now_seconds() {
 int dalloc(lgc_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (ctx->alloc_fns.alloc) {
+    *p = ctx->alloc_fns.alloc(bytes, (void*)ctx->stream, ctx->alloc_fns.user);
+    return *p ? LGC_OK : LGC_ENOMEM;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -133,7 +137,9 @@ int dalloc(lgc_ctx* ctx, void** p, size_t bytes) {
 }
 
 void dfree(lgc_ctx* ctx, void* p) {
-  if (p) cudaFreeAsync(p, ctx->stream);
+  if (!p) return;
+  if (ctx->alloc_fns.free) ctx->alloc_fns.free(p, (void*)ctx->stream, ctx->alloc_fns.user);
+  else cudaFreeAsync(p, ctx->stream);
 }
 
 int64_t pow2_at_least(int64_t x) {

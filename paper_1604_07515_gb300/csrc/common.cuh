@@ -191,6 +191,7 @@ struct Serve;  // request loop (serve.cu)
 struct lgc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  lgc_alloc_fns alloc_fns = {nullptr, nullptr, nullptr};  // caller's allocator, if set
   bool own_stream = false;
   bool result_on_device = false;
   bool trace = false;

@@ -39,6 +39,28 @@ class LgcError(RuntimeError):
         self.status = status
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class AllocFns(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+def torch_allocator(device: int):
+    """(alloc, free) callables that take the library's device memory from
+    PyTorch's caching allocator (stream-ordered per stream)."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc, free
+
+
 class Svec(ctypes.Structure):
     _fields_ = [("nnz", c_int64), ("idx", c_void_p), ("val", c_void_p), ("on_device", c_int)]
 
@@ -92,6 +114,7 @@ _lock = threading.Lock()
 _P = c_void_p
 SIGNATURES = {
     "lgc_ctx_create": (c_int, [c_int, _P, POINTER(_P)]),
+    "lgc_ctx_create_with_alloc": (c_int, [c_int, POINTER(AllocFns), _P, POINTER(_P)]),
     "lgc_ctx_destroy": (None, [_P]),
     "lgc_ctx_set_option": (c_int, [_P, c_int, c_int64]),
     "lgc_ctx_synchronize": (c_int, [_P]),
@@ -191,12 +214,37 @@ def _ptr(a) -> int:
 class Context:
     """lgc_ctx: one CUDA stream (the caller's, e.g. torch's current stream)."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, allocator=None):
+        """allocator: None (the device's stream-ordered pool), "torch"
+        (PyTorch's caching allocator), or a pair of callables
+        alloc(nbytes, stream) -> int pointer (0 on failure) and
+        free(ptr, stream) (lgc_ctx_create_with_alloc)."""
         lib = load()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
         h = c_void_p()
-        _check(lib.lgc_ctx_create(device, stream, byref(h)), "lgc_ctx_create")
+        self._alloc_fns = None
+        if allocator is None:
+            _check(lib.lgc_ctx_create(device, stream, byref(h)), "lgc_ctx_create")
+        else:
+            a, f = torch_allocator(device) if allocator == "torch" else allocator
+
+            def c_alloc(nbytes, strm, user):
+                try:
+                    return a(int(nbytes), int(strm or 0)) or None
+                except Exception:
+                    return None  # the library reports LGC_ENOMEM
+
+            def c_free(ptr, strm, user):
+                try:
+                    f(int(ptr), int(strm or 0))
+                except Exception:
+                    pass
+
+            # the callbacks live as long as the context
+            self._alloc_fns = AllocFns(ALLOC_FN(c_alloc), FREE_FN(c_free), None)
+            _check(lib.lgc_ctx_create_with_alloc(device, byref(self._alloc_fns), stream,
+                                                 byref(h)), "lgc_ctx_create_with_alloc")
         self.handle = h
         self.device = device
         self._graphs = weakref.WeakSet()  # graphs must be destroyed before the context
