@@ -302,6 +302,10 @@ int lgc_sweep_noalloc(lgc_graph *g, int64_t nnz, const int32_t *d_idx, const dou
                       int32_t *d_ids, lgc_cluster *out);
 
 /* ---- tracing (deterministic-mode parity tests) ---- */
+#define LGC_TRACE_FRONTIERS 1 /* record every round's frontier */
+/* lgc_ctx_set_option(ctx, LGC_OPT_TRACE, flags & LGC_TRACE_FRONTIERS): flags
+ * 0 turns recording off; other bits are reserved (LGC_EINVAL). */
+int lgc_set_trace(lgc_ctx *ctx, int flags);
 /* Frontiers of the last diffusion call recorded under LGC_OPT_TRACE:
  * *rounds receives the round count; if sizes != NULL it receives the size of
  * each round's frontier (up to cap_rounds entries); if frontiers != NULL it

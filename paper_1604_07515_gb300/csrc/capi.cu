@@ -408,6 +408,11 @@ void lgc_ctx_destroy(lgc_ctx* ctx) {
   delete ctx;
 }
 
+int lgc_set_trace(lgc_ctx* ctx, int flags) {
+  if (!ctx || (flags & ~LGC_TRACE_FRONTIERS)) return LGC_EINVAL;
+  return lgc_ctx_set_option(ctx, LGC_OPT_TRACE, flags & LGC_TRACE_FRONTIERS);
+}
+
 int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
   if (!ctx) return LGC_EINVAL;
   switch (option) {

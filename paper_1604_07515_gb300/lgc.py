@@ -115,6 +115,7 @@ _P = c_void_p
 SIGNATURES = {
     "lgc_ctx_create": (c_int, [c_int, _P, POINTER(_P)]),
     "lgc_ctx_create_with_alloc": (c_int, [c_int, POINTER(AllocFns), _P, POINTER(_P)]),
+    "lgc_set_trace": (c_int, [_P, c_int]),
     "lgc_ctx_destroy": (None, [_P]),
     "lgc_ctx_set_option": (c_int, [_P, c_int, c_int64]),
     "lgc_ctx_synchronize": (c_int, [_P]),
@@ -251,6 +252,10 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(load().lgc_ctx_set_option(self.handle, option, int(value)), "lgc_ctx_set_option")
+
+    def set_trace(self, flags: int = 1):
+        """lgc_set_trace: 1 records every round's frontier, 0 stops."""
+        _check(load().lgc_set_trace(self.handle, int(flags)), "lgc_set_trace")
 
     def synchronize(self):
         _check(load().lgc_ctx_synchronize(self.handle), "lgc_ctx_synchronize")

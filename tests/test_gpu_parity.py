@@ -22,7 +22,7 @@ PHI_TOL = 1e-9
 @pytest.fixture(scope="module")
 def ctx():
     c = lgc.Context(0)
-    c.set_option(lgc.OPT_TRACE, 1)
+    c.set_trace(1)  # lgc_set_trace(ctx, LGC_TRACE_FRONTIERS)
     yield c
     c.close()
 
