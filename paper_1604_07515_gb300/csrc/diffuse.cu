@@ -165,13 +165,11 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
 
 // Nibble, Fig. alg:nibble: p'[v] = p[v]/2 on the frontier (S = p, D = p',
 // fresh), share p[v]/(2 d(v)).
-__global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
-                                   const int32_t* __restrict__ fs, Table S, Table D,
-                                   const int64_t* __restrict__ off, double eps, int fmode,
-                                   int det, int self_append, double* __restrict__ share,
-                                   int64_t* __restrict__ cnt,
-                                   int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
-                                   int32_t ncap, Counters* C) {
+__device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int32_t* fs,
+                                        Table S, Table D, const int64_t* __restrict__ off,
+                                        double eps, int fmode, int det, int self_append,
+                                        double* share, int64_t* cnt, int64_t* foff, int32_t* nfv,
+                                        int32_t* nfs, int32_t ncap, Counters* C) {
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -196,6 +194,17 @@ __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
     count_inserted(ins, &C->aux);
     frontier_append(pred, v, ds, d, nfv, nfs, C, ncap);
   }
+}
+
+__global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                   const int32_t* __restrict__ fs, Table S, Table D,
+                                   const int64_t* __restrict__ off, double eps, int fmode,
+                                   int det, int self_append, double* __restrict__ share,
+                                   int64_t* __restrict__ cnt,
+                                   int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
+                                   int32_t ncap, Counters* C) {
+  nibble_vmap_body(nf, fv, fs, S, D, off, eps, fmode, det, self_append, share, cnt, foff, nfv,
+                   nfs, ncap, C);
 }
 
 // HK-PR, Fig. alg:hkpr: p[v] += r[v] on the frontier; share
@@ -423,6 +432,7 @@ struct RoundsState {
   int32_t cur;   // frontier buffer of the current round (0 or 1)
   int32_t stop;  // 1 empty frontier, 2 round limit, 3 round not small, 4 error flagged
   int64_t count, rounds, pushes, pushed_edges;
+  int32_t ptab;  // Nibble: the table holding p (0 the initial one, 1 A, 2 B)
 };
 
 __device__ inline int64_t block_sum_i64(int64_t x, int64_t* s_red) {
@@ -435,6 +445,51 @@ __device__ inline int64_t block_sum_i64(int64_t x, int64_t* s_red) {
   return t;
 }
 
+// Exclusive prefix sum of cnt[0, nf) into epos by the whole grid (block b
+// scans its chunk after adding the sums of the chunks before it); returns
+// the total.  Contains grid barriers: every thread of the grid calls it.
+__device__ inline int64_t grid_exclusive_scan(cg::grid_group& grid, const int64_t* cnt,
+                                              int64_t nf, int64_t* epos, int64_t* bsum) {
+  __shared__ int64_t s_red[kBlock / 32];
+  __shared__ int64_t s_scan[kBlock / 32];
+  const int G = gridDim.x;
+  const int64_t chunk = (nf + G - 1) / G;
+  const int64_t c0 = min(nf, (int64_t)blockIdx.x * chunk), c1 = min(nf, c0 + chunk);
+  int64_t part = 0;
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) part += cnt[i];
+  part = block_sum_i64(part, s_red);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = part;
+  grid.sync();
+  int64_t pre = 0, tot = 0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    const int64_t x = __ldcg(&bsum[b]);
+    tot += x;
+    if (b < (int)blockIdx.x) pre += x;
+  }
+  pre = block_sum_i64(pre, s_red);
+  tot = block_sum_i64(tot, s_red);
+  for (int64_t base = c0; base < c1; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t x = i < c1 ? cnt[i] : 0;
+    int64_t inc = x;  // inclusive scan within the warp, then across warps
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((threadIdx.x & 31) >= o) inc += y;
+    }
+    if ((threadIdx.x & 31) == 31) s_scan[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    int64_t wpre = 0, btot = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+      if (k < (int)(threadIdx.x >> 5)) wpre += s_scan[k];
+      btot += s_scan[k];
+    }
+    if (i < c1) epos[i] = pre + wpre + inc - x;
+    pre += btot;
+    __syncthreads();
+  }
+  return tot;
+}
+
 __global__ void __launch_bounds__(kBlock)
     rounds_prnibble_kernel(Table T, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
@@ -444,9 +499,6 @@ __global__ void __launch_bounds__(kBlock)
                            int64_t* bsum, Counters* Cn, RoundsState* S, int64_t max_rounds,
                            int64_t e_max, int64_t key_limit) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ int64_t s_red[kBlock / 32];
-  __shared__ int64_t s_scan[kBlock / 32];
-  const int G = gridDim.x;
   for (;;) {
     const int cur = __ldcg(&S->cur), nxt = cur ^ 1;
     const int64_t nf = __ldcg(&Cn[cur].next_size);
@@ -471,42 +523,7 @@ __global__ void __launch_bounds__(kBlock)
     prnibble_vmap_body(nf, fv, fs, T, off, alpha, cs, cn, eps, rule, 0, 1, share, cnt, foff, nfv,
                        nfs, fcap, &Cn[nxt]);
     grid.sync();
-    // exclusive prefix sum of the degrees: block b scans its chunk after
-    // adding the sums of the chunks before it
-    const int64_t chunk = (nf + G - 1) / G;
-    const int64_t c0 = min(nf, (int64_t)blockIdx.x * chunk), c1 = min(nf, c0 + chunk);
-    int64_t part = 0;
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) part += cnt[i];
-    part = block_sum_i64(part, s_red);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = part;
-    grid.sync();
-    int64_t pre = 0, tot = 0;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) {
-      const int64_t x = __ldcg(&bsum[b]);
-      tot += x;
-      if (b < (int)blockIdx.x) pre += x;
-    }
-    pre = block_sum_i64(pre, s_red);
-    tot = block_sum_i64(tot, s_red);
-    for (int64_t base = c0; base < c1; base += blockDim.x) {
-      const int64_t i = base + threadIdx.x;
-      const int64_t x = i < c1 ? cnt[i] : 0;
-      int64_t inc = x;  // inclusive scan within the warp, then across warps
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if ((threadIdx.x & 31) >= o) inc += y;
-      }
-      if ((threadIdx.x & 31) == 31) s_scan[threadIdx.x >> 5] = inc;
-      __syncthreads();
-      int64_t wpre = 0, btot = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
-        if (k < (int)(threadIdx.x >> 5)) wpre += s_scan[k];
-        btot += s_scan[k];
-      }
-      if (i < c1) epos[i] = pre + wpre + inc - x;
-      pre += btot;
-      __syncthreads();
-    }
+    const int64_t tot = grid_exclusive_scan(grid, cnt, nf, epos, bsum);
     grid.sync();
     // edge push into the same table, appending crossings to the next frontier
     const int64_t Er = min(E, tot);
@@ -526,6 +543,77 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// Nibble (Fig. alg:nibble, atomic mode) the same way: each round fills a
+// fresh p' from p, so two hashed tables of capacity cap alternate as p'
+// (A in device round 0, 2, ..., B in 1, 3, ...) and p starts in T0 (any
+// form), the table the host's rounds left.  A round clears its p' table,
+// runs the vertexMap (p'[v] = p[v]/2, appending v if that reaches the
+// threshold), the scan and the edge push into p'.  When the new frontier is
+// empty the run is over and p stays where it was (the method returns the
+// previous p); otherwise p' becomes p.  key_limit is cap / 2: a round whose
+// keys (at most |F| + its edges) could pass it stops the kernel first.
+__global__ void __launch_bounds__(kBlock)
+    rounds_nibble_kernel(Table T0, Table A, Table B, const int64_t* __restrict__ off,
+                         const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+                         double eps, int fmode, int32_t* fv0, int32_t* fs0, int32_t* fv1,
+                         int32_t* fs1, int32_t fcap, double* share, int64_t* cnt, int64_t* epos,
+                         int64_t* foff, int64_t* bsum, Counters* Cn, RoundsState* S,
+                         int64_t max_rounds, int64_t e_max, int64_t key_limit) {
+  cg::grid_group grid = cg::this_grid();
+  for (;;) {
+    const int cur = __ldcg(&S->cur), nxt = cur ^ 1;
+    const int64_t nf = __ldcg(&Cn[cur].next_size);
+    const int64_t E = __ldcg(&Cn[cur].next_edges);
+    const int64_t k = __ldcg(&S->rounds);
+    const int err = __ldcg(&Cn[cur].err) | __ldcg(&Cn[nxt].err);
+    int stop = 0;
+    if (err) stop = 4;
+    else if (nf == 0) stop = 1;
+    else if (k >= max_rounds) stop = 2;
+    else if (E > e_max || nf + E > fcap || nf + E > key_limit) stop = 3;
+    if (stop) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) S->stop = stop;
+      return;  // the same decision in every thread: no barrier is left waiting
+    }
+    const int ptab = __ldcg(&S->ptab);
+    const Table P = ptab == 0 ? T0 : ptab == 1 ? A : B;
+    const Table Q = (k & 1) ? B : A;  // never P: P is T0 or the other one
+    int32_t* fv = cur ? fv1 : fv0;
+    int32_t* fs = cur ? fs1 : fs0;
+    int32_t* nfv = cur ? fv0 : fv1;
+    int32_t* nfs = cur ? fs0 : fs1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Q.cap;
+         i += (int64_t)gridDim.x * blockDim.x)
+      Q.s[i] = Slot{};  // p' = {}
+    grid.sync();
+    nibble_vmap_body(nf, fv, fs, P, Q, off, eps, fmode, 0, 1, share, cnt, foff, nfv, nfs, fcap,
+                     &Cn[nxt]);
+    grid.sync();
+    const int64_t tot = grid_exclusive_scan(grid, cnt, nf, epos, bsum);
+    grid.sync();
+    emap_atomic_body(col, deg, share, epos, foff, nf, min(E, tot), Q, eps, fmode, nfv, nfs, fcap,
+                     &Cn[nxt]);
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->rounds = k + 1;
+      S->pushes += nf;
+      S->pushed_edges += E;
+      if (Cn[nxt].next_size == 0) {
+        S->stop = 1;  // the previous p is the result
+      } else {
+        S->ptab = (k & 1) ? 2 : 1;
+        S->count = Cn[nxt].aux + Cn[nxt].inserted;
+        Cn[nxt].aux = 0;
+        Cn[nxt].inserted = 0;
+        Cn[cur] = Counters{};
+        S->cur = nxt;
+      }
+    }
+    grid.sync();
+    if (__ldcg(&S->stop)) return;
+  }
+}
+
 __global__ void rounds_init_kernel(Counters* Cn, RoundsState* S, int64_t nf, int64_t E,
                                    int64_t count) {
   Cn[0] = Counters{};
@@ -536,11 +624,11 @@ __global__ void rounds_init_kernel(Counters* Cn, RoundsState* S, int64_t nf, int
   S->count = count;
 }
 
-// out: stop | err << 8, cur, frontier size, its edges, keys, rounds, pushes,
-// pushed edges
+// out: stop | err << 8 | ptab << 16, cur, frontier size, its edges, keys,
+// rounds, pushes, pushed edges
 __global__ void rounds_pack_kernel(const Counters* Cn, const RoundsState* S, int64_t* out) {
   const int cur = S->cur;
-  out[0] = (int64_t)S->stop | ((int64_t)(Cn[0].err | Cn[1].err) << 8);
+  out[0] = (int64_t)S->stop | ((int64_t)(Cn[0].err | Cn[1].err) << 8) | ((int64_t)S->ptab << 16);
   out[1] = cur;
   out[2] = Cn[cur].next_size;
   out[3] = Cn[cur].next_edges;
@@ -2037,6 +2125,10 @@ struct PushWork {
   int64_t rounds_emax() const { return std::min<int64_t>(kRoundsEmax, g->nnz / 16); }
   int64_t rounds_fcap() const { return std::min<int64_t>(g->n, 2 * kRoundsEmax); }
   static int64_t key_limit(const Table& T) { return T.dense ? INT64_MAX : T.cap / 2; }
+  bool small_round_nibble() const {
+    return ctx->device_rounds && !ctx->trace && F.size > 0 && F.edges <= rounds_emax() &&
+           F.size + F.edges <= rounds_fcap();
+  }
   bool small_round(const Table& T, int64_t count) const {
     return ctx->device_rounds && !ctx->trace && F.size > 0 && F.edges <= rounds_emax() &&
            F.size + F.edges <= rounds_fcap() && count + F.edges <= key_limit(T);
@@ -2107,6 +2199,112 @@ struct PushWork {
     st.rounds += rounds;
     st.pushes += o[6];
     st.pushed_edges += o[7];
+    return LGC_OK;
+  }
+
+  // Nibble's rounds on the device (rounds_nibble_kernel) from the host's p
+  // table P and frontier F, at most rounds_left of them.  Afterwards P holds
+  // p (a table of the kernel's, or the same one), Pn is a spare, F and the
+  // counters are the host's again, *done counts the rounds run and *over is
+  // set when a round's frontier came out empty (the run is over).
+  int device_rounds_nibble(Table& P, Table& Pn, int64_t* count, double eps, int fmode,
+                           int64_t rounds_left, int64_t* done, bool* over) {
+    cudaStream_t s = ctx->stream;
+    *done = 0;
+    *over = false;
+    static int blocks_per_sm = -1;  // the same for every device of this build
+    if (blocks_per_sm < 0) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rounds_nibble_kernel, kBlock, 0) !=
+          cudaSuccess)
+        nb = 0;
+      blocks_per_sm = nb;
+    }
+    int sms = 0;
+    LGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int G = sms * std::min(blocks_per_sm, 2);
+    if (G < 1) {  // no co-resident grid possible: rounds stay on the host
+      ctx->device_rounds = false;
+      return LGC_OK;
+    }
+    const int64_t fcap = rounds_fcap();
+    // p' tables with room for 8 times this round's keys (a round that
+    // would not fit returns to the host, which comes back with bigger ones)
+    const int64_t cap = pow2_at_least(2 * std::max<int64_t>(
+                                              1024, std::min<int64_t>(g->n, 8 * (F.size + F.edges))));
+    Table A, B;
+    int st_ = table_create(ctx, &A, cap, false);
+    if (st_ == LGC_OK) st_ = table_create(ctx, &B, cap, false);
+    if (st_ != LGC_OK) {
+      table_destroy(ctx, &A);
+      table_destroy(ctx, &B);
+      return st_;
+    }
+    auto fail = [&](int code) {
+      table_destroy(ctx, &A);
+      table_destroy(ctx, &B);
+      return code;
+    };
+    for (int k = 0; k < 2; k++) {
+      if (X[k].v.reserve(ctx, fcap) || X[k].s.reserve(ctx, fcap)) return fail(LGC_ENOMEM);
+    }
+    if (reserve_frontier_scratch(fcap) || xbsum.reserve(ctx, G) || xcn.reserve(ctx, 2) ||
+        xst.reserve(ctx, 1) || total.reserve(ctx, 8))
+      return fail(LGC_ENOMEM);
+    if (cudaMemcpyAsync(X[0].v.ptr, F.v.ptr, 4 * F.size, cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(X[0].s.ptr, F.s.ptr, 4 * F.size, cudaMemcpyDeviceToDevice, s))
+      return fail(LGC_ECUDA);
+    rounds_init_kernel<<<1, 1, 0, s>>>(xcn.ptr, xst.ptr, F.size, F.edges, *count);
+    LGC_COUNT_LAUNCH(ctx);
+    int32_t fc = (int32_t)fcap;
+    int64_t mr = std::min<int64_t>(rounds_left, kRoundsPerLaunch), em = rounds_emax(),
+            kl = cap / 2;
+    void* args[] = {&P, &A, &B, &g->off, &g->col, &g->deg, &eps, &fmode, &X[0].v.ptr,
+                    &X[0].s.ptr, &X[1].v.ptr, &X[1].s.ptr, &fc, &share.ptr, &cnt.ptr, &epos.ptr,
+                    &foff.ptr, &xbsum.ptr, &xcn.ptr, &xst.ptr, &mr, &em, &kl};
+    {
+      ProfScope ps(ctx, LGC_PROF_EDGEMAP, 0.0);
+      if (cudaLaunchCooperativeKernel((const void*)rounds_nibble_kernel, G, kBlock, args, 0, s))
+        return fail(LGC_ECUDA);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    rounds_pack_kernel<<<1, 1, 0, s>>>(xcn.ptr, xst.ptr, total.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaMemcpyAsync(ctx->h_scratch, total.ptr, 64, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+      return fail(LGC_ECUDA);
+    const int64_t* o = ctx->h_scratch;
+    const int64_t stop = o[0] & 0xff, err = (o[0] >> 8) & 0xff, ptab = (o[0] >> 16) & 0xff;
+    const int64_t cur = o[1], nf = o[2], E = o[3], rounds = o[5];
+    if (ctx->profile && !ctx->prof_pending.empty())
+      ctx->prof_pending.back().bytes += 24.0 * (double)o[7] + 88.0 * (double)o[6];
+    if (err != 0) return fail(LGC_ETABLEFULL);
+    if (rounds < 1) return fail(LGC_ECUDA);  // the host checked that the first round is small
+    st.rounds += rounds;
+    st.pushes += o[6];
+    st.pushed_edges += o[7];
+    *done = rounds;
+    // p: where the kernel left it; the other tables are spares or freed
+    if (ptab != 0) {
+      table_destroy(ctx, &P);
+      table_destroy(ctx, &Pn);
+      P = ptab == 1 ? A : B;
+      Pn = ptab == 1 ? B : A;
+    } else {
+      table_destroy(ctx, &A);
+      table_destroy(ctx, &B);
+    }
+    if (stop == 1) {
+      *over = true;
+      return LGC_OK;
+    }
+    LGC_TRY(F.v.reserve(ctx, std::max<int64_t>(nf, 1024)));
+    LGC_TRY(F.s.reserve(ctx, std::max<int64_t>(nf, 1024)));
+    LGC_CUDA_TRY(cudaMemcpyAsync(F.v.ptr, X[cur].v.ptr, 4 * nf, cudaMemcpyDeviceToDevice, s));
+    LGC_CUDA_TRY(cudaMemcpyAsync(F.s.ptr, X[cur].s.ptr, 4 * nf, cudaMemcpyDeviceToDevice, s));
+    F.size = nf;
+    F.edges = E;
+    *count = o[4];
     return LGC_OK;
   }
 
@@ -2546,6 +2744,14 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
     W.F.edges = dx;
     lgc_stats& st = W.st;
     for (int t = 1; t <= prm->T; t++) {
+      if (!det && W.small_round_nibble()) {
+        int64_t done = 0;
+        bool over = false;
+        status = W.device_rounds_nibble(Pc, Pn, &count, eps, fmode, prm->T - t + 1, &done, &over);
+        if (status != LGC_OK || over) break;
+        t += (int)done - 1;  // the loop adds the last one
+        continue;
+      }
       W.record_trace();
       const int64_t nf = W.F.size;
       const int64_t need = min64(g->n, nf + W.F.edges);

@@ -443,6 +443,40 @@ def test_prnibble_device_rounds_round_limit(ctx_notrace):
         g.close()
 
 
+NIB_DEV_CASES = [("paper", 4, 1e-3), ("path9", 10, 0.3), ("star40", 6, 1e-4),
+                 ("grid6", 12, 1e-5), ("rand500", 15, 1e-6), ("rmat10", 20, 1e-6),
+                 ("rmat13", 20, 1e-7), ("rmat13", 4, 0.0), ("rmat16", 20, 1e-7),
+                 ("rmat16", 30, 1e-6)]
+
+
+@pytest.mark.parametrize("form_", [0, 1, 2], ids=["auto", "hashed", "dense"])
+@pytest.mark.parametrize("name,T,eps", NIB_DEV_CASES)
+def test_nibble_device_rounds(ctx_notrace, name, T, eps, form_):
+    """Nibble's device-driven rounds (atomic mode, tracing off): the same
+    rounds, pushes and p as the host-driven rounds and the oracle, including
+    runs that end on an empty frontier (the previous p is returned) and runs
+    cut by T."""
+    c = ctx_notrace
+    off, col = GRAPHS[name]()
+    g = lgc.Graph(c, off, col)
+    c.set_option(lgc.OPT_TABLE_FORM, form_)
+    try:
+        for x in seeds_for(off, col, 3, salt=11):
+            ref = oracle.nibble(off, col, x, T, eps)
+            c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
+            p1, s1 = lgc.nibble(g, x, T, eps, mode="atomic")
+            c.set_option(lgc.OPT_DEVICE_ROUNDS, 0)
+            p0, s0 = lgc.nibble(g, x, T, eps, mode="atomic")
+            for p, s in ((p1, s1), (p0, s0)):
+                assert (s.rounds, s.pushes, s.pushed_edges) == (ref.rounds, ref.pushes,
+                                                                 ref.pushed_edges)
+                assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
+        c.set_option(lgc.OPT_TABLE_FORM, 0)
+        g.close()
+
+
 # ---------------------------------------------------------------------------
 # Heavy-vertex pull gather: every batch depth gives the same (exact) sums, and
 # the autotuner picks one of them.
