@@ -48,14 +48,25 @@ constexpr int kEdgeTile = kBlock * kEdgeItems;  // edges per CTA tile
 
 enum FrontierMode { kFmNone = 0, kFmThreshold = 1, kFmInserted = 2 };
 
-__device__ inline int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t x) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (a[mid] <= x) lo = mid + 1;
-    else hi = mid;
+// The first index of a[0, n) (non-decreasing) whose entry exceeds x, found
+// by all 32 lanes of a warp (the same result in each): every step probes the
+// last entry of 32 equal chunks of the range and keeps the chunk where the
+// entries start to exceed x, so a search over n entries takes about
+// log32(n) dependent loads instead of log2(n).
+__device__ inline int64_t warp_upper_bound(const int64_t* a, int64_t n, int64_t x) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t pos = lo + (int64_t)(lane + 1) * step - 1;
+    const bool le = pos < hi && a[pos] <= x;  // true on a prefix of the lanes
+    const int c = __popc(__ballot_sync(0xffffffffu, le));
+    lo += (int64_t)c * step;
+    if (lo >= hi) return hi;
+    hi = min(hi, lo + step);
   }
-  return lo;
+  const bool le = lo + lane < hi && a[lo + lane] <= x;
+  return lo + __popc(__ballot_sync(0xffffffffu, le));
 }
 
 // Stages, for the block's record range [e0, e1), the exclusive prefix sums of
@@ -66,8 +77,11 @@ __device__ inline int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t x
 __device__ inline int stage_sources(const int64_t* epos, int64_t nf, int64_t total,
                                     int64_t e0, int64_t e1, int64_t* s_i0, int64_t* s_i1,
                                     int64_t* s_epos) {
-  if (threadIdx.x == 0) *s_i0 = upper_bound_i64(epos, nf, e0) - 1;
-  if (threadIdx.x == 32) *s_i1 = upper_bound_i64(epos, nf, e1 - 1) - 1;
+  const int warp = threadIdx.x >> 5;
+  if (warp < 2) {  // the two ends at once, each by a whole warp
+    const int64_t b = warp_upper_bound(epos, nf, warp == 0 ? e0 : e1 - 1) - 1;
+    if ((threadIdx.x & 31) == 0) *(warp == 0 ? s_i0 : s_i1) = b;
+  }
   __syncthreads();
   const int64_t i0 = *s_i0;
   int64_t c = *s_i1 - i0 + 1;
