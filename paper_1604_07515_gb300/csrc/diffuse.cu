@@ -1375,33 +1375,37 @@ __global__ void bits_count_kernel(const uint32_t* __restrict__ bits, int64_t wor
     cnt[w] = __popc(bits[w]);
 }
 
+// One thread per vertex (a warp per bitmap word): a set bit's vertex goes to
+// the word's position plus the set bits below it, so a warp's writes are
+// consecutive.  The degrees are summed per thread over the grid-stride loop
+// and added once per block (one address: per-warp atomics would queue on it).
 __global__ void bits_write_kernel(const uint32_t* __restrict__ bits, int64_t words,
                                   const int64_t* __restrict__ pos, const int32_t* __restrict__ deg,
                                   int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    int64_t dsum = 0;
-    if (w < words) {
-      uint32_t q = bits[w];
-      int64_t at = pos[w];
-      while (q) {
-        const int b = __ffs(q) - 1;
-        q &= q - 1;
-        const int32_t v = (int32_t)(w * 32 + b);
-        if (at < ncap) {
-          nfv[at] = v;
-          nfs[at] = v;
-        } else {
-          atomicOr(&C->err, kErrFrontierOverflow);
-        }
-        at++;
-        dsum += deg[v];
+  __shared__ int64_t s_red[kBlock / 32];
+  const int lane = threadIdx.x & 31;
+  int64_t dsum = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - lane < words * 32;
+       v += (int64_t)gridDim.x * blockDim.x) {  // whole warps are in range or out
+    const uint32_t q = bits[v >> 5];
+    if ((q >> lane) & 1u) {
+      const int64_t at = pos[v >> 5] + __popc(q & ((1u << lane) - 1u));
+      if (at < ncap) {
+        nfv[at] = (int32_t)v;
+        nfs[at] = (int32_t)v;
+      } else {
+        atomicOr(&C->err, kErrFrontierOverflow);
       }
+      dsum += deg[v];
     }
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if ((threadIdx.x & 31) == 0 && dsum)
-      atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)dsum);
+  }
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+  if (lane == 0) s_red[threadIdx.x >> 5] = dsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_red[k];
+    if (t) atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)t);
   }
 }
 
@@ -2112,9 +2116,9 @@ struct PushWork {
       bits_count_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr);
       LGC_COUNT_LAUNCH(ctx);
       LGC_TRY(scan_i64(ctx, pcnt.ptr, pcnt.ptr, words, false, total.ptr));
-      bits_write_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg,
-                                                            G.v.ptr, G.s.ptr, ncap,
-                                                            ctx->d_counters);
+      const int wg = std::min(grid_for(words * 32), 152 * 8);
+      bits_write_kernel<<<wg, kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg, G.v.ptr, G.s.ptr,
+                                               ncap, ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
       set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
       LGC_COUNT_LAUNCH(ctx);
