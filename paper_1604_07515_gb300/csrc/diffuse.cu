@@ -111,6 +111,21 @@ __device__ inline int find_source(const int64_t* s_epos, int cnt, int64_t e, int
   return j;
 }
 
+// Adds every thread's count n into *counter with one atomic per block (a
+// per-warp atomic on one address queues when a launch has many warps).  All
+// threads of the block call it, once, where every thread arrives.
+__device__ inline void flush_count(int64_t n, int64_t* counter) {
+  __shared__ int64_t s_cnt[kBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_cnt[k];
+    if (t) atomicAdd((unsigned long long*)counter, (unsigned long long)t);
+  }
+}
+
 __device__ inline void count_inserted(int ins, int64_t* counter) {
   const unsigned active = __activemask();
   const unsigned m = __ballot_sync(active, ins);
@@ -748,6 +763,7 @@ __global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t
                                   int64_t n, const double* __restrict__ sh, Table D, double c,
                                   int fmode, uint32_t* __restrict__ qbits, Counters* C) {
   const int64_t words = (n + 31) / 32;
+  int64_t nins = 0;  // keys inserted here, counted once per block
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words * 32;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t w = base + threadIdx.x;
@@ -780,8 +796,9 @@ __global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t
     const unsigned word = __ballot_sync(0xffffffffu, q);
     if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
       qbits[(base + threadIdx.x) >> 5] = word;
-    count_inserted(ins, &C->inserted);
+    nins += ins;
   }
+  flush_count(nins, &C->inserted);
 }
 
 // Heavy vertices are read in batches of 32 * BATCH edges: every lane issues
@@ -790,16 +807,16 @@ __global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t
 // (kPullBatch until tuned).
 constexpr int kPullBatch = 8;
 
-// Writes a heavy vertex's gathered value (lane 0 calls it).
-__device__ inline void pull_finish(const Table& D, int32_t w, int64_t d, double acc, bool touched,
-                                   bool present, double c, int fmode, uint32_t* qbits,
-                                   Counters* C) {
-  if (!touched) return;
+// Writes a heavy vertex's gathered value (lane 0 calls it); 1 if the vertex
+// became a key here (the caller counts it).
+__device__ inline int pull_finish(const Table& D, int32_t w, int64_t d, double acc, bool touched,
+                                  bool present, double c, int fmode, uint32_t* qbits) {
+  if (!touched) return 0;
   const uint32_t m = 1u << (w & 31);
   D.dval[w] = acc;
-  if (!present && !(atomicOr(&D.bits[w >> 5], m) & m))
-    atomicAdd((unsigned long long*)&C->inserted, 1ull);
+  const int ins = !present && !(atomicOr(&D.bits[w >> 5], m) & m);
   if (pull_qualifies(acc, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
+  return ins;
 }
 
 // ---------------------------------------------------------------------------
@@ -885,6 +902,7 @@ __global__ void __launch_bounds__(kBlock)
                         const int32_t* __restrict__ mid, int64_t nmid,
                         const double* __restrict__ sh, Table D, double c, int fmode,
                         uint32_t* __restrict__ qbits, Counters* C) {
+  int64_t nins = 0;  // keys inserted here, counted once per block
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nmid;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -917,8 +935,9 @@ __global__ void __launch_bounds__(kBlock)
         if (pull_qualifies(acc, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
       }
     }
-    count_inserted(ins, &C->inserted);
+    nins += ins;
   }
+  flush_count(nins, &C->inserted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1023,6 +1042,7 @@ __global__ void __launch_bounds__(kBlock)
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t nins = 0;
   for (int64_t b = warp0; b < nbig; b += nwarps) {
     const int32_t w = big_w[b];
     const bool present = (D.bits[w >> 5] >> (w & 31)) & 1u;
@@ -1063,8 +1083,9 @@ __global__ void __launch_bounds__(kBlock)
       }
     }
     if (lane == 0)
-      pull_finish(D, w, off[w + 1] - off[w], acc, touched, present, c, fmode, qbits, C);
+      nins += pull_finish(D, w, off[w + 1] - off[w], acc, touched, present, c, fmode, qbits);
   }
+  flush_count(nins, &C->inserted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1187,6 +1208,7 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
                                           Counters* C) {
   const int L = round_scale(range, g);
   const int64_t words = (n + 31) / 32;
+  int64_t nins = 0;  // keys inserted here, counted once per block
   for (int64_t base = bid * blockDim.x; base < words * 32; base += nblk * blockDim.x) {
     const int64_t w = base + threadIdx.x;
     bool q = false;
@@ -1228,8 +1250,9 @@ __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
     const unsigned word = __ballot_sync(0xffffffffu, q);
     if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
       qbits[(base + threadIdx.x) >> 5] = word;
-    count_inserted(ins, &C->inserted);
+    nins += ins;
   }
+  flush_count(nins, &C->inserted);
 }
 
 // Heavy vertices: one warp per work item (at most kPullItem edges of one
@@ -1257,6 +1280,7 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
                                           int32_t* __restrict__ htouch, Counters* C) {
   constexpr int kGroups = 32 / GL;
   const int L = round_scale(range, g);
+  int64_t nins = 0;  // vertices that became keys here
   const int lane = threadIdx.x & 31, gl = lane % GL, gid = lane / GL;
   const int64_t warp0 = (bid * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (nblk * blockDim.x) >> 5;
@@ -1315,8 +1339,8 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
     const bool present = (bword >> (w & 31)) & 1u;
     if (I.nparts == 1) {
       if (present || any)
-        pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(part, L), true, present, c,
-                    fmode, qbits, C);
+        nins += pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(part, L), true,
+                            present, c, fmode, qbits);
       continue;
     }
     const int32_t h = I.h;
@@ -1334,14 +1358,15 @@ __device__ inline void pull_heavy_fx_body(int64_t bid, int64_t nblk,
       total.lo = atomicAdd(&acc[0], 0ull);
       total.hi = atomicAdd(&acc[1], 0ull);
       if (present || atomicOr(&htouch[h], 0) != 0)
-        pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(total, L), true, present, c,
-                    fmode, qbits, C);
+        nins += pull_finish(D, w, d, (present ? cur : 0.0) + fx_to_double(total, L), true,
+                            present, c, fmode, qbits);
       acc[0] = 0;
       acc[1] = 0;
       hcnt[h] = 0;
       htouch[h] = 0;
     }
   }
+  flush_count(nins, &C->inserted);
 }
 
 template <int BATCH, int GL, typename SH>
