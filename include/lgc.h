@@ -174,10 +174,14 @@ enum {
                                    (default) the graph's tuned value, or 8, 16, 32 (only
                                    the pairs lgc_graph_autotune tries are compiled: 4 with
                                    32; 8 and 16 with 8, 16, 32) */
-  LGC_OPT_PULL_SHARE = 11       /* bytes per gathered share in atomic pull rounds: 0
+  LGC_OPT_PULL_SHARE = 11,      /* bytes per gathered share in atomic pull rounds: 0
                                    (default) the graph's tuned value, 16 (fixed-point
                                    records) or 8 (doubles, converted per edge); same
                                    results either way */
+  LGC_OPT_BATCH_HANDOFF = 12    /* lgc_prnibble_batch: a seed whose frontier's degree sum
+                                   reaches this many edges leaves the batch and finishes
+                                   alone (pull rounds, dense sets), with the same result;
+                                   0 (default) max(2^20, 2m/64), -1 never */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */

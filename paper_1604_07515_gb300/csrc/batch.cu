@@ -367,6 +367,13 @@ __global__ void batch_keep_flags_kernel(int64_t nf, const int32_t* __restrict__ 
     flag[i] = alive[fseed[i]] ? 1 : 0;
 }
 
+__global__ void batch_seed_flags_kernel(int64_t nf, const int32_t* __restrict__ fseed,
+                                        int32_t b, int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = fseed[i] == b ? 1 : 0;
+}
+
 __global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ flag,
                                         const int64_t* __restrict__ pos,
                                         const int32_t* __restrict__ a, const int32_t* __restrict__ b,
@@ -499,14 +506,17 @@ __global__ void batch_gather_kernel(const Table* __restrict__ tabs,
   }
 }
 
-// Per-seed output ranges: start[b] = pos[capoff[b]] (start[B] = total kept),
-// and the vertex ids without the seed bits.
-__global__ void batch_bounds_kernel(const int64_t* __restrict__ capoff, int64_t B,
-                                    const int64_t* __restrict__ pos, const int64_t* __restrict__ kept,
+// Per-seed output ranges, and (below) the vertex ids without the seed bits.
+// start[b] = the first kept position of seed b's slots, start[B] = the total
+// kept; a seed without slots (capacity 0: it finished outside the batch)
+// starts where the next one does, and one at the end at the total kept.
+__global__ void batch_bounds_kernel(const int64_t* __restrict__ capoff, int64_t B, int64_t total,
+                                    const int64_t* __restrict__ pos,
+                                    const int64_t* __restrict__ kept,
                                     int64_t* __restrict__ start) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
        b += (int64_t)gridDim.x * blockDim.x)
-    start[b] = b == B ? *kept : pos[capoff[b]];
+    start[b] = (b == B || capoff[b] >= total) ? *kept : pos[capoff[b]];
 }
 
 __global__ void batch_ids_kernel(const uint64_t* __restrict__ key, int64_t m, int vbits,
@@ -542,11 +552,14 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
       st = LGC_ECUDA;
       break;
     }
-    const int grid = (int)std::min<int64_t>(ceil_div(total, kBlock), 152 * 16);
+    // (at least one block: every seed may have finished alone, total = 0)
+    const int grid =
+        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, kBlock), 152 * 16));
     batch_keep_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag);
     LGC_COUNT_LAUNCH(ctx);
     if ((st = scan_i64(ctx, flag, pos, total, false, kept)) != LGC_OK) break;
-    batch_bounds_kernel<<<grid_for(B + 1), kBlock, 0, s>>>(d_capoff, B, pos, kept, start);
+    batch_bounds_kernel<<<grid_for(B + 1), kBlock, 0, s>>>(d_capoff, B, total, pos, kept,
+                                                            start);
     LGC_COUNT_LAUNCH(ctx);
     if (cudaMemcpyAsync(hstart.data(), start, 8 * (B + 1), cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s)) {
@@ -554,6 +567,10 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
       break;
     }
     const int64_t m = hstart[B];
+    for (int64_t b = 0; b < B; b++)
+      if (hstart[b] < 0 || hstart[b] > hstart[b + 1] || hstart[b + 1] > m || m > total)
+        st = LGC_ECUDA;  // inconsistent bounds: never size anything from them
+    if (st != LGC_OK) break;
     if ((st = dalloc_t(ctx, &key, m)) || (st = dalloc_t(ctx, &key2, m)) ||
         (st = dalloc_t(ctx, &val, m)) || (st = dalloc_t(ctx, &val2, m)) ||
         (st = dalloc_t(ctx, &idx, m)))
@@ -647,6 +664,16 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   DBuf<int64_t> d_rgbeg;
   std::vector<int32_t> grown(B, 0), alive(B, 1);
   std::vector<SeedCount> sc_h(B);
+  // seeds whose frontier grew past handoff_edges finish alone, where pull
+  // rounds and dense sets serve them far better than the batch's hashed
+  // push; their results and counters come from that run
+  const int64_t handoff_edges = ctx->batch_handoff > 0    ? ctx->batch_handoff
+                                : ctx->batch_handoff == 0 ? std::max<int64_t>(int64_t{1} << 20,
+                                                                              g->nnz / 64)
+                                                          : INT64_MAX;
+  std::vector<lgc_svec*> p_alone(B, nullptr);
+  std::vector<lgc_stats> st_alone(B);
+  std::vector<char> alone(B, 0);
 
   int32_t *d_seeds = nullptr, *d_grown = nullptr, *d_alive = nullptr, *gsize = nullptr;
   Table* d_tabs = nullptr;
@@ -723,6 +750,32 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
           alive[b] = 0;
           drop = true;
         }
+      // seeds with a big frontier continue alone from their state
+      for (int64_t b = 0; b < B && status == LGC_OK; b++) {
+        if (!alive[b] || nfs[b] == 0 || edges[b] < handoff_edges || tabs[b].cap < 64) continue;
+        if (fail(flag.reserve(ctx, nf)) || fail(qpos.reserve(ctx, nf)) ||
+            fail(Gs.reserve(ctx, nf)) || fail(Gv.reserve(ctx, nf)) || fail(Gslot.reserve(ctx, nf)))
+          break;
+        batch_seed_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, (int32_t)b, flag.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        if (fail(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr)) != LGC_OK) break;
+        batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr,
+                                                                 Fv.ptr, Fslot.ptr, Gs.ptr, Gv.ptr,
+                                                                 Gslot.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+        lgc_stats so_far{};
+        so_far.rounds = rounds[b];
+        so_far.pushes = pushes[b];
+        so_far.pushed_edges = pushed[b];
+        if (fail(run_prnibble_from(ctx, g, tabs[b], Gv.ptr, Gslot.ptr, nfs[b], edges[b],
+                                   count[b], &prm_h[b], so_far, &p_alone[b], &st_alone[b])) !=
+            LGC_OK)
+          break;
+        alone[b] = 1;
+        alive[b] = 0;
+        drop = true;
+      }
+      if (status != LGC_OK) break;
       if (drop) {
         cudaMemcpyAsync(d_alive, alive.data(), 4 * B, cudaMemcpyHostToDevice, s);
         if (fail(flag.reserve(ctx, nf)) || fail(qpos.reserve(ctx, nf)) ||
@@ -896,11 +949,25 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
     }
     if (status != LGC_OK) break;
     // results of all seeds at once: keep {p > 0}, sort by (seed, vertex),
-    // one copy out, then one vector per seed
-    status = extract_all(ctx, B, n, vbits, tabs, p_out);
+    // one copy out, then one vector per seed (those that finished alone
+    // already have theirs)
+    std::vector<Table> tabs_x = tabs;
+    for (int64_t b = 0; b < B; b++)
+      if (alone[b]) tabs_x[b] = Table{};
+    status = extract_all(ctx, B, n, vbits, tabs_x, p_out);
     if (status != LGC_OK) break;
+    for (int64_t b = 0; b < B; b++)
+      if (alone[b]) {
+        lgc_svec_free(p_out[b]);
+        p_out[b] = p_alone[b];
+        p_alone[b] = nullptr;
+      }
     if (st_out) {
       for (int64_t b = 0; b < B; b++) {
+        if (alone[b]) {
+          st_out[b] = st_alone[b];
+          continue;
+        }
         st_out[b] = lgc_stats{};
         st_out[b].rounds = rounds[b];
         st_out[b].pushes = pushes[b];
@@ -927,6 +994,7 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
     d->release(ctx);
   rk.release(ctx);
   rk2.release(ctx);
+  for (int64_t b = 0; b < B; b++) lgc_svec_free(p_alone[b]);  // left only on failure
   if (status != LGC_OK) {
     for (int64_t b = 0; b < B; b++) {
       lgc_svec_free(p_out[b]);

@@ -443,6 +443,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 8 && value != 16) return LGC_EINVAL;
       ctx->pull_share = (int)value;
       return LGC_OK;
+    case LGC_OPT_BATCH_HANDOFF:
+      if (value < -1) return LGC_EINVAL;
+      ctx->batch_handoff = value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;

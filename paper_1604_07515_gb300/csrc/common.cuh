@@ -202,6 +202,7 @@ struct lgc_ctx {
   int pull_batch = 0;          // LGC_OPT_PULL_BATCH: 0 = the graph's tuned value
   int pull_group = 0;          // LGC_OPT_PULL_GROUP: 0 = the graph's tuned value
   int pull_share = 0;          // LGC_OPT_PULL_SHARE: 0 = the graph's tuned value
+  int64_t batch_handoff = 0;   // LGC_OPT_BATCH_HANDOFF: 0 default, -1 never
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back
@@ -389,6 +390,17 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g);
 int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds,
                      const double* weights, double beta, const lgc_prnibble_params* prm,
                      lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out);
+// Continues PR-Nibble for one seed from the state batched rounds left: its
+// hashed table src (r in the slot values, p in src.p; copied, same capacity
+// so the frontier's slots stay valid), its frontier d_fv/d_fs (nf entries,
+// ascending in deterministic mode) with degree sum E, the table's key count,
+// and the rounds, pushes and pushed edges run so far.  The result and the
+// counters are those of one uninterrupted run (status_detail
+// LGC_EMAXROUNDS when the round limit ended it).
+int run_prnibble_from(lgc_ctx* ctx, lgc_graph* g, const Table& src, const int32_t* d_fv,
+                      const int32_t* d_fs, int64_t nf, int64_t E, int64_t count,
+                      const lgc_prnibble_params* prm, const lgc_stats& so_far, lgc_svec** p,
+                      lgc_stats* st_out);
 int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out);
 int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const* ps,
                     lgc_cluster** out);

@@ -2589,6 +2589,92 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   return st;
 }
 
+namespace {
+
+// The synchronous PR-Nibble rounds (Sec. 3.3) from the state in W.F, T and
+// count until the frontier is empty, or LGC_EMAXROUNDS once max_rounds
+// rounds have run in all (W.st.rounds holds the rounds already run).
+int prnibble_rounds(lgc_ctx* ctx, lgc_graph* g, PushWork& W, Table& T, int64_t& count,
+                    const lgc_prnibble_params* prm, double beta) {
+  const double alpha = prm->alpha, eps = prm->eps;
+  const bool det = prm->mode == LGC_MODE_DET;
+  const double cs = (2.0 * alpha) / (1.0 + alpha);
+  const double cn = (1.0 - alpha) / (1.0 + alpha);
+  const int64_t max_rounds = prm->max_rounds > 0 ? prm->max_rounds : INT64_MAX;
+  int status = LGC_OK;
+  lgc_stats& st = W.st;
+  while (W.F.size > 0) {
+    if (st.rounds >= max_rounds) return LGC_EMAXROUNDS;
+    if (!det && beta >= 1.0 && W.small_round(T, count)) {
+      status = W.device_rounds_prnibble(T, &count, alpha, cs, cn, eps, prm->rule,
+                                        max_rounds - st.rounds);
+      if (status != LGC_OK) return status;
+      continue;
+    }
+    // room for the round's new keys (at most the frontier's edges)
+    if ((status = ensure_capacity(ctx, &T, count, W.F.edges, g->n, W.F.v.ptr, W.F.s.ptr,
+                                  W.F.size)) != LGC_OK)
+      return status;
+    const bool pull = use_pull(ctx, g, W.F.edges);
+    if (pull && !T.dense &&
+        (status = table_to_dense(ctx, &T, g->n, W.F.v.ptr, W.F.s.ptr, W.F.size)) != LGC_OK)
+      return status;
+    const bool bulk = use_bulk(det, T, W.F.edges, g->n);
+    // beta-fraction rounds: the top ceil(beta |F|) candidates push, the
+    // others wait in W.U (after every change of the table's slots)
+    if (beta < 1.0 && W.F.size > 1) {
+      int64_t m = (int64_t)std::ceil(beta * (double)W.F.size);
+      m = std::max<int64_t>(1, std::min<int64_t>(m, W.F.size));
+      if (m < W.F.size && (status = W.select_top(T, m)) != LGC_OK) return status;
+    }
+    W.record_trace();
+    const int64_t nf = W.F.size;
+    if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) return status;
+    if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) return status;
+    if ((status = W.reset_counters()) != LGC_OK) return status;
+    {
+      ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+      vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+          nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
+          (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr,
+          (int32_t)W.G.v.cap, ctx->d_counters);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      return LGC_ECUDA;
+    }
+    Counters C;
+    if (pull) {
+      status = W.pull_phase(T, eps, kFmThreshold, &C, det);
+    } else {
+      int64_t nrec = W.F.edges;
+      if (det) {
+        // one record per edge and one self record per frontier vertex
+        // (cnt[i] = d + 1): the total is known without reading it back
+        nrec = W.F.edges + nf;
+        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+          return status;
+      } else {
+        if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
+          return status;
+      }
+      status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C, bulk);
+    }
+    if (status != LGC_OK) return status;
+    st.rounds++;
+    st.pushes += nf;
+    st.pushed_edges += W.F.edges;
+    count += C.inserted;
+    W.G.size = C.next_size;
+    W.G.edges = C.next_edges;
+    if ((status = W.merge_rest(T, eps)) != LGC_OK) return status;  // candidates that waited
+    W.swap_frontiers();
+  }
+  return status;
+}
+
+}  // namespace
+
 // PR-Nibble from the seed set seeds[0..k) with weights (null: all 1) and
 // beta-fraction rounds (beta = 1: every candidate pushes).  One seed of
 // weight 1 with beta = 1 is Fig. alg:pr-nibble2 / alg:pr-nibble exactly.
@@ -2620,10 +2706,6 @@ int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds
             });
   for (int64_t i = 1; i < k; i++)
     if (init[i].first == init[i - 1].first) return LGC_EINVAL;  // seeds must be distinct
-  const bool det = prm->mode == LGC_MODE_DET;
-  const double cs = (2.0 * alpha) / (1.0 + alpha);
-  const double cn = (1.0 - alpha) / (1.0 + alpha);
-  const int64_t max_rounds = prm->max_rounds > 0 ? prm->max_rounds : INT64_MAX;
   ctx->trace_ids.clear();
   ctx->trace_sizes.clear();
 
@@ -2662,79 +2744,8 @@ int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds
     LGC_COUNT_LAUNCH(ctx);
     W.F.size = k;
     W.F.edges = dsum;
-    lgc_stats& st = W.st;
-    while (W.F.size > 0) {
-      if (st.rounds >= max_rounds) {
-        status = LGC_EMAXROUNDS;
-        break;
-      }
-      if (!det && beta >= 1.0 && W.small_round(T, count)) {
-        status = W.device_rounds_prnibble(T, &count, alpha, cs, cn, eps, prm->rule,
-                                          max_rounds - st.rounds);
-        if (status != LGC_OK) break;
-        continue;
-      }
-      // room for the round's new keys (at most the frontier's edges)
-      if ((status = ensure_capacity(ctx, &T, count, W.F.edges, g->n, W.F.v.ptr, W.F.s.ptr,
-                                    W.F.size)) != LGC_OK)
-        break;
-      const bool pull = use_pull(ctx, g, W.F.edges);
-      if (pull && !T.dense &&
-          (status = table_to_dense(ctx, &T, g->n, W.F.v.ptr, W.F.s.ptr, W.F.size)) != LGC_OK)
-        break;
-      const bool bulk = use_bulk(det, T, W.F.edges, g->n);
-      // beta-fraction rounds: the top ceil(beta |F|) candidates push, the
-      // others wait in W.U (after every change of the table's slots)
-      if (beta < 1.0 && W.F.size > 1) {
-        int64_t m = (int64_t)std::ceil(beta * (double)W.F.size);
-        m = std::max<int64_t>(1, std::min<int64_t>(m, W.F.size));
-        if (m < W.F.size && (status = W.select_top(T, m)) != LGC_OK) break;
-      }
-      W.record_trace();
-      const int64_t nf = W.F.size;
-      if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
-      if ((status = W.reserve_next(min64(g->n, count + W.F.edges + nf))) != LGC_OK) break;
-      if ((status = W.reset_counters()) != LGC_OK) break;
-      {
-        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-        vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
-            nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
-            (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr,
-            (int32_t)W.G.v.cap, ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
-      }
-      if (cudaGetLastError() != cudaSuccess) {
-        status = LGC_ECUDA;
-        break;
-      }
-      Counters C;
-      if (pull) {
-        status = W.pull_phase(T, eps, kFmThreshold, &C, det);
-      } else {
-        int64_t nrec = W.F.edges;
-        if (det) {
-          // one record per edge and one self record per frontier vertex
-          // (cnt[i] = d + 1): the total is known without reading it back
-          nrec = W.F.edges + nf;
-          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
-            break;
-        } else {
-          if ((status = scan_i64(ctx, W.cnt.ptr, W.epos.ptr, nf, false, W.total.ptr)) != LGC_OK)
-            break;
-        }
-        status = W.edge_phase(T, eps, kFmThreshold, det, true, nrec, &C, bulk);
-      }
-      if (status != LGC_OK) break;
-      st.rounds++;
-      st.pushes += nf;
-      st.pushed_edges += W.F.edges;
-      count += C.inserted;
-      W.G.size = C.next_size;
-      W.G.edges = C.next_edges;
-      if ((status = W.merge_rest(T, eps)) != LGC_OK) break;  // candidates that waited
-      W.swap_frontiers();
-    }
-    st.touched = count;
+    status = prnibble_rounds(ctx, g, W, T, count, prm, beta);
+    W.st.touched = count;
   } while (0);
   if (status == LGC_OK || status == LGC_EMAXROUNDS) {
     int s2 = finish_svec(ctx, g, T, T.p, p, st_out, W.st);
@@ -2759,6 +2770,47 @@ int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds
 int run_prnibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_prnibble_params* prm,
                  lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out) {
   return run_prnibble_set(ctx, g, 1, &x, nullptr, 1.0, prm, p, st_out, r_out);
+}
+
+int run_prnibble_from(lgc_ctx* ctx, lgc_graph* g, const Table& src, const int32_t* d_fv,
+                      const int32_t* d_fs, int64_t nf, int64_t E, int64_t count,
+                      const lgc_prnibble_params* prm, const lgc_stats& so_far, lgc_svec** p,
+                      lgc_stats* st_out) {
+  if (src.dense || !src.p || src.cap < 64 || nf < 1) return LGC_EINVAL;
+  cudaStream_t s = ctx->stream;
+  PushWork W(ctx, g);
+  Table T;
+  LGC_TRY(table_create(ctx, &T, src.cap, true));  // the same capacity: the same slots
+  int status = LGC_OK;
+  do {
+    if (T.cap != src.cap ||
+        cudaMemcpyAsync(T.s, src.s, sizeof(Slot) * src.cap, cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(T.p, src.p, 8 * src.cap, cudaMemcpyDeviceToDevice, s)) {
+      status = LGC_ECUDA;
+      break;
+    }
+    if ((status = W.F.v.reserve(ctx, std::max<int64_t>(nf, 1024))) != LGC_OK) break;
+    if ((status = W.F.s.reserve(ctx, std::max<int64_t>(nf, 1024))) != LGC_OK) break;
+    if (cudaMemcpyAsync(W.F.v.ptr, d_fv, 4 * nf, cudaMemcpyDeviceToDevice, s) ||
+        cudaMemcpyAsync(W.F.s.ptr, d_fs, 4 * nf, cudaMemcpyDeviceToDevice, s)) {
+      status = LGC_ECUDA;
+      break;
+    }
+    W.F.size = nf;
+    W.F.edges = E;
+    W.st.rounds = so_far.rounds;
+    W.st.pushes = so_far.pushes;
+    W.st.pushed_edges = so_far.pushed_edges;
+    status = prnibble_rounds(ctx, g, W, T, count, prm, 1.0);
+    W.st.touched = count;
+  } while (0);
+  if (status == LGC_OK || status == LGC_EMAXROUNDS) {
+    const int s2 = finish_svec(ctx, g, T, T.p, p, st_out, W.st);
+    if (s2 != LGC_OK) status = s2;
+    else if (st_out && status == LGC_EMAXROUNDS) st_out->status_detail = LGC_EMAXROUNDS;
+  }
+  table_destroy(ctx, &T);
+  return status == LGC_EMAXROUNDS ? LGC_OK : status;
 }
 
 int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* prm, lgc_svec** p,

@@ -51,6 +51,49 @@ def test_batch_equals_single_seed(setup, name, mode):
             assert rel_l1(ps[b].idx, ps[b].val, ref.idx, ref.val) <= 1e-12
 
 
+@pytest.mark.parametrize("handoff", [200, 3000])
+@pytest.mark.parametrize("rule", ["opt", "orig"])
+@pytest.mark.parametrize("mode", ["det", "atomic"])
+def test_batch_handoff_to_single_seed(setup, handoff, rule, mode):
+    """Seeds whose frontier passes LGC_OPT_BATCH_HANDOFF edges finish alone
+    from the state the batch left: results and counters as in one
+    uninterrupted run (det bit-identical to the oracle), round limits
+    included."""
+    ctx, graphs = setup
+    off, col, g = graphs["rmat16"]
+    B = 24
+    seeds = inputs.seeds_deg2(off, B, 31)
+    eps = inputs.eps_loguniform(B, 32, -7.0, -4.5)
+    ctx.set_option(lgc.OPT_BATCH_HANDOFF, handoff)
+    try:
+        prm_alpha = 0.01
+        ps, sts = lgc.prnibble_batch(g, seeds, prm_alpha, eps, rule=rule, mode=mode)
+        for b in range(B):
+            ref = oracle.prnibble(off, col, int(seeds[b]), prm_alpha, float(eps[b]),
+                                  rule=0 if rule == "opt" else 1)
+            assert (sts[b].rounds, sts[b].pushes, sts[b].pushed_edges) == (
+                ref.rounds, ref.pushes, ref.pushed_edges)
+            if mode == "det":
+                assert np.array_equal(ps[b].idx, ref.idx) and np.array_equal(ps[b].val, ref.val)
+            else:
+                assert rel_l1(ps[b].idx, ps[b].val, ref.idx, ref.val) <= 1e-12
+        # round limits across the hand-off
+        for b, k in ((3, 2), (5, 6)):
+            p1, s1 = lgc.prnibble_batch(g, seeds[b:b + 2], prm_alpha, eps[b:b + 2], rule=rule,
+                                        mode=mode, max_rounds=k)
+            for j in range(2):
+                ref = oracle.prnibble(off, col, int(seeds[b + j]), prm_alpha, float(eps[b + j]),
+                                      rule=0 if rule == "opt" else 1, max_rounds=k)
+                assert s1[j].rounds == ref.rounds and s1[j].pushed_edges == ref.pushed_edges
+                if mode == "det":
+                    assert np.array_equal(p1[j].idx, ref.idx)
+                    assert np.array_equal(p1[j].val, ref.val)
+                else:
+                    assert rel_l1(p1[j].idx, p1[j].val, ref.idx, ref.val) <= 1e-12
+    finally:
+        ctx.set_option(lgc.OPT_BATCH_HANDOFF, 0)
+
+
 def test_batch_original_rule_and_round_limit(setup):
     ctx, graphs = setup
     off, col, g = graphs["rmat13"]
