@@ -173,6 +173,57 @@ int build_big_segments(lgc_ctx* ctx, lgc_graph* g) {
   return LGC_OK;
 }
 
+__global__ void light_items_kernel(const int32_t* __restrict__ order, int64_t k,
+                                   const int64_t* __restrict__ off, LightItem* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = order[i];
+    const int64_t o0 = off[w];
+    out[i] = LightItem{o0, w, (int32_t)(off[w + 1] - o0)};
+  }
+}
+
+// The vertices of degree 1..kPullLight grouped by degree, highest first, ids
+// ascending within a degree (a counting sort of the host degree copy).
+int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = g->n;
+  int64_t cnt[kPullLight + 2] = {0};
+  for (int64_t v = 0; v < n; v++)
+    if (g->hdeg[v] >= 1 && g->hdeg[v] <= kPullLight) cnt[g->hdeg[v]]++;
+  int64_t at[kPullLight + 2] = {0}, k = 0;
+  for (int d = kPullLight; d >= 1; d--) {
+    at[d] = k;
+    k += cnt[d];
+  }
+  g->nlight = k;
+  if (k == 0) return LGC_OK;
+  std::vector<int32_t> order;
+  try {
+    order.resize(k);
+  } catch (...) {
+    return LGC_ENOMEM;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    const int32_t d = g->hdeg[v];
+    if (d >= 1 && d <= kPullLight) order[at[d]++] = (int32_t)v;
+  }
+  int32_t* d_order = nullptr;
+  LGC_TRY(dalloc_t(ctx, &d_order, k));
+  int st = dalloc_t(ctx, &g->light, k);
+  if (st == LGC_OK &&
+      cudaMemcpyAsync(d_order, order.data(), 4 * k, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = LGC_ECUDA;
+  if (st == LGC_OK) {
+    light_items_kernel<<<grid_for(k), kBlock, 0, s>>>(d_order, k, g->off, g->light);
+    LGC_COUNT_LAUNCH(ctx);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      st = LGC_ECUDA;  // (the host order goes out of scope)
+  }
+  dfree(ctx, d_order);
+  return st;
+}
+
 // The vertices of degree > kPullLight, ascending, for pull rounds, and their
 // adjacency cut into work items.
 int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
@@ -535,6 +586,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     }
     st = build_heavy_list(ctx, g);
     if (st == LGC_OK) st = build_big_segments(ctx, g);
+    if (st == LGC_OK) st = build_light_items(ctx, g);
   } while (0);
   if (st != LGC_OK) {
     dfree(ctx, g->off);
@@ -546,6 +598,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     dfree(ctx, g->big_seg0);
     dfree(ctx, g->segs);
     dfree(ctx, g->det_mid);
+    dfree(ctx, g->light);
     cudaStreamSynchronize(s);
     delete g;
     return st;
@@ -576,6 +629,7 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->big_seg0);
   dfree(ctx, g->segs);
   dfree(ctx, g->det_mid);
+  dfree(ctx, g->light);
   cudaStreamSynchronize(ctx->stream);
   delete g;
 }

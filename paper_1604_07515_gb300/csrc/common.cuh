@@ -239,6 +239,14 @@ struct __align__(32) PullItem {
   int64_t pad;
 };
 
+// A vertex of degree 1..kPullLight for the atomic pull gather: its list
+// [beg, beg + d).  The graph keeps them grouped by degree (highest first), so
+// the threads of a warp walk lists of one length.
+struct __align__(16) LightItem {
+  int64_t beg;
+  int32_t w, d;
+};
+
 // A 256-edge segment of a big vertex's list (deterministic pull rounds):
 // edges [beg, beg + len) of vertex w, the big vertex's index `big`.
 struct __align__(32) DetSeg {
@@ -278,6 +286,9 @@ struct lgc_graph {
   int64_t nbig = 0;
   DetSeg* segs = nullptr;
   int64_t nsegs = 0;
+  // vertices of degree 1..kPullLight grouped by degree (atomic pull rounds)
+  LightItem* light = nullptr;
+  int64_t nlight = 0;
 };
 
 namespace lgc {

@@ -1194,63 +1194,49 @@ __global__ void tune_fill_kernel(SH* __restrict__ shx, int64_t n, int32_t* __res
   }
 }
 
-// Vertices of degree 1..kPullLight, one thread each, their edges read four
-// at a time (all column loads, then all share loads).  Every bitmap word of
-// qbits is written here (by ballot, heavy vertices' bits zero); the heavy
-// kernel, launched after this one, ORs its vertices in.
+// Vertices of degree 1..kPullLight, one thread each, taken from the graph's
+// list grouped by degree so that the threads of a warp walk lists of one
+// length (in id order most of a warp idled behind its longest list); the
+// edges are read four at a time (all column loads, then all share loads).
+// The bitmap qbits is cleared before this launch; this kernel and the heavy
+// one OR their qualifying vertices in.
 template <typename SH>
 __device__ inline void pull_light_fx_body(int64_t bid, int64_t nblk,
-                                          const int64_t* __restrict__ off,
-                                          const int32_t* __restrict__ col, int64_t n,
+                                          const LightItem* __restrict__ items, int64_t nl,
+                                          const int32_t* __restrict__ col,
                                           const SH* __restrict__ shx,
                                           const int32_t* __restrict__ range, int g, Table D,
                                           double c, int fmode, uint32_t* __restrict__ qbits,
                                           Counters* C) {
   const int L = round_scale(range, g);
-  const int64_t words = (n + 31) / 32;
   int64_t nins = 0;  // keys inserted here, counted once per block
-  for (int64_t base = bid * blockDim.x; base < words * 32; base += nblk * blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    bool q = false;
-    int ins = 0;
-    if (w < n) {
-      const int64_t o0 = off[w], d = off[w + 1] - o0;
-      if (d >= 1 && d <= kPullLight) {
-        Fx acc = {0, 0};
-        uint64_t flag = 0;
-        for (int64_t k = 0; k < d; k += 4) {
-          int32_t u[4];
+  for (int64_t i = bid * blockDim.x + threadIdx.x; i < nl; i += nblk * blockDim.x) {
+    const LightItem it = items[i];
+    const int32_t w = it.w, d = it.d;
+    Fx acc = {0, 0};
+    uint64_t flag = 0;
+    for (int k = 0; k < d; k += 4) {
+      int32_t u[4];
 #pragma unroll
-          for (int j = 0; j < 4; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
-          SH raw[4];
+      for (int j = 0; j < 4; j++) u[j] = k + j < d ? col[it.beg + k + j] : -1;
+      SH raw[4];
 #pragma unroll
-          for (int j = 0; j < 4; j++) raw[j] = u[j] >= 0 ? shx[u[j]] : no_share<SH>();
+      for (int j = 0; j < 4; j++) raw[j] = u[j] >= 0 ? shx[u[j]] : no_share<SH>();
 #pragma unroll
-          for (int j = 0; j < 4; j++) {
-            const Fx x = to_fx(raw[j], L);
-            flag |= x.hi;
-            fx_add(acc, x);
-          }
-        }
-        const uint32_t m = 1u << (w & 31);
-        const bool present = (D.bits[w >> 5] & m) != 0;
-        if (present || (flag & kFxFlag)) {
-          const double v = (present ? D.dval[w] : 0.0) + fx_to_double(acc, L);
-          D.dval[w] = v;
-          if (!present) {
-            atomicOr(&D.bits[w >> 5], m);
-            ins = 1;
-          }
-          q = pull_qualifies(v, d, c, fmode);
-        }
+      for (int j = 0; j < 4; j++) {
+        const Fx x = to_fx(raw[j], L);
+        flag |= x.hi;
+        fx_add(acc, x);
       }
     }
-    // every bitmap word is written whole here (the heavy vertices' bits
-    // zero); the heavy gather, launched after this one, ORs its vertices in
-    const unsigned word = __ballot_sync(0xffffffffu, q);
-    if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
-      qbits[(base + threadIdx.x) >> 5] = word;
-    nins += ins;
+    const uint32_t m = 1u << (w & 31);
+    const bool present = (D.bits[w >> 5] & m) != 0;
+    if (present || (flag & kFxFlag)) {
+      const double v = (present ? D.dval[w] : 0.0) + fx_to_double(acc, L);
+      D.dval[w] = v;
+      if (!present && !(atomicOr(&D.bits[w >> 5], m) & m)) nins++;
+      if (pull_qualifies(v, d, c, fmode)) atomicOr(&qbits[w >> 5], m);
+    }
   }
   flush_count(nins, &C->inserted);
 }
@@ -1382,13 +1368,13 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 template <typename SH>
-__global__ void pull_light_fx_kernel(const int64_t* __restrict__ off,
-                                     const int32_t* __restrict__ col, int64_t n,
+__global__ void pull_light_fx_kernel(const LightItem* __restrict__ items, int64_t nl,
+                                     const int32_t* __restrict__ col,
                                      const SH* __restrict__ shx,
                                      const int32_t* __restrict__ range, int g, Table D, double c,
                                      int fmode, uint32_t* __restrict__ qbits, Counters* C) {
-  pull_light_fx_body<SH>(blockIdx.x, gridDim.x, off, col, n, shx, range, g, D, c, fmode, qbits,
-                         C);
+  pull_light_fx_body<SH>(blockIdx.x, gridDim.x, items, nl, col, shx, range, g, D, c, fmode,
+                         qbits, C);
 }
 
 // Ordered compaction of a vertex bitmap into a frontier (ascending id), with
@@ -2118,9 +2104,13 @@ struct PushWork {
         // (ORing their vertices in); the two in one grid measured slower
         auto gather = [&](auto* shv) {
           using SH = std::remove_const_t<std::remove_pointer_t<decltype(shv)>>;
-          pull_light_fx_kernel<SH><<<lg, kBlock, 0, s>>>(g->off, g->col, n, shv, prange.ptr, gb,
-                                                          D, c, fmode, pq.ptr, ctx->d_counters);
-          LGC_COUNT_LAUNCH(ctx);
+          if (g->nlight > 0) {
+            const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), 152 * 32);
+            pull_light_fx_kernel<SH><<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, shv,
+                                                             prange.ptr, gb, D, c, fmode, pq.ptr,
+                                                             ctx->d_counters);
+            LGC_COUNT_LAUNCH(ctx);
+          }
           if (g->nitems > 0) {
             const int gw = ctx->pull_group ? ctx->pull_group : g->pull_group;
             const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / gw));
@@ -2133,6 +2123,8 @@ struct PushWork {
             LGC_COUNT_LAUNCH(ctx);
           }
         };
+        // both gathers OR their qualifying vertices into the cleared bitmap
+        LGC_CUDA_TRY(cudaMemsetAsync(pq.ptr, 0, 4 * words, s));
         if (sb == 8) gather(psh.ptr);
         else gather(pshx.ptr);
       }
