@@ -337,7 +337,7 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
 # rounds_prnibble_kernel and rounds_nibble_kernel, summed over one step
 # (shapes (8, 32, 8) and (8, 32, 16)).  Re-capture when any of these kernels
 # changes.
-EDGE_TRAFFIC_PER_STEP = {8: 8.470e9, 16: 10.084e9}
+EDGE_TRAFFIC_PER_STEP = {8: 9.082e9, 16: 10.896e9}
 TRAFFIC_SOURCE = "profiles/traffic_edge_phase_rmat22.md"
 
 # bytes of the per-step inputs handed to the library (seed + parameter structs)
