@@ -759,44 +759,35 @@ __device__ inline bool pull_qualifies(double acc, int64_t d, double c, int fmode
   return fmode == kFmInserted;
 }
 
-__global__ void pull_light_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                  int64_t n, const double* __restrict__ sh, Table D, double c,
-                                  int fmode, uint32_t* __restrict__ qbits, Counters* C) {
-  const int64_t words = (n + 31) / 32;
+// Deterministic pull, vertices of degree 1..kPullLight: one thread folds its
+// list in order (acc <- RN(acc + s) from the present value), taking the
+// vertices from the graph's list grouped by degree so that a warp's chains
+// have one length.  qbits is cleared before; qualifying vertices are ORed in.
+__global__ void pull_light_kernel(const LightItem* __restrict__ items, int64_t nl,
+                                  const int32_t* __restrict__ col,
+                                  const double* __restrict__ sh, Table D, double c, int fmode,
+                                  uint32_t* __restrict__ qbits, Counters* C) {
   int64_t nins = 0;  // keys inserted here, counted once per block
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words * 32;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    bool q = false;
-    int ins = 0;
-    if (w < n) {
-      const int64_t o0 = off[w], d = off[w + 1] - o0;
-      if (d >= 1 && d <= kPullLight) {
-        const uint32_t m = 1u << (w & 31);
-        const bool present = (D.bits[w >> 5] & m) != 0;
-        double acc = present ? D.dval[w] : 0.0;
-        bool touched = present;
-        for (int64_t k = 0; k < d; k++) {
-          const double x = sh[col[o0 + k]];
-          if (pull_member(x)) {
-            acc = acc + x;
-            touched = true;
-          }
-        }
-        if (touched) {
-          D.dval[w] = acc;
-          if (!present) {
-            atomicOr(&D.bits[w >> 5], m);
-            ins = 1;
-          }
-          q = pull_qualifies(acc, d, c, fmode);
-        }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const LightItem it = items[i];
+    const int32_t w = it.w;
+    const uint32_t m = 1u << (w & 31);
+    const bool present = (D.bits[w >> 5] & m) != 0;
+    double acc = present ? D.dval[w] : 0.0;
+    bool touched = present;
+    for (int k = 0; k < it.d; k++) {
+      const double x = sh[col[it.beg + k]];
+      if (pull_member(x)) {
+        acc = acc + x;
+        touched = true;
       }
     }
-    const unsigned word = __ballot_sync(0xffffffffu, q);
-    if ((threadIdx.x & 31) == 0 && (base + threadIdx.x) / 32 < words)
-      qbits[(base + threadIdx.x) >> 5] = word;
-    nins += ins;
+    if (touched) {
+      D.dval[w] = acc;
+      if (!present && !(atomicOr(&D.bits[w >> 5], m) & m)) nins++;
+      if (pull_qualifies(acc, it.d, c, fmode)) atomicOr(&qbits[w >> 5], m);
+    }
   }
   flush_count(nins, &C->inserted);
 }
@@ -2065,11 +2056,15 @@ struct PushWork {
     {
       ProfScope ps(ctx, det ? LGC_PROF_DET_EDGE : LGC_PROF_EDGEMAP,
                    24.0 * (double)F.edges + 24.0 * nf);
-      int lg = grid_for(words * 32);
       if (det) {
-        pull_light_kernel<<<lg, kBlock, 0, s>>>(g->off, g->col, n, psh.ptr, D, c, fmode, pq.ptr,
-                                                 ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
+        // every gather ORs its qualifying vertices into the cleared bitmap
+        LGC_CUDA_TRY(cudaMemsetAsync(pq.ptr, 0, 4 * words, s));
+        if (g->nlight > 0) {
+          const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), 152 * 32);
+          pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, psh.ptr, D, c,
+                                                   fmode, pq.ptr, ctx->d_counters);
+          LGC_COUNT_LAUNCH(ctx);
+        }
         if (g->ndet_mid > 0) {
           const int mg = (int)std::min<int64_t>(ceil_div(g->ndet_mid, kBlock), 152 * 32);
           pull_mid_det_kernel<<<mg, kBlock, 0, s>>>(g->off, g->col, g->det_mid, g->ndet_mid,
