@@ -47,12 +47,23 @@ __global__ void scan_reduce_kernel(const int64_t* __restrict__ in, int64_t n,
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// Scans one tile; offsets[blockIdx.x] (exclusive block prefix) or 0.
+// Scans one tile, starting from offsets[blockIdx.x] (an exclusive block
+// prefix), or, with tile_sums set, from the sum of offsets[0, blockIdx.x)
+// (the tiles' own sums: one launch fewer when there are few tiles), or 0.
 __global__ void scan_tile_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out,
                                  int64_t n, const int64_t* __restrict__ offsets, int inclusive,
-                                 int64_t* __restrict__ total) {
+                                 int64_t* __restrict__ total, int tile_sums) {
   __shared__ int64_t tile[kScanTile];
   __shared__ int64_t warp_tot[kBlock / 32];
+  __shared__ int64_t pre_tot[kBlock / 32];
+  int64_t pre = 0;
+  if (offsets && tile_sums) {
+    int64_t part = 0;
+    for (int64_t j = threadIdx.x; j < (int64_t)blockIdx.x; j += blockDim.x) part += offsets[j];
+    block_inclusive_scan(part, pre_tot, &pre);
+  } else if (offsets) {
+    pre = offsets[blockIdx.x];
+  }
   int64_t base = (int64_t)blockIdx.x * kScanTile;
   for (int k = 0; k < kScanItems; k++) {
     int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
@@ -67,7 +78,7 @@ __global__ void scan_tile_kernel(const int64_t* __restrict__ in, int64_t* __rest
   }
   int64_t tot;
   int64_t incl = block_inclusive_scan(s, warp_tot, &tot);
-  int64_t run = incl - s + (offsets ? offsets[blockIdx.x] : 0);
+  int64_t run = incl - s + pre;
   for (int k = 0; k < kScanItems; k++) {
     int64_t x = v[k];
     tile[threadIdx.x * kScanItems + k] = inclusive ? run + x : run;
@@ -113,7 +124,7 @@ int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool incl
   }
   int64_t nb = ceil_div(n, kScanTile);
   if (nb == 1) {
-    scan_tile_kernel<<<1, kBlock, 0, st>>>(in, out, n, nullptr, inclusive, total);
+    scan_tile_kernel<<<1, kBlock, 0, st>>>(in, out, n, nullptr, inclusive, total, 0);
     LGC_COUNT_LAUNCH(ctx);
     LGC_CUDA_TRY(cudaGetLastError());
     return LGC_OK;
@@ -123,9 +134,13 @@ int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool incl
   scan_reduce_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, n, partial);
   LGC_COUNT_LAUNCH(ctx);
   LGC_CUDA_TRY(cudaGetLastError());
-  int s = scan_i64(ctx, partial, partial, nb, false, nullptr);
+  // up to kScanTile tiles: each block sums the tile sums before its own
+  // (at most kScanTile loads); beyond that the sums are scanned first
+  const bool direct = nb <= kScanTile;
+  int s = direct ? LGC_OK : scan_i64(ctx, partial, partial, nb, false, nullptr);
   if (s == LGC_OK) {
-    scan_tile_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, out, n, partial, inclusive, total);
+    scan_tile_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, out, n, partial, inclusive, total,
+                                                      direct ? 1 : 0);
     LGC_COUNT_LAUNCH(ctx);
     if (cudaGetLastError() != cudaSuccess) s = LGC_ECUDA;
   }
