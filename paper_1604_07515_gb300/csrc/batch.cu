@@ -376,7 +376,8 @@ __global__ void batch_seed_flags_kernel(int64_t nf, const int32_t* __restrict__ 
 
 __global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ flag,
                                         const int64_t* __restrict__ pos,
-                                        const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                                        const int32_t* __restrict__ a,
+                                        const int32_t* __restrict__ b,
                                         const int32_t* __restrict__ c, int32_t* oa, int32_t* ob,
                                         int32_t* oc) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
@@ -493,8 +494,9 @@ __global__ void batch_keep_kernel(const Table* __restrict__ tabs,
 
 __global__ void batch_gather_kernel(const Table* __restrict__ tabs,
                                     const int64_t* __restrict__ capoff, int64_t B, int64_t total,
-                                    const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
-                                    int vbits, uint64_t* __restrict__ key, double* __restrict__ val) {
+                                    const int64_t* __restrict__ flag,
+                                    const int64_t* __restrict__ pos, int vbits,
+                                    uint64_t* __restrict__ key, double* __restrict__ val) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!flag[i]) continue;

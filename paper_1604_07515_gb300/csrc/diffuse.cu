@@ -1662,9 +1662,10 @@ __global__ void sel_split_kernel(const int32_t* __restrict__ fv, const int32_t* 
   }
 }
 
-__global__ void copy_frontier_kernel(const uint32_t* __restrict__ sv, const int32_t* __restrict__ ss,
-                                     int64_t m, const int32_t* __restrict__ deg, int32_t* fv,
-                                     int32_t* fs, unsigned long long* edges) {
+__global__ void copy_frontier_kernel(const uint32_t* __restrict__ sv,
+                                     const int32_t* __restrict__ ss, int64_t m,
+                                     const int32_t* __restrict__ deg, int32_t* fv, int32_t* fs,
+                                     unsigned long long* edges) {
   unsigned long long e = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -2260,8 +2261,8 @@ struct PushWork {
     const int64_t fcap = rounds_fcap();
     // p' tables with room for 8 times this round's keys (a round that
     // would not fit returns to the host, which comes back with bigger ones)
-    const int64_t cap = pow2_at_least(2 * std::max<int64_t>(
-                                              1024, std::min<int64_t>(g->n, 8 * (F.size + F.edges))));
+    const int64_t keys8 = std::min<int64_t>(g->n, 8 * (F.size + F.edges));
+    const int64_t cap = pow2_at_least(2 * std::max<int64_t>(1024, keys8));
     Table A, B;
     int st_ = table_create(ctx, &A, cap, false);
     if (st_ == LGC_OK) st_ = table_create(ctx, &B, cap, false);
@@ -2510,7 +2511,8 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
         (st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
         (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
       break;
-    if (cudaMemsetAsync(q, 0, 4 * words, s) || cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
+    if (cudaMemsetAsync(q, 0, 4 * words, s) ||
+        cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
         cudaMemsetAsync(hcnt, 0, 4 * (g->nheavy + 1), s) ||
         cudaMemsetAsync(htouch, 0, 4 * (g->nheavy + 1), s) ||
         cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
@@ -2569,7 +2571,8 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   table_destroy(ctx, &D);
-  for (void* p : {(void*)shx, (void*)shd, (void*)range, (void*)q, (void*)hacc, (void*)hcnt, (void*)htouch})
+  for (void* p : {(void*)shx, (void*)shd, (void*)range, (void*)q, (void*)hacc, (void*)hcnt,
+                  (void*)htouch})
     dfree(ctx, p);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(Counters), s);
   if (cudaGetLastError() != cudaSuccess && st == LGC_OK) st = LGC_ECUDA;
@@ -2623,8 +2626,8 @@ int prnibble_rounds(lgc_ctx* ctx, lgc_graph* g, PushWork& W, Table& T, int64_t& 
       ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
       vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
           nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
-          (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr,
-          (int32_t)W.G.v.cap, ctx->d_counters);
+          (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr,
+          W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
     }
     if (cudaGetLastError() != cudaSuccess) {

@@ -285,7 +285,8 @@ __device__ inline int64_t seg_of(const int64_t* __restrict__ beg, int64_t B, int
   return lo;
 }
 
-__global__ void bsweep_keys_kernel(const SweepIn* __restrict__ in, const int64_t* __restrict__ inoff,
+__global__ void bsweep_keys_kernel(const SweepIn* __restrict__ in,
+                                   const int64_t* __restrict__ inoff,
                                    int64_t B, int64_t M, const int32_t* __restrict__ deg, int64_t n,
                                    uint64_t* __restrict__ key, int32_t* __restrict__ id,
                                    int32_t* __restrict__ seg, int64_t* __restrict__ keep,
@@ -329,7 +330,8 @@ __global__ void bsweep_compact_kernel(const int64_t* __restrict__ keep,
 
 __global__ void bsweep_bounds_kernel(const int64_t* __restrict__ inoff, int64_t B, int64_t M,
                                      const int64_t* __restrict__ pos,
-                                     const int64_t* __restrict__ total, int64_t* __restrict__ nbeg) {
+                                     const int64_t* __restrict__ total,
+                                     int64_t* __restrict__ nbeg) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
        b += (int64_t)gridDim.x * blockDim.x)
     nbeg[b] = (b == B || inoff[b] >= M) ? *total : pos[inoff[b]];
