@@ -469,7 +469,7 @@ def main():
         clusters += cl
         for i, name in enumerate(STEP_ALGOS):
             split[name]["ms"] += evs[i].elapsed_time(evs[i + 1]) / args.steps
-            split[name]["edges"] += evs[-1][i] // args.steps
+            split[name]["edges"] += evs[-1][i] / args.steps  # mean over the steps
     barrier()
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
