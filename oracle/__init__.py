@@ -21,9 +21,9 @@ ctypes.  Functions and the paper passages they follow:
 * ``sweep_zpath``     Sec. 3.1, Theorem thm:sweep (the Z array construction)
 * ``philox4x32_10``   Salmon et al., SC'11 (random stream of ``rand_hkpr``)
 
-parity: every function is pinned by the ``-m "not gpu"`` tests except the
-Philox words, which are pinned statistically and by agreement with an
-independent implementation only (partially pinned).
+parity: every function is pinned by the ``-m "not gpu"`` tests; the Philox
+words against cuRAND's host-side Philox4x32-10 generator (a library routine)
+on the counter words ``rand_hkpr`` uses.
 """
 from __future__ import annotations
 

@@ -28,8 +28,9 @@
 //  * parity: PR-Nibble, Nibble, HK-PR and the sweep cut are pinned by the
 //    CPU tests (dense linear-algebra closed forms, invariants, the paper's
 //    worked sweep example, brute force).  The Philox4x32-10 words are pinned
-//    only statistically and by agreement with an independent implementation
-//    (partially pinned).
+//    to cuRAND's host-side Philox4x32-10 generator (a library routine) over
+//    several keys and counters with words 0-2 in use, the words rand_hkpr
+//    draws from, plus uniformity and avalanche checks.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>

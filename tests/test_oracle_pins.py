@@ -466,3 +466,58 @@ def test_philox_uniformity_and_avalanche():
     assert 48 < np.mean(flips) < 80
     assert not np.array_equal(oracle.philox4x32_10([1, 2, 3, 4], key),
                               oracle.philox4x32_10([1, 2, 3, 4], key ^ np.uint32(1)))
+
+
+def _curand_host_philox_blocks(seed, first_block, nblocks):
+    """Words of cuRAND's host-side Philox4x32-10 generator (a library routine
+    written independently of the oracle), starting at 4-word block
+    ``first_block``.  None when libcurand cannot be loaded."""
+    import ctypes
+    import ctypes.util
+    names = ["libcurand.so", "libcurand.so.10"]
+    found = ctypes.util.find_library("curand")
+    if found:
+        names.insert(0, found)
+    for root in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if root:
+            names.append(os.path.join(root, "lib64", "libcurand.so"))
+    lib = None
+    for name in names:
+        try:
+            lib = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if lib is None:
+        return None
+    gen = ctypes.c_void_p()
+    philox4_32_10 = 161                      # curandRngType_t value in curand.h
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), philox4_32_10) != 0:
+        return None
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(4 * first_block)) == 0
+        out = np.zeros(4 * nblocks, np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_size_t(len(out))) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out.reshape(nblocks, 4)
+
+
+@pytest.mark.parametrize("seed", [0, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF, 7])
+def test_philox_matches_curand_host_generator(seed):
+    # cuRAND's host generator keys Philox4x32-10 with the 64-bit seed (low
+    # word first) and emits 4-word block b from the counter
+    # (b div 2^16 as a 64-bit value in words 0-1, b mod 2^16 in word 2, 0).
+    # Blocks near 0, past 2^16 and past 2^48 exercise counter words 0, 1, 2.
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    for first in (0, (3 << 16) - 5, (1 << 48) + (9 << 16) + 11):
+        got = _curand_host_philox_blocks(seed, first, 32)
+        if got is None:
+            pytest.skip("libcurand is not available")
+        for j in range(32):
+            b = first + j
+            q, r = b >> 16, b & 0xFFFF
+            ctr = [q & 0xFFFFFFFF, q >> 32, r, 0]
+            assert np.array_equal(oracle.philox4x32_10(ctr, key), got[j]), (seed, b)
