@@ -1,0 +1,97 @@
+"""Host logic of bench.py, on CPU: the clock record taken from nvidia-smi's
+CSV, the rank reduction at one rank, the serving HK-PR degree, and the
+reference arm's JSON line (the oracle timed on a small R-MAT)."""
+import argparse
+import json
+import math
+
+import pytest
+
+import bench
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.proc = _FakeProc()
+    s.lines = list(lines)
+    return s
+
+
+def test_clock_record_median_max_and_reasons():
+    na, act = "Not Active", "Active"
+    lines = [
+        f"0, 1965, 2070, 900.1, 0x0, {na}, {na}, {na}, {na}",
+        f"0, 1980, 2070, 1100.4, 0x4, {na}, {na}, {na}, {act}",
+        f"0, 1995, 2070, 1200.0, 0x4, {na}, {na}, {na}, {act}",
+        "0, [N/A], 2070, 0, 0x0, N/A, N/A, N/A, N/A",      # unreadable sample: skipped
+        "garbage",                                          # short line: skipped
+    ]
+    rec = _sampler(lines).stop()
+    assert rec["sm_mhz"] == 1980 and rec["sm_max_mhz"] == 2070
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples"] == 3
+
+
+def test_clock_record_flags_slowdowns():
+    act, na = "Active", "Not Active"
+    rec = _sampler([f"0, 900, 2070, 1400, 0x8, {act}, {act}, {na}, {na}"]).stop()
+    assert rec["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+
+
+def test_clock_record_without_nvidia_smi():
+    rec = bench.ClockSampler(0).stop()
+    assert rec["sm_mhz"] is None and rec["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reduce_ranks_is_identity_on_one_rank():
+    assert bench.reduce_ranks([1.5, 2.0], [3.0], 1, "cpu") == ([1.5, 2.0], [3.0])
+
+
+def test_hk_terms_tail_bound():
+    for t, eps in [(10.0, 1e-7), (5.0, 1e-4), (1.0, 1e-9)]:
+        N = bench.hk_terms(t, eps)
+        tail = 1.0 - sum(math.exp(-t) * t ** k / math.factorial(k) for k in range(N + 1))
+        assert tail <= eps * 1.0001
+        prev = 1.0 - sum(math.exp(-t) * t ** k / math.factorial(k) for k in range(N))
+        assert N == 1 or prev > eps
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "SCALE", 11)
+    args = argparse.Namespace(gpus=1, steps=4, warmup=1)
+    assert bench.run_reference(args) == 0
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert line["impl"] == "reference" and line["metric"] == "pushed_edges_per_s"
+    assert line["value"] > 0 and line["unit"] == "edges/s"
+    assert line["steps"] == 4 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["ms_per_step"] > 0 and line["data"] == "synthetic"
+    assert "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    def boom(*a, **k):
+        raise AssertionError("rank 1 must not run the oracle")
+
+    monkeypatch.setattr(bench, "cpu_oracle_step", boom)
+    assert bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0)) == 0
+    assert capsys.readouterr().out == ""
