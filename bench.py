@@ -81,8 +81,12 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.mark = 0  # samples taken before the timed region began
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Starts nvidia-smi and returns once its first sample is in (or it
+        has exited, or wait_s passed), so that the region timed after this
+        call is covered from its start; that first sample is not counted."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
@@ -92,6 +96,12 @@ class ClockSampler:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while (not self.lines and self.proc.poll() is None
+               and time.perf_counter() - t0 < wait_s):
+            time.sleep(0.005)
+        self.mark = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -107,7 +117,11 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.mark:]
+        in_region = bool(lines)
+        if not in_region:  # region shorter than the sampling period: the sample just before it
+            lines = self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -121,7 +135,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm) if in_region else 0}
 
 
 ALGOS = ("prnibble", "nibble", "hkpr", "rand_hkpr")
@@ -394,7 +408,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    # default: 80 timed steps (about 1.2 s, several clock samples); the
+    # reference arm's oracle, about 10 s per cycle of the four diffusions, 8
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="atomic", choices=["atomic", "det"])
@@ -407,6 +423,8 @@ def main():
     ap.add_argument("--algos", default=",".join(ALGOS),
                     help="comma-separated subset of the step (for profiling one diffusion)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 8 if args.impl == "reference" else 80
     global MODE, STEP_ALGOS
     MODE = args.mode
     STEP_ALGOS = tuple(a for a in args.algos.split(",") if a)

@@ -4,6 +4,8 @@ reference arm's JSON line (the oracle timed on a small R-MAT)."""
 import argparse
 import json
 import math
+import os
+import time
 
 import pytest
 
@@ -95,3 +97,46 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
     monkeypatch.setattr(bench, "cpu_oracle_step", boom)
     assert bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0)) == 0
     assert capsys.readouterr().out == ""
+
+
+def _fake_smi(tmp_path, body):
+    d = tmp_path / "bin"
+    d.mkdir()
+    f = d / "nvidia-smi"
+    f.write_text("#!/bin/sh\n" + body)
+    f.chmod(0o755)
+    return str(d)
+
+
+def test_clock_sampler_counts_only_samples_inside_the_region(tmp_path, monkeypatch):
+    line = "0, 2070, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    path = _fake_smi(tmp_path, f'while true; do echo "{line}"; sleep 0.05; done\n')
+    monkeypatch.setenv("PATH", path + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.mark >= 1                        # returned after the first sample
+    time.sleep(0.4)
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2070 and rec["reasons"] == []
+    assert 2 <= rec["samples"] == len(s.lines) - s.mark
+
+
+def test_clock_sampler_region_shorter_than_the_period(tmp_path, monkeypatch):
+    line = "0, 1980, 2070, 500.0, 0x4, Not Active, Not Active, Not Active, Active"
+    path = _fake_smi(tmp_path, f'echo "{line}"; exec sleep 30\n')
+    monkeypatch.setenv("PATH", path + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    rec = s.stop()                            # no sample inside: the one just before
+    assert rec["samples"] == 0 and rec["sm_mhz"] == 1980 and rec["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_does_not_wait_for_a_dead_nvidia_smi(tmp_path, monkeypatch):
+    path = _fake_smi(tmp_path, "exit 9\n")
+    monkeypatch.setenv("PATH", path + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    t0 = time.perf_counter()
+    s.start(wait_s=20.0)
+    assert time.perf_counter() - t0 < 5.0
+    rec = s.stop()
+    assert rec["sm_mhz"] is None and rec["samples"] == 0
