@@ -56,3 +56,42 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lgc.NibbleParams) == 24
     assert ctypes.sizeof(lgc.HKPRParams) == 24
     assert ctypes.sizeof(lgc.RandHKPRParams) == 32
+
+
+LAYOUTS = [
+    ("lgc_svec", "Svec"), ("lgc_cluster", "Cluster"), ("lgc_stats", "Stats"),
+    ("lgc_prnibble_params", "PRNibbleParams"), ("lgc_nibble_params", "NibbleParams"),
+    ("lgc_hkpr_params", "HKPRParams"), ("lgc_rand_hkpr_params", "RandHKPRParams"),
+    ("lgc_alloc_fns", "AllocFns"), ("lgc_kernel_profile", "KernelProfile"),
+    ("lgc_request", "Request"), ("lgc_result", "Result"),
+]
+
+
+def test_binding_structs_match_the_c_compilers_layout(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the
+    C compiler gives the header's struct (compiled here with the host cc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lgc.h"', 'int main(void) {']
+    for cname, pyname in LAYOUTS:
+        cls = getattr(lgc, pyname)
+        lines.append(f'  printf("{pyname} :sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{pyname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = 0
+    for ln in out.splitlines():
+        pyname, what, value = ln.split()
+        cls = getattr(lgc, pyname)
+        got = ctypes.sizeof(cls) if what == ":sizeof" else getattr(cls, what).offset
+        assert got == int(value), (pyname, what, got, value)
+        seen += 1
+    assert seen == sum(1 + len(getattr(lgc, p)._fields_) for _, p in LAYOUTS)
