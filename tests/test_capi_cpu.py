@@ -95,3 +95,14 @@ def test_binding_structs_match_the_c_compilers_layout(tmp_path):
         assert got == int(value), (pyname, what, got, value)
         seen += 1
     assert seen == sum(1 + len(getattr(lgc, p)._fields_) for _, p in LAYOUTS)
+
+
+def test_binding_argument_counts_match_the_header():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    protos = re.findall(r"\b(lgc_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", text)
+    assert sorted(name for name, _ in protos) == declared_symbols()
+    for name, params in protos:
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(lgc.SIGNATURES[name][1]) == n, name
