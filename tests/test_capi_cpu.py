@@ -106,3 +106,47 @@ def test_binding_argument_counts_match_the_header():
         params = params.strip()
         n = 0 if params in ("", "void") else params.count(",") + 1
         assert len(lgc.SIGNATURES[name][1]) == n, name
+
+
+_C_SCALARS = {"int": ("i", 4), "int32_t": ("i", 4), "uint32_t": ("i", 4), "int64_t": ("i", 8),
+              "uint64_t": ("i", 8), "size_t": ("i", 8), "double": ("f", 8), "float": ("f", 4)}
+
+
+def _c_kind(decl, named=True):
+    """('p', 8) for a pointer, ('i'|'f', bytes) for a scalar, None for void."""
+    decl = decl.replace("const", " ").strip()
+    if "*" in decl:
+        return ("p", 8)
+    words = decl.split()
+    base = words[0] if not named or len(words) == 1 else " ".join(words[:-1])
+    return None if base == "void" else _C_SCALARS[base]
+
+
+def _py_kind(t):
+    if t is None:
+        return None
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type) \
+            or getattr(t, "_flags_", 0) & ctypes._FUNCFLAG_CDECL:
+        return ("p", 8)
+    if t in (ctypes.c_double, ctypes.c_float):
+        return ("f", ctypes.sizeof(t))
+    return ("i", ctypes.sizeof(t))
+
+
+def test_binding_argument_and_return_types_match_the_header():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = re.sub(r"#[^\n]*", "", text)
+    protos = []
+    for stmt in text.split(";"):
+        stmt = re.split(r"[{}]", stmt)[-1]
+        m = re.fullmatch(r"\s*([A-Za-z_][\w\s\*]*?)\b(lgc_[a-z0-9_]+)\s*\(([^()]*)\)\s*", stmt)
+        if m:
+            protos.append(m.groups())
+    assert sorted(name for _, name, _ in protos) == declared_symbols()
+    for ret, name, params in protos:
+        res, args = lgc.SIGNATURES[name]
+        assert _py_kind(res) == _c_kind(ret, named=False), (name, ret, res)
+        params = params.strip()
+        decls = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        assert [_py_kind(a) for a in args] == [_c_kind(d) for d in decls], name
