@@ -150,3 +150,18 @@ def test_binding_argument_and_return_types_match_the_header():
         params = params.strip()
         decls = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
         assert [_py_kind(a) for a in args] == [_c_kind(d) for d in decls], name
+
+
+def test_make_request_marshals_every_algorithm():
+    r = lgc.make_request(lgc.ALGO_PRNIBBLE, 17, True, alpha=0.01, eps=1e-6, rule="orig",
+                         mode="det", max_rounds=9)
+    assert (r.algo, r.seed, r.want_sweep) == (lgc.ALGO_PRNIBBLE, 17, 1)
+    assert (r.pr.alpha, r.pr.eps, r.pr.rule, r.pr.mode, r.pr.max_rounds) == (0.01, 1e-6, 1, 1, 9)
+    r = lgc.make_request(lgc.ALGO_NIBBLE, 3, False, T=20, eps=1e-7)
+    assert (r.want_sweep, r.nb.T, r.nb.eps, r.nb.mode) == (0, 20, 1e-7, 0)
+    r = lgc.make_request(lgc.ALGO_HKPR, 5, True, t=10.0, N=20, eps=1e-7, mode="det")
+    assert (r.hk.t, r.hk.N, r.hk.eps, r.hk.mode) == (10.0, 20, 1e-7, 1)
+    r = lgc.make_request(lgc.ALGO_RAND_HKPR, 8, True, t=10.0, K=10, n_walks=10**6, rng_seed=7)
+    assert (r.rh.t, r.rh.K, r.rh.n_walks, r.rh.rng_seed) == (10.0, 10, 10**6, 7)
+    with pytest.raises(KeyError):
+        lgc.make_request(lgc.ALGO_PRNIBBLE, 1, True, alpha=0.01, eps=1e-6, mode="fast")
