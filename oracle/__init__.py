@@ -85,6 +85,7 @@ def _load():
             ("orc_prnibble_set", [i64, P, P, f64, f64, ci, f64, i64, ci]),
             ("orc_nibble", [i32, ci, f64, ci]),
             ("orc_hkpr", [i32, f64, ci, f64, ci]),
+            ("orc_hkpr_signed", [i32, f64, ci, f64, ci, ci]),
             ("orc_hkpr_queue", [i32, f64, ci, f64]),
             ("orc_rand_hkpr", [i32, f64, ci, i64, ctypes.c_uint64]),
             ("orc_sweep", [i64, P, P]),
@@ -209,10 +210,13 @@ def nibble(off, col, seed, T, eps, trace=False) -> Result:
     return _collect(h)
 
 
-def hkpr(off, col, seed, t, N, eps, trace=False) -> Result:
+def hkpr(off, col, seed, t, N, eps, trace=False, threshold_sign=1) -> Result:
+    """threshold_sign -1: the entry thresholds with e^{-t} (Sec. 3.4's
+    sequential description) instead of the parallel figure's e^{t}."""
     off, col, n = _g(off, col)
-    h = _load().orc_hkpr(n, off.ctypes.data, col.ctypes.data, int(seed), float(t), int(N),
-                         float(eps), int(bool(trace)))
+    h = _load().orc_hkpr_signed(n, off.ctypes.data, col.ctypes.data, int(seed), float(t),
+                                int(N), float(eps), int(bool(trace)),
+                                -1 if threshold_sign < 0 else 1)
     return _collect(h)
 
 

@@ -510,10 +510,14 @@ void orc_hkpr_psi(double t, int N, double* psi) {
   for (int k = N - 1; k >= 0; k--) psi[k] = 1.0 + (t / (double)(k + 1)) * psi[k + 1];
 }
 
-static std::vector<double> hk_thresholds(double t, int N, double eps) {
+// sign = -1 takes e^{-t} in place of e^{t}: the sequential description of
+// Sec. 3.4 writes the threshold with e^{-t}, the parallel figure with e^{t};
+// +1 is the reading followed everywhere, -1 exists to compare the two.
+static std::vector<double> hk_thresholds(double t, int N, double eps, int sign = 1) {
   std::vector<double> psi(N + 1), c(N + 1);
   orc_hkpr_psi(t, N, psi.data());
-  for (int j = 0; j <= N; j++) c[j] = (std::exp(t) * eps) / (2.0 * (double)N * psi[j]);
+  const double et = sign < 0 ? std::exp(-t) : std::exp(t);
+  for (int j = 0; j <= N; j++) c[j] = (et * eps) / (2.0 * (double)N * psi[j]);
   return c;
 }
 
@@ -523,15 +527,15 @@ static std::vector<double> hk_thresholds(double t, int N, double eps) {
 // {v : r[v] >= c_{j+1} d(v)}.  Otherwise (the last level) edgeMap adds
 // r[s]/d(s) into p[w] and the loop ends.  The loop also ends when the
 // frontier is empty.  p is returned unscaled.
-orc_result* orc_hkpr(int64_t n, const int64_t* off, const int32_t* col, int32_t x, double t,
-                     int N, double eps, int trace) {
+orc_result* orc_hkpr_signed(int64_t n, const int64_t* off, const int32_t* col, int32_t x,
+                            double t, int N, double eps, int trace, int sign) {
   orc_result* res = new orc_result();
   Graph g{n, off, col};
   if (x < 0 || x >= n || g.deg(x) < 1 || N < 1 || !(t > 0.0) || !(eps >= 0.0)) {
     res->stats[ORC_ST_STATUS] = -1;
     return res;
   }
-  std::vector<double> c = hk_thresholds(t, N, eps);
+  std::vector<double> c = hk_thresholds(t, N, eps, sign);
   SparseSet p(n), ra(n), rb(n);
   SparseSet* r = &ra;
   SparseSet* rr = &rb;
@@ -587,6 +591,11 @@ orc_result* orc_hkpr(int64_t n, const int64_t* off, const int32_t* col, int32_t 
   res->stats[ORC_ST_TOUCHED] = (int64_t)p.keys.size();
   emit_sorted(p, res->i32[ORC_IDX], res->f64[ORC_VAL], true);
   return res;
+}
+
+orc_result* orc_hkpr(int64_t n, const int64_t* off, const int32_t* col, int32_t x, double t,
+                     int N, double eps, int trace) {
+  return orc_hkpr_signed(n, off, col, x, t, N, eps, trace, 1);
 }
 
 // Sequential HK-PR with a queue over (vertex, level) pairs, Sec. 3.4

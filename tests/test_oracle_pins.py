@@ -410,6 +410,41 @@ def test_hkpr_hand_worked_threshold():
     np.testing.assert_allclose(res.val, [2.0, 1 / 3, 1 / 3, 1 / 3], rtol=1e-15)
 
 
+def test_hkpr_threshold_sign_hand_worked():
+    """The e^{-t} thresholds of Sec. 3.4's sequential description (the
+    debug reading; the parallel figure's e^{t} is the default).  Same star,
+    t = 1, N = 2: c_1 = e^-1 eps / (2 * 2 * 1.5) = eps / (6e).  eps = 1 gives
+    0.0613 <= 1/3, so the leaves go on (with e^{t} they did not); eps = 6
+    gives 1/e = 0.368 > 1/3: frontier empty."""
+    off, col = inputs.star(3)
+    res = oracle.hkpr(off, col, 0, 1.0, 2, 1.0, threshold_sign=-1)
+    assert res.idx.tolist() == [0, 1, 2, 3]
+    np.testing.assert_allclose(res.val, [2.0, 1 / 3, 1 / 3, 1 / 3], rtol=1e-15)
+    res = oracle.hkpr(off, col, 0, 1.0, 2, 6.0, threshold_sign=-1)
+    assert res.idx.tolist() == [0] and res.val.tolist() == [1.0]
+    a = oracle.hkpr(off, col, 0, 1.0, 2, 0.5)
+    b = oracle.hkpr(off, col, 0, 1.0, 2, 0.5, threshold_sign=1)
+    assert a.val.tolist() == b.val.tolist()
+
+
+@pytest.mark.parametrize("t,N,eps", [(3.0, 10, 1e-3), (5.0, 12, 1e-2)])
+def test_hkpr_threshold_sign_monotone(t, N, eps):
+    """Lower thresholds only add work: with e^{-t} every level's frontier
+    contains the e^{t} one and p is pointwise at least as large (each r' is a
+    left fold of a superset of larger non-negative terms, and rounding to
+    nearest is monotone).  At t >= 3 the e^{-t} run pushes strictly more."""
+    off, col = inputs.rmat(10, seed=7)
+    n = len(off) - 1
+    x = inputs.config1_seed(off, col)
+    hi = oracle.hkpr(off, col, x, t, N, eps, trace=True)
+    lo = oracle.hkpr(off, col, x, t, N, eps, trace=True, threshold_sign=-1)
+    assert len(lo.trace) >= len(hi.trace)
+    for f_hi, f_lo in zip(hi.trace, lo.trace):
+        assert set(f_hi.tolist()) <= set(f_lo.tolist())
+    assert np.all(to_dense(n, lo.idx, lo.val) >= to_dense(n, hi.idx, hi.val))
+    assert lo.pushed_edges > hi.pushed_edges
+
+
 # ---------------------------------------------------------------------------
 # rand-HK-PR (Sec. 3.5) and the Philox stream
 # ---------------------------------------------------------------------------
