@@ -114,8 +114,9 @@ typedef struct {
   int mode;
 } lgc_hkpr_params;
 
-/* rand-HK-PR (Sec. 3.5): n_walks >= 1 walks of Poisson(t) length capped at
- * K >= 0, random stream Philox4x32-10 keyed by rng_seed. */
+/* rand-HK-PR (Sec. 3.5): 1 <= n_walks <= INT32_MAX walks of Poisson(t)
+ * length capped at K, 0 <= K <= 128, t >= 0; random stream Philox4x32-10
+ * keyed by rng_seed.  Other values: LGC_EINVAL. */
 typedef struct {
   double t;
   int K;
@@ -178,10 +179,16 @@ enum {
                                    (default) the graph's tuned value, 16 (fixed-point
                                    records) or 8 (doubles, converted per edge); same
                                    results either way */
-  LGC_OPT_BATCH_HANDOFF = 12    /* lgc_prnibble_batch: a seed whose frontier's degree sum
+  LGC_OPT_BATCH_HANDOFF = 12,   /* lgc_prnibble_batch: a seed whose frontier's degree sum
                                    reaches this many edges leaves the batch and finishes
                                    alone (pull rounds, dense sets), with the same result;
                                    0 (default) max(2^20, 2m/64), -1 never */
+  LGC_OPT_HK_THRESHOLD_SIGN = 13 /* debug: the sign of the exponent in lgc_hkpr's entry
+                                   thresholds.  +1 (default): e^t eps d(v) / (2 N psi_j),
+                                   as in the parallel HK-PR figure (Sec. 3.4); -1: e^-t,
+                                   as in the sequential description of Sec. 3.4, which
+                                   makes the diffusion spread much further.  Request-loop
+                                   workers always use +1 */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */
@@ -290,11 +297,15 @@ int lgc_sweep_batch(lgc_graph *g, int64_t B, const lgc_svec *const *p, lgc_clust
  * size, vol, cut and conductance, with out->ids = d_ids and out->on_device = 1.
  * Do not pass *out to lgc_cluster_free.
  *
- * No device memory is allocated or freed: all temporaries live in one
- * fixed-size device array (about 5.6 MB) that every device loading the
- * library holds until the process exits.  Limits and behaviour:
+ * No device memory is allocated or freed by the call: all temporaries live
+ * in one fixed-size device array (about 5.6 MB), held until the process
+ * exits.  With CUDA's lazy module loading (the default) the driver reserves
+ * that array on a device at the first lgc_sweep_noalloc call there (an empty
+ * vector, nnz = 0, will do): make that call before handing the rest of the
+ * GPU's memory to another allocator.  Limits and behaviour:
  *  - nnz > LGC_SWEEP_NOALLOC_MAX_N is rejected with LGC_EINVAL;
- *  - an entry that is not a vertex of degree >= 1: LGC_EINVAL;
+ *  - an entry that is not a vertex of degree >= 1, or a vertex named twice:
+ *    LGC_EINVAL (as lgc_sweep);
  *  - all calls share the array, so calls that overlap on the GPU (different
  *    streams, contexts or threads) race and return wrong results; serialise
  *    them;

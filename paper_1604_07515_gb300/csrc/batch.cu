@@ -556,7 +556,7 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
     }
     // (at least one block: every seed may have finished alone, total = 0)
     const int grid =
-        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, kBlock), 152 * 16));
+        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, kBlock), (ctx->sms * 16)));
     batch_keep_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag);
     LGC_COUNT_LAUNCH(ctx);
     if ((st = scan_i64(ctx, flag, pos, total, false, kept)) != LGC_OK) break;
@@ -832,7 +832,7 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
         cudaMemcpyAsync(d_rg.ptr, rg.data(), sizeof(Regrow) * gw.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_rgbeg.ptr, rgbeg.data(), 8 * (gw.size() + 1), cudaMemcpyHostToDevice, s);
         const int64_t tot = rgbeg[gw.size()];
-        batch_rehash_kernel<<<(int)std::min<int64_t>(ceil_div(tot, kBlock), 152 * 16), kBlock, 0,
+        batch_rehash_kernel<<<(int)std::min<int64_t>(ceil_div(tot, kBlock), (ctx->sms * 16)), kBlock, 0,
                               s>>>(d_rg.ptr, d_rgbeg.ptr, (int64_t)gw.size(), tot, gsize + 2);
         LGC_COUNT_LAUNCH(ctx);
         for (size_t k = 0; k < gw.size(); k++) slabs.release(ctx, old_slab[k]);
@@ -852,7 +852,7 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
       cudaMemsetAsync(gsize, 0, 8, s);
       {
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-        batch_vmap_kernel<<<std::min(grid_for(nf), 152 * 32), kBlock, 0, s>>>(
+        batch_vmap_kernel<<<std::min(grid_for(nf), (ctx->sms * 32)), kBlock, 0, s>>>(
             nf, Fs.ptr, Fv.ptr, Fslot.ptr, d_tabs, d_prm, g->off, det ? 1 : 0, share.ptr,
             cnt.ptr, foff.ptr, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
         LGC_COUNT_LAUNCH(ctx);
@@ -862,7 +862,7 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
         if (E > 0) {
           const int64_t tiles = ceil_div(E, kTileB);
           ProfScope ps(ctx, LGC_PROF_EDGEMAP, 24.0 * (double)E + 28.0 * nf);
-          batch_emap_kernel<<<(int)std::min<int64_t>(tiles, 152 * 16), kBlock, 0, s>>>(
+          batch_emap_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
               g->col, g->deg, share.ptr, epos.ptr, foff.ptr, Fs.ptr, nf, E, total.ptr, d_tabs,
               d_prm, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
           LGC_COUNT_LAUNCH(ctx);
@@ -876,7 +876,7 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
         {
           const int64_t tiles = ceil_div(R, kTileB);
           ProfScope ps(ctx, LGC_PROF_DET_EDGE, 24.0 * (double)E + 28.0 * nf);
-          batch_emit_kernel<<<(int)std::min<int64_t>(tiles, 152 * 16), kBlock, 0, s>>>(
+          batch_emit_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
               g->col, Fv.ptr, Fs.ptr, share.ptr, epos.ptr, foff.ptr, nf, R, vbits, rk.ptr,
               rv.ptr);
           LGC_COUNT_LAUNCH(ctx);

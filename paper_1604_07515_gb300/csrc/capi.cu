@@ -498,6 +498,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value < -1) return LGC_EINVAL;
       ctx->batch_handoff = value;
       return LGC_OK;
+    case LGC_OPT_HK_THRESHOLD_SIGN:
+      if (value != 1 && value != -1) return LGC_EINVAL;
+      ctx->hk_threshold_sign = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
@@ -556,7 +560,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
         validate_kernel<<<grid_for(n), kBlock, 0, s>>>(g->off, g->col, n, nnz, dflags);
         LGC_COUNT_LAUNCH(ctx);
       }
-      degree_kernel<<<std::min(grid_for(n), 152 * 64), kBlock, 0, s>>>(g->off, n, g->deg,
+      degree_kernel<<<std::min(grid_for(n), (ctx->sms * 64)), kBlock, 0, s>>>(g->off, n, g->deg,
                                                                        dflags + 1);
       LGC_COUNT_LAUNCH(ctx);
     }

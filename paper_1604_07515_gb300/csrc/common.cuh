@@ -203,6 +203,7 @@ struct lgc_ctx {
   int pull_group = 0;          // LGC_OPT_PULL_GROUP: 0 = the graph's tuned value
   int pull_share = 0;          // LGC_OPT_PULL_SHARE: 0 = the graph's tuned value
   int64_t batch_handoff = 0;   // LGC_OPT_BATCH_HANDOFF: 0 default, -1 never
+  int hk_threshold_sign = 1;   // LGC_OPT_HK_THRESHOLD_SIGN: +1 (e^t, default) or -1 (e^-t)
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   // small pinned host block for per-round read-back

@@ -1896,7 +1896,7 @@ struct PushWork {
     if (bulk) {
       if (nrec > 0) {
         int64_t tiles = ceil_div(nrec, kEdgeTile);
-        int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+        int grid = (int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16));
         ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
         emap_red_kernel<<<grid, kBlock, 0, s>>>(g->col, share.ptr, epos.ptr, foff.ptr, nf, nrec,
                                                  total.ptr, D, ctx->d_counters);
@@ -1925,7 +1925,7 @@ struct PushWork {
     if (!det) {
       if (nrec > 0) {
         int64_t tiles = ceil_div(nrec, kEdgeTile);
-        int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+        int grid = (int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16));
         ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
         emap_atomic_kernel<<<grid, kBlock, 0, s>>>(g->col, g->deg, share.ptr, epos.ptr, foff.ptr,
                                                     nf, nrec, total.ptr, D, c, fmode, G.v.ptr,
@@ -1947,7 +1947,7 @@ struct PushWork {
     LGC_TRY(segid.reserve(ctx, nrec));
     if (nrec > 0) {
       int64_t tiles = ceil_div(nrec, kEdgeTile);
-      int grid = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+      int grid = (int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16));
       ProfScope ps(ctx, LGC_PROF_DET_EDGE, alg_bytes);
       emit_records_kernel<<<grid, kBlock, 0, s>>>(g->col, F.v.ptr, share.ptr, epos.ptr, foff.ptr,
                                                    nf, nrec, self_rec ? 1 : 0, rk.ptr, rv.ptr);
@@ -1981,7 +1981,7 @@ struct PushWork {
                                                      segslot.ptr, longs.ptr, nlong.ptr,
                                                      ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
-      fold_long_kernel<<<152 * 4, kBlock, 0, s>>>(rv.ptr, nrec, segstart.ptr, nseg, longs.ptr,
+      fold_long_kernel<<<(ctx->sms * 4), kBlock, 0, s>>>(rv.ptr, nrec, segstart.ptr, nseg, longs.ptr,
                                                    nlong.ptr, D, g->deg, c, fmode, qflag.ptr,
                                                    segv.ptr, segslot.ptr);
       LGC_COUNT_LAUNCH(ctx);
@@ -2043,7 +2043,7 @@ struct PushWork {
     } else {
       LGC_CUDA_TRY(cudaMemsetAsync(prange.ptr, 0, 8, s));
       const int64_t rb = ceil_div(nf, kBlock);
-      share_range_kernel<<<(int)(rb < 1 ? 1 : rb > 152 * 4 ? 152 * 4 : rb), kBlock, 0, s>>>(
+      share_range_kernel<<<(int)(rb < 1 ? 1 : rb > (ctx->sms * 4) ? (ctx->sms * 4) : rb), kBlock, 0, s>>>(
           nf, share.ptr, prange.ptr);
       LGC_COUNT_LAUNCH(ctx);
       if (sb == 8) {
@@ -2061,13 +2061,13 @@ struct PushWork {
         // every gather ORs its qualifying vertices into the cleared bitmap
         LGC_CUDA_TRY(cudaMemsetAsync(pq.ptr, 0, 4 * words, s));
         if (g->nlight > 0) {
-          const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), 152 * 32);
+          const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), (ctx->sms * 32));
           pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, psh.ptr, D, c,
                                                    fmode, pq.ptr, ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
         }
         if (g->ndet_mid > 0) {
-          const int mg = (int)std::min<int64_t>(ceil_div(g->ndet_mid, kBlock), 152 * 32);
+          const int mg = (int)std::min<int64_t>(ceil_div(g->ndet_mid, kBlock), (ctx->sms * 32));
           pull_mid_det_kernel<<<mg, kBlock, 0, s>>>(g->off, g->col, g->det_mid, g->ndet_mid,
                                                     psh.ptr, D, c, fmode, pq.ptr,
                                                     ctx->d_counters);
@@ -2078,7 +2078,7 @@ struct PushWork {
           LGC_TRY(dany.reserve(ctx, g->nsegs));
           LGC_TRY(dpred.reserve(ctx, g->nsegs));
           LGC_TRY(dstep.reserve(ctx, g->nsegs));
-          const int sg = (int)std::min<int64_t>(ceil_div(g->nsegs, kBlock / 32), 152 * 16);
+          const int sg = (int)std::min<int64_t>(ceil_div(g->nsegs, kBlock / 32), (ctx->sms * 16));
           det_seg_sum_kernel<<<sg, kBlock, 0, s>>>(g->col, g->segs, g->nsegs, psh.ptr, dsum.ptr,
                                                    dany.ptr);
           LGC_COUNT_LAUNCH(ctx);
@@ -2088,7 +2088,7 @@ struct PushWork {
           det_seg_step_kernel<<<sg, kBlock, 0, s>>>(g->col, g->segs, g->nsegs, psh.ptr, dpred.ptr,
                                                     dstep.ptr);
           LGC_COUNT_LAUNCH(ctx);
-          const int vg = (int)std::min<int64_t>(ceil_div(g->nbig, kBlock / 32), 152 * 16);
+          const int vg = (int)std::min<int64_t>(ceil_div(g->nbig, kBlock / 32), (ctx->sms * 16));
           det_seg_verify_kernel<<<vg, kBlock, 0, s>>>(g->off, g->col, g->segs, g->big_w,
                                                       g->big_seg0, g->nbig, psh.ptr, dpred.ptr,
                                                       dstep.ptr, dany.ptr, D, c, fmode, pq.ptr,
@@ -2101,7 +2101,7 @@ struct PushWork {
         auto gather = [&](auto* shv) {
           using SH = std::remove_const_t<std::remove_pointer_t<decltype(shv)>>;
           if (g->nlight > 0) {
-            const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), 152 * 32);
+            const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), (ctx->sms * 32));
             pull_light_fx_kernel<SH><<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, shv,
                                                              prange.ptr, gb, D, c, fmode, pq.ptr,
                                                              ctx->d_counters);
@@ -2110,7 +2110,7 @@ struct PushWork {
           if (g->nitems > 0) {
             const int gw = ctx->pull_group ? ctx->pull_group : g->pull_group;
             const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / gw));
-            const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+            const int hg = (int)(hb < (ctx->sms * 16) ? hb : (ctx->sms * 16));
             const int batch = ctx->pull_batch ? ctx->pull_batch : g->pull_batch;
             HeavyKernel<SH> heavy = heavy_kernel<SH>(batch, gw);
             heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shv, prange.ptr, gb,
@@ -2129,7 +2129,7 @@ struct PushWork {
       bits_count_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr);
       LGC_COUNT_LAUNCH(ctx);
       LGC_TRY(scan_i64(ctx, pcnt.ptr, pcnt.ptr, words, false, total.ptr));
-      const int wg = std::min(grid_for(words * 32), 152 * 8);
+      const int wg = std::min(grid_for(words * 32), (ctx->sms * 8));
       bits_write_kernel<<<wg, kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg, G.v.ptr, G.s.ptr,
                                                ncap, ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
@@ -2426,9 +2426,9 @@ struct PushWork {
   }
 };
 
-int vgrid(int64_t nf) {
+int vgrid(const lgc_ctx* ctx, int64_t nf) {
   int64_t g = ceil_div(nf, kBlock);
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > (ctx->sms * 32)) g = (ctx->sms * 32);
   return (int)(g < 1 ? 1 : g);
 }
 
@@ -2532,7 +2532,7 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
       using SH = std::remove_pointer_t<decltype(shv)>;
       HeavyKernel<SH> heavy = heavy_kernel<SH>(cb, cg);
       const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / cg));
-      const int hg = (int)(hb < 152 * 16 ? hb : 152 * 16);
+      const int hg = (int)(hb < (ctx->sms * 16) ? hb : (ctx->sms * 16));
       float t[3] = {0.f, 0.f, 0.f};
       for (int r = -1; r < 3; r++) {
         if (cudaEventRecord(e0, s)) st = LGC_ECUDA;
@@ -2624,7 +2624,7 @@ int prnibble_rounds(lgc_ctx* ctx, lgc_graph* g, PushWork& W, Table& T, int64_t& 
     if ((status = W.reset_counters()) != LGC_OK) return status;
     {
       ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-      vmap_prnibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+      vmap_prnibble_kernel<<<vgrid(ctx, nf), kBlock, 0, ctx->stream>>>(
           nf, W.F.v.ptr, W.F.s.ptr, T, g->off, alpha, cs, cn, eps, prm->rule, det ? 1 : 0,
           (!det && !bulk && !pull) ? 1 : 0, W.share.ptr, W.cnt.ptr, W.foff.ptr, W.G.v.ptr,
           W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
@@ -2849,7 +2849,7 @@ int run_nibble(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_nibble_params* p
       if ((status = W.reset_counters()) != LGC_OK) break;
       {
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-        vmap_nibble_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+        vmap_nibble_kernel<<<vgrid(ctx, nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, Pc, Pn, g->off, eps, fmode, det ? 1 : 0,
             (!det && !bulk && !pull) ? 1 : 0, W.share.ptr,
             W.cnt.ptr, W.foff.ptr, W.G.v.ptr, W.G.s.ptr, (int32_t)W.G.v.cap, ctx->d_counters);
@@ -2905,10 +2905,13 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
     return LGC_EINVAL;
   const bool det = prm->mode == LGC_MODE_DET;
   // psi_N = 1, psi_k = 1 + (t/(k+1)) psi_{k+1}; c_j = e^t eps / (2 N psi_j)
+  // (the parallel figure's sign of the exponent; LGC_OPT_HK_THRESHOLD_SIGN
+  // -1 takes the sequential description's e^-t instead, for comparison)
   std::vector<double> psi(N + 1), c(N + 1);
   psi[N] = 1.0;
   for (int k = N - 1; k >= 0; k--) psi[k] = 1.0 + (t / (double)(k + 1)) * psi[k + 1];
-  for (int j = 0; j <= N; j++) c[j] = (exp(t) * eps) / (2.0 * (double)N * psi[j]);
+  const double et = ctx->hk_threshold_sign < 0 ? exp(-t) : exp(t);
+  for (int j = 0; j <= N; j++) c[j] = (et * eps) / (2.0 * (double)N * psi[j]);
   ctx->trace_ids.clear();
   ctx->trace_sizes.clear();
 
@@ -2944,7 +2947,7 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       if ((status = W.reset_counters()) != LGC_OK) break;
       {
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-        vmap_hkpr_kernel<<<vgrid(nf), kBlock, 0, ctx->stream>>>(
+        vmap_hkpr_kernel<<<vgrid(ctx, nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, Rc, P, g->off, t, j, last ? 1 : 0, W.share.ptr, W.cnt.ptr,
             W.foff.ptr, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);

@@ -112,8 +112,8 @@ int bits_for(int64_t max_value) {
   return b < 1 ? 1 : b;
 }
 
-int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
-             int64_t* total) {
+int scan_i64_with(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+                  int64_t* total, int64_t* partial_scratch) {
   cudaStream_t st = ctx->stream;
   if (n <= 0) {
     if (total) {
@@ -129,8 +129,9 @@ int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool incl
     LGC_CUDA_TRY(cudaGetLastError());
     return LGC_OK;
   }
-  int64_t* partial = nullptr;
-  LGC_TRY(dalloc_t(ctx, &partial, nb));
+  int64_t* partial = partial_scratch;
+  if (partial_scratch && nb > kScanTile) return LGC_EINVAL;  // the caller's scratch is one level
+  if (!partial) LGC_TRY(dalloc_t(ctx, &partial, nb));
   scan_reduce_kernel<<<(unsigned)nb, kBlock, 0, st>>>(in, n, partial);
   LGC_COUNT_LAUNCH(ctx);
   LGC_CUDA_TRY(cudaGetLastError());
@@ -144,8 +145,13 @@ int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool incl
     LGC_COUNT_LAUNCH(ctx);
     if (cudaGetLastError() != cudaSuccess) s = LGC_ECUDA;
   }
-  dfree(ctx, partial);
+  if (!partial_scratch) dfree(ctx, partial);
   return s;
+}
+
+int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+             int64_t* total) {
+  return scan_i64_with(ctx, in, out, n, inclusive, total, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,7 +293,8 @@ __global__ void __launch_bounds__(kSmallSort)
 
 template <class K, class V>
 int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
-                    int bits) {
+                    int bits, int64_t* hist_scratch = nullptr,
+                    int64_t* partial_scratch = nullptr) {
   if (n <= 1) return LGC_OK;
   cudaStream_t st = ctx->stream;
   if (n <= kSmallSort) {
@@ -298,8 +305,8 @@ int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, in
     return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
   }
   const int64_t ntiles = ceil_div(n, kTile);
-  int64_t* hist = nullptr;
-  LGC_TRY(dalloc_t(ctx, &hist, (size_t)kRadix * ntiles));
+  int64_t* hist = hist_scratch;
+  if (!hist) LGC_TRY(dalloc_t(ctx, &hist, (size_t)kRadix * ntiles));
   K* a = keys;
   V* va = vals;
   K* b = keys_tmp;
@@ -309,7 +316,8 @@ int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, in
   for (int shift = 0; shift < bits; shift += 8, passes++) {
     radix_hist_kernel<K><<<(unsigned)ntiles, kBlock, 0, st>>>(a, n, shift, hist, ntiles);
     LGC_COUNT_LAUNCH(ctx);
-    status = scan_i64(ctx, hist, hist, (int64_t)kRadix * ntiles, false, nullptr);
+    status = scan_i64_with(ctx, hist, hist, (int64_t)kRadix * ntiles, false, nullptr,
+                           partial_scratch);
     if (status != LGC_OK) break;
     radix_scatter_kernel<K, V><<<(unsigned)ntiles, kBlock, 0, st>>>(
         a, va, b, vb, n, shift, hist, ntiles, vals != nullptr);
@@ -325,7 +333,7 @@ int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, in
     cudaMemcpyAsync(keys, a, sizeof(K) * n, cudaMemcpyDeviceToDevice, st);
     if (vals) cudaMemcpyAsync(vals, va, sizeof(V) * n, cudaMemcpyDeviceToDevice, st);
   }
-  dfree(ctx, hist);
+  if (!hist_scratch) dfree(ctx, hist);
   if (status == LGC_OK && cudaGetLastError() != cudaSuccess) status = LGC_ECUDA;
   return status;
 }
@@ -343,6 +351,12 @@ int radix_sort_u64_f64(lgc_ctx* ctx, uint64_t* keys, double* vals, uint64_t* key
 int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
                        int32_t* vals_tmp, int64_t n, int bits) {
   return radix_sort_impl<uint64_t, int32_t>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
+}
+int radix_sort_u64_i32_with(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                            int32_t* vals_tmp, int64_t n, int bits, int64_t* hist,
+                            int64_t* partial) {
+  return radix_sort_impl<uint64_t, int32_t>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits, hist,
+                                            partial);
 }
 int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
                        int32_t* vals_tmp, int64_t n, int bits) {

@@ -11,6 +11,11 @@ namespace lgc {
 // *total (device).  in and out may alias.
 int scan_i64(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
              int64_t* total);
+// As scan_i64 with the caller's scratch for the per-tile sums
+// (partial_scratch: ceil(n / 2048) int64, n <= 2048 * 2048), so that nothing
+// is allocated; partial_scratch == nullptr is scan_i64.
+int scan_i64_with(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+                  int64_t* total, int64_t* partial_scratch);
 
 // Stable LSD radix sort of (key, value) pairs by key bits [0, bits), 8 bits
 // per pass.  keys/vals hold the input; the sorted result ends in keys/vals
@@ -23,6 +28,12 @@ int radix_sort_u64_i32(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* ke
                        int32_t* vals_tmp, int64_t n, int bits);
 int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
                        int32_t* vals_tmp, int64_t n, int bits);
+// As radix_sort_u64_i32 with the caller's scratch, allocating nothing: hist
+// holds 256 * ceil(n / 2048) int64 and partial ceil(hist entries / 2048)
+// int64 (hist entries <= 2048 * 2048).
+int radix_sort_u64_i32_with(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_t* keys_tmp,
+                            int32_t* vals_tmp, int64_t n, int bits, int64_t* hist,
+                            int64_t* partial);
 // Keys only.
 int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, int bits);
 

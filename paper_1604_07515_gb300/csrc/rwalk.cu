@@ -136,7 +136,7 @@ int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_par
     if ((status = dalloc_t(ctx, &total, 2)) != LGC_OK) break;
     LGC_CUDA_TRY(cudaMemsetAsync(total, 0, 16, s));
     int grid = grid_for(nw);
-    if (grid > 152 * 64) grid = 152 * 64;
+    if (grid > (ctx->sms * 64)) grid = (ctx->sms * 64);
     {
       // algorithmic bytes: 4 per walk (endpoint) now, 20 per step added below
       ProfScope ps(ctx, LGC_PROF_WALK, 4.0 * nw);

@@ -479,7 +479,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
     if ((status = dalloc_t(ctx, &id, n0)) != LGC_OK) break;
     if ((status = dalloc_t(ctx, &id2, n0)) != LGC_OK) break;
     int grid = grid_for(n0);
-    if (grid > 152 * 32) grid = 152 * 32;
+    if (grid > (ctx->sms * 32)) grid = (ctx->sms * 32);
     // S1
     sweep_keys_kernel<<<grid, kBlock, 0, s>>>(idx, val, n0, g->deg, g->n, key, id,
                                                (unsigned long long*)misc, (int*)(misc + 3));
@@ -521,7 +521,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
       LGC_COUNT_LAUNCH(ctx);
       // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
       ProfScope ps(ctx, LGC_PROF_SWEEP, 0.0);
-      sweep_cross_kernel<<<152 * 16, kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1,
+      sweep_cross_kernel<<<(ctx->sms * 16), kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1,
                                                       tile0, cap, T, drank, before);
       LGC_COUNT_LAUNCH(ctx);
     }
@@ -673,7 +673,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
         st = LGC_ECUDA;
         break;
       }
-      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), 152 * 32);
+      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), (ctx->sms * 32));
       // S1: keys of the positive entries, seed-major, ids ascending per seed
       bsweep_keys_kernel<<<grid, kBlock, 0, s>>>(d_in, d_inoff, B, M, g->deg, g->n, key, id, seg,
                                                  keep, d_err);
@@ -701,7 +701,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
           (st = dalloc_t(ctx, &vol, N)) || (st = dalloc_t(ctx, &cut, N)) ||
           (st = dalloc_t(ctx, &before, N)))
         break;
-      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), 152 * 32);
+      const int grid = (int)std::min<int64_t>(ceil_div(M, kBlock), (ctx->sms * 32));
       bsweep_compact_kernel<<<grid, kBlock, 0, s>>>(keep, pos, M, key, id, seg, ko, eo);
       LGC_COUNT_LAUNCH(ctx);
       // S2: by key, then stably by seed
@@ -756,7 +756,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
                                                           d_err + 1, kErrDuplicate);
         LGC_COUNT_LAUNCH(ctx);
         ProfScope ps_(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
-        bsweep_cross_kernel<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), kBlock, 0, s>>>(
+        bsweep_cross_kernel<<<(int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16)), kBlock, 0, s>>>(
             g->off, g->col, order, sk, d_nbeg, vol, N, V, tile0, d_tabs, before);
         LGC_COUNT_LAUNCH(ctx);
       }
@@ -768,7 +768,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
     // S7, per seed
     if ((st = dalloc_t(ctx, &d_best, B)) || (st = dalloc_t(ctx, &d_bvol, B))) break;
     if (N > 0) {
-      bsweep_argmin_kernel<<<(int)std::min<int64_t>(B, 152 * 8), kBlock, 0, s>>>(
+      bsweep_argmin_kernel<<<(int)std::min<int64_t>(B, (ctx->sms * 8)), kBlock, 0, s>>>(
           cut, vol, d_nbeg, B, g->nnz, d_best, d_bvol);
       LGC_COUNT_LAUNCH(ctx);
       if (cudaGetLastError() != cudaSuccess ||

@@ -7,9 +7,12 @@
 // cudaMalloc, and a latency-critical caller cannot afford an allocation that
 // may fail with out-of-memory or synchronize the device mid-request.  This
 // entry point makes no allocation at all: every temporary buffer it needs is
-// carved out of one file-scope device array of fixed size, so the memory is
-// reserved once, when the library is loaded on a device, and held until the
-// process exits.
+// carved out of one file-scope device array of fixed size, held until the
+// process exits.  With CUDA's lazy module loading (the default) the driver
+// reserves that array on a device when this file's code is first used there
+// -- the first lgc_sweep_noalloc call on the device -- so a caller that is
+// about to hand the rest of the GPU's memory to its own allocator makes one
+// call (an empty vector will do) before doing so.
 //
 // Limits and sharing:
 //  * at most kMaxN = LGC_SWEEP_NOALLOC_MAX_N entries in the input vector
@@ -28,6 +31,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "prim.cuh"
 
 namespace lgc {
 namespace {
@@ -50,7 +54,9 @@ constexpr size_t kOffCut = kOffVol + 8 * kMaxN;
 constexpr size_t kOffBefore = kOffCut + 8 * kMaxN;
 constexpr size_t kOffSlots = kOffBefore + 4 * kMaxN;
 constexpr size_t kOffHist = kOffSlots + 16 * kSlots;
-constexpr size_t kOffMisc = kOffHist + 8 * 256 * kMaxTiles;
+constexpr size_t kOffPartial = kOffHist + 8 * 256 * kMaxTiles;
+constexpr int64_t kPartial = 256;  // per-tile sums of a scan: ceil(8192 / 2048) or ceil(kMaxN / 2048)
+constexpr size_t kOffMisc = kOffPartial + 8 * kPartial;
 constexpr size_t kScratchBytes = kOffMisc + 256;
 
 // The scratch memory: device-resident for the life of the process.  In host
@@ -72,6 +78,7 @@ struct Scratch {
   int32_t* before;
   Slot* slots;
   int64_t* hist;
+  int64_t* partial;
   Misc* misc;
 };
 
@@ -87,6 +94,7 @@ Scratch carve(unsigned char* base) {
   s.before = (int32_t*)(base + kOffBefore);
   s.slots = (Slot*)(base + kOffSlots);
   s.hist = (int64_t*)(base + kOffHist);
+  s.partial = (int64_t*)(base + kOffPartial);
   s.misc = (Misc*)(base + kOffMisc);
   return s;
 }
@@ -136,93 +144,6 @@ __global__ void na_keys_kernel(const int32_t* __restrict__ idx, const double* __
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&S.misc->npos, c);
 }
 
-// S2: one LSD pass (8 bits): tile histograms, a single-block scan of the
-// (digit, tile) counts, a stable scatter.
-__global__ void na_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
-                               int64_t* __restrict__ hist, int ntiles) {
-  __shared__ int h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kTileN;
-  for (int k = 0; k < kTileItems; k++) {
-    const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
-    if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 0xFF)], 1);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive (or inclusive) scan of up to kMaxN int64 values by one block of
-// 1024 threads, each owning a contiguous run.
-__global__ void na_scan_kernel(int64_t* __restrict__ a, int64_t n, int inclusive) {
-  __shared__ int64_t part[1024];
-  const int64_t per = (n + 1023) / 1024;
-  const int64_t b = (int64_t)threadIdx.x * per, e = min(n, b + per);
-  int64_t s = 0;
-  for (int64_t i = b; i < e; i++) s += a[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    int64_t y = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += y;
-    __syncthreads();
-  }
-  int64_t run = part[threadIdx.x] - s;
-  for (int64_t i = b; i < e; i++) {
-    const int64_t x = a[i];
-    a[i] = inclusive ? run + x : run;
-    run += x;
-  }
-}
-
-__global__ void na_scatter_kernel(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
-                                  uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
-                                  int64_t n, int shift, const int64_t* __restrict__ offs,
-                                  int ntiles) {
-  __shared__ int wcnt[kBlock / 32][256];
-  __shared__ int64_t goff[256];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-  for (int w = 0; w < kBlock / 32; w++) wcnt[w][threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kTileN + (int64_t)warp * (32 * kTileItems);
-  uint64_t key[kTileItems];
-  int32_t val[kTileItems];
-  int rank[kTileItems], digit[kTileItems];
-  const unsigned lt = (1u << lane) - 1;
-  for (int k = 0; k < kTileItems; k++) {
-    const int64_t i = base + (int64_t)k * 32 + lane;
-    const bool ok = i < n;
-    key[k] = ok ? kin[i] : 0;
-    val[k] = ok ? vin[i] : 0;
-    const int d = ok ? (int)((key[k] >> shift) & 0xFF) : 256;
-    digit[k] = d;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int before = d < 256 ? wcnt[warp][d] : 0;
-    __syncwarp();
-    rank[k] = before + __popc(peers & lt);
-    if (lane == __ffs(peers) - 1 && d < 256) wcnt[warp][d] = before + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  {
-    int run = 0;
-    for (int w = 0; w < kBlock / 32; w++) {
-      const int c = wcnt[w][threadIdx.x];
-      wcnt[w][threadIdx.x] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (int k = 0; k < kTileItems; k++)
-    if (digit[k] < 256) {
-      const int64_t pos = goff[digit[k]] + wcnt[warp][digit[k]] + rank[k];
-      kout[pos] = key[k];
-      vout[pos] = val[k];
-    }
-}
-
 // S3/S4: rank table and degrees in sweep order.
 __global__ void na_rank_kernel(const int32_t* __restrict__ order, int64_t N, Table T,
                                const int32_t* __restrict__ deg, Scratch S) {
@@ -230,6 +151,7 @@ __global__ void na_rank_kernel(const int32_t* __restrict__ order, int64_t N, Tab
        i += (int64_t)gridDim.x * blockDim.x) {
     int ins = 0;
     const int64_t s = ht_find_or_insert(T, order[i], &ins, &S.misc->err);
+    if (s >= 0 && !ins) atomicOr(&S.misc->bad, 1);  // a vertex named twice
     if (s >= 0) T.s[s].aux = (int32_t)(i + 1);
     S.deg[i] = deg[order[i]];
   }
@@ -371,21 +293,10 @@ extern "C" int lgc_sweep_noalloc(lgc_graph* g, int64_t nnz, const int32_t* d_idx
   // S1
   na_keys_kernel<<<(unsigned)((nnz + kBlock - 1) / kBlock), kBlock, 0, st>>>(
       d_idx, d_val, nnz, g->deg, g->n, S);
-  // S2: 8 passes of 8 bits; the result lands back in keyA / idA
-  const int ntiles = (int)((nnz + kTileN - 1) / kTileN);
-  uint64_t *ka = S.keyA, *kb = S.keyB;
-  int32_t *va = S.idA, *vb = S.idB;
-  for (int shift = 0; shift < 64; shift += 8) {
-    na_hist_kernel<<<ntiles, kBlock, 0, st>>>(ka, nnz, shift, S.hist, ntiles);
-    na_scan_kernel<<<1, 1024, 0, st>>>(S.hist, 256 * (int64_t)ntiles, 0);
-    na_scatter_kernel<<<ntiles, kBlock, 0, st>>>(ka, va, kb, vb, nnz, shift, S.hist, ntiles);
-    uint64_t* tk = ka;
-    ka = kb;
-    kb = tk;
-    int32_t* tv = va;
-    va = vb;
-    vb = tv;
-  }
+  // S2: stable LSD radix sort of (key, id), 8 passes of 8 bits, in the
+  // scratch array (histograms and scan partials included)
+  LGC_TRY(radix_sort_u64_i32_with(ctx, S.keyA, S.idA, S.keyB, S.idB, nnz, 64, S.hist,
+                                  S.partial));
   LGC_CUDA_TRY(cudaGetLastError());
   Misc m;
   LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, S.misc, sizeof(Misc), cudaMemcpyDeviceToHost, st));
@@ -404,25 +315,26 @@ extern "C" int lgc_sweep_noalloc(lgc_graph* g, int64_t nnz, const int32_t* d_idx
   LGC_CUDA_TRY(cudaMemsetAsync(S.slots, 0, sizeof(Slot) * kSlots, st));
   LGC_CUDA_TRY(cudaMemsetAsync(S.before, 0, sizeof(int32_t) * N, st));
   na_rank_kernel<<<(unsigned)((N + kBlock - 1) / kBlock), kBlock, 0, st>>>(S.idA, N, T, g->deg, S);
-  LGC_CUDA_TRY(cudaMemcpyAsync(S.vol, S.deg, 8 * N, cudaMemcpyDeviceToDevice, st));
-  na_scan_kernel<<<1, 1024, 0, st>>>(S.vol, N, 1);
+  LGC_TRY(scan_i64_with(ctx, S.deg, S.vol, N, true, nullptr, S.partial));
   LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, S.vol + N - 1, 8, cudaMemcpyDeviceToHost, st));
   LGC_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t V = ctx->h_scratch[0];
   // S5, S6
   if (V > 0) {
     int64_t tiles = (V + kCrossTile - 1) / kCrossTile;
-    na_cross_kernel<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), kBlock, 0, st>>>(
+    const int64_t cap = (int64_t)ctx->sms * 8;
+    na_cross_kernel<<<(unsigned)(tiles < cap ? tiles : cap), kBlock, 0, st>>>(
         g->off, g->col, S.idA, N, V, T, S);
   }
   na_delta_kernel<<<(unsigned)((N + kBlock - 1) / kBlock), kBlock, 0, st>>>(N, S);
-  na_scan_kernel<<<1, 1024, 0, st>>>(S.cut, N, 1);
+  LGC_TRY(scan_i64_with(ctx, S.cut, S.cut, N, true, nullptr, S.partial));
   // S7
   na_argmin_kernel<<<1, 1024, 0, st>>>(N, g->nnz, S, d_ids);
   LGC_CUDA_TRY(cudaGetLastError());
   LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, S.misc, sizeof(Misc), cudaMemcpyDeviceToHost, st));
   LGC_CUDA_TRY(cudaStreamSynchronize(st));
   memcpy(&m, ctx->h_scratch, sizeof(Misc));
+  if (m.bad) return LGC_EINVAL;  // a vertex named twice (as lgc_sweep)
   if (m.err) return LGC_ETABLEFULL;
   if (m.best_i >= 0) {
     out->size = m.best_i + 1;

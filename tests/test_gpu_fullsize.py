@@ -1,9 +1,22 @@
 """Full-size parity on the scale-22 R-MAT workload (4.19M vertices, 128M
-directed edges; seed = vertex 0's highest-degree neighbour), in the launch
-configuration bench.py times: Nibble (T=20, eps=1e-7), HK-PR (t=10, N=20,
-eps=1e-7), rand-HK-PR (t=10, K=10, 1e6 walks, Philox 7) and PR-Nibble
-(alpha=0.01, eps=1e-7), each followed by the sweep cut.  The oracle finishes
-each of these in seconds on one core."""
+directed edges; seed = vertex 0's highest-degree neighbour): Nibble (T=20,
+eps=1e-7), HK-PR (t=10, N=20, eps=1e-7), rand-HK-PR (t=10, K=10, 1e6 walks,
+Philox 7) and PR-Nibble (alpha=0.01, eps=1e-7), each followed by the sweep
+cut.  The oracle finishes each of these in seconds on one core.
+
+Two contexts:
+
+* the timed configuration of bench.py: PyTorch's current stream, no
+  tracing (so consecutive small rounds of PR-Nibble and Nibble run in the
+  cooperative device-round kernels, which the test checks through the
+  edgeMap launch count), the graph's launch shapes autotuned, atomic mode;
+  and, on the same context, each of the two gathered-share widths forced
+  (8 and 16 bytes per share) so that both pull gathers the autotuner can
+  pick are compared with the oracle.  Bar: 1e-12 relative L1 on p, the
+  sweep's conductance within 1e-9 (and the push counts equal);
+* a traced context in deterministic mode: p, PR-Nibble's residual r and
+  every round's frontier (PR-Nibble, Nibble, HK-PR) bit-identical, the
+  sweep cut exact.  rand-HK-PR walk endpoints are compared bit for bit."""
 import numpy as np
 import pytest
 
@@ -12,15 +25,66 @@ from paper_1604_07515_gb300 import inputs, lgc
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
+REL_L1 = 1e-12
+PHI_TOL = 1e-9
+PR = dict(alpha=0.01, eps=1e-7)
+NB = dict(T=20, eps=1e-7)
+HK = dict(t=10.0, N=20, eps=1e-7)
+RH = dict(t=10.0, K=10, n_walks=1_000_000, rng_seed=7)
+
 
 @pytest.fixture(scope="module")
-def big():
+def graph22():
     off, col = inputs.rmat(22, seed=2)
-    ctx = lgc.Context(0)
-    ctx.set_option(lgc.OPT_TRACE, 1)
+    return off, col, inputs.config1_seed(off, col)
+
+
+_refs = {}
+
+
+@pytest.fixture(scope="module")
+def refs(graph22):
+    """Oracle results, each computed once (traces included)."""
+    off, col, x = graph22
+
+    def get(name):
+        if name not in _refs:
+            if name == "prnibble":
+                _refs[name] = oracle.prnibble(off, col, x, PR["alpha"], PR["eps"], trace=True)
+            elif name == "nibble":
+                _refs[name] = oracle.nibble(off, col, x, NB["T"], NB["eps"], trace=True)
+            elif name == "hkpr":
+                _refs[name] = oracle.hkpr(off, col, x, HK["t"], HK["N"], HK["eps"], trace=True)
+            else:
+                _refs[name] = oracle.rand_hkpr(off, col, x, RH["t"], RH["K"], RH["n_walks"],
+                                               RH["rng_seed"])
+            r = _refs[name]
+            _refs[name + "_sweep"] = oracle.sweep(off, col, r.idx, r.val)
+        return _refs[name], _refs[name + "_sweep"]
+
+    return get
+
+
+@pytest.fixture(scope="module")
+def bench_ctx(graph22):
+    """The context and graph exactly as bench.py sets them up."""
+    torch = pytest.importorskip("torch")
+    off, col, x = graph22
+    ctx = lgc.Context(0, torch.cuda.current_stream())
     g = lgc.Graph(ctx, off, col)
-    x = inputs.config1_seed(off, col)
-    yield ctx, g, off, col, x
+    shape = g.autotune()
+    yield ctx, g, shape
+    g.close()
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def traced_ctx(graph22):
+    off, col, x = graph22
+    ctx = lgc.Context(0)
+    ctx.set_trace(1)
+    g = lgc.Graph(ctx, off, col)
+    yield ctx, g
     g.close()
     ctx.close()
 
@@ -32,56 +96,93 @@ def rel_l1(a_idx, a_val, b_idx, b_val, n):
     return np.abs(a - b).sum() / np.abs(b).sum()
 
 
-def check_sweep(g, off, col, p, ref, exact=True):
+def check_sweep(g, p, rs, exact=True):
     c = lgc.sweep(g, p)
-    rs = oracle.sweep(off, col, ref.idx, ref.val)
     if exact:
         assert c.size == rs.best and c.vol == rs.best_vol and c.cut == rs.best_cut
         assert np.array_equal(c.ids, rs.cluster)
         assert c.conductance == rs.conductance
     else:
-        assert abs(c.conductance - rs.conductance) <= 1e-9
+        assert abs(c.conductance - rs.conductance) <= PHI_TOL
 
 
-def test_nibble_scale22(big):
-    ctx, g, off, col, x = big
-    ref = oracle.nibble(off, col, x, 20, 1e-7, trace=True)
-    p, st = lgc.nibble(g, x, 20, 1e-7, mode="det")
+def run(g, name, mode):
+    if name == "prnibble":
+        return lgc.prnibble(g, X[0], PR["alpha"], PR["eps"], mode=mode)
+    if name == "nibble":
+        return lgc.nibble(g, X[0], NB["T"], NB["eps"], mode=mode)
+    if name == "hkpr":
+        return lgc.hkpr(g, X[0], HK["t"], HK["N"], HK["eps"], mode=mode)
+    return lgc.rand_hkpr(g, X[0], RH["t"], RH["K"], RH["n_walks"], RH["rng_seed"])
+
+
+X = [None]
+
+
+@pytest.fixture(autouse=True)
+def _seed(graph22):
+    X[0] = graph22[2]
+
+
+SHAPES = {"autotuned": None, "share8": (8, 32, 8), "share16": (8, 32, 16)}
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("name", ["prnibble", "nibble", "hkpr"])
+def test_atomic_in_bench_configuration(bench_ctx, graph22, refs, shape, name):
+    ctx, g, tuned = bench_ctx
+    off, col, x = graph22
+    n = len(off) - 1
+    want = SHAPES[shape] or tuned
+    for opt, v in zip((lgc.OPT_PULL_BATCH, lgc.OPT_PULL_GROUP, lgc.OPT_PULL_SHARE), want):
+        ctx.set_option(opt, v)
+    try:
+        ref, rs = refs(name)
+        ctx.set_option(lgc.OPT_PROFILE, 1)
+        ctx.profile_reset()
+        p, st = run(g, name, "atomic")
+        emap = ctx.profile(lgc.PROF_EDGEMAP)
+        ctx.set_option(lgc.OPT_PROFILE, 0)
+        assert st.rounds == ref.rounds and st.pushed_edges == ref.pushed_edges
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val, n) <= REL_L1
+        check_sweep(g, p, rs, exact=False)
+        if name in ("prnibble", "nibble"):
+            # device-driven rounds ran: fewer edgeMap launches than rounds
+            assert 0 < emap["launches"] < st.rounds, (emap, st.rounds)
+    finally:
+        for opt in (lgc.OPT_PULL_BATCH, lgc.OPT_PULL_GROUP, lgc.OPT_PULL_SHARE):
+            ctx.set_option(opt, 0)
+
+
+def test_rand_hkpr_in_bench_configuration(bench_ctx, refs):
+    ctx, g, _ = bench_ctx
+    ref, rs = refs("rand_hkpr")
+    p, st = run(g, "rand_hkpr", "atomic")
     assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
-    assert [f.tolist() for f in ctx.trace()] == [f.tolist() for f in ref.trace]
-    check_sweep(g, off, col, p, ref)
-    p, st = lgc.nibble(g, x, 20, 1e-7, mode="atomic")
-    assert rel_l1(p.idx, p.val, ref.idx, ref.val, len(off) - 1) <= 1e-12
+    check_sweep(g, p, rs)
 
 
-def test_hkpr_scale22(big):
-    ctx, g, off, col, x = big
-    ref = oracle.hkpr(off, col, x, 10.0, 20, 1e-7)
-    p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="atomic")
-    assert st.pushed_edges == ref.pushed_edges
-    assert rel_l1(p.idx, p.val, ref.idx, ref.val, len(off) - 1) <= 1e-12
-    check_sweep(g, off, col, p, ref, exact=False)
-    p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="det")
+@pytest.mark.parametrize("name", ["prnibble", "nibble", "hkpr"])
+def test_det_bit_exact_with_frontiers(traced_ctx, refs, name):
+    ctx, g = traced_ctx
+    ref, rs = refs(name)
+    p, st = run(g, name, "det")
     assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
-    check_sweep(g, off, col, p, ref)
+    assert st.rounds == ref.rounds and st.pushed_edges == ref.pushed_edges
+    got = ctx.trace()
+    assert len(got) == len(ref.trace)
+    for k, (f, r) in enumerate(zip(got, ref.trace)):
+        assert np.array_equal(f, r), f"frontier of round {k} differs"
+    if name == "prnibble":
+        r = ctx.residual()
+        assert np.array_equal(r.idx, ref.idx2) and np.array_equal(r.val, ref.val2)
+    check_sweep(g, p, rs)
 
 
-def test_rand_hkpr_scale22(big):
-    ctx, g, off, col, x = big
-    ref = oracle.rand_hkpr(off, col, x, 10.0, 10, 1_000_000, 7)
-    p, st = lgc.rand_hkpr(g, x, 10.0, 10, 1_000_000, 7)
-    assert np.array_equal(ctx.rand_hkpr_endpoints(1_000_000), ref.endpoints)
+def test_rand_hkpr_endpoints(traced_ctx, refs):
+    ctx, g = traced_ctx
+    ref, rs = refs("rand_hkpr")
+    p, st = run(g, "rand_hkpr", "atomic")
+    assert np.array_equal(ctx.rand_hkpr_endpoints(RH["n_walks"]), ref.endpoints)
     assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
-    check_sweep(g, off, col, p, ref)
-
-
-def test_prnibble_scale22(big):
-    ctx, g, off, col, x = big
-    ref = oracle.prnibble(off, col, x, 0.01, 1e-7, trace=True)
-    p, st = lgc.prnibble(g, x, 0.01, 1e-7, mode="det")
-    assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
-    assert [f.tolist() for f in ctx.trace()] == [f.tolist() for f in ref.trace]
-    check_sweep(g, off, col, p, ref)
-    p, st = lgc.prnibble(g, x, 0.01, 1e-7, mode="atomic")
-    assert rel_l1(p.idx, p.val, ref.idx, ref.val, len(off) - 1) <= 1e-12
-    check_sweep(g, off, col, p, ref, exact=False)
+    check_sweep(g, p, rs)

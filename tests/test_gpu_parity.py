@@ -299,6 +299,31 @@ def test_hkpr_atomic_within_tolerance(ctx, form, name, t, N, eps):
         assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
 
 
+@pytest.mark.parametrize("name,t,N,eps", [("rmat10", 5.0, 12, 1e-2), ("rmat13", 3.0, 10, 1e-3),
+                                          ("paper", 1.0, 2, 1.0)])
+def test_hkpr_threshold_sign_debug_flag(ctx, name, t, N, eps):
+    """LGC_OPT_HK_THRESHOLD_SIGN = -1 (Sec. 3.4's sequential e^{-t} in the
+    entry thresholds): the GPU matches the oracle's same reading, bit for bit
+    in deterministic mode, and the flag does change the result."""
+    off, col, g = gpu_graph(ctx, name)
+    x = seeds_for(off, col, 1)[0]
+    ctx.set_option(lgc.OPT_HK_THRESHOLD_SIGN, -1)
+    try:
+        ref = oracle.hkpr(off, col, x, t, N, eps, trace=True, threshold_sign=-1)
+        p, st = lgc.hkpr(g, x, t, N, eps, mode="det")
+        assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+        assert_trace_equal(ctx.trace(), ref.trace)
+        assert st.pushed_edges == ref.pushed_edges
+        p, st = lgc.hkpr(g, x, t, N, eps, mode="atomic")
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        ctx.set_option(lgc.OPT_HK_THRESHOLD_SIGN, 1)
+    plus = oracle.hkpr(off, col, x, t, N, eps)
+    assert plus.pushed_edges < ref.pushed_edges
+    p, st = lgc.hkpr(g, x, t, N, eps, mode="det")
+    assert np.array_equal(p.val, plus.val) and st.pushed_edges == plus.pushed_edges
+
+
 # ---------------------------------------------------------------------------
 # rand-HK-PR
 # ---------------------------------------------------------------------------

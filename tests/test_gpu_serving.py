@@ -1,13 +1,20 @@
 """Request loop (lgc_submit / lgc_poll / lgc_wait): requests that arrive while others run
-are admitted as slots and memory free up, run concurrently on worker
-streams, and each result is the same alone and in the mix (bit-identical in
-deterministic mode, within 1e-12 relative L1 in atomic mode)."""
+are admitted as slots and memory free up, run concurrently on the device,
+and each result is the same alone and in the mix (bit-identical in
+deterministic mode, within 1e-12 relative L1 in atomic mode) -- and the same
+as the oracle's: deterministic results bit for bit (p, cluster, vol, cut),
+atomic ones within 1e-12 relative L1 with the conductance within 1e-9,
+rand-HK-PR exactly."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1604_07515_gb300 import inputs, lgc
+
+REL_L1 = 1e-12
+PHI_TOL = 1e-9
 
 pytestmark = pytest.mark.gpu
 
@@ -73,24 +80,61 @@ def submit_all(ctx, g, reqs, collect="poll"):
     return [results[t] for t in tickets]
 
 
+_oracle_cache = {}
+
+
+def oracle_of(off, col, kind, kw, seed):
+    """The oracle's vector and sweep cut for one request (cached: both modes
+    of a request have the same canonical result)."""
+    key = (kind, seed, tuple(sorted((k, v) for k, v in kw.items() if k != "mode")))
+    if key not in _oracle_cache:
+        if kind == "pr":
+            r = oracle.prnibble(off, col, seed, kw["alpha"], kw["eps"])
+        elif kind == "hkpr":
+            r = oracle.hkpr(off, col, seed, kw["t"], kw["N"], kw["eps"])
+        else:
+            r = oracle.rand_hkpr(off, col, seed, kw["t"], kw["K"], kw["n_walks"], kw["rng_seed"])
+        _oracle_cache[key] = (r, oracle.sweep(off, col, r.idx, r.val))
+    return _oracle_cache[key]
+
+
+def dense_rel_l1(n, a_idx, a_val, b_idx, b_val):
+    a, b = np.zeros(n), np.zeros(n)
+    a[a_idx] = a_val
+    b[b_idx] = b_val
+    return np.abs(a - b).sum() / np.abs(b).sum()
+
+
 @pytest.mark.parametrize("mode", ["det", "atomic"])
-def test_results_same_alone_and_in_mix(setup, mode):
+def test_results_same_alone_in_mix_and_oracle(setup, mode):
+    """All requests are submitted at once, so many run side by side: the
+    HK-PR requests (t up to 10, eps 1e-6) and the PR-Nibble requests at
+    eps 1e-8 cover a large part of this graph, and their big rounds run as
+    pull rounds next to the small requests' push rounds."""
     ctx, g, off, col = setup
+    n = len(off) - 1
     reqs = requests(off, 40, mode)
+    big = inputs.seeds_deg2(off, 4, 55)
+    reqs += [("pr", dict(alpha=0.01, eps=1e-8, mode=mode), int(s)) for s in big]
     mixed = submit_all(ctx, g, reqs)
     for (kind, kw, seed), res in zip(reqs, mixed):
         assert res["status"] == 0
         p, c = alone(g, kind, kw, seed)
+        ref, rs = oracle_of(off, col, kind, kw, seed)
+        cl = res["cluster"]
         if mode == "det" or kind == "rand":
             assert np.array_equal(res["idx"], p.idx) and np.array_equal(res["val"], p.val)
-            assert res["cluster"]["size"] == c.size and res["cluster"]["cut"] == c.cut
-            assert np.array_equal(res["cluster"]["ids"], c.ids)
+            assert cl["size"] == c.size and cl["cut"] == c.cut
+            assert np.array_equal(cl["ids"], c.ids)
+            # the oracle's canonical result, bit for bit
+            assert np.array_equal(res["idx"], ref.idx) and np.array_equal(res["val"], ref.val)
+            assert (cl["size"], cl["vol"], cl["cut"]) == (rs.best, rs.best_vol, rs.best_cut)
+            assert np.array_equal(cl["ids"], rs.cluster)
+            assert cl["conductance"] == rs.conductance
         else:
-            n = len(off) - 1
-            a, b = np.zeros(n), np.zeros(n)
-            a[res["idx"]] = res["val"]
-            b[p.idx] = p.val
-            assert np.abs(a - b).sum() <= 1e-12 * np.abs(b).sum()
+            assert dense_rel_l1(n, res["idx"], res["val"], p.idx, p.val) <= REL_L1
+            assert dense_rel_l1(n, res["idx"], res["val"], ref.idx, ref.val) <= REL_L1
+            assert abs(cl["conductance"] - rs.conductance) <= PHI_TOL
         assert res["end_s"] >= res["start_s"] >= res["submit_s"]
 
 
