@@ -345,12 +345,16 @@ int64_t lgc_launch_count(const lgc_ctx *ctx);
  * walk kernel; 12 per edge of vol(S_N) plus 24 per swept vertex for the
  * sweep's crossing count). */
 enum {
-  LGC_PROF_EDGEMAP = 0,    /* atomic-mode edgeMap (push scatter) */
+  LGC_PROF_EDGEMAP = 0,    /* atomic-mode edgeMap of push rounds (push scatter, and the
+                              device-round kernels) */
   LGC_PROF_VERTEXMAP = 1,  /* vertexMap kernels */
-  LGC_PROF_DET_EDGE = 2,   /* deterministic-mode emit + sort + fold + compact */
+  LGC_PROF_DET_EDGE = 2,   /* deterministic-mode emit + sort + fold + compact, and the
+                              deterministic pull gathers */
   LGC_PROF_WALK = 3,       /* rand-HK-PR walk kernel */
   LGC_PROF_SWEEP = 4,      /* sweep crossing-count kernel */
-  LGC_PROF_COUNT = 5
+  LGC_PROF_PULL = 5,       /* atomic-mode edgeMap of pull rounds (the light and heavy
+                              gathers); same algorithmic bytes as LGC_PROF_EDGEMAP */
+  LGC_PROF_COUNT = 6
 };
 #define LGC_OPT_PROFILE 5
 typedef struct {

@@ -2055,7 +2055,7 @@ struct PushWork {
       LGC_COUNT_LAUNCH(ctx);
     }
     {
-      ProfScope ps(ctx, det ? LGC_PROF_DET_EDGE : LGC_PROF_EDGEMAP,
+      ProfScope ps(ctx, det ? LGC_PROF_DET_EDGE : LGC_PROF_PULL,
                    24.0 * (double)F.edges + 24.0 * nf);
       if (det) {
         // every gather ORs its qualifying vertices into the cleared bitmap

@@ -162,9 +162,10 @@ OPT_PULL_GROUP = 10
 OPT_PULL_SHARE = 11
 OPT_BATCH_HANDOFF = 12
 OPT_HK_THRESHOLD_SIGN = 13
-PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP = range(5)
-PROF_NAMES = {PROF_EDGEMAP: "edgemap_atomic", PROF_VERTEXMAP: "vertexmap",
-              PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross"}
+PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP, PROF_PULL = range(6)
+PROF_NAMES = {PROF_EDGEMAP: "edgemap_push", PROF_VERTEXMAP: "vertexmap",
+              PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross",
+              PROF_PULL: "edgemap_pull"}
 
 
 class KernelProfile(ctypes.Structure):

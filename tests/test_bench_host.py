@@ -140,3 +140,45 @@ def test_clock_sampler_does_not_wait_for_a_dead_nvidia_smi(tmp_path, monkeypatch
     assert time.perf_counter() - t0 < 5.0
     rec = s.stop()
     assert rec["sm_mhz"] is None and rec["samples"] == 0
+
+
+def test_cpu_all_cores_counts_completed_clusters():
+    """The all-cores oracle baseline: forked workers split the work list,
+    the parent counts what completed within the budget."""
+    from paper_1604_07515_gb300 import inputs
+    off, col = inputs.rmat(10, seed=4)
+    seeds, eps = bench.many_seed_list(inputs, off)
+    items = [("pr", int(s), dict(alpha=0.01, eps=float(e))) for s, e in zip(seeds[:24], eps[:24])]
+    bench._SHARED["t"] = (off, col, items)
+    try:
+        rec = bench.cpu_all_cores("t", 30.0)
+    finally:
+        bench._SHARED.clear()
+    assert rec["clusters"] == 24 and rec["unfinished_workers"] >= 0
+    assert rec["cores"] == (os.cpu_count() or 1) and rec["clusters_per_s"] > 0
+    assert rec["edges_per_s"] > 0 and rec["per_cluster_s_mean"] > 0
+
+
+def test_serving_mix_shape():
+    from paper_1604_07515_gb300 import inputs
+    off, col = inputs.rmat(10, seed=4)
+    mix = bench.serving_mix(inputs, off, 500)
+    kinds = [k for k, _, _ in mix]
+    assert 0.7 < kinds.count("pr") / 500 < 0.9
+    d = inputs.degrees(off)
+    assert all(d[s] >= 2 for _, s, _ in mix)
+    for k, _, prm in mix:
+        if k == "hkpr":
+            assert 3.0 <= prm["t"] <= 30.0 and prm["eps"] == 1e-7
+            assert prm["N"] == bench.hk_terms(prm["t"], 1e-7)
+        else:
+            assert 1e-8 <= prm["eps"] <= 1e-5 and prm["alpha"] == 0.01
+
+
+def test_occupancy_from_request_times():
+    res = [dict(submit_s=0.0, start_s=0.0, end_s=2.0), dict(submit_s=1.0, start_s=2.0, end_s=3.0),
+           dict(submit_s=1.5, start_s=2.5, end_s=4.0)]
+    occ = bench.occupancy(res, None)
+    # at t=0: 1 admitted, 0 queued; t=1: 1 admitted, 1 queued; t=1.5: 1 admitted, 2 queued
+    assert occ["queued_max"] == 2 and occ["admitted_max"] == 1
+    assert abs(occ["queued_mean"] - 1.0) < 1e-12
