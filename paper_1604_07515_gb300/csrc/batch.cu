@@ -174,7 +174,12 @@ __device__ inline int batch_find(const int64_t* s_epos, int cnt, int64_t e, int6
   return j;
 }
 
-// edgeMap (atomic mode) over all seeds' edges.
+// edgeMap (atomic mode) over all seeds' edges.  Each thread takes kItemsB
+// edges and runs them through the phases side by side, as the single-seed
+// push does: every item's column, then every item's first probe, then the
+// slots, then all the adds, so that a thread keeps kItemsB independent
+// memory trips in flight instead of walking one edge's chain after another.
+// Keys inserted are counted once per (warp, seed).
 __global__ void __launch_bounds__(kBlock)
     batch_emap_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
                       const double* __restrict__ share, const int64_t* __restrict__ epos,
@@ -188,6 +193,7 @@ __global__ void __launch_bounds__(kBlock)
   __shared__ double s_share[kTileB];
   __shared__ int32_t s_seed[kTileB];
   __shared__ int64_t s_i0, s_i1;
+  const int lane = threadIdx.x & 31;
   const int64_t E = min(E_host, *E_dev);
   const int64_t ntiles = (E + kTileB - 1) / kTileB;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -200,34 +206,79 @@ __global__ void __launch_bounds__(kBlock)
       s_seed[j] = fseed[i0 + j];
     }
     __syncthreads();
+    int32_t seed[kItemsB], w[kItemsB];
+    double sh[kItemsB];
 #pragma unroll
     for (int k = 0; k < kItemsB; k++) {
       const int64_t e = e0 + k * kBlock + threadIdx.x;
       int64_t q = 0;
       const int j = e < e1 ? batch_find(s_epos, cntsrc, e, &q) : -1;
-      bool pred = false;
-      int32_t seed = 0, w = 0, slot = -1;
-      int64_t dw = 0;
+      seed[k] = -1;
+      w[k] = -1;
+      sh[k] = 0.0;
       if (j >= 0) {
-        seed = s_seed[j];
-        w = col[s_off[j] + q];
-        const Table T = tabs[seed];
-        int ins = 0;
-        slot = (int32_t)ht_find_or_insert(T, w, &ins, &sc[seed].err);
-        if (ins) atomicAdd((unsigned long long*)&sc[seed].inserted, 1ull);
-        if (slot >= 0) {
-          const double sh = s_share[j];
-          const double old = atomicAdd(&T.s[slot].val, sh);
-          const double nv = old + sh;
-          const double eps = prm[seed].eps;
-          if (nv >= eps) {
-            dw = deg[w];
-            const double thr = eps * (double)dw;
-            pred = old < thr && nv >= thr;
-          }
+        seed[k] = s_seed[j];
+        w[k] = col[s_off[j] + q];
+        sh[k] = s_share[j];
+      }
+    }
+    Slot* ts[kItemsB];  // the item's table: slots and hash shift
+    int tshift[kItemsB];
+    int32_t probe[kItemsB];
+#pragma unroll
+    for (int k = 0; k < kItemsB; k++) {
+      probe[k] = 0;
+      ts[k] = nullptr;
+      tshift[k] = 32;
+      if (w[k] >= 0) {
+        ts[k] = tabs[seed[k]].s;
+        tshift[k] = tabs[seed[k]].shift;
+        probe[k] = __ldcg(&ts[k][hash_slot(w[k], tshift[k])].key);
+      }
+    }
+    int32_t slot[kItemsB];
+    int ins[kItemsB];
+#pragma unroll
+    for (int k = 0; k < kItemsB; k++) {
+      slot[k] = -1;
+      ins[k] = 0;
+      if (w[k] < 0) continue;
+      if (probe[k] == w[k] + 1) {
+        slot[k] = (int32_t)hash_slot(w[k], tshift[k]);
+      } else {
+        Table T;
+        T.s = ts[k];
+        T.shift = tshift[k];
+        T.cap = int64_t{1} << (32 - tshift[k]);
+        slot[k] = (int32_t)ht_find_or_insert(T, w[k], &ins[k], &sc[seed[k]].err);
+      }
+    }
+    double old[kItemsB];
+#pragma unroll
+    for (int k = 0; k < kItemsB; k++)
+      old[k] = slot[k] >= 0 ? atomicAdd(&ts[k][slot[k]].val, sh[k]) : 0.0;
+#pragma unroll
+    for (int k = 0; k < kItemsB; k++) {
+      bool pred = false;
+      int64_t dw = 0;
+      if (slot[k] >= 0) {
+        const double nv = old[k] + sh[k];
+        const double eps = prm[seed[k]].eps;
+        if (nv >= eps) {  // eps*d(w) >= eps for d(w) >= 1: cheap pre-test
+          dw = deg[w[k]];
+          const double thr = eps * (double)dw;
+          pred = old[k] < thr && nv >= thr;
         }
       }
-      batch_append(pred, seed, w, slot, dw, nseed, nfv, nfs, ncap, gsize, gerr, sc);
+      // inserted keys, one atomic per (warp, seed)
+      const unsigned im = __ballot_sync(0xffffffffu, ins[k] != 0);
+      if (im) {
+        const unsigned peers = __match_any_sync(0xffffffffu, seed[k]);
+        if (seed[k] >= 0 && lane == __ffs(peers) - 1 && (im & peers))
+          atomicAdd((unsigned long long*)&sc[seed[k]].inserted,
+                    (unsigned long long)__popc(im & peers));
+      }
+      batch_append(pred, seed[k], w[k], slot[k], dw, nseed, nfv, nfs, ncap, gsize, gerr, sc);
     }
     __syncthreads();
   }
@@ -345,6 +396,26 @@ __global__ void batch_compact_kernel(const int64_t* __restrict__ qflag,
     }
     atomicAdd(&sc[seed].next_size, 1);
     atomicAdd((unsigned long long*)&sc[seed].next_edges, (unsigned long long)deg[v]);
+  }
+}
+
+// Groups the next frontier by seed: entry i goes to the next free position
+// of its seed's range (cursor[b] starts at the range's first position), so
+// that the next round's edge tiles are seed-major and the tables written at
+// one time are those of a few seeds.  Order inside a seed is arbitrary,
+// which the atomic mode does not depend on.
+__global__ void batch_group_kernel(int64_t nf, const int32_t* __restrict__ gs,
+                                   const int32_t* __restrict__ gv,
+                                   const int32_t* __restrict__ gslot, int32_t* cursor,
+                                   int32_t* __restrict__ fs, int32_t* __restrict__ fv,
+                                   int32_t* __restrict__ fslot) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = gs[i];
+    const int32_t pos = atomicAdd(&cursor[b], 1);
+    fs[pos] = b;
+    fv[pos] = gv[i];
+    fslot[pos] = gslot[i];
   }
 }
 
@@ -479,46 +550,75 @@ __global__ void batch_rehash_kernel(const Regrow* __restrict__ rg,
   }
 }
 
-// Virtual slot i of the whole batch is slot i - capoff[b] of seed b's table.
-__global__ void batch_keep_kernel(const Table* __restrict__ tabs,
-                                  const int64_t* __restrict__ capoff, int64_t B, int64_t total,
-                                  int64_t* __restrict__ flag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = ub_i64(capoff, B, i) - 1;
-    const int64_t j = i - capoff[b];
+// Result extraction works on chunks of kChunk slots: chunk c belongs to the
+// table b with choff[b] <= c < choff[b + 1] (found once per chunk), so the
+// cost is one pass over the tables' slots, with no per-slot search and no
+// array as long as all the slots together.
+constexpr int kChunk = 4096;
+
+__device__ inline int chunk_table(const int64_t* __restrict__ choff, int64_t B, int64_t c,
+                                  int* s_b) {
+  if (threadIdx.x == 0) *s_b = (int)(ub_i64(choff, B, c) - 1);
+  __syncthreads();
+  const int b = *s_b;
+  __syncthreads();
+  return b;
+}
+
+// Per table, the number of kept entries (keys with p > 0).
+__global__ void batch_count_kernel(const Table* __restrict__ tabs,
+                                   const int64_t* __restrict__ choff, int64_t B,
+                                   int64_t nchunks, unsigned long long* __restrict__ kept) {
+  __shared__ int s_b;
+  __shared__ unsigned s_cnt;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int b = chunk_table(choff, B, c, &s_b);
     const Table T = tabs[b];
-    flag[i] = (T.s[j].key != 0 && T.p[j] > 0.0) ? 1 : 0;
+    const int64_t j0 = (c - choff[b]) * kChunk;
+    const int64_t j1 = min(T.cap, j0 + kChunk);
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    unsigned k = 0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+      k += (T.s[j].key != 0 && T.p[j] > 0.0) ? 1u : 0u;
+    k = __reduce_add_sync(0xffffffffu, k);
+    if ((threadIdx.x & 31) == 0 && k) atomicAdd(&s_cnt, k);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(&kept[b], (unsigned long long)s_cnt);
   }
 }
 
+// Writes every kept entry of table b at the next free position of b's
+// output range (cursor[b] starts at the range's first position) as the key
+// (b << vbits) | vertex and p; the order within a range is fixed afterwards
+// by the sort.
 __global__ void batch_gather_kernel(const Table* __restrict__ tabs,
-                                    const int64_t* __restrict__ capoff, int64_t B, int64_t total,
-                                    const int64_t* __restrict__ flag,
-                                    const int64_t* __restrict__ pos, int vbits,
+                                    const int64_t* __restrict__ choff, int64_t B,
+                                    int64_t nchunks, unsigned long long* cursor, int vbits,
                                     uint64_t* __restrict__ key, double* __restrict__ val) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (!flag[i]) continue;
-    const int64_t b = ub_i64(capoff, B, i) - 1;
-    const int64_t j = i - capoff[b];
+  __shared__ int s_b;
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int b = chunk_table(choff, B, c, &s_b);
     const Table T = tabs[b];
-    key[pos[i]] = ((uint64_t)b << vbits) | (uint64_t)(T.s[j].key - 1);
-    val[pos[i]] = T.p[j];
+    const int64_t j0 = (c - choff[b]) * kChunk;
+    const int64_t j1 = min(T.cap, j0 + kChunk);
+    // whole warps iterate together (the chunk is a multiple of the block)
+    for (int64_t jb = j0; jb < j1; jb += blockDim.x) {
+      const int64_t j = jb + threadIdx.x;
+      const bool keep = j < j1 && T.s[j].key != 0 && T.p[j] > 0.0;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (!m) continue;
+      unsigned long long base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(&cursor[b], (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (keep) {
+        const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
+        key[at] = ((uint64_t)b << vbits) | (uint64_t)(T.s[j].key - 1);
+        val[at] = T.p[j];
+      }
+    }
   }
-}
-
-// Per-seed output ranges, and (below) the vertex ids without the seed bits.
-// start[b] = the first kept position of seed b's slots, start[B] = the total
-// kept; a seed without slots (capacity 0: it finished outside the batch)
-// starts where the next one does, and one at the end at the total kept.
-__global__ void batch_bounds_kernel(const int64_t* __restrict__ capoff, int64_t B, int64_t total,
-                                    const int64_t* __restrict__ pos,
-                                    const int64_t* __restrict__ kept,
-                                    int64_t* __restrict__ start) {
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
-       b += (int64_t)gridDim.x * blockDim.x)
-    start[b] = (b == B || capoff[b] >= total) ? *kept : pos[capoff[b]];
 }
 
 __global__ void batch_ids_kernel(const uint64_t* __restrict__ key, int64_t m, int vbits,
@@ -530,56 +630,65 @@ __global__ void batch_ids_kernel(const uint64_t* __restrict__ key, int64_t m, in
 
 int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector<Table>& tabs,
                 lgc_svec** p_out) {
+  (void)n;
   cudaStream_t s = ctx->stream;
-  std::vector<int64_t> capoff(B + 1, 0);
-  for (int64_t b = 0; b < B; b++) capoff[b + 1] = capoff[b] + tabs[b].cap;
-  const int64_t total = capoff[B];
+  // chunks per table (a table with capacity 0 -- its seed finished outside
+  // the batch -- has none)
+  std::vector<int64_t> choff(B + 1, 0);
+  for (int64_t b = 0; b < B; b++) choff[b + 1] = choff[b] + ceil_div(tabs[b].cap, kChunk);
+  const int64_t nchunks = choff[B];
   const int kbits = vbits + bits_for(B);
   Table* d_tabs = nullptr;
-  int64_t *d_capoff = nullptr, *flag = nullptr, *pos = nullptr, *kept = nullptr, *start = nullptr;
+  int64_t* d_choff = nullptr;
+  unsigned long long* d_cnt = nullptr;
   uint64_t *key = nullptr, *key2 = nullptr;
   double *val = nullptr, *val2 = nullptr;
   int32_t* idx = nullptr;
-  std::vector<int64_t> hstart(B + 1);
+  std::vector<int64_t> hstart(B + 1, 0);
+  std::vector<unsigned long long> hcnt(B, 0);
   int32_t* hidx = nullptr;
   double* hval = nullptr;
   int st = LGC_OK;
   do {
-    if ((st = dalloc_t(ctx, &d_tabs, B)) || (st = dalloc_t(ctx, &d_capoff, B + 1)) ||
-        (st = dalloc_t(ctx, &flag, total)) || (st = dalloc_t(ctx, &pos, total)) ||
-        (st = dalloc_t(ctx, &kept, 1)) || (st = dalloc_t(ctx, &start, B + 1)))
+    if ((st = dalloc_t(ctx, &d_tabs, B)) || (st = dalloc_t(ctx, &d_choff, B + 1)) ||
+        (st = dalloc_t(ctx, &d_cnt, B)))
       break;
     if (cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(d_capoff, capoff.data(), 8 * (B + 1), cudaMemcpyHostToDevice, s)) {
+        cudaMemcpyAsync(d_choff, choff.data(), 8 * (B + 1), cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(d_cnt, 0, 8 * B, s)) {
       st = LGC_ECUDA;
       break;
     }
-    // (at least one block: every seed may have finished alone, total = 0)
-    const int grid =
-        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, kBlock), (ctx->sms * 16)));
-    batch_keep_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag);
-    LGC_COUNT_LAUNCH(ctx);
-    if ((st = scan_i64(ctx, flag, pos, total, false, kept)) != LGC_OK) break;
-    batch_bounds_kernel<<<grid_for(B + 1), kBlock, 0, s>>>(d_capoff, B, total, pos, kept,
-                                                            start);
-    LGC_COUNT_LAUNCH(ctx);
-    if (cudaMemcpyAsync(hstart.data(), start, 8 * (B + 1), cudaMemcpyDeviceToHost, s) ||
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nchunks, (ctx->sms * 16)));
+    if (nchunks > 0) {
+      batch_count_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_choff, B, nchunks, d_cnt);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+    if (cudaMemcpyAsync(hcnt.data(), d_cnt, 8 * B, cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s)) {
       st = LGC_ECUDA;
       break;
     }
-    const int64_t m = hstart[B];
-    for (int64_t b = 0; b < B; b++)
-      if (hstart[b] < 0 || hstart[b] > hstart[b + 1] || hstart[b + 1] > m || m > total)
-        st = LGC_ECUDA;  // inconsistent bounds: never size anything from them
+    for (int64_t b = 0; b < B; b++) {
+      if ((int64_t)hcnt[b] > tabs[b].cap) st = LGC_ECUDA;  // never size anything from it
+      hstart[b + 1] = hstart[b] + (int64_t)hcnt[b];
+    }
     if (st != LGC_OK) break;
+    const int64_t m = hstart[B];
     if ((st = dalloc_t(ctx, &key, m)) || (st = dalloc_t(ctx, &key2, m)) ||
         (st = dalloc_t(ctx, &val, m)) || (st = dalloc_t(ctx, &val2, m)) ||
         (st = dalloc_t(ctx, &idx, m)))
       break;
-    batch_gather_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_capoff, B, total, flag, pos, vbits, key,
-                                                 val);
-    LGC_COUNT_LAUNCH(ctx);
+    if (nchunks > 0) {
+      // the counters become the cursors: each starts at its range
+      if (cudaMemcpyAsync(d_cnt, hstart.data(), 8 * B, cudaMemcpyHostToDevice, s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      batch_gather_kernel<<<grid, kBlock, 0, s>>>(d_tabs, d_choff, B, nchunks, d_cnt, vbits,
+                                                   key, val);
+      LGC_COUNT_LAUNCH(ctx);
+    }
     if ((st = radix_sort_u64_f64(ctx, key, val, key2, val2, m, kbits)) != LGC_OK) break;
     batch_ids_kernel<<<grid_for(m), kBlock, 0, s>>>(key, m, vbits, idx);
     LGC_COUNT_LAUNCH(ctx);
@@ -630,8 +739,8 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
       p_out[b] = &box->pub;
     }
   } while (0);
-  for (void* q : {(void*)d_tabs, (void*)d_capoff, (void*)flag, (void*)pos, (void*)kept,
-                  (void*)start, (void*)key, (void*)key2, (void*)val, (void*)val2, (void*)idx})
+  for (void* q : {(void*)d_tabs, (void*)d_choff, (void*)d_cnt, (void*)key, (void*)key2,
+                  (void*)val, (void*)val2, (void*)idx})
     dfree(ctx, q);
   host_free(hidx);
   host_free(hval);
@@ -685,7 +794,8 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   DBuf<double> share, rv, rv2;
   DBuf<int64_t> cnt, epos, foff, total, flag, segid, segstart, qflag, qpos;
   DBuf<uint64_t> rk, rk2;
-  DBuf<int32_t> segseed, segv, segslot;
+  DBuf<int32_t> segseed, segv, segslot, d_cursor;
+  std::vector<int32_t> cursor_h(B);
   int status = LGC_OK;
   int64_t nf = B;
 
@@ -942,11 +1052,32 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
         next += nfs[b];
       }
       if (status != LGC_OK) break;
-      // the deterministic next frontier is in (seed, vertex) order; the
-      // atomic one is grouped by nothing, which the round does not need
-      std::swap(Fs, Gs);
-      std::swap(Fv, Gv);
-      std::swap(Fslot, Gslot);
+      if (!det && next > 0) {
+        // the atomic next frontier arrives in no order: group it by seed
+        int64_t at = 0;
+        for (int64_t b = 0; b < B; b++) {
+          cursor_h[b] = (int32_t)at;
+          at += nfs[b];
+        }
+        if (at != next || fail(Fs.reserve(ctx, next)) || fail(Fv.reserve(ctx, next)) ||
+            fail(Fslot.reserve(ctx, next)) || fail(d_cursor.reserve(ctx, B))) {
+          if (status == LGC_OK) fail(LGC_ECUDA);  // counters disagree with the sizes
+          break;
+        }
+        if (cudaMemcpyAsync(d_cursor.ptr, cursor_h.data(), 4 * B, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+          fail(LGC_ECUDA);
+          break;
+        }
+        batch_group_kernel<<<std::min(grid_for(next), (ctx->sms * 32)), kBlock, 0, s>>>(
+            next, Gs.ptr, Gv.ptr, Gslot.ptr, d_cursor.ptr, Fs.ptr, Fv.ptr, Fslot.ptr);
+        LGC_COUNT_LAUNCH(ctx);
+      } else {
+        // the deterministic next frontier is in (seed, vertex) order already
+        std::swap(Fs, Gs);
+        std::swap(Fv, Gv);
+        std::swap(Fslot, Gslot);
+      }
       nf = next;
     }
     if (status != LGC_OK) break;
@@ -990,7 +1121,8 @@ int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* see
   dfree(ctx, d_grown);
   dfree(ctx, d_alive);
   dfree(ctx, gsize);
-  for (auto* d : {&Fs, &Fv, &Fslot, &Gs, &Gv, &Gslot, &segseed, &segv, &segslot}) d->release(ctx);
+  for (auto* d : {&Fs, &Fv, &Fslot, &Gs, &Gv, &Gslot, &segseed, &segv, &segslot, &d_cursor})
+    d->release(ctx);
   for (auto* d : {&share, &rv, &rv2}) d->release(ctx);
   for (auto* d : {&cnt, &epos, &foff, &total, &flag, &segid, &segstart, &qflag, &qpos})
     d->release(ctx);
