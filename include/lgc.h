@@ -183,6 +183,11 @@ enum {
                                    reaches this many edges leaves the batch and finishes
                                    alone (pull rounds, dense sets), with the same result;
                                    0 (default) max(2^20, 2m/64), -1 never */
+  LGC_OPT_SERVE_LANE = 14,      /* request loop: PR-Nibble requests resident at once in its
+                                   batched lane (their rounds run together, requests join
+                                   as they are admitted); 0 runs them on the worker
+                                   contexts like the other requests.  Default 1024; set
+                                   before the first lgc_submit (LGC_EBUSY after) */
   LGC_OPT_HK_THRESHOLD_SIGN = 13 /* debug: the sign of the exponent in lgc_hkpr's entry
                                    thresholds.  +1 (default): e^t eps d(v) / (2 N psi_j),
                                    as in the parallel HK-PR figure (Sec. 3.4); -1: e^-t,
@@ -383,10 +388,20 @@ typedef struct {
   lgc_stats stats;
   double submit_s, start_s, end_s; /* host monotonic clock, seconds */
 } lgc_result;
-/* Queues one request against graph g (which must outlive it).  Admission is
- * by the hash-table memory the request may need (bounded by
- * LGC_OPT_SERVE_MEM_BUDGET) and by LGC_OPT_SERVE_MAX_BATCH; requests that do
- * not fit wait in the queue.  Returns LGC_EBUSY if the queue is full. */
+/* Queues one request against graph g (which must outlive it).  The loop
+ * batches continuously: PR-Nibble requests (unless LGC_OPT_SERVE_LANE is 0)
+ * join one batched lane whose admitted seeds all advance one synchronous
+ * round per pass (lgc_prnibble_batch's engine; a request admitted while
+ * others run starts at the next round, a finished one leaves with its vector
+ * and sweep cut), admitted while the lane's live tables plus the workers'
+ * reservations stay within LGC_OPT_SERVE_MEM_BUDGET and at most
+ * LGC_OPT_SERVE_LANE seeds are resident.  The other requests run on up to
+ * LGC_OPT_SERVE_MAX_BATCH worker contexts side by side with the lane, each
+ * admitted when the memory it may need fits the budget; the first queued
+ * request that fits goes next, and a request passed over 16 times is
+ * admitted before anything behind it.  Each result equals that of the same
+ * call made alone (bit for bit in LGC_MODE_DET).  Returns LGC_EBUSY if the
+ * queue is full. */
 int lgc_submit(lgc_ctx *ctx, lgc_graph *g, const lgc_request *req, uint64_t *ticket);
 /* LGC_PENDING while the request runs; LGC_OK and *out when done (the ticket
  * is then released); LGC_ENOTFOUND for an unknown ticket. */

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "prim.cuh"
 
@@ -29,19 +30,6 @@ namespace {
 
 constexpr int kItemsB = 4;
 constexpr int kTileB = kBlock * kItemsB;
-
-struct SeedParam {
-  double alpha, eps, cs, cn;
-  int rule;
-  int pad;
-};
-
-struct SeedCount {
-  int32_t next_size;
-  int32_t err;
-  int64_t next_edges;
-  int64_t inserted;
-};
 
 // Appends (seed, v, slot) to the next frontier: warp-aggregated position,
 // per-seed counters by atomics.  Every lane of the calling group must call it.
@@ -70,18 +58,22 @@ __device__ inline void batch_append(bool pred, int32_t seed, int32_t v, int32_t 
   }
 }
 
-__global__ void batch_init_kernel(int64_t B, const int32_t* __restrict__ seeds,
-                                  const Table* __restrict__ tabs, int32_t* fseed, int32_t* fv,
-                                  int32_t* fs, SeedCount* sc) {
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
-       b += (int64_t)gridDim.x * blockDim.x) {
+// Seeds k of this admission: table slots[k] gets r = {seed: 1}, and the
+// frontier entry at + k is (slots[k], seed, its table slot).
+__global__ void batch_init_kernel(int64_t k, const int32_t* __restrict__ seeds,
+                                  const int32_t* __restrict__ slots,
+                                  const Table* __restrict__ tabs, int64_t at, int32_t* fseed,
+                                  int32_t* fv, int32_t* fs, int* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = slots[i];
     const Table T = tabs[b];
     int ins = 0;
-    const int64_t s = ht_find_or_insert(T, seeds[b], &ins, &sc[b].err);
+    const int64_t s = ht_find_or_insert(T, seeds[i], &ins, err);
     if (s >= 0) T.s[s].val = 1.0;
-    fseed[b] = (int32_t)b;
-    fv[b] = seeds[b];
-    fs[b] = (int32_t)s;
+    fseed[at + i] = b;
+    fv[at + i] = seeds[i];
+    fs[at + i] = (int32_t)s;
   }
 }
 
@@ -470,23 +462,6 @@ __global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ 
 // rehash launch over all their old slots; the results of all seeds are
 // extracted, sorted and copied out together.
 // ---------------------------------------------------------------------------
-struct Slabs {
-  std::vector<void*> ptr;
-  std::vector<int64_t> refs;
-  void release(lgc_ctx* ctx, int id) {
-    if (id >= 0 && --refs[id] == 0) {
-      dfree(ctx, ptr[id]);
-      ptr[id] = nullptr;
-    }
-  }
-  void release_all(lgc_ctx* ctx) {
-    for (size_t i = 0; i < ptr.size(); i++)
-      if (ptr[i]) dfree(ctx, ptr[i]);
-    ptr.clear();
-    refs.clear();
-  }
-};
-
 int64_t table_bytes(int64_t cap) { return ceil_div(cap * (int64_t)(sizeof(Slot) + 8), 256) * 256; }
 
 int64_t pow2_cap(int64_t min_cap) { return pow2_at_least(min_cap < 64 ? 64 : min_cap); }
@@ -524,10 +499,6 @@ int carve_tables(lgc_ctx* ctx, Slabs* S, const std::vector<int64_t>& which,
   }
   return LGC_OK;
 }
-
-struct Regrow {
-  Table from, to;
-};
 
 // Re-inserts every key of the old tables rg[k].from into rg[k].to; old slot
 // i of table k is virtual slot beg[k] + i.
@@ -747,388 +718,488 @@ int extract_all(lgc_ctx* ctx, int64_t B, int64_t n, int vbits, const std::vector
   return st;
 }
 
-int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,
-                       const lgc_prnibble_params* prm_h, lgc_svec** p_out, lgc_stats* st_out) {
-  if (!g || B < 1 || B > (1 << 24) || !seeds_h || !prm_h || !p_out) return LGC_EINVAL;
-  const int mode = prm_h[0].mode;
-  for (int64_t b = 0; b < B; b++) {
-    const lgc_prnibble_params& P = prm_h[b];
-    if (!(P.alpha > 0.0 && P.alpha < 1.0) || !(P.eps > 0.0) || (P.rule != 0 && P.rule != 1) ||
-        P.mode != mode || (mode != 0 && mode != 1))
+// ---------------------------------------------------------------------------
+// The batch engine: seeds occupy slots; seeds can be added between rounds
+// (they start with their first round at the next one), and a slot whose
+// seed has finished is extracted and reused.  lgc_prnibble_batch adds all
+// its seeds at once and runs rounds until none has a frontier; the request
+// loop adds PR-Nibble requests as they are admitted (continuous batching).
+// A seed's rounds are the same whatever else shares them.
+// ---------------------------------------------------------------------------
+int BatchEngine::init(lgc_ctx* c, lgc_graph* gr, int m) {
+  ctx = c;
+  g = gr;
+  mode = m;
+  det = m == LGC_MODE_DET;
+  n = g->n;
+  vbits = bits_for(n);
+  handoff_edges = ctx->batch_handoff > 0    ? ctx->batch_handoff
+                  : ctx->batch_handoff == 0 ? std::max<int64_t>(int64_t{1} << 20, g->nnz / 64)
+                                            : INT64_MAX;
+  LGC_TRY(dalloc_t(ctx, &gsize, 4));  // frontier size, overflow, rehash error, init error
+  LGC_CUDA_TRY(cudaMemsetAsync(gsize, 0, 16, ctx->stream));
+  return LGC_OK;
+}
+
+int BatchEngine::reserve_slots(int64_t want) {
+  if (want <= cap) return LGC_OK;
+  int64_t nc = std::max<int64_t>(cap ? cap : 64, 64);
+  while (nc < want) nc *= 2;
+  if (nc > (int64_t{1} << 24)) return LGC_EINVAL;
+  auto grow = [&](auto& v, auto fill) { v.resize(nc, fill); };
+  grow(seed_of, 0);
+  grow(dseed, 0);
+  grow(count, 0);
+  grow(nfs, 0);
+  grow(edges, 0);
+  grow(rounds, 0);
+  grow(pushes, 0);
+  grow(pushed, 0);
+  grow(max_rounds, 0);
+  grow(sp, SeedParam{});
+  grow(prm, lgc_prnibble_params{});
+  grow(tabs, Table{});
+  grow(slab_of, -1);
+  grow(grown, 0);
+  grow(alive, 0);
+  grow(state, kFree);
+  grow(alone, 0);
+  grow(p_alone, (lgc_svec*)nullptr);
+  grow(st_alone, lgc_stats{});
+  grow(sc_h, SeedCount{});
+  grow(cursor_h, 0);
+  grow(fin_status, 0);
+  for (int64_t b = nc - 1; b >= cap; b--) free_slots.push_back(b);
+  cap = nc;
+  if (det && vbits + bits_for(cap) > 64) return LGC_EINVAL;
+  LGC_TRY(d_tabs.reserve(ctx, cap));
+  LGC_TRY(d_prm.reserve(ctx, cap));
+  LGC_TRY(d_sc.reserve(ctx, cap));
+  LGC_TRY(d_grown.reserve(ctx, cap));
+  LGC_TRY(d_alive.reserve(ctx, cap));
+  tabs_dirty = prm_dirty = true;
+  return LGC_OK;
+}
+
+int BatchEngine::add(int64_t k, const int32_t* seeds, const lgc_prnibble_params* P,
+                     int64_t* slots_out) {
+  if (k < 1) return LGC_EINVAL;
+  for (int64_t i = 0; i < k; i++) {
+    const lgc_prnibble_params& q = P[i];
+    if (!(q.alpha > 0.0 && q.alpha < 1.0) || !(q.eps > 0.0) || (q.rule != 0 && q.rule != 1) ||
+        q.mode != mode)
       return LGC_EINVAL;
-    p_out[b] = nullptr;
+    if (seeds[i] < 0 || seeds[i] >= n || g->hdeg[seeds[i]] < 1) return LGC_EINVAL;
   }
-  const bool det = mode == LGC_MODE_DET;
+  if ((int64_t)free_slots.size() < k) LGC_TRY(reserve_slots(cap + k));
+  std::vector<int64_t> which(k), caps(k);
+  std::vector<int32_t> slot32(k);
+  for (int64_t i = 0; i < k; i++) {
+    const int64_t b = free_slots.back();
+    free_slots.pop_back();
+    which[i] = b;
+    slot32[i] = (int32_t)b;
+    if (slots_out) slots_out[i] = b;
+    const lgc_prnibble_params& q = P[i];
+    seed_of[b] = seeds[i];
+    dseed[b] = g->hdeg[seeds[i]];
+    count[b] = 1;
+    nfs[b] = 1;
+    edges[b] = dseed[b];
+    rounds[b] = pushes[b] = pushed[b] = 0;
+    max_rounds[b] = q.max_rounds > 0 ? q.max_rounds : INT64_MAX;
+    prm[b] = q;
+    sp[b].alpha = q.alpha;
+    sp[b].eps = q.eps;
+    sp[b].cs = (2.0 * q.alpha) / (1.0 + q.alpha);
+    sp[b].cn = (1.0 - q.alpha) / (1.0 + q.alpha);
+    sp[b].rule = q.rule;
+    sp[b].pad = 0;
+    alive[b] = 1;
+    alone[b] = 0;
+    state[b] = kRunning;
+    fin_status[b] = 0;
+    caps[i] = pow2_cap(2 * (1 + dseed[b]));
+  }
+  LGC_TRY(carve_tables(ctx, &slabs, which, caps, &tabs, &slab_of));
+  tabs_dirty = prm_dirty = true;
+  LGC_TRY(upload());
   cudaStream_t s = ctx->stream;
-  const int64_t n = g->n;
-  const int vbits = bits_for(n);
-  if (det && vbits + bits_for(B) > 64) return LGC_EINVAL;
+  // the new seeds' entries go after the running ones (each seed's own
+  // entries stay in ascending id, which the deterministic order needs)
+  LGC_TRY(Fs.reserve_keep(ctx, nf + k, nf));
+  LGC_TRY(Fv.reserve_keep(ctx, nf + k, nf));
+  LGC_TRY(Fslot.reserve_keep(ctx, nf + k, nf));
+  LGC_TRY(d_new.reserve(ctx, 2 * k));
+  LGC_CUDA_TRY(cudaMemcpyAsync(d_new.ptr, seeds, 4 * k, cudaMemcpyHostToDevice, s));
+  LGC_CUDA_TRY(cudaMemcpyAsync(d_new.ptr + k, slot32.data(), 4 * k, cudaMemcpyHostToDevice, s));
+  batch_init_kernel<<<grid_for(k), kBlock, 0, s>>>(k, d_new.ptr, d_new.ptr + k, d_tabs.ptr, nf,
+                                                    Fs.ptr, Fv.ptr, Fslot.ptr, gsize + 3);
+  LGC_COUNT_LAUNCH(ctx);
+  LGC_CUDA_TRY(cudaGetLastError());
+  // the host arrays above go out of scope: the copies must have been made
+  LGC_CUDA_TRY(cudaStreamSynchronize(s));
+  nf += k;
+  running += k;
+  return LGC_OK;
+}
 
-  // per-seed host state
-  std::vector<int64_t> dseed(B), count(B, 1), nfs(B, 1), edges(B), rounds(B, 0), pushes(B, 0),
-      pushed(B, 0), max_rounds(B);
-  std::vector<SeedParam> sp(B);
-  std::vector<Table> tabs(B);
-  std::vector<int> slab_of(B, -1);
-  Slabs slabs;
-  DBuf<Regrow> d_rg;
-  DBuf<int64_t> d_rgbeg;
-  std::vector<int32_t> grown(B, 0), alive(B, 1);
-  std::vector<SeedCount> sc_h(B);
-  // seeds whose frontier grew past handoff_edges finish alone, where pull
-  // rounds and dense sets serve them far better than the batch's hashed
-  // push; their results and counters come from that run
-  const int64_t handoff_edges = ctx->batch_handoff > 0    ? ctx->batch_handoff
-                                : ctx->batch_handoff == 0 ? std::max<int64_t>(int64_t{1} << 20,
-                                                                              g->nnz / 64)
-                                                          : INT64_MAX;
-  std::vector<lgc_svec*> p_alone(B, nullptr);
-  std::vector<lgc_stats> st_alone(B);
-  std::vector<char> alone(B, 0);
+int BatchEngine::upload() {
+  cudaStream_t s = ctx->stream;
+  if (tabs_dirty)
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_tabs.ptr, tabs.data(), sizeof(Table) * cap,
+                                 cudaMemcpyHostToDevice, s));
+  if (prm_dirty)
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_prm.ptr, sp.data(), sizeof(SeedParam) * cap,
+                                 cudaMemcpyHostToDevice, s));
+  tabs_dirty = prm_dirty = false;
+  return LGC_OK;
+}
 
-  int32_t *d_seeds = nullptr, *d_grown = nullptr, *d_alive = nullptr, *gsize = nullptr;
-  Table* d_tabs = nullptr;
-  SeedParam* d_prm = nullptr;
-  SeedCount* d_sc = nullptr;
-  DBuf<int32_t> Fs, Fv, Fslot, Gs, Gv, Gslot;
-  DBuf<double> share, rv, rv2;
-  DBuf<int64_t> cnt, epos, foff, total, flag, segid, segstart, qflag, qpos;
-  DBuf<uint64_t> rk, rk2;
-  DBuf<int32_t> segseed, segv, segslot, d_cursor;
-  std::vector<int32_t> cursor_h(B);
-  int status = LGC_OK;
-  int64_t nf = B;
+// Keeps the frontier entries of the seeds still alive (order kept).
+int BatchEngine::compact_alive() {
+  cudaStream_t s = ctx->stream;
+  LGC_CUDA_TRY(cudaMemcpyAsync(d_alive.ptr, alive.data(), 4 * cap, cudaMemcpyHostToDevice, s));
+  LGC_TRY(flag.reserve(ctx, nf));
+  LGC_TRY(qpos.reserve(ctx, nf));
+  LGC_TRY(Gs.reserve(ctx, nf));
+  LGC_TRY(Gv.reserve(ctx, nf));
+  LGC_TRY(Gslot.reserve(ctx, nf));
+  batch_keep_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, d_alive.ptr, flag.ptr);
+  LGC_COUNT_LAUNCH(ctx);
+  LGC_TRY(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr));
+  batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr, Fv.ptr,
+                                                           Fslot.ptr, Gs.ptr, Gv.ptr, Gslot.ptr);
+  LGC_COUNT_LAUNCH(ctx);
+  std::swap(Fs, Gs);
+  std::swap(Fv, Gv);
+  std::swap(Fslot, Gslot);
+  int64_t k = 0;
+  for (int64_t b = 0; b < cap; b++) {
+    if (!alive[b]) nfs[b] = 0;
+    k += nfs[b];
+  }
+  nf = k;
+  return LGC_OK;
+}
 
-  auto fail = [&](int st) {
-    status = st;
-    return st;
-  };
-  do {
-    if (fail(dalloc_t(ctx, &d_seeds, B)) != LGC_OK) break;
-    if (cudaMemcpyAsync(d_seeds, seeds_h, 4 * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      fail(LGC_ECUDA);
-      break;
-    }
-    // seed degrees from the graph's host copy (out-of-range seeds read 0)
-    for (int64_t b = 0; b < B; b++)
-      dseed[b] = (seeds_h[b] >= 0 && seeds_h[b] < n) ? g->hdeg[seeds_h[b]] : 0;
-    bool bad = false;
-    for (int64_t b = 0; b < B; b++) bad = bad || dseed[b] < 1;
-    if (bad) {
-      fail(LGC_EINVAL);
-      break;
-    }
-    for (int64_t b = 0; b < B; b++) {
-      const lgc_prnibble_params& P = prm_h[b];
-      sp[b].alpha = P.alpha;
-      sp[b].eps = P.eps;
-      sp[b].cs = (2.0 * P.alpha) / (1.0 + P.alpha);
-      sp[b].cn = (1.0 - P.alpha) / (1.0 + P.alpha);
-      sp[b].rule = P.rule;
-      sp[b].pad = 0;
-      edges[b] = dseed[b];
-      max_rounds[b] = P.max_rounds > 0 ? P.max_rounds : INT64_MAX;
-    }
-    {
-      std::vector<int64_t> all(B), caps(B);
-      for (int64_t b = 0; b < B; b++) {
-        all[b] = b;
-        caps[b] = pow2_cap(2 * (1 + dseed[b]));
-      }
-      if (fail(carve_tables(ctx, &slabs, all, caps, &tabs, &slab_of)) != LGC_OK) break;
-    }
-    if (fail(dalloc_t(ctx, &d_tabs, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &d_prm, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &d_sc, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &d_grown, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &d_alive, B)) != LGC_OK) break;
-    if (fail(dalloc_t(ctx, &gsize, 3)) != LGC_OK) break;  // size, overflow, rehash error
-    cudaMemsetAsync(gsize, 0, 12, s);
-    cudaMemcpyAsync(d_prm, sp.data(), sizeof(SeedParam) * B, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(d_sc, 0, sizeof(SeedCount) * B, s);
-    if (fail(Fs.reserve(ctx, B)) || fail(Fv.reserve(ctx, B)) || fail(Fslot.reserve(ctx, B)) ||
-        fail(total.reserve(ctx, 1)))
-      break;
-    batch_init_kernel<<<grid_for(B), kBlock, 0, s>>>(B, d_seeds, d_tabs, Fs.ptr, Fv.ptr,
-                                                      Fslot.ptr, d_sc);
+void BatchEngine::finish(int64_t b, int status) {
+  alive[b] = 0;
+  state[b] = kDone;
+  fin_status[b] = status;
+  running--;
+  done.push_back(b);
+}
+
+int BatchEngine::round() {
+  cudaStream_t s = ctx->stream;
+  if (nf == 0) return LGC_OK;
+  bool drop = false;
+  // seeds with a big frontier continue alone from their state
+  for (int64_t b = 0; b < cap; b++) {
+    if (state[b] != kRunning || !alive[b] || nfs[b] == 0 || edges[b] < handoff_edges ||
+        tabs[b].cap < 64)
+      continue;
+    LGC_TRY(flag.reserve(ctx, nf));
+    LGC_TRY(qpos.reserve(ctx, nf));
+    LGC_TRY(Gs.reserve(ctx, nf));
+    LGC_TRY(Gv.reserve(ctx, nf));
+    LGC_TRY(Gslot.reserve(ctx, nf));
+    batch_seed_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, (int32_t)b, flag.ptr);
     LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr));
+    batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr,
+                                                             Fv.ptr, Fslot.ptr, Gs.ptr, Gv.ptr,
+                                                             Gslot.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    lgc_stats so_far{};
+    so_far.rounds = rounds[b];
+    so_far.pushes = pushes[b];
+    so_far.pushed_edges = pushed[b];
+    const int st = run_prnibble_from(ctx, g, tabs[b], Gv.ptr, Gslot.ptr, nfs[b], edges[b],
+                                     count[b], &prm[b], so_far, &p_alone[b], &st_alone[b]);
+    if (st != LGC_OK && st != LGC_EMAXROUNDS) return st;
+    alone[b] = 1;
+    finish(b, st);
+    drop = true;
+  }
+  if (drop) {
+    LGC_TRY(compact_alive());
+    if (nf == 0) return LGC_OK;
+  }
+  // grow the tables of the seeds whose round's new keys would not fit at
+  // load 1/2: one slab for all new tables, one rehash launch for all
+  std::vector<int64_t> gw, gcap;
+  int64_t next_cap = 0, E = 0;
+  for (int64_t b = 0; b < cap; b++) {
+    grown[b] = 0;
+    if (nfs[b] == 0) continue;
+    const int64_t need = std::min<int64_t>(count[b] + edges[b], n);
+    if (2 * need > tabs[b].cap) {
+      gw.push_back(b);
+      gcap.push_back(pow2_cap(2 * need));
+      grown[b] = 1;
+    }
+    next_cap += std::min<int64_t>(n, count[b] + edges[b] + nfs[b]);
+    E += edges[b];
+  }
+  if (!gw.empty()) {
+    std::vector<Regrow> rg(gw.size());
+    std::vector<int64_t> rgbeg(gw.size() + 1, 0);
+    std::vector<int> old_slab(gw.size());
+    for (size_t k = 0; k < gw.size(); k++) {
+      rg[k].from = tabs[gw[k]];
+      old_slab[k] = slab_of[gw[k]];
+      rgbeg[k + 1] = rgbeg[k] + tabs[gw[k]].cap;
+    }
+    LGC_TRY(carve_tables(ctx, &slabs, gw, gcap, &tabs, &slab_of));
+    for (size_t k = 0; k < gw.size(); k++) rg[k].to = tabs[gw[k]];
+    LGC_TRY(d_rg.reserve(ctx, gw.size()));
+    LGC_TRY(d_rgbeg.reserve(ctx, gw.size() + 1));
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_rg.ptr, rg.data(), sizeof(Regrow) * gw.size(),
+                                 cudaMemcpyHostToDevice, s));
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_rgbeg.ptr, rgbeg.data(), 8 * (gw.size() + 1),
+                                 cudaMemcpyHostToDevice, s));
+    const int64_t tot = rgbeg[gw.size()];
+    batch_rehash_kernel<<<(int)std::min<int64_t>(ceil_div(tot, kBlock), (ctx->sms * 16)), kBlock,
+                          0, s>>>(d_rg.ptr, d_rgbeg.ptr, (int64_t)gw.size(), tot, gsize + 2);
+    LGC_COUNT_LAUNCH(ctx);
+    // the old tables are released in stream order, after the rehash
+    for (size_t k = 0; k < gw.size(); k++) slabs.release(ctx, old_slab[k]);
+    tabs_dirty = true;
+    LGC_TRY(upload());
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_grown.ptr, grown.data(), 4 * cap, cudaMemcpyHostToDevice, s));
+    batch_reresolve_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, Fv.ptr, Fslot.ptr,
+                                                            d_tabs.ptr, d_grown.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+  }
+  LGC_TRY(share.reserve(ctx, nf));
+  LGC_TRY(cnt.reserve(ctx, nf));
+  LGC_TRY(epos.reserve(ctx, nf));
+  LGC_TRY(foff.reserve(ctx, nf));
+  LGC_TRY(total.reserve(ctx, 1));
+  LGC_TRY(Gs.reserve(ctx, next_cap));
+  LGC_TRY(Gv.reserve(ctx, next_cap));
+  LGC_TRY(Gslot.reserve(ctx, next_cap));
+  const int32_t ncap = (int32_t)std::min<size_t>(Gv.cap, INT32_MAX);
+  LGC_CUDA_TRY(cudaMemsetAsync(d_sc.ptr, 0, sizeof(SeedCount) * cap, s));
+  LGC_CUDA_TRY(cudaMemsetAsync(gsize, 0, 8, s));
+  {
+    ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
+    batch_vmap_kernel<<<std::min(grid_for(nf), (ctx->sms * 32)), kBlock, 0, s>>>(
+        nf, Fs.ptr, Fv.ptr, Fslot.ptr, d_tabs.ptr, d_prm.ptr, g->off, det ? 1 : 0, share.ptr,
+        cnt.ptr, foff.ptr, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+  }
+  LGC_TRY(scan_i64(ctx, cnt.ptr, epos.ptr, nf, false, total.ptr));
+  if (!det) {
+    if (E > 0) {
+      const int64_t tiles = ceil_div(E, kTileB);
+      ProfScope ps(ctx, LGC_PROF_EDGEMAP, 24.0 * (double)E + 28.0 * nf);
+      batch_emap_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
+          g->col, g->deg, share.ptr, epos.ptr, foff.ptr, Fs.ptr, nf, E, total.ptr, d_tabs.ptr,
+          d_prm.ptr, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+    }
+  } else {
+    const int64_t R = E + nf;  // one self record per frontier entry
+    LGC_TRY(rk.reserve(ctx, R));
+    LGC_TRY(rk2.reserve(ctx, R));
+    LGC_TRY(rv.reserve(ctx, R));
+    LGC_TRY(rv2.reserve(ctx, R));
+    LGC_TRY(flag.reserve(ctx, R));
+    LGC_TRY(segid.reserve(ctx, R));
+    {
+      const int64_t tiles = ceil_div(R, kTileB);
+      ProfScope ps(ctx, LGC_PROF_DET_EDGE, 24.0 * (double)E + 28.0 * nf);
+      batch_emit_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
+          g->col, Fv.ptr, Fs.ptr, share.ptr, epos.ptr, foff.ptr, nf, R, vbits, rk.ptr, rv.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_TRY(radix_sort_u64_f64(ctx, rk.ptr, rv.ptr, rk2.ptr, rv2.ptr, R, vbits + bits_for(cap)));
+      batch_heads_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, flag.ptr);
+      LGC_COUNT_LAUNCH(ctx);
+      LGC_TRY(scan_i64(ctx, flag.ptr, segid.ptr, R, false, total.ptr));
+    }
+    LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, total.ptr, 8, cudaMemcpyDeviceToHost, s));
+    LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nseg = ctx->h_scratch[0];
+    LGC_TRY(segstart.reserve(ctx, nseg));
+    LGC_TRY(qflag.reserve(ctx, nseg));
+    LGC_TRY(qpos.reserve(ctx, nseg));
+    LGC_TRY(segseed.reserve(ctx, nseg));
+    LGC_TRY(segv.reserve(ctx, nseg));
+    LGC_TRY(segslot.reserve(ctx, nseg));
+    ProfScope ps(ctx, LGC_PROF_DET_EDGE, 0.0);
+    batch_starts_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, segid.ptr, segstart.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    batch_fold_kernel<<<grid_for(nseg), kBlock, 0, s>>>(rk.ptr, rv.ptr, R, segstart.ptr, nseg,
+                                                         vbits, d_tabs.ptr, d_prm.ptr, g->deg,
+                                                         qflag.ptr, segseed.ptr, segv.ptr,
+                                                         segslot.ptr, d_sc.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+    LGC_TRY(scan_i64(ctx, qflag.ptr, qpos.ptr, nseg, false, total.ptr));
+    batch_compact_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
+        qflag.ptr, qpos.ptr, nseg, segseed.ptr, segv.ptr, segslot.ptr, g->deg, Gs.ptr, Gv.ptr,
+        Gslot.ptr, ncap, gsize + 1, d_sc.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+  }
+  LGC_CUDA_TRY(cudaGetLastError());
+  // one read-back per round for the whole batch
+  LGC_CUDA_TRY(cudaMemcpyAsync(sc_h.data(), d_sc.ptr, sizeof(SeedCount) * cap,
+                               cudaMemcpyDeviceToHost, s));
+  LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, gsize, 16, cudaMemcpyDeviceToHost, s));
+  LGC_CUDA_TRY(cudaStreamSynchronize(s));
+  const int32_t* gs = (const int32_t*)ctx->h_scratch;
+  if (gs[1] != 0 || gs[2] != 0 || gs[3] != 0) return LGC_ETABLEFULL;
+  int64_t next = 0;
+  for (int64_t b = 0; b < cap; b++) {
+    if (state[b] != kRunning) continue;
+    if (sc_h[b].err) return LGC_ETABLEFULL;
+    if (nfs[b] > 0) {
+      rounds[b]++;
+      pushes[b] += nfs[b];
+      pushed[b] += edges[b];
+    }
+    count[b] += sc_h[b].inserted;
+    nfs[b] = sc_h[b].next_size;
+    edges[b] = sc_h[b].next_edges;
+    next += nfs[b];
+  }
+  if (!det && next > 0) {
+    // the atomic next frontier arrives in no order: group it by seed
+    int64_t at = 0;
+    for (int64_t b = 0; b < cap; b++) {
+      cursor_h[b] = (int32_t)at;
+      at += state[b] == kRunning ? nfs[b] : 0;
+    }
+    if (at != next) return LGC_ECUDA;  // counters disagree with the sizes
+    LGC_TRY(Fs.reserve(ctx, next));
+    LGC_TRY(Fv.reserve(ctx, next));
+    LGC_TRY(Fslot.reserve(ctx, next));
+    LGC_TRY(d_cursor.reserve(ctx, cap));
+    LGC_CUDA_TRY(cudaMemcpyAsync(d_cursor.ptr, cursor_h.data(), 4 * cap, cudaMemcpyHostToDevice,
+                                 s));
+    batch_group_kernel<<<std::min(grid_for(next), (ctx->sms * 32)), kBlock, 0, s>>>(
+        next, Gs.ptr, Gv.ptr, Gslot.ptr, d_cursor.ptr, Fs.ptr, Fv.ptr, Fslot.ptr);
+    LGC_COUNT_LAUNCH(ctx);
+  } else {
+    // the deterministic next frontier is in (seed, vertex) order already
+    std::swap(Fs, Gs);
+    std::swap(Fv, Gv);
+    std::swap(Fslot, Gslot);
+  }
+  nf = next;
+  // seeds whose frontier is empty are done; seeds at their round limit
+  // leave with what they have
+  drop = false;
+  for (int64_t b = 0; b < cap; b++) {
+    if (state[b] != kRunning) continue;
+    if (nfs[b] == 0) {
+      finish(b, LGC_OK);
+    } else if (rounds[b] >= max_rounds[b]) {
+      finish(b, LGC_EMAXROUNDS);
+      drop = true;
+    }
+  }
+  if (drop && nf > 0) LGC_TRY(compact_alive());
+  return LGC_OK;
+}
 
-    while (nf > 0) {
-      // seeds at their round limit leave the batch
-      bool drop = false;
-      for (int64_t b = 0; b < B; b++)
-        if (alive[b] && nfs[b] > 0 && rounds[b] >= max_rounds[b]) {
-          alive[b] = 0;
-          drop = true;
-        }
-      // seeds with a big frontier continue alone from their state
-      for (int64_t b = 0; b < B && status == LGC_OK; b++) {
-        if (!alive[b] || nfs[b] == 0 || edges[b] < handoff_edges || tabs[b].cap < 64) continue;
-        if (fail(flag.reserve(ctx, nf)) || fail(qpos.reserve(ctx, nf)) ||
-            fail(Gs.reserve(ctx, nf)) || fail(Gv.reserve(ctx, nf)) || fail(Gslot.reserve(ctx, nf)))
-          break;
-        batch_seed_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, (int32_t)b, flag.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        if (fail(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr)) != LGC_OK) break;
-        batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr,
-                                                                 Fv.ptr, Fslot.ptr, Gs.ptr, Gv.ptr,
-                                                                 Gslot.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        lgc_stats so_far{};
-        so_far.rounds = rounds[b];
-        so_far.pushes = pushes[b];
-        so_far.pushed_edges = pushed[b];
-        if (fail(run_prnibble_from(ctx, g, tabs[b], Gv.ptr, Gslot.ptr, nfs[b], edges[b],
-                                   count[b], &prm_h[b], so_far, &p_alone[b], &st_alone[b])) !=
-            LGC_OK)
-          break;
-        alone[b] = 1;
-        alive[b] = 0;
-        drop = true;
-      }
-      if (status != LGC_OK) break;
-      if (drop) {
-        cudaMemcpyAsync(d_alive, alive.data(), 4 * B, cudaMemcpyHostToDevice, s);
-        if (fail(flag.reserve(ctx, nf)) || fail(qpos.reserve(ctx, nf)) ||
-            fail(Gs.reserve(ctx, nf)) || fail(Gv.reserve(ctx, nf)) || fail(Gslot.reserve(ctx, nf)))
-          break;
-        batch_keep_flags_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, d_alive, flag.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        if (fail(scan_i64(ctx, flag.ptr, qpos.ptr, nf, false, total.ptr)) != LGC_OK) break;
-        batch_keep_write_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, flag.ptr, qpos.ptr, Fs.ptr,
-                                                                 Fv.ptr, Fslot.ptr, Gs.ptr, Gv.ptr,
-                                                                 Gslot.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        std::swap(Fs, Gs);
-        std::swap(Fv, Gv);
-        std::swap(Fslot, Gslot);
-        nf = 0;
-        for (int64_t b = 0; b < B; b++) {
-          if (!alive[b]) nfs[b] = 0;
-          nf += nfs[b];
-        }
-        if (nf == 0) break;
-      }
-      // grow the tables of the seeds whose round's new keys would not fit at
-      // load 1/2: one slab for all new tables, one rehash launch for all
-      std::vector<int64_t> gw, gcap;
-      int64_t next_cap = 0, E = 0;
-      for (int64_t b = 0; b < B; b++) {
-        grown[b] = 0;
-        if (nfs[b] == 0) continue;
-        const int64_t need = std::min<int64_t>(count[b] + edges[b], n);
-        if (2 * need > tabs[b].cap) {
-          gw.push_back(b);
-          gcap.push_back(pow2_cap(2 * need));
-          grown[b] = 1;
-        }
-        next_cap += std::min<int64_t>(n, count[b] + edges[b] + nfs[b]);
-        E += edges[b];
-      }
-      if (!gw.empty()) {
-        std::vector<Regrow> rg(gw.size());
-        std::vector<int64_t> rgbeg(gw.size() + 1, 0);
-        std::vector<int> old_slab(gw.size());
-        for (size_t k = 0; k < gw.size(); k++) {
-          rg[k].from = tabs[gw[k]];
-          old_slab[k] = slab_of[gw[k]];
-          rgbeg[k + 1] = rgbeg[k] + tabs[gw[k]].cap;
-        }
-        if (fail(carve_tables(ctx, &slabs, gw, gcap, &tabs, &slab_of)) != LGC_OK) break;
-        for (size_t k = 0; k < gw.size(); k++) rg[k].to = tabs[gw[k]];
-        if (fail(d_rg.reserve(ctx, gw.size())) || fail(d_rgbeg.reserve(ctx, gw.size() + 1)))
-          break;
-        cudaMemcpyAsync(d_rg.ptr, rg.data(), sizeof(Regrow) * gw.size(), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_rgbeg.ptr, rgbeg.data(), 8 * (gw.size() + 1), cudaMemcpyHostToDevice, s);
-        const int64_t tot = rgbeg[gw.size()];
-        batch_rehash_kernel<<<(int)std::min<int64_t>(ceil_div(tot, kBlock), (ctx->sms * 16)), kBlock, 0,
-                              s>>>(d_rg.ptr, d_rgbeg.ptr, (int64_t)gw.size(), tot, gsize + 2);
-        LGC_COUNT_LAUNCH(ctx);
-        for (size_t k = 0; k < gw.size(); k++) slabs.release(ctx, old_slab[k]);
-        cudaMemcpyAsync(d_tabs, tabs.data(), sizeof(Table) * B, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_grown, grown.data(), 4 * B, cudaMemcpyHostToDevice, s);
-        batch_reresolve_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, Fs.ptr, Fv.ptr, Fslot.ptr,
-                                                                d_tabs, d_grown);
-        LGC_COUNT_LAUNCH(ctx);
-      }
-      if (fail(share.reserve(ctx, nf)) || fail(cnt.reserve(ctx, nf)) ||
-          fail(epos.reserve(ctx, nf)) || fail(foff.reserve(ctx, nf)) ||
-          fail(Gs.reserve(ctx, next_cap)) || fail(Gv.reserve(ctx, next_cap)) ||
-          fail(Gslot.reserve(ctx, next_cap)))
-        break;
-      const int32_t ncap = (int32_t)std::min<size_t>(Gv.cap, INT32_MAX);
-      cudaMemsetAsync(d_sc, 0, sizeof(SeedCount) * B, s);
-      cudaMemsetAsync(gsize, 0, 8, s);
-      {
-        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
-        batch_vmap_kernel<<<std::min(grid_for(nf), (ctx->sms * 32)), kBlock, 0, s>>>(
-            nf, Fs.ptr, Fv.ptr, Fslot.ptr, d_tabs, d_prm, g->off, det ? 1 : 0, share.ptr,
-            cnt.ptr, foff.ptr, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
-        LGC_COUNT_LAUNCH(ctx);
-      }
-      if (fail(scan_i64(ctx, cnt.ptr, epos.ptr, nf, false, total.ptr)) != LGC_OK) break;
-      if (!det) {
-        if (E > 0) {
-          const int64_t tiles = ceil_div(E, kTileB);
-          ProfScope ps(ctx, LGC_PROF_EDGEMAP, 24.0 * (double)E + 28.0 * nf);
-          batch_emap_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
-              g->col, g->deg, share.ptr, epos.ptr, foff.ptr, Fs.ptr, nf, E, total.ptr, d_tabs,
-              d_prm, Gs.ptr, Gv.ptr, Gslot.ptr, ncap, gsize, gsize + 1, d_sc);
-          LGC_COUNT_LAUNCH(ctx);
-        }
-      } else {
-        const int64_t R = E + nf;  // one self record per frontier entry
-        if (fail(rk.reserve(ctx, R)) || fail(rk2.reserve(ctx, R)) || fail(rv.reserve(ctx, R)) ||
-            fail(rv2.reserve(ctx, R)) || fail(flag.reserve(ctx, R)) ||
-            fail(segid.reserve(ctx, R)))
-          break;
-        {
-          const int64_t tiles = ceil_div(R, kTileB);
-          ProfScope ps(ctx, LGC_PROF_DET_EDGE, 24.0 * (double)E + 28.0 * nf);
-          batch_emit_kernel<<<(int)std::min<int64_t>(tiles, (ctx->sms * 16)), kBlock, 0, s>>>(
-              g->col, Fv.ptr, Fs.ptr, share.ptr, epos.ptr, foff.ptr, nf, R, vbits, rk.ptr,
-              rv.ptr);
-          LGC_COUNT_LAUNCH(ctx);
-          if (fail(radix_sort_u64_f64(ctx, rk.ptr, rv.ptr, rk2.ptr, rv2.ptr, R,
-                                      vbits + bits_for(B))) != LGC_OK)
-            break;
-          batch_heads_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, flag.ptr);
-          LGC_COUNT_LAUNCH(ctx);
-          if (fail(scan_i64(ctx, flag.ptr, segid.ptr, R, false, total.ptr)) != LGC_OK) break;
-        }
-        if (cudaMemcpyAsync(ctx->h_scratch, total.ptr, 8, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-          fail(LGC_ECUDA);
-          break;
-        }
-        const int64_t nseg = ctx->h_scratch[0];
-        if (fail(segstart.reserve(ctx, nseg)) || fail(qflag.reserve(ctx, nseg)) ||
-            fail(qpos.reserve(ctx, nseg)) || fail(segseed.reserve(ctx, nseg)) ||
-            fail(segv.reserve(ctx, nseg)) || fail(segslot.reserve(ctx, nseg)))
-          break;
-        ProfScope ps(ctx, LGC_PROF_DET_EDGE, 0.0);
-        batch_starts_kernel<<<grid_for(R), kBlock, 0, s>>>(rk.ptr, R, segid.ptr, segstart.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        batch_fold_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
-            rk.ptr, rv.ptr, R, segstart.ptr, nseg, vbits, d_tabs, d_prm, g->deg, qflag.ptr,
-            segseed.ptr, segv.ptr, segslot.ptr, d_sc);
-        LGC_COUNT_LAUNCH(ctx);
-        if (fail(scan_i64(ctx, qflag.ptr, qpos.ptr, nseg, false, total.ptr)) != LGC_OK) break;
-        batch_compact_kernel<<<grid_for(nseg), kBlock, 0, s>>>(
-            qflag.ptr, qpos.ptr, nseg, segseed.ptr, segv.ptr, segslot.ptr, g->deg, Gs.ptr,
-            Gv.ptr, Gslot.ptr, ncap, gsize + 1, d_sc);
-        LGC_COUNT_LAUNCH(ctx);
-      }
-      if (cudaGetLastError() != cudaSuccess) {
-        fail(LGC_ECUDA);
-        break;
-      }
-      // one read-back per round for the whole batch
-      if (cudaMemcpyAsync(sc_h.data(), d_sc, sizeof(SeedCount) * B, cudaMemcpyDeviceToHost, s) !=
-              cudaSuccess ||
-          cudaMemcpyAsync(ctx->h_scratch, gsize, 12, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) {
-        fail(LGC_ECUDA);
-        break;
-      }
-      const int32_t* gs = (const int32_t*)ctx->h_scratch;
-      if (gs[1] != 0 || gs[2] != 0) {
-        fail(LGC_ETABLEFULL);
-        break;
-      }
-      int64_t next = 0;
-      for (int64_t b = 0; b < B; b++) {
-        if (sc_h[b].err) status = LGC_ETABLEFULL;
-        if (nfs[b] > 0) {
-          rounds[b]++;
-          pushes[b] += nfs[b];
-          pushed[b] += edges[b];
-        }
-        count[b] += sc_h[b].inserted;
-        nfs[b] = sc_h[b].next_size;
-        edges[b] = sc_h[b].next_edges;
-        next += nfs[b];
-      }
-      if (status != LGC_OK) break;
-      if (!det && next > 0) {
-        // the atomic next frontier arrives in no order: group it by seed
-        int64_t at = 0;
-        for (int64_t b = 0; b < B; b++) {
-          cursor_h[b] = (int32_t)at;
-          at += nfs[b];
-        }
-        if (at != next || fail(Fs.reserve(ctx, next)) || fail(Fv.reserve(ctx, next)) ||
-            fail(Fslot.reserve(ctx, next)) || fail(d_cursor.reserve(ctx, B))) {
-          if (status == LGC_OK) fail(LGC_ECUDA);  // counters disagree with the sizes
-          break;
-        }
-        if (cudaMemcpyAsync(d_cursor.ptr, cursor_h.data(), 4 * B, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess) {
-          fail(LGC_ECUDA);
-          break;
-        }
-        batch_group_kernel<<<std::min(grid_for(next), (ctx->sms * 32)), kBlock, 0, s>>>(
-            next, Gs.ptr, Gv.ptr, Gslot.ptr, d_cursor.ptr, Fs.ptr, Fv.ptr, Fslot.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-      } else {
-        // the deterministic next frontier is in (seed, vertex) order already
-        std::swap(Fs, Gs);
-        std::swap(Fv, Gv);
-        std::swap(Fslot, Gslot);
-      }
-      nf = next;
+int BatchEngine::extract(const std::vector<int64_t>& which, lgc_svec** outs, lgc_stats* sts) {
+  for (size_t i = 0; i < which.size(); i++) outs[i] = nullptr;
+  if (which.empty()) return LGC_OK;
+  // the chosen slots' tables in a list of their own (seeds that finished
+  // alone have theirs already)
+  std::vector<Table> tx(which.size());
+  for (size_t i = 0; i < which.size(); i++) {
+    const int64_t b = which[i];
+    if (state[b] != kDone) return LGC_EINVAL;
+    tx[i] = alone[b] ? Table{} : tabs[b];
+  }
+  std::vector<lgc_svec*> got(which.size(), nullptr);
+  LGC_TRY(extract_all(ctx, (int64_t)which.size(), n, vbits, tx, got.data()));
+  for (size_t i = 0; i < which.size(); i++) {
+    const int64_t b = which[i];
+    if (alone[b]) {
+      lgc_svec_free(got[i]);
+      got[i] = p_alone[b];
+      p_alone[b] = nullptr;
     }
-    if (status != LGC_OK) break;
-    // results of all seeds at once: keep {p > 0}, sort by (seed, vertex),
-    // one copy out, then one vector per seed (those that finished alone
-    // already have theirs)
-    std::vector<Table> tabs_x = tabs;
-    for (int64_t b = 0; b < B; b++)
-      if (alone[b]) tabs_x[b] = Table{};
-    status = extract_all(ctx, B, n, vbits, tabs_x, p_out);
-    if (status != LGC_OK) break;
-    for (int64_t b = 0; b < B; b++)
+    outs[i] = got[i];
+    if (sts) {
       if (alone[b]) {
-        lgc_svec_free(p_out[b]);
-        p_out[b] = p_alone[b];
-        p_alone[b] = nullptr;
-      }
-    if (st_out) {
-      for (int64_t b = 0; b < B; b++) {
-        if (alone[b]) {
-          st_out[b] = st_alone[b];
-          continue;
-        }
-        st_out[b] = lgc_stats{};
-        st_out[b].rounds = rounds[b];
-        st_out[b].pushes = pushes[b];
-        st_out[b].pushed_edges = pushed[b];
-        st_out[b].touched = count[b];
-        st_out[b].table_capacity = tabs[b].cap;
-        st_out[b].status_detail = rounds[b] >= max_rounds[b] ? LGC_EMAXROUNDS : 0;
+        sts[i] = st_alone[b];
+      } else {
+        sts[i] = lgc_stats{};
+        sts[i].rounds = rounds[b];
+        sts[i].pushes = pushes[b];
+        sts[i].pushed_edges = pushed[b];
+        sts[i].touched = count[b];
+        sts[i].table_capacity = tabs[b].cap;
+        sts[i].status_detail = fin_status[b] == LGC_EMAXROUNDS ? LGC_EMAXROUNDS : 0;
       }
     }
-  } while (0);
+  }
+  return LGC_OK;
+}
+
+void BatchEngine::release(int64_t b) {
+  if (b < 0 || b >= cap || state[b] == kFree) return;
+  slabs.release(ctx, slab_of[b]);
+  slab_of[b] = -1;
+  tabs[b] = Table{};
+  tabs_dirty = true;
+  lgc_svec_free(p_alone[b]);
+  p_alone[b] = nullptr;
+  if (state[b] == kRunning) running--;
+  state[b] = kFree;
+  alive[b] = 0;
+  nfs[b] = 0;
+  free_slots.push_back(b);
+}
+
+int64_t BatchEngine::table_bytes_live() const {
+  int64_t t = 0;
+  for (int64_t b = 0; b < cap; b++)
+    if (state[b] != kFree) t += table_bytes(tabs[b].cap);
+  return t;
+}
+
+void BatchEngine::fini() {
   slabs.release_all(ctx);
-  d_rg.release(ctx);
-  d_rgbeg.release(ctx);
-  dfree(ctx, d_seeds);
-  dfree(ctx, d_tabs);
-  dfree(ctx, d_prm);
-  dfree(ctx, d_sc);
-  dfree(ctx, d_grown);
-  dfree(ctx, d_alive);
-  dfree(ctx, gsize);
-  for (auto* d : {&Fs, &Fv, &Fslot, &Gs, &Gv, &Gslot, &segseed, &segv, &segslot, &d_cursor})
+  for (int64_t b = 0; b < cap; b++) lgc_svec_free(p_alone[b]);
+  p_alone.clear();
+  for (auto* d : {&Fs, &Fv, &Fslot, &Gs, &Gv, &Gslot, &segseed, &segv, &segslot, &d_cursor,
+                  &d_new, &d_grown, &d_alive})
     d->release(ctx);
   for (auto* d : {&share, &rv, &rv2}) d->release(ctx);
   for (auto* d : {&cnt, &epos, &foff, &total, &flag, &segid, &segstart, &qflag, &qpos})
     d->release(ctx);
   rk.release(ctx);
   rk2.release(ctx);
-  for (int64_t b = 0; b < B; b++) lgc_svec_free(p_alone[b]);  // left only on failure
+  d_rg.release(ctx);
+  d_rgbeg.release(ctx);
+  d_tabs.release(ctx);
+  d_prm.release(ctx);
+  d_sc.release(ctx);
+  dfree(ctx, gsize);
+  gsize = nullptr;
+}
+
+int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,
+                       const lgc_prnibble_params* prm_h, lgc_svec** p_out, lgc_stats* st_out) {
+  if (!g || B < 1 || B > (1 << 24) || !seeds_h || !prm_h || !p_out) return LGC_EINVAL;
+  const int mode = prm_h[0].mode;
+  if (mode != 0 && mode != 1) return LGC_EINVAL;
+  for (int64_t b = 0; b < B; b++) p_out[b] = nullptr;
+  BatchEngine E;
+  int status = E.init(ctx, g, mode);
+  std::vector<int64_t> slot(B);
+  if (status == LGC_OK) status = E.reserve_slots(B);
+  if (status == LGC_OK) status = E.add(B, seeds_h, prm_h, slot.data());
+  while (status == LGC_OK && E.nf > 0) status = E.round();
+  if (status == LGC_OK) status = E.extract(slot, p_out, st_out);
+  E.fini();
   if (status != LGC_OK) {
     for (int64_t b = 0; b < B; b++) {
       lgc_svec_free(p_out[b]);

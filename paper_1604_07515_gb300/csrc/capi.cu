@@ -4,8 +4,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "prim.cuh"
 
@@ -281,7 +283,11 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// request loop: continuous batching over worker streams
+// request loop: continuous batching.  PR-Nibble requests go to one lane
+// that runs all admitted PR-Nibble seeds' rounds together in a batch engine
+// (a request that arrives while others run joins at the next round; a seed
+// that finishes leaves with its result); the other requests run on worker
+// contexts, each on its own stream, side by side with the lane.
 // ---------------------------------------------------------------------------
 namespace lgc {
 
@@ -292,40 +298,79 @@ struct Serve {
     lgc_request req;
     double submit_s;
     int64_t bytes;
+    int bypassed;  // times a later request was admitted before this one
   };
   lgc_ctx* owner = nullptr;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Item> queue;
+  std::deque<Item> queue;  // worker requests
+  std::deque<Item> prq;    // PR-Nibble requests for the lane
   std::map<uint64_t, lgc_result*> done;
   std::map<uint64_t, int> known;  // ticket -> 1 while queued or running
   int64_t inflight_bytes = 0;
   int inflight = 0;
+  int64_t lane_bytes = 0;     // the lane's live table bytes after its last round
+  int64_t lane_resident = 0;  // PR-Nibble requests admitted to the lane, not finished
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
   std::vector<lgc_ctx*> wctx;
+  std::thread lane;
+  lgc_ctx* lane_ctx = nullptr;
   size_t max_queue = 1 << 20;
 };
 
-// Hash-table bytes a request may need: slots at load 1/2, 16 bytes per slot
-// plus 8 for PR-Nibble's p, bounded by the graph size.
+// A request may jump ahead of a queued one that does not fit; a queued
+// request passed over this many times is admitted next, before anything
+// behind it.
+constexpr int kMaxBypass = 16;
+
+// Device memory a worker request may need: its sparse sets in the form they
+// take (hashed while they may stay below n/8 keys at load 1/2, else dense
+// arrays with a presence bitmap), plus frontier and share arrays.
 static int64_t request_bytes(const lgc_graph* g, const lgc_request& r) {
   const int64_t n = g->n;
   auto slots = [&](int64_t keys) { return pow2_at_least(2 * std::max<int64_t>(keys, 32)); };
+  const int64_t dense_set = 8 * n + n / 8;  // values + presence bits
+  const int64_t frontier = 16 * n;          // frontier ids, slots, shares, offsets
   switch (r.algo) {
     case LGC_ALGO_PRNIBBLE: {
       double bound = 1.0 + 1.0 / (r.pr.alpha * r.pr.eps);
       int64_t keys = bound < (double)n ? (int64_t)bound : n;
-      return slots(keys) * 24 + keys * 24;
+      return std::min<int64_t>(slots(keys) * 24 + keys * 24, 2 * dense_set + 8 * n + frontier);
     }
     case LGC_ALGO_NIBBLE:
-      return 2 * slots(n) * 16 + n * 24;
+      return std::min<int64_t>(2 * slots(n) * 16 + n * 24, 2 * dense_set + frontier);
     case LGC_ALGO_HKPR:
-      return 3 * slots(n) * 16 + n * 24;
+      return std::min<int64_t>(3 * slots(n) * 16 + n * 24, 3 * dense_set + frontier);
     default:
       return r.rh.n_walks * 40;
   }
+}
+
+// Takes the first queued request that fits (bounded bypass); S->mu held.
+static bool take_fitting(Serve* S, std::deque<Serve::Item>& q, Serve::Item* out) {
+  for (auto it = q.begin(); it != q.end(); ++it) {
+    const bool fits = S->inflight == 0 ||
+                      (S->inflight < S->owner->serve_max_batch &&
+                       S->inflight_bytes + S->lane_bytes + it->bytes <= S->owner->serve_mem_budget);
+    if (fits) {
+      for (auto jt = q.begin(); jt != it; ++jt) jt->bypassed++;
+      *out = *it;
+      q.erase(it);
+      return true;
+    }
+    if (it->bypassed >= kMaxBypass) return false;  // nothing may pass it any more
+  }
+  return false;
+}
+
+static void publish(Serve* S, uint64_t ticket, lgc_result* res) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->done[ticket] = res;
+  }
+  S->cv.notify_all();
 }
 
 static void serve_worker(Serve* S, lgc_ctx* wc) {
@@ -333,18 +378,8 @@ static void serve_worker(Serve* S, lgc_ctx* wc) {
     Serve::Item it;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait(lk, [&] {
-        if (S->stop) return true;
-        if (S->queue.empty()) return false;
-        const Serve::Item& h = S->queue.front();
-        const bool fits = S->inflight == 0 ||
-                          (S->inflight < S->owner->serve_max_batch &&
-                           S->inflight_bytes + h.bytes <= S->owner->serve_mem_budget);
-        return fits;
-      });
+      S->cv.wait(lk, [&] { return S->stop || take_fitting(S, S->queue, &it); });
       if (S->stop) return;
-      it = S->queue.front();
-      S->queue.pop_front();
       S->inflight++;
       S->inflight_bytes += it.bytes;
     }
@@ -379,9 +414,187 @@ static void serve_worker(Serve* S, lgc_ctx* wc) {
       std::lock_guard<std::mutex> lk(S->mu);
       S->inflight--;
       S->inflight_bytes -= it.bytes;
-      S->done[it.ticket] = res;
     }
-    S->cv.notify_all();
+    publish(S, it.ticket, res);
+  }
+}
+
+// The PR-Nibble lane: one batch engine per (graph, mode); every pass admits
+// the queued PR-Nibble requests that fit, runs one round of every engine
+// with running seeds, and hands out the finished seeds' results (vectors
+// extracted together, sweep cuts of all of them in one batched sweep).
+struct LaneJob {
+  Serve::Item item;
+  double start_s;
+};
+
+static void lane_fail(Serve* S, const LaneJob& j, int st) {
+  lgc_result* res = new lgc_result();
+  memset(res, 0, sizeof(*res));
+  res->status = st;
+  res->submit_s = j.item.submit_s;
+  res->start_s = j.start_s;
+  res->end_s = now_seconds();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->lane_resident--;
+  }
+  publish(S, j.item.ticket, res);
+}
+
+static void serve_lane(Serve* S, lgc_ctx* lc) {
+  struct Eng {
+    BatchEngine E;
+    std::map<int64_t, LaneJob> jobs;  // slot -> request
+  };
+  // engines by (graph serial, mode); an engine without requests is dropped
+  // at the end of the pass that emptied it
+  std::map<std::pair<uint64_t, int>, Eng*> engines;
+  lc->result_on_device = false;
+  for (;;) {
+    std::vector<Serve::Item> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      bool busy = false;
+      for (auto& kv : engines) busy = busy || kv.second->E.nf > 0;
+      if (!busy) S->cv.wait(lk, [&] { return S->stop || !S->prq.empty(); });
+      if (S->stop) break;
+      // admission by live table memory: the lane's tables after its last
+      // round plus the workers' reservations stay within the budget
+      const int64_t lane_cap = S->owner->serve_lane_seeds;
+      int64_t adding = 0;  // first tables of the seeds admitted in this pass
+      while (!S->prq.empty() && S->lane_resident < lane_cap) {
+        const Serve::Item& h = S->prq.front();
+        const int64_t d = h.g->hdeg[h.req.seed];
+        const int64_t first = table_bytes(pow2_at_least(std::max<int64_t>(64, 2 * (1 + d))));
+        const bool fits = S->lane_resident == 0 ||
+                          S->inflight_bytes + S->lane_bytes + adding + first <=
+                              S->owner->serve_mem_budget;
+        if (!fits) break;
+        adding += first;
+        admit.push_back(h);
+        S->prq.pop_front();
+        S->lane_resident++;
+      }
+    }
+    // new seeds join their engine at the next round
+    const double t_admit = now_seconds();
+    std::map<std::pair<uint64_t, int>, std::vector<Serve::Item>> by_engine;
+    for (const Serve::Item& it : admit) by_engine[{it.g->serial, it.req.pr.mode}].push_back(it);
+    for (auto& kv : by_engine) {
+      Eng*& e = engines[kv.first];
+      if (!e) {
+        e = new Eng();
+        const int st = e->E.init(lc, kv.second[0].g, kv.first.second);
+        if (st != LGC_OK) {
+          for (const Serve::Item& it : kv.second) lane_fail(S, LaneJob{it, t_admit}, st);
+          e->E.fini();
+          delete e;
+          engines.erase(kv.first);
+          continue;
+        }
+      }
+      // one at a time on a refusal, so that a bad request fails alone
+      std::vector<int32_t> seeds;
+      std::vector<lgc_prnibble_params> prms;
+      for (const Serve::Item& it : kv.second) {
+        seeds.push_back(it.req.seed);
+        prms.push_back(it.req.pr);
+      }
+      std::vector<int64_t> slots(seeds.size());
+      int st = e->E.add((int64_t)seeds.size(), seeds.data(), prms.data(), slots.data());
+      if (st == LGC_OK) {
+        for (size_t i = 0; i < slots.size(); i++) e->jobs[slots[i]] = LaneJob{kv.second[i], t_admit};
+      } else {
+        for (size_t i = 0; i < seeds.size(); i++) {
+          int64_t sl = -1;
+          const int s1 = e->E.add(1, &seeds[i], &prms[i], &sl);
+          if (s1 == LGC_OK) e->jobs[sl] = LaneJob{kv.second[i], t_admit};
+          else lane_fail(S, LaneJob{kv.second[i], t_admit}, s1);
+        }
+      }
+    }
+    // one round of every engine, then the finished seeds' results
+    int64_t live = 0;
+    for (auto& kv : engines) {
+      Eng* e = kv.second;
+      lgc_graph* g = e->E.g;
+      if (e->E.nf > 0) {
+        const int st = e->E.round();
+        if (st != LGC_OK) {  // every request of this engine fails; the engine restarts
+          for (auto& jv : e->jobs) lane_fail(S, jv.second, st);
+          e->jobs.clear();
+          e->E.fini();
+          e->E = BatchEngine();
+          e->E.init(lc, g, kv.first.second);
+          continue;
+        }
+      }
+      if (!e->E.done.empty()) {
+        std::vector<int64_t> fin;
+        fin.swap(e->E.done);
+        std::vector<lgc_svec*> ps(fin.size(), nullptr);
+        std::vector<lgc_stats> sts(fin.size());
+        int st = e->E.extract(fin, ps.data(), sts.data());
+        std::vector<lgc_cluster*> cl(fin.size(), nullptr);
+        std::vector<const lgc_svec*> want;
+        std::vector<size_t> at;
+        for (size_t i = 0; st == LGC_OK && i < fin.size(); i++)
+          if (e->jobs[fin[i]].item.req.want_sweep && ps[i]) {
+            want.push_back(ps[i]);
+            at.push_back(i);
+          }
+        std::vector<lgc_cluster*> got(want.size(), nullptr);
+        if (st == LGC_OK && !want.empty())
+          st = run_sweep_batch(lc, g, (int64_t)want.size(), want.data(), got.data());
+        for (size_t k = 0; k < at.size(); k++) cl[at[k]] = got[k];
+        const double t_end = now_seconds();
+        for (size_t i = 0; i < fin.size(); i++) {
+          const LaneJob j = e->jobs[fin[i]];
+          e->jobs.erase(fin[i]);
+          e->E.release(fin[i]);
+          lgc_result* res = new lgc_result();
+          memset(res, 0, sizeof(*res));
+          res->status = st;
+          res->p = st == LGC_OK ? ps[i] : nullptr;
+          res->cluster = st == LGC_OK ? cl[i] : nullptr;
+          if (st != LGC_OK) {
+            lgc_svec_free(ps[i]);
+            lgc_cluster_free(cl[i]);
+          }
+          res->stats = sts[i];
+          res->submit_s = j.item.submit_s;
+          res->start_s = j.start_s;
+          res->end_s = t_end;
+          {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->lane_resident--;
+            S->done[j.item.ticket] = res;
+          }
+        }
+        S->cv.notify_all();
+      }
+      live += e->E.table_bytes_live();
+    }
+    for (auto it = engines.begin(); it != engines.end();) {
+      if (it->second->jobs.empty() && it->second->E.nf == 0) {
+        it->second->E.fini();
+        delete it->second;
+        it = engines.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->lane_bytes = live;
+    }
+    S->cv.notify_all();  // workers may fit now
+  }
+  for (auto& kv : engines) {
+    for (auto& jv : kv.second->jobs) lane_fail(S, jv.second, LGC_ECUDA);
+    kv.second->E.fini();
+    delete kv.second;
   }
 }
 
@@ -394,9 +607,14 @@ static void serve_shutdown(lgc_ctx* ctx) {
   }
   S->cv.notify_all();
   for (auto& t : S->workers) t.join();
+  if (S->lane.joinable()) S->lane.join();
   for (lgc_ctx* w : S->wctx) {
     ctx_fini(w);
     delete w;
+  }
+  if (S->lane_ctx) {
+    ctx_fini(S->lane_ctx);
+    delete S->lane_ctx;
   }
   for (auto& kv : S->done) lgc_result_free(kv.second);
   delete S;
@@ -506,6 +724,11 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;
       return LGC_OK;
+    case LGC_OPT_SERVE_LANE:
+      if (value < 0 || value > (1 << 20)) return LGC_EINVAL;
+      if (ctx->serve) return LGC_EBUSY;  // fixed once the loop has started
+      ctx->serve_lane_seeds = value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MAX_BATCH:
       if (value <= 0 || value > 1024) return LGC_EINVAL;
       if (ctx->serve) return LGC_EBUSY;  // fixed once the loop has started
@@ -534,6 +757,8 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
   nnz = ctx->h_scratch[0];
   if (nnz < 0) return LGC_EINVAL;
   lgc_graph* g = new (std::nothrow) lgc_graph();
+  static std::atomic<uint64_t> graphs_made{0};
+  if (g) g->serial = ++graphs_made;
   if (!g) return LGC_ENOMEM;
   g->ctx = ctx;
   g->n = n;
@@ -776,20 +1001,34 @@ int lgc_submit(lgc_ctx* ctx, lgc_graph* g, const lgc_request* req, uint64_t* tic
       delete S;
       return LGC_ECUDA;
     }
+    if (ctx->serve_lane_seeds > 0) {
+      lgc_ctx* l = new (std::nothrow) lgc_ctx();
+      if (l && ctx_init(l, ctx->device, nullptr) == LGC_OK) {
+        l->device_rounds = false;
+        l->batch_handoff = ctx->batch_handoff;
+        S->lane_ctx = l;
+      } else if (l) {
+        ctx_fini(l);
+        delete l;
+      }
+    }
     for (lgc_ctx* w : S->wctx) S->workers.emplace_back(serve_worker, S, w);
+    if (S->lane_ctx) S->lane = std::thread(serve_lane, S, S->lane_ctx);
     ctx->serve = S;
   }
   Serve* S = ctx->serve;
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->queue.size() >= S->max_queue) return LGC_EBUSY;
+    if (S->queue.size() + S->prq.size() >= S->max_queue) return LGC_EBUSY;
     Serve::Item it;
     it.ticket = S->next_ticket++;
     it.g = g;
     it.req = *req;
     it.submit_s = now_seconds();
     it.bytes = request_bytes(g, *req);
-    S->queue.push_back(it);
+    it.bypassed = 0;
+    if (req->algo == LGC_ALGO_PRNIBBLE && S->lane_ctx) S->prq.push_back(it);
+    else S->queue.push_back(it);
     S->known[it.ticket] = 1;
     *ticket = it.ticket;
   }

@@ -206,6 +206,7 @@ struct lgc_ctx {
   int hk_threshold_sign = 1;   // LGC_OPT_HK_THRESHOLD_SIGN: +1 (e^t, default) or -1 (e^-t)
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
+  int64_t serve_lane_seeds = 1024;  // LGC_OPT_SERVE_LANE
   // small pinned host block for per-round read-back
   lgc::Counters* h_counters = nullptr;
   lgc::Counters* d_counters = nullptr;
@@ -258,6 +259,7 @@ struct __align__(32) DetSeg {
 
 struct lgc_graph {
   lgc_ctx* ctx = nullptr;
+  uint64_t serial = 0;  // unique per graph of the process (a freed graph's address may recur)
   int64_t n = 0, nnz = 0;
   int64_t* off = nullptr;  // device, n + 1
   int32_t* col = nullptr;  // device, nnz
@@ -326,6 +328,24 @@ struct DBuf {
     ptr = nullptr;
     cap = 0;
     LGC_TRY(dalloc_t(ctx, &ptr, nc));
+    cap = nc;
+    return LGC_OK;
+  }
+  // As reserve, keeping the first `keep` elements when it reallocates.
+  int reserve_keep(lgc_ctx* ctx, size_t count, size_t keep) {
+    if (count <= cap) return LGC_OK;
+    size_t nc = cap ? cap : 1024;
+    while (nc < count) nc *= 2;
+    T* np = nullptr;
+    LGC_TRY(dalloc_t(ctx, &np, nc));
+    if (keep && ptr &&
+        cudaMemcpyAsync(np, ptr, sizeof(T) * keep, cudaMemcpyDeviceToDevice, ctx->stream) !=
+            cudaSuccess) {
+      dfree(ctx, np);
+      return LGC_ECUDA;
+    }
+    if (ptr) dfree(ctx, ptr);
+    ptr = np;
     cap = nc;
     return LGC_OK;
   }

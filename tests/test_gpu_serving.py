@@ -205,3 +205,28 @@ def test_wait_unknown_ticket(setup):
     with pytest.raises(lgc.LgcError) as e:
         lgc.wait(ctx, 10 ** 12)
     assert e.value.status == lgc.LGC_ENOTFOUND
+
+
+def test_lane_across_graphs_of_different_sizes():
+    """PR-Nibble requests on a second, larger graph created after the first
+    one was released: the batched lane serves each graph with its own
+    engine (a released graph's address may come back for the new one), and
+    every result is the oracle's."""
+    ctx = lgc.Context(0)
+    try:
+        for scale, gseed, k in ((11, 3, 6), (14, 11, 10)):
+            off, col = inputs.rmat(scale, seed=gseed)
+            g = lgc.Graph(ctx, off, col)
+            seeds = inputs.seeds_deg2(off, k, 40 + scale)
+            if scale == 14:  # seeds beyond the first graph's vertex range
+                big = np.flatnonzero(np.diff(off) >= 2)
+                seeds[: k // 2] = big[big >= (1 << 11)][: k // 2]
+            reqs = [("pr", dict(alpha=0.01, eps=1e-6, mode="det"), int(s)) for s in seeds]
+            res = submit_all(ctx, g, reqs, collect="wait")
+            for (kind, kw, seed), r in zip(reqs, res):
+                assert r["status"] == 0
+                ref = oracle.prnibble(off, col, seed, kw["alpha"], kw["eps"])
+                assert np.array_equal(r["idx"], ref.idx) and np.array_equal(r["val"], ref.val)
+            g.close()
+    finally:
+        ctx.close()
