@@ -541,7 +541,16 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
 PULL_TRAFFIC = {"sources": ["paper_1604_07515_gb300/csrc/diffuse.cu",
                             "paper_1604_07515_gb300/csrc/fx128.cuh",
                             "paper_1604_07515_gb300/csrc/common.cuh"],
-                "sha256": None, "per_launch": {}}
+                "sha256": "4f02b28e6ee1e88f361bd803935f44033abb63caddfb2f8669c9df35c4e1bec3",
+                # bytes per pull round (light + heavy gather), by gathered share width
+                "per_launch": {"8": 802.5e6, "16": 966.2e6},
+                # ncu --set full of one heavy gather launch (share width 8, shape (8, 16)):
+                # the units that bind it, as fractions of their peaks
+                "heavy_gather_full": {"kernel": "pull_heavy_fx_kernel<8, 16, double>",
+                                      "duration_us": 544.0, "dram_gb": 0.595,
+                                      "dram_frac": 0.161, "lts_throughput_frac": 0.514,
+                                      "l1tex_throughput_frac": 0.625, "issue_active_frac": 0.530,
+                                      "l2_hit_rate": 0.770}}
 
 
 def sources_sha(paths):
@@ -611,6 +620,54 @@ def timed_steps(lgc, torch, ctx, g, x, mode, steps, flush, stream, barrier):
     return sum(step_ms), pushed, clusters, split, ctx.launch_count() - launches0
 
 
+# One named workload, run a given number of times (for ncu captures: the
+# capture selects launches with -k / -s / -c; nothing here is timed).
+CASES = {
+    "batch256_rmat22": "lgc_prnibble_batch of 256 seeds (degree >= 2, stream 4) of R-MAT scale 22 "
+                       "(seed 2), eps log-uniform [1e-7, 1e-5], alpha 0.01, atomic",
+    "batch1024_rmat24": "lgc_prnibble_batch + lgc_sweep_batch of the 1024 many-seed seeds of R-MAT "
+                        "scale 24 (seed 4), atomic",
+    "hkpr_serving_rmat26": "the HK-PR request of the serving mix with the largest t, alone, on "
+                           "R-MAT scale 26 (seed 3), atomic",
+}
+
+
+def run_case(name, reps):
+    import torch
+    from paper_1604_07515_gb300 import inputs, lgc
+    if name == "batch256_rmat22":
+        off, col = inputs.rmat(22, seed=2)
+    elif name == "batch1024_rmat24":
+        off, col = inputs.rmat(MANY["scale"], seed=MANY["graph_seed"])
+    else:
+        off, col = inputs.rmat(SERVE["scale"], seed=SERVE["graph_seed"])
+    ctx = lgc.Context(0, torch.cuda.current_stream())
+    g = lgc.Graph(ctx, off, col)
+    ctx.set_option(lgc.OPT_RESULT_ON_DEVICE, 1)
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        if name == "batch256_rmat22":
+            seeds = inputs.seeds_deg2(off, 256, 4)
+            ps, sts = lgc.prnibble_batch(g, seeds, 0.01, inputs.eps_loguniform(256, 4, -7.0, -5.0))
+            edges = sum(s.pushed_edges for s in sts)
+        elif name == "batch1024_rmat24":
+            seeds, eps = many_seed_list(inputs, off)
+            ps, sts = lgc.prnibble_batch(g, seeds, MANY["alpha"], eps)
+            lgc.sweep_batch(g, ps)
+            edges = sum(s.pushed_edges for s in sts)
+        else:
+            big = max((m for m in serving_mix(inputs, off, SERVE["requests"]) if m[0] == "hkpr"),
+                      key=lambda m: m[2]["t"])
+            p, st = lgc.hkpr(g, big[1], big[2]["t"], big[2]["N"], big[2]["eps"])
+            lgc.sweep(g, p)
+            edges = st.pushed_edges
+        torch.cuda.synchronize()
+        print(f"{name}: {time.perf_counter() - t0:.4f} s, {edges} pushed edges", flush=True)
+    g.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,6 +686,9 @@ def main():
                          "graph's autotuned one (e.g. 8,32,8)")
     ap.add_argument("--algos", default=",".join(ALGOS),
                     help="comma-separated subset of the step (for profiling one diffusion)")
+    ap.add_argument("--case", default="", choices=[""] + list(CASES),
+                    help="run one named workload --steps times and exit (for profiling): "
+                         + "; ".join(f"{k}: {v}" for k, v in CASES.items()))
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 8 if args.impl == "reference" else 80
@@ -639,6 +699,8 @@ def main():
         ap.error(f"--algos takes a subset of {','.join(ALGOS)}")
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case, args.steps)
 
     rank, world, local = dist_env()
     from paper_1604_07515_gb300 import inputs
@@ -786,6 +848,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": traffic, "launches": d["launches"],
+                "ncu_units": PULL_TRAFFIC["heavy_gather_full"] if traffic is not None else None,
                 "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
                 "alg_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                 "share_of_step": d["ms"] / total_ms if total_ms else None}
