@@ -160,7 +160,9 @@ enum {
   LGC_OPT_SERVE_MEM_BUDGET = 3, /* bytes of hash-table memory admitted at once */
   LGC_OPT_SERVE_MAX_BATCH = 4,  /* requests resident on the device at once */
   LGC_OPT_TABLE_FORM = 6,       /* sparse sets: 0 automatic (dense once a set may reach
-                                   n/8 keys), 1 always hashed, 2 always dense */
+                                   n/8 keys; in lgc_prnibble_batch, once a seed's hashed
+                                   table would take more memory than the dense form), 1
+                                   always hashed, 2 always dense (lgc_prnibble_batch: as 0) */
   LGC_OPT_PULL = 7,             /* deterministic rounds gather from the frontier instead of
                                    sorting pushed records: 0 automatic (rounds of >= 2m/16
                                    edges), 1 never, 2 always; same results either way */

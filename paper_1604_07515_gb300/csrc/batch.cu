@@ -101,7 +101,7 @@ __global__ void batch_vmap_kernel(int64_t nf, const int32_t* __restrict__ fseed,
       const Table T = tabs[seed];
       const SeedParam P = prm[seed];
       const bool ok = slot >= 0;
-      const double r = ok ? T.s[slot].val : 0.0;
+      const double r = ok ? *tb_val(T, slot) : 0.0;
       const int64_t o0 = off[v];
       d = off[v + 1] - o0;
       double sh, rbase;
@@ -114,7 +114,7 @@ __global__ void batch_vmap_kernel(int64_t nf, const int32_t* __restrict__ fseed,
         rbase = ((1.0 - P.alpha) * r) / 2.0;
         sh = ((1.0 - P.alpha) * r) / (2.0 * (double)d);
       }
-      if (ok) T.s[slot].val = rbase;
+      if (ok) *tb_val(T, slot) = rbase;
       share[i] = sh;
       cnt[i] = d + (det ? 1 : 0);
       foff[i] = o0;
@@ -214,18 +214,18 @@ __global__ void __launch_bounds__(kBlock)
         sh[k] = s_share[j];
       }
     }
-    Slot* ts[kItemsB];  // the item's table: slots and hash shift
-    int tshift[kItemsB];
+    // the item's table: a dense one is the value array and the presence
+    // bitmap (slot = vertex), a hashed one its slots and hash shift
+    const Table* tp[kItemsB];
     int32_t probe[kItemsB];
 #pragma unroll
     for (int k = 0; k < kItemsB; k++) {
       probe[k] = 0;
-      ts[k] = nullptr;
-      tshift[k] = 32;
+      tp[k] = nullptr;
       if (w[k] >= 0) {
-        ts[k] = tabs[seed[k]].s;
-        tshift[k] = tabs[seed[k]].shift;
-        probe[k] = __ldcg(&ts[k][hash_slot(w[k], tshift[k])].key);
+        tp[k] = &tabs[seed[k]];
+        probe[k] = tp[k]->dense ? (int32_t)__ldcg(&tp[k]->bits[w[k] >> 5])
+                                : __ldcg(&tp[k]->s[hash_slot(w[k], tp[k]->shift)].key);
       }
     }
     int32_t slot[kItemsB];
@@ -235,20 +235,20 @@ __global__ void __launch_bounds__(kBlock)
       slot[k] = -1;
       ins[k] = 0;
       if (w[k] < 0) continue;
-      if (probe[k] == w[k] + 1) {
-        slot[k] = (int32_t)hash_slot(w[k], tshift[k]);
+      if (tp[k]->dense) {
+        slot[k] = w[k];
+        const uint32_t m = 1u << (w[k] & 31);
+        if (!((uint32_t)probe[k] & m) && !(atomicOr(&tp[k]->bits[w[k] >> 5], m) & m)) ins[k] = 1;
+      } else if (probe[k] == w[k] + 1) {
+        slot[k] = (int32_t)hash_slot(w[k], tp[k]->shift);
       } else {
-        Table T;
-        T.s = ts[k];
-        T.shift = tshift[k];
-        T.cap = int64_t{1} << (32 - tshift[k]);
-        slot[k] = (int32_t)ht_find_or_insert(T, w[k], &ins[k], &sc[seed[k]].err);
+        slot[k] = (int32_t)ht_find_or_insert(*tp[k], w[k], &ins[k], &sc[seed[k]].err);
       }
     }
     double old[kItemsB];
 #pragma unroll
     for (int k = 0; k < kItemsB; k++)
-      old[k] = slot[k] >= 0 ? atomicAdd(&ts[k][slot[k]].val, sh[k]) : 0.0;
+      old[k] = slot[k] >= 0 ? atomicAdd(tb_val(*tp[k], slot[k]), sh[k]) : 0.0;
 #pragma unroll
     for (int k = 0; k < kItemsB; k++) {
       bool pred = false;
@@ -351,13 +351,14 @@ __global__ void batch_fold_kernel(const uint64_t* __restrict__ rkey,
     const int32_t w = (int32_t)(rkey[b] & ((1ull << vbits) - 1));
     const Table T = tabs[seed];
     int ins = 0;
-    const int64_t slot = ht_find_or_insert(T, w, &ins, &sc[seed].err);
+    const int64_t slot = tb_find_or_insert(T, w, &ins, &sc[seed].err);
     if (ins) atomicAdd((unsigned long long*)&sc[seed].inserted, 1ull);
     int64_t q = 0;
     if (slot >= 0) {
-      double acc = T.s[slot].val;
+      double* vp = tb_val(T, slot);
+      double acc = *vp;
       for (int64_t k = b; k < e; k++) acc = acc + rval[k];
-      T.s[slot].val = acc;
+      *vp = acc;
       q = acc >= prm[seed].eps * (double)deg[w] ? 1 : 0;
     }
     qflag[sg] = q;
@@ -418,7 +419,7 @@ __global__ void batch_reresolve_kernel(int64_t nf, const int32_t* __restrict__ f
                                        const int32_t* __restrict__ grown) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (grown[fseed[i]]) fs[i] = (int32_t)ht_find(tabs[fseed[i]], fv[i]);
+    if (grown[fseed[i]]) fs[i] = (int32_t)tb_find(tabs[fseed[i]], fv[i]);
 }
 
 // Keeps the frontier entries of seeds that are still running (order kept).
@@ -464,18 +465,25 @@ __global__ void batch_keep_write_kernel(int64_t nf, const int64_t* __restrict__ 
 // ---------------------------------------------------------------------------
 int64_t table_bytes(int64_t cap) { return ceil_div(cap * (int64_t)(sizeof(Slot) + 8), 256) * 256; }
 
+// A dense table over n vertices: values, p, presence bits (each part
+// 256-aligned).
+int64_t dense_bytes(int64_t n) {
+  return 2 * ceil_div(8 * n, 256) * 256 + ceil_div(4 * ceil_div(n, 32), 256) * 256;
+}
+
 int64_t pow2_cap(int64_t min_cap) { return pow2_at_least(min_cap < 64 ? 64 : min_cap); }
 
-// Hashed tables (slots + p) of the given capacities (powers of two >= 64)
-// for seeds `which`, carved from one new cleared slab.
+// Tables for seeds `which`, carved from one new cleared slab: hashed ones
+// (slots + p) of the given capacities (powers of two >= 64), or dense ones
+// over all n vertices where caps[k] == -1.
 int carve_tables(lgc_ctx* ctx, Slabs* S, const std::vector<int64_t>& which,
-                 const std::vector<int64_t>& caps, std::vector<Table>* tabs,
+                 const std::vector<int64_t>& caps, int64_t n, std::vector<Table>* tabs,
                  std::vector<int>* slab_of) {
   if (which.empty()) return LGC_OK;
   int64_t bytes = 0;
   for (int64_t c : caps) {
     if (c > (int64_t{1} << 31)) return LGC_EINVAL;  // 32-bit slot hashes
-    bytes += table_bytes(c);
+    bytes += c < 0 ? dense_bytes(n) : table_bytes(c);
   }
   char* base = nullptr;
   LGC_TRY(dalloc_t(ctx, &base, (size_t)bytes));
@@ -486,6 +494,18 @@ int carve_tables(lgc_ctx* ctx, Slabs* S, const std::vector<int64_t>& which,
   int64_t at = 0;
   for (size_t k = 0; k < which.size(); k++) {
     const int64_t cap = caps[k];
+    if (cap < 0) {
+      Table T;
+      T.dense = 1;
+      T.cap = n;
+      T.dval = reinterpret_cast<double*>(base + at);
+      T.p = reinterpret_cast<double*>(base + at + ceil_div(8 * n, 256) * 256);
+      T.bits = reinterpret_cast<uint32_t*>(base + at + 2 * ceil_div(8 * n, 256) * 256);
+      at += dense_bytes(n);
+      (*tabs)[which[k]] = T;
+      (*slab_of)[which[k]] = id;
+      continue;
+    }
     int lg = 0;
     while (((int64_t)1 << lg) < cap) lg++;
     Table T;
@@ -512,8 +532,15 @@ __global__ void batch_rehash_kernel(const Regrow* __restrict__ rg,
     const int64_t j = i - beg[k];
     const Slot s = from.s[j];
     if (s.key == 0) continue;
+    const int32_t v = s.key - 1;
+    if (to.dense) {  // distinct keys: plain writes
+      atomicOr(&to.bits[v >> 5], 1u << (v & 31));
+      to.dval[v] = s.val;
+      to.p[v] = from.p[j];
+      continue;
+    }
     int ins = 0;
-    const int64_t q = ht_find_or_insert(to, s.key - 1, &ins, err);
+    const int64_t q = ht_find_or_insert(to, v, &ins, err);
     if (q < 0) continue;
     to.s[q].aux = s.aux;
     to.s[q].val = s.val;
@@ -536,6 +563,12 @@ __device__ inline int chunk_table(const int64_t* __restrict__ choff, int64_t B, 
   return b;
 }
 
+// Slot j of T holds a key with p > 0 (dense: slot = vertex).
+__device__ inline bool kept_entry(const Table& T, int64_t j) {
+  if (T.dense) return ((T.bits[j >> 5] >> (j & 31)) & 1u) && T.p[j] > 0.0;
+  return T.s[j].key != 0 && T.p[j] > 0.0;
+}
+
 // Per table, the number of kept entries (keys with p > 0).
 __global__ void batch_count_kernel(const Table* __restrict__ tabs,
                                    const int64_t* __restrict__ choff, int64_t B,
@@ -551,7 +584,7 @@ __global__ void batch_count_kernel(const Table* __restrict__ tabs,
     __syncthreads();
     unsigned k = 0;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
-      k += (T.s[j].key != 0 && T.p[j] > 0.0) ? 1u : 0u;
+      k += kept_entry(T, j) ? 1u : 0u;
     k = __reduce_add_sync(0xffffffffu, k);
     if ((threadIdx.x & 31) == 0 && k) atomicAdd(&s_cnt, k);
     __syncthreads();
@@ -577,7 +610,7 @@ __global__ void batch_gather_kernel(const Table* __restrict__ tabs,
     // whole warps iterate together (the chunk is a multiple of the block)
     for (int64_t jb = j0; jb < j1; jb += blockDim.x) {
       const int64_t j = jb + threadIdx.x;
-      const bool keep = j < j1 && T.s[j].key != 0 && T.p[j] > 0.0;
+      const bool keep = j < j1 && kept_entry(T, j);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (!m) continue;
       unsigned long long base = 0;
@@ -585,7 +618,7 @@ __global__ void batch_gather_kernel(const Table* __restrict__ tabs,
       base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
       if (keep) {
         const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
-        key[at] = ((uint64_t)b << vbits) | (uint64_t)(T.s[j].key - 1);
+        key[at] = ((uint64_t)b << vbits) | (uint64_t)(T.dense ? j : T.s[j].key - 1);
         val[at] = T.p[j];
       }
     }
@@ -821,7 +854,7 @@ int BatchEngine::add(int64_t k, const int32_t* seeds, const lgc_prnibble_params*
     fin_status[b] = 0;
     caps[i] = pow2_cap(2 * (1 + dseed[b]));
   }
-  LGC_TRY(carve_tables(ctx, &slabs, which, caps, &tabs, &slab_of));
+  LGC_TRY(carve_tables(ctx, &slabs, which, caps, n, &tabs, &slab_of));
   tabs_dirty = prm_dirty = true;
   LGC_TRY(upload());
   cudaStream_t s = ctx->stream;
@@ -898,7 +931,7 @@ int BatchEngine::round() {
   // seeds with a big frontier continue alone from their state
   for (int64_t b = 0; b < cap; b++) {
     if (state[b] != kRunning || !alive[b] || nfs[b] == 0 || edges[b] < handoff_edges ||
-        tabs[b].cap < 64)
+        (!tabs[b].dense && tabs[b].cap < 64))
       continue;
     LGC_TRY(flag.reserve(ctx, nf));
     LGC_TRY(qpos.reserve(ctx, nf));
@@ -929,15 +962,17 @@ int BatchEngine::round() {
   }
   // grow the tables of the seeds whose round's new keys would not fit at
   // load 1/2: one slab for all new tables, one rehash launch for all
+  // (a table that would take more memory hashed than dense becomes dense)
   std::vector<int64_t> gw, gcap;
   int64_t next_cap = 0, E = 0;
   for (int64_t b = 0; b < cap; b++) {
     grown[b] = 0;
     if (nfs[b] == 0) continue;
     const int64_t need = std::min<int64_t>(count[b] + edges[b], n);
-    if (2 * need > tabs[b].cap) {
+    if (!tabs[b].dense && 2 * need > tabs[b].cap) {
       gw.push_back(b);
-      gcap.push_back(pow2_cap(2 * need));
+      const int64_t hc = pow2_cap(2 * need);
+      gcap.push_back(ctx->table_form != 1 && table_bytes(hc) > dense_bytes(n) ? -1 : hc);
       grown[b] = 1;
     }
     next_cap += std::min<int64_t>(n, count[b] + edges[b] + nfs[b]);
@@ -952,7 +987,7 @@ int BatchEngine::round() {
       old_slab[k] = slab_of[gw[k]];
       rgbeg[k + 1] = rgbeg[k] + tabs[gw[k]].cap;
     }
-    LGC_TRY(carve_tables(ctx, &slabs, gw, gcap, &tabs, &slab_of));
+    LGC_TRY(carve_tables(ctx, &slabs, gw, gcap, n, &tabs, &slab_of));
     for (size_t k = 0; k < gw.size(); k++) rg[k].to = tabs[gw[k]];
     LGC_TRY(d_rg.reserve(ctx, gw.size()));
     LGC_TRY(d_rgbeg.reserve(ctx, gw.size() + 1));
@@ -1161,7 +1196,7 @@ void BatchEngine::release(int64_t b) {
 int64_t BatchEngine::table_bytes_live() const {
   int64_t t = 0;
   for (int64_t b = 0; b < cap; b++)
-    if (state[b] != kFree) t += table_bytes(tabs[b].cap);
+    if (state[b] != kFree) t += tabs[b].dense ? dense_bytes(n) : table_bytes(tabs[b].cap);
   return t;
 }
 

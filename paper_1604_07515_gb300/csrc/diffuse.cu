@@ -419,17 +419,15 @@ __global__ void __launch_bounds__(kBlock)
     }
     int ins[kEdgeItems];
     if (D.dense) {
-      uint32_t bw[kEdgeItems];
-#pragma unroll
-      for (int k = 0; k < kEdgeItems; k++)
-        bw[k] = w[k] >= 0 ? __ldcg(&D.bits[w[k] >> 5]) : 0u;
+      // nothing waits here: the add and the presence bit are both reductions
+      // (results unused); the keys this round inserted are counted by the
+      // caller from the bitmap's population before and after
 #pragma unroll
       for (int k = 0; k < kEdgeItems; k++) {
         ins[k] = 0;
         if (w[k] < 0) continue;
-        atomicAdd(&D.dval[w[k]], sh[k]);  // result unused: compiled as a reduction
-        const uint32_t m = 1u << (w[k] & 31);
-        if (!(bw[k] & m) && !(atomicOr(&D.bits[w[k] >> 5], m) & m)) ins[k] = 1;
+        atomicAdd(&D.dval[w[k]], sh[k]);
+        atomicOr(&D.bits[w[k] >> 5], 1u << (w[k] & 31));
       }
     } else {
 #pragma unroll
@@ -665,6 +663,23 @@ __global__ void rounds_pack_kernel(const Counters* Cn, const RoundsState* S, int
   out[5] = S->rounds;
   out[6] = S->pushes;
   out[7] = S->pushed_edges;
+}
+
+// sign * (set bits of the bitmap) added into *out, one atomic per block.
+__global__ void bits_pop_kernel(const uint32_t* __restrict__ bits, int64_t words, int sign,
+                                int64_t* out) {
+  __shared__ unsigned long long s_pop;
+  if (threadIdx.x == 0) s_pop = 0;
+  __syncthreads();
+  unsigned long long c = 0;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    c += __popc(bits[w]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_pop, c);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_pop)
+    atomicAdd((unsigned long long*)out, (unsigned long long)((int64_t)sign * (int64_t)s_pop));
 }
 
 // Filter of a dense set, in ascending vertex order: vertex v qualifies when it
@@ -1897,10 +1912,23 @@ struct PushWork {
       if (nrec > 0) {
         int64_t tiles = ceil_div(nrec, kEdgeTile);
         int grid = (int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16));
-        ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
-        emap_red_kernel<<<grid, kBlock, 0, s>>>(g->col, share.ptr, epos.ptr, foff.ptr, nf, nrec,
-                                                 total.ptr, D, ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
+        // a dense destination's inserted keys: population after - before
+        const int64_t words = (g->n + 31) / 32;
+        const int pg = std::min(grid_for(words), ctx->sms * 8);
+        if (D.dense) {
+          bits_pop_kernel<<<pg, kBlock, 0, s>>>(D.bits, words, -1, &ctx->d_counters->inserted);
+          LGC_COUNT_LAUNCH(ctx);
+        }
+        {
+          ProfScope ps(ctx, LGC_PROF_EDGEMAP, alg_bytes);
+          emap_red_kernel<<<grid, kBlock, 0, s>>>(g->col, share.ptr, epos.ptr, foff.ptr, nf, nrec,
+                                                   total.ptr, D, ctx->d_counters);
+          LGC_COUNT_LAUNCH(ctx);
+        }
+        if (D.dense) {
+          bits_pop_kernel<<<pg, kBlock, 0, s>>>(D.bits, words, 1, &ctx->d_counters->inserted);
+          LGC_COUNT_LAUNCH(ctx);
+        }
         LGC_CUDA_TRY(cudaGetLastError());
       }
       if (fmode != kFmNone) {
@@ -2766,16 +2794,30 @@ int run_prnibble_from(lgc_ctx* ctx, lgc_graph* g, const Table& src, const int32_
                       const int32_t* d_fs, int64_t nf, int64_t E, int64_t count,
                       const lgc_prnibble_params* prm, const lgc_stats& so_far, lgc_svec** p,
                       lgc_stats* st_out) {
-  if (src.dense || !src.p || src.cap < 64 || nf < 1) return LGC_EINVAL;
+  if (!src.p || (!src.dense && src.cap < 64) || (src.dense && src.cap != g->n) || nf < 1)
+    return LGC_EINVAL;
   cudaStream_t s = ctx->stream;
   PushWork W(ctx, g);
   Table T;
-  LGC_TRY(table_create(ctx, &T, src.cap, true));  // the same capacity: the same slots
+  // the same form and capacity: the same slots
+  if (src.dense) LGC_TRY(table_create_dense(ctx, &T, g->n, true));
+  else LGC_TRY(table_create(ctx, &T, src.cap, true));
   int status = LGC_OK;
   do {
-    if (T.cap != src.cap ||
-        cudaMemcpyAsync(T.s, src.s, sizeof(Slot) * src.cap, cudaMemcpyDeviceToDevice, s) ||
-        cudaMemcpyAsync(T.p, src.p, 8 * src.cap, cudaMemcpyDeviceToDevice, s)) {
+    const bool copy_ok =
+        src.dense
+            ? T.dense && cudaMemcpyAsync(T.dval, src.dval, 8 * src.cap, cudaMemcpyDeviceToDevice,
+                                         s) == cudaSuccess &&
+                  cudaMemcpyAsync(T.bits, src.bits, 4 * ((src.cap + 31) / 32),
+                                  cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+                  cudaMemcpyAsync(T.p, src.p, 8 * src.cap, cudaMemcpyDeviceToDevice, s) ==
+                      cudaSuccess
+            : T.cap == src.cap &&
+                  cudaMemcpyAsync(T.s, src.s, sizeof(Slot) * src.cap, cudaMemcpyDeviceToDevice,
+                                  s) == cudaSuccess &&
+                  cudaMemcpyAsync(T.p, src.p, 8 * src.cap, cudaMemcpyDeviceToDevice, s) ==
+                      cudaSuccess;
+    if (!copy_ok) {
       status = LGC_ECUDA;
       break;
     }
