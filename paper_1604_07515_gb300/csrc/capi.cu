@@ -446,7 +446,14 @@ static void serve_lane(Serve* S, lgc_ctx* lc) {
   struct Eng {
     BatchEngine E;
     std::map<int64_t, LaneJob> jobs;  // slot -> request
+    double first_done_s = 0.0;        // when the oldest unharvested seed finished
   };
+  // Finished seeds are handed out together (one extraction, one batched
+  // sweep): when no seed of the engine is running any more, when they are a
+  // quarter of its seeds, when admission is waiting for memory they hold, or
+  // when the oldest has waited kHarvestWait seconds.
+  constexpr double kHarvestWait = 0.002;
+  bool admission_blocked = false;
   // engines by (graph serial, mode); an engine without requests is dropped
   // at the end of the pass that emptied it
   std::map<std::pair<uint64_t, int>, Eng*> engines;
@@ -476,6 +483,7 @@ static void serve_lane(Serve* S, lgc_ctx* lc) {
         S->prq.pop_front();
         S->lane_resident++;
       }
+      admission_blocked = !S->prq.empty();
     }
     // new seeds join their engine at the next round
     const double t_admit = now_seconds();
@@ -530,7 +538,13 @@ static void serve_lane(Serve* S, lgc_ctx* lc) {
           continue;
         }
       }
-      if (!e->E.done.empty()) {
+      if (!e->E.done.empty() && e->first_done_s == 0.0) e->first_done_s = now_seconds();
+      const int64_t ndone = (int64_t)e->E.done.size();
+      const bool harvest =
+          ndone > 0 && (e->E.running == 0 || 4 * ndone >= (int64_t)e->jobs.size() ||
+                        admission_blocked || now_seconds() - e->first_done_s >= kHarvestWait);
+      if (harvest) {
+        e->first_done_s = 0.0;
         std::vector<int64_t> fin;
         fin.swap(e->E.done);
         std::vector<lgc_svec*> ps(fin.size(), nullptr);
