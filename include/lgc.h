@@ -184,7 +184,8 @@ enum {
   LGC_OPT_BATCH_HANDOFF = 12,   /* lgc_prnibble_batch: a seed whose frontier's degree sum
                                    reaches this many edges leaves the batch and finishes
                                    alone (pull rounds, dense sets), with the same result;
-                                   0 (default) max(2^20, 2m/64), -1 never */
+                                   0 (default) the graph's value (see
+                                   lgc_graph_batch_handoff), -1 never */
   LGC_OPT_SERVE_LANE = 14,      /* request loop: PR-Nibble requests resident at once in its
                                    batched lane (their rounds run together, requests join
                                    as they are admitted); 0 runs them on the worker
@@ -210,14 +211,24 @@ int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int3
                      int flags, lgc_graph **out);
 void lgc_graph_destroy(lgc_graph *g);
 /* Tunes the graph's launch shapes by timing them on the graph itself (the
- * paper has no counterpart; it affects speed only): for the heavy-vertex
- * pull gather of atomic rounds, the edges each lane loads per batch and the
- * lanes per work item, from (4, 32), (8, 32), (16, 32), (8, 16), (16, 16),
- * (8, 8), (16, 8), each with 16- and 8-byte gathered shares, on a frontier
- * of all vertices.  Takes a few launches of that gather per candidate; the
- * choice is written to *pull_batch, *pull_group, *pull_share (nullable).
- * Until it is called the graph uses (8, 32, 16). */
+ * paper has no counterpart; it affects speed only, never results):
+ *  - for the heavy-vertex pull gather of atomic rounds, the edges each lane
+ *    loads per batch and the lanes per work item, from (4, 32), (8, 32),
+ *    (16, 32), (8, 16), (16, 16), (8, 8), (16, 8), each with 16- and 8-byte
+ *    gathered shares, on a frontier of all vertices (a few launches of that
+ *    gather per candidate); the choice is written to *pull_batch,
+ *    *pull_group, *pull_share (nullable);
+ *  - for lgc_prnibble_batch and the request loop's PR-Nibble lane, the
+ *    frontier size (in edges) at which a seed leaves the batch and finishes
+ *    alone, from 2m/64, 2m/16, 2m/4 (each at least 2^20) and never, timing
+ *    one batch of 256 seeds of the graph at each (lgc_graph_batch_handoff
+ *    reports the choice).
+ * Until it is called the graph uses (8, 32, 16) and max(2^20, 2m/64). */
 int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group, int *pull_share);
+/* The hand-off threshold (edges) the graph's batches use while
+ * LGC_OPT_BATCH_HANDOFF is 0: the tuned value, else max(2^20, 2m/64);
+ * INT64_MAX means never. */
+int64_t lgc_graph_batch_handoff(const lgc_graph *g);
 int64_t lgc_graph_num_vertices(const lgc_graph *g);
 int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
 

@@ -766,9 +766,9 @@ int BatchEngine::init(lgc_ctx* c, lgc_graph* gr, int m) {
   det = m == LGC_MODE_DET;
   n = g->n;
   vbits = bits_for(n);
-  handoff_edges = ctx->batch_handoff > 0    ? ctx->batch_handoff
-                  : ctx->batch_handoff == 0 ? std::max<int64_t>(int64_t{1} << 20, g->nnz / 64)
-                                            : INT64_MAX;
+  handoff_edges = ctx->batch_handoff != 0 ? (ctx->batch_handoff > 0 ? ctx->batch_handoff
+                                                                     : INT64_MAX)
+                                           : batch_handoff_of(g);
   LGC_TRY(dalloc_t(ctx, &gsize, 4));  // frontier size, overflow, rehash error, init error
   LGC_CUDA_TRY(cudaMemsetAsync(gsize, 0, 16, ctx->stream));
   return LGC_OK;
@@ -1219,6 +1219,73 @@ void BatchEngine::fini() {
   d_sc.release(ctx);
   dfree(ctx, gsize);
   gsize = nullptr;
+}
+
+int64_t batch_handoff_of(const lgc_graph* g) {
+  return g->batch_handoff ? g->batch_handoff
+                          : std::max<int64_t>(int64_t{1} << 20, g->nnz / 64);
+}
+
+// Times one batch of 256 seeds (degree >= 2, drawn by a fixed SplitMix64
+// stream; eps log-uniform in [1e-7, 1e-5]; alpha 0.01; atomic) at each
+// candidate hand-off threshold -- 2m/64, 2m/16, 2m/4, never -- after one
+// untimed run, and keeps the fastest for the graph.
+int autotune_batch(lgc_ctx* ctx, lgc_graph* g) {
+  if (g->nnz == 0) return LGC_OK;
+  std::vector<int32_t> seeds;
+  std::vector<lgc_prnibble_params> prm;
+  uint64_t k = 0;
+  auto mix = [](uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  while ((int)seeds.size() < 256 && k < 64 * (uint64_t)g->n + 4096) {
+    const uint64_t w = mix(k++);
+    const int32_t v = (int32_t)(w % (uint64_t)g->n);
+    if (g->hdeg[v] < 2) continue;
+    const double u = (double)(mix(w) >> 11) * 0x1.0p-53;
+    lgc_prnibble_params p{};
+    p.alpha = 0.01;
+    p.eps = pow(10.0, -7.0 + 2.0 * u);
+    p.rule = LGC_RULE_OPT;
+    p.mode = LGC_MODE_ATOMIC;
+    seeds.push_back(v);
+    prm.push_back(p);
+  }
+  const int64_t B = (int64_t)seeds.size();
+  if (B == 0) return LGC_OK;
+  const bool dev = ctx->result_on_device;
+  const int64_t user = ctx->batch_handoff;
+  ctx->result_on_device = true;
+  ctx->batch_handoff = 0;  // the graph's value decides below
+  const int64_t cand[4] = {std::max<int64_t>(int64_t{1} << 20, g->nnz / 64),
+                           std::max<int64_t>(int64_t{1} << 20, g->nnz / 16),
+                           std::max<int64_t>(int64_t{1} << 20, g->nnz / 4), INT64_MAX};
+  std::vector<lgc_svec*> out(B, nullptr);
+  int st = LGC_OK;
+  double best_s = 0.0;
+  int64_t best = cand[0];
+  for (int c = -1; c < 4 && st == LGC_OK; c++) {
+    g->batch_handoff = cand[c < 0 ? 0 : c];
+    const double t0 = now_seconds();
+    st = run_prnibble_batch(ctx, g, B, seeds.data(), prm.data(), out.data(), nullptr);
+    if (st == LGC_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = LGC_ECUDA;
+    const double dt = now_seconds() - t0;
+    for (int64_t b = 0; b < B; b++) {
+      lgc_svec_free(out[b]);
+      out[b] = nullptr;
+    }
+    if (st == LGC_OK && c >= 0 && (c == 0 || dt < best_s)) {
+      best_s = dt;
+      best = cand[c];
+    }
+  }
+  g->batch_handoff = st == LGC_OK ? best : 0;
+  ctx->result_on_device = dev;
+  ctx->batch_handoff = user;
+  return st;
 }
 
 int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,

@@ -115,5 +115,11 @@ struct BatchEngine {
 };
 
 int64_t table_bytes(int64_t cap);
+// The hand-off threshold of graph g when the context leaves it to the graph:
+// its tuned value, else max(2^20, 2m/64).
+int64_t batch_handoff_of(const lgc_graph* g);
+int autotune_batch(lgc_ctx* ctx, lgc_graph* g);
+int run_prnibble_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const int32_t* seeds_h,
+                       const lgc_prnibble_params* prm_h, lgc_svec** p_out, lgc_stats* st_out);
 
 }  // namespace lgc

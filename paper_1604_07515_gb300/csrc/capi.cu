@@ -880,11 +880,14 @@ void lgc_graph_destroy(lgc_graph* g) {
 int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group, int* pull_share) {
   if (!g) return LGC_EINVAL;
   LGC_TRY(autotune_pull(g->ctx, g));
+  LGC_TRY(autotune_batch(g->ctx, g));
   if (pull_batch) *pull_batch = g->pull_batch;
   if (pull_group) *pull_group = g->pull_group;
   if (pull_share) *pull_share = g->pull_share;
   return LGC_OK;
 }
+
+int64_t lgc_graph_batch_handoff(const lgc_graph* g) { return g ? batch_handoff_of(g) : -1; }
 
 int64_t lgc_graph_num_vertices(const lgc_graph* g) { return g ? g->n : -1; }
 int64_t lgc_graph_num_entries(const lgc_graph* g) { return g ? g->nnz : -1; }

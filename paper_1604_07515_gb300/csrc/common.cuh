@@ -269,6 +269,7 @@ struct lgc_graph {
   int pull_batch = 8;          // edges per lane per batch in heavy pull gathers (tuned)
   int pull_group = 32;         // lanes per work item in heavy pull gathers (tuned)
   int pull_share = 16;         // bytes per gathered share in atomic pull gathers (tuned)
+  int64_t batch_handoff = 0;   // batched PR-Nibble hand-off threshold (tuned; 0: untuned)
   // vertices of degree > kPullLight in ascending id, for the pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;

@@ -122,6 +122,7 @@ SIGNATURES = {
     "lgc_graph_create": (c_int, [_P, c_int64, _P, _P, c_int, POINTER(_P)]),
     "lgc_graph_destroy": (None, [_P]),
     "lgc_graph_num_vertices": (c_int64, [_P]),
+    "lgc_graph_batch_handoff": (c_int64, [_P]),
     "lgc_graph_num_entries": (c_int64, [_P]),
     "lgc_prnibble": (c_int, [_P, c_int32, POINTER(PRNibbleParams), POINTER(POINTER(Svec)),
                              POINTER(Stats)]),
@@ -355,6 +356,11 @@ class Graph:
         _check(load().lgc_graph_autotune(self.handle, byref(b), byref(gr), byref(sb)),
                "lgc_graph_autotune")
         return b.value, gr.value, sb.value
+
+    def batch_handoff(self) -> int:
+        """lgc_graph_batch_handoff: the frontier size (edges) at which a seed
+        leaves a batch and finishes alone (2**63 - 1: never)."""
+        return load().lgc_graph_batch_handoff(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

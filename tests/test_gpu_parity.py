@@ -531,9 +531,17 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         c.set_option(lgc.OPT_PULL_BATCH, 0)
         c.set_option(lgc.OPT_PULL_GROUP, 0)
         c.set_option(lgc.OPT_PULL_SHARE, 0)
+        default_handoff = g.batch_handoff()
+        assert default_handoff == max(1 << 20, g.nnz // 64)
         assert g.autotune() in shapes
         p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
         assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
+        # the batch hand-off threshold is one of the tuner's candidates
+        assert g.batch_handoff() in {max(1 << 20, g.nnz // k) for k in (64, 16, 4)} | {2 ** 63 - 1}
+        ps, sts = lgc.prnibble_batch(g, [x, int(col[0])], 0.01, 1e-6, mode="det")
+        ref2 = oracle.prnibble(off, col, int(col[0]), 0.01, 1e-6)
+        assert np.array_equal(ps[0].idx, ref.idx) and np.array_equal(ps[0].val, ref.val)
+        assert np.array_equal(ps[1].idx, ref2.idx) and np.array_equal(ps[1].val, ref2.val)
     finally:
         c.set_option(lgc.OPT_PULL_BATCH, 0)
         c.set_option(lgc.OPT_PULL_GROUP, 0)
