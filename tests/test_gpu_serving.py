@@ -230,3 +230,25 @@ def test_lane_across_graphs_of_different_sizes():
             g.close()
     finally:
         ctx.close()
+
+
+def test_lane_rejects_bad_requests_and_serves_the_rest(setup):
+    """A PR-Nibble request the batch engine refuses (a seed of degree 0, an
+    alpha outside (0, 1)) ends with LGC_EINVAL on its own, while the requests
+    admitted with it are served, and match the oracle."""
+    ctx, g, off, col = setup
+    d = np.diff(off)
+    iso = int(np.flatnonzero(d == 0)[0])
+    good = [int(s) for s in inputs.seeds_deg2(off, 5, 91)]
+    reqs = [lgc.make_request(lgc.ALGO_PRNIBBLE, s, True, alpha=0.01, eps=1e-5, mode="det")
+            for s in good[:3]]
+    reqs.append(lgc.make_request(lgc.ALGO_PRNIBBLE, iso, True, alpha=0.01, eps=1e-5, mode="det"))
+    reqs.append(lgc.make_request(lgc.ALGO_PRNIBBLE, good[3], True, alpha=1.5, eps=1e-5,
+                                 mode="det"))
+    reqs.append(lgc.make_request(lgc.ALGO_PRNIBBLE, good[4], True, alpha=0.01, eps=1e-5,
+                                 mode="det"))
+    res = [lgc.wait(ctx, t) for t in [lgc.submit(ctx, g, r) for r in reqs]]
+    assert [r["status"] for r in res] == [0, 0, 0, lgc.LGC_EINVAL, lgc.LGC_EINVAL, 0]
+    for s, r in zip(good[:3] + [good[4]], res[:3] + res[5:]):
+        ref = oracle.prnibble(off, col, s, 0.01, 1e-5)
+        assert np.array_equal(r["idx"], ref.idx) and np.array_equal(r["val"], ref.val)
