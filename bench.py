@@ -762,6 +762,7 @@ def main():
             ctx.set_option(opt, v)
     else:
         pull_shape = g.autotune()  # launch-shape tuning on this graph, before any timing
+    pull_light = g.pull_light()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -866,7 +867,8 @@ def main():
             "config": {"workload": WORKLOAD if STEP_ALGOS == ALGOS
                        else WORKLOAD + f" (only: {','.join(STEP_ALGOS)})", "mode": MODE,
                        "l2": "inputs larger than L2 and L2 flushed between steps",
-                       "parallelism": f"replicas{world}", "pull_shape": list(pull_shape)},
+                       "parallelism": f"replicas{world}", "pull_shape": list(pull_shape),
+                       "pull_light": pull_light},
             "clusters_per_s": clusters / (total_ms / 1e3),
             "pushed_edges_per_step": pushed / args.steps / max(1, world),
             "roofline": roofline, "kernels": prof,

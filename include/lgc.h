@@ -212,12 +212,14 @@ int lgc_graph_create(lgc_ctx *ctx, int64_t n, const int64_t *offsets, const int3
 void lgc_graph_destroy(lgc_graph *g);
 /* Tunes the graph's launch shapes by timing them on the graph itself (the
  * paper has no counterpart; it affects speed only, never results):
- *  - for the heavy-vertex pull gather of atomic rounds, the edges each lane
- *    loads per batch and the lanes per work item, from (4, 32), (8, 32),
- *    (16, 32), (8, 16), (16, 16), (8, 8), (16, 8), each with 16- and 8-byte
- *    gathered shares, on a frontier of all vertices (a few launches of that
- *    gather per candidate); the choice is written to *pull_batch,
- *    *pull_group, *pull_share (nullable);
+ *  - for the pull gathers of atomic rounds, the degree bin (vertices of
+ *    degree <= 16, 32 or 64 gather one thread each, the others in work items
+ *    of up to 4096 edges; see lgc_graph_set_pull_light) and the heavy
+ *    gather's edges per lane per batch and lanes per work item, from (4, 32),
+ *    (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8), each with 16- and
+ *    8-byte gathered shares, on a frontier of all vertices (a few launches of
+ *    the light and the heavy gather per candidate); the shape is written to
+ *    *pull_batch, *pull_group, *pull_share (nullable);
  *  - for lgc_prnibble_batch and the request loop's PR-Nibble lane, the
  *    frontier size (in edges) at which a seed leaves the batch and finishes
  *    alone, from 2m/64, 2m/16, 2m/4 (each at least 2^20) and never, timing
@@ -229,6 +231,16 @@ int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group, int *pull
  * LGC_OPT_BATCH_HANDOFF is 0: the tuned value, else max(2^20, 2m/64);
  * INT64_MAX means never. */
 int64_t lgc_graph_batch_handoff(const lgc_graph *g);
+/* The degree bin of the graph's pull rounds: vertices of degree 1..light
+ * gather with one thread each (in deterministic mode, fold their list in
+ * one thread), the others in work items (deterministic mode: degree up to
+ * 1024 one lane each, longer lists segment-parallel).  Default 32;
+ * lgc_graph_autotune picks one of 16, 32, 64.  lgc_graph_set_pull_light
+ * rebuilds the graph's vertex lists for 4 <= light <= 256 (LGC_EINVAL
+ * otherwise); it waits for the request loop's requests on the graph.  Speed
+ * only: results do not depend on it. */
+int lgc_graph_pull_light(const lgc_graph *g);
+int lgc_graph_set_pull_light(lgc_graph *g, int light);
 int64_t lgc_graph_num_vertices(const lgc_graph *g);
 int64_t lgc_graph_num_entries(const lgc_graph *g); /* 2m */
 

@@ -68,18 +68,18 @@ __global__ void validate_kernel(const int64_t* __restrict__ off, const int32_t* 
   }
 }
 
-__global__ void heavy_flag_kernel(const int32_t* __restrict__ deg, int64_t n,
+__global__ void heavy_flag_kernel(const int32_t* __restrict__ deg, int64_t n, int light,
                                   int64_t* __restrict__ flag) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    flag[v] = deg[v] > kPullLight ? 1 : 0;
+    flag[v] = deg[v] > light ? 1 : 0;
 }
 
-__global__ void heavy_write_kernel(const int32_t* __restrict__ deg, int64_t n,
+__global__ void heavy_write_kernel(const int32_t* __restrict__ deg, int64_t n, int light,
                                    const int64_t* __restrict__ pos, int32_t* __restrict__ out) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    if (deg[v] > kPullLight) out[pos[v]] = (int32_t)v;
+    if (deg[v] > light) out[pos[v]] = (int32_t)v;
 }
 
 __global__ void items_count_kernel(const int32_t* __restrict__ heavy, int64_t nh,
@@ -124,7 +124,7 @@ int build_big_segments(lgc_ctx* ctx, lgc_graph* g) {
   {
     std::vector<int32_t> mid;
     for (int64_t v = 0; v < g->n; v++)
-      if (g->hdeg[v] > kPullLight && g->hdeg[v] <= kDetBig) mid.push_back((int32_t)v);
+      if (g->hdeg[v] > g->pull_light && g->hdeg[v] <= kDetBig) mid.push_back((int32_t)v);
     std::stable_sort(mid.begin(), mid.end(),
                      [&](int32_t a, int32_t b) { return g->hdeg[a] > g->hdeg[b]; });
     g->ndet_mid = (int64_t)mid.size();
@@ -185,16 +185,17 @@ __global__ void light_items_kernel(const int32_t* __restrict__ order, int64_t k,
   }
 }
 
-// The vertices of degree 1..kPullLight grouped by degree, highest first, ids
+// The vertices of degree 1..pull_light grouped by degree, highest first, ids
 // ascending within a degree (a counting sort of the host degree copy).
 int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
   cudaStream_t s = ctx->stream;
   const int64_t n = g->n;
-  int64_t cnt[kPullLight + 2] = {0};
+  const int L = g->pull_light;
+  std::vector<int64_t> cnt(L + 2, 0), at(L + 2, 0);
+  int64_t k = 0;
   for (int64_t v = 0; v < n; v++)
-    if (g->hdeg[v] >= 1 && g->hdeg[v] <= kPullLight) cnt[g->hdeg[v]]++;
-  int64_t at[kPullLight + 2] = {0}, k = 0;
-  for (int d = kPullLight; d >= 1; d--) {
+    if (g->hdeg[v] >= 1 && g->hdeg[v] <= L) cnt[g->hdeg[v]]++;
+  for (int d = L; d >= 1; d--) {
     at[d] = k;
     k += cnt[d];
   }
@@ -208,7 +209,7 @@ int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
   }
   for (int64_t v = 0; v < n; v++) {
     const int32_t d = g->hdeg[v];
-    if (d >= 1 && d <= kPullLight) order[at[d]++] = (int32_t)v;
+    if (d >= 1 && d <= L) order[at[d]++] = (int32_t)v;
   }
   int32_t* d_order = nullptr;
   LGC_TRY(dalloc_t(ctx, &d_order, k));
@@ -236,7 +237,7 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
   int st = dalloc_t(ctx, &flag, n);
   if (st == LGC_OK) st = dalloc_t(ctx, &tot, 1);
   if (st == LGC_OK) {
-    heavy_flag_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, flag);
+    heavy_flag_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, g->pull_light, flag);
     LGC_COUNT_LAUNCH(ctx);
     st = scan_i64(ctx, flag, flag, n, false, tot);
   }
@@ -250,7 +251,7 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
     st = dalloc_t(ctx, &g->heavy, g->nheavy);
   }
   if (st == LGC_OK && g->nheavy > 0) {
-    heavy_write_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, flag, g->heavy);
+    heavy_write_kernel<<<grid_for(n), kBlock, 0, s>>>(g->deg, n, g->pull_light, flag, g->heavy);
     LGC_COUNT_LAUNCH(ctx);
     if (cudaGetLastError() != cudaSuccess) st = LGC_ECUDA;
   }
@@ -281,6 +282,33 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
 }
 
 }  // namespace
+
+namespace lgc {
+
+// Rebuilds the degree-binned vertex lists of the pull rounds for light
+// threshold L: vertices of degree 1..L one thread each (grouped by degree),
+// the others in work items; in deterministic mode the lists of degree
+// (L, kDetBig] fold one lane each and longer ones segment-parallel.
+int rebuild_pull_lists(lgc_ctx* ctx, lgc_graph* g, int L) {
+  if (L < 4 || L > 256) return LGC_EINVAL;
+  for (void* p : {(void*)g->heavy, (void*)g->items, (void*)g->big_w, (void*)g->big_seg0,
+                  (void*)g->segs, (void*)g->det_mid, (void*)g->light})
+    dfree(ctx, p);
+  g->heavy = nullptr;
+  g->items = nullptr;
+  g->big_w = nullptr;
+  g->big_seg0 = nullptr;
+  g->segs = nullptr;
+  g->det_mid = nullptr;
+  g->light = nullptr;
+  g->nheavy = g->nitems = g->nbig = g->nsegs = g->ndet_mid = g->nlight = 0;
+  g->pull_light = L;
+  LGC_TRY(build_heavy_list(ctx, g));
+  LGC_TRY(build_big_segments(ctx, g));
+  return build_light_items(ctx, g);
+}
+
+}  // namespace lgc
 
 // ---------------------------------------------------------------------------
 // request loop: continuous batching.  PR-Nibble requests go to one lane
@@ -850,19 +878,26 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
   return LGC_OK;
 }
 
+// Waits until no queued or running request of the context's request loop
+// uses g.
+static void wait_graph_idle(lgc_graph* g) {
+  lgc_ctx* ctx = g->ctx;
+  if (!ctx->serve) return;
+  Serve* S = ctx->serve;
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->cv.wait(lk, [&] {
+    for (auto& it : S->queue)
+      if (it.g == g) return false;
+    for (auto& it : S->prq)
+      if (it.g == g) return false;
+    return S->inflight == 0 && S->lane_resident == 0;
+  });
+}
+
 void lgc_graph_destroy(lgc_graph* g) {
   if (!g) return;
   lgc_ctx* ctx = g->ctx;
-  if (ctx->serve) {
-    // wait until no queued or running request uses g
-    Serve* S = ctx->serve;
-    std::unique_lock<std::mutex> lk(S->mu);
-    S->cv.wait(lk, [&] {
-      for (auto& it : S->queue)
-        if (it.g == g) return false;
-      return S->inflight == 0;
-    });
-  }
+  wait_graph_idle(g);
   dfree(ctx, g->off);
   dfree(ctx, g->col);
   dfree(ctx, g->deg);
@@ -879,6 +914,7 @@ void lgc_graph_destroy(lgc_graph* g) {
 
 int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group, int* pull_share) {
   if (!g) return LGC_EINVAL;
+  wait_graph_idle(g);  // the pull lists are rebuilt: no request may be using them
   LGC_TRY(autotune_pull(g->ctx, g));
   LGC_TRY(autotune_batch(g->ctx, g));
   if (pull_batch) *pull_batch = g->pull_batch;
@@ -888,6 +924,15 @@ int lgc_graph_autotune(lgc_graph* g, int* pull_batch, int* pull_group, int* pull
 }
 
 int64_t lgc_graph_batch_handoff(const lgc_graph* g) { return g ? batch_handoff_of(g) : -1; }
+
+int lgc_graph_pull_light(const lgc_graph* g) { return g ? g->pull_light : -1; }
+
+int lgc_graph_set_pull_light(lgc_graph* g, int light) {
+  if (!g || light < 4 || light > 256) return LGC_EINVAL;
+  wait_graph_idle(g);
+  if (light == g->pull_light) return LGC_OK;
+  return rebuild_pull_lists(g->ctx, g, light);
+}
 
 int64_t lgc_graph_num_vertices(const lgc_graph* g) { return g ? g->n : -1; }
 int64_t lgc_graph_num_entries(const lgc_graph* g) { return g ? g->nnz : -1; }

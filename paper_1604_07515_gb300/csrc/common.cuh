@@ -270,6 +270,7 @@ struct lgc_graph {
   int pull_group = 32;         // lanes per work item in heavy pull gathers (tuned)
   int pull_share = 16;         // bytes per gathered share in atomic pull gathers (tuned)
   int64_t batch_handoff = 0;   // batched PR-Nibble hand-off threshold (tuned; 0: untuned)
+  int pull_light = 32;         // pull rounds: degree <= pull_light one thread per vertex (tuned)
   // vertices of degree > kPullLight in ascending id, for the pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;
@@ -298,7 +299,7 @@ struct lgc_graph {
 namespace lgc {
 // A pull round handles vertices of degree <= kPullLight with one thread each
 // and the rest in work items of at most kPullItem edges.
-constexpr int kPullLight = 32;
+constexpr int kPullLight = 32;  // the default of lgc_graph::pull_light
 constexpr int kDetBig = 1024;  // longer lists fold segment-parallel in deterministic mode
 constexpr int kDetSeg = 256;
 constexpr int kPullItem = 4096;
@@ -420,6 +421,7 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
 int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_params* prm,
                   lgc_svec** p, lgc_stats* st);
 int autotune_pull(lgc_ctx* ctx, lgc_graph* g);
+int rebuild_pull_lists(lgc_ctx* ctx, lgc_graph* g, int L);
 int run_prnibble_set(lgc_ctx* ctx, lgc_graph* g, int64_t k, const int32_t* seeds,
                      const double* weights, double beta, const lgc_prnibble_params* prm,
                      lgc_svec** p, lgc_stats* st_out, lgc_svec** r_out);

@@ -2514,13 +2514,16 @@ int finish_svec(lgc_ctx* ctx, lgc_graph* g, const Table& T, const double* vals, 
 
 }  // namespace
 
-// Picks the shape of the heavy-vertex pull gather for this graph (edges per
-// lane per batch, lanes per work item, bytes per gathered share): each
-// candidate gathers a frontier of all vertices into a scratch dense set three
-// times (after one untimed launch), and the fastest median wins.  The
+// Picks the degree bins and the shape of the atomic pull gather for this
+// graph: for each light threshold L (vertices of degree <= L one thread each,
+// the rest in work items), the lists are rebuilt and every heavy-gather shape
+// (edges per lane per batch, lanes per work item, bytes per gathered share)
+// gathers a frontier of all vertices into a scratch dense set three times
+// after one untimed launch; the light gather of the same share width is
+// timed the same way, and the fastest sum of the two medians wins.  The
 // gathered sums are exact, so every candidate gives the same values.
 int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
-  if (g->nheavy == 0 || g->nitems == 0) return LGC_OK;
+  if (g->n == 0 || g->nnz == 0) return LGC_OK;
   cudaStream_t s = ctx->stream;
   const int64_t n = g->n, words = (n + 31) / 32;
   Table D;
@@ -2534,16 +2537,10 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
   while (gb < 62 && (int64_t{1} << gb) <= g->max_deg) gb++;
   do {
     if ((st = table_create_dense(ctx, &D, n, false)) || (st = dalloc_t(ctx, &shx, n)) ||
-        (st = dalloc_t(ctx, &shd, n)) ||
-        (st = dalloc_t(ctx, &range, 2)) || (st = dalloc_t(ctx, &q, words)) ||
-        (st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
-        (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
+        (st = dalloc_t(ctx, &shd, n)) || (st = dalloc_t(ctx, &range, 2)) ||
+        (st = dalloc_t(ctx, &q, words)))
       break;
-    if (cudaMemsetAsync(q, 0, 4 * words, s) ||
-        cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
-        cudaMemsetAsync(hcnt, 0, 4 * (g->nheavy + 1), s) ||
-        cudaMemsetAsync(htouch, 0, 4 * (g->nheavy + 1), s) ||
-        cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+    if (cudaMemsetAsync(q, 0, 4 * words, s) || cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
       st = LGC_ECUDA;
       break;
     }
@@ -2551,46 +2548,96 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
     LGC_COUNT_LAUNCH(ctx);
     tune_fill_kernel<double><<<grid_for(n), kBlock, 0, s>>>(shd, n, range, gb);
     LGC_COUNT_LAUNCH(ctx);
-    // (batch depth, lanes per item) x (16- or 8-byte shares)
-    const int cand[7][2] = {{4, 32}, {8, 32}, {16, 32}, {8, 16}, {16, 16}, {8, 8}, {16, 8}};
-    float best_ms = 0.f;
-    int best = kPullBatch, best_group = 32, best_share = 16;
-    bool first = true;
-    auto time_shape = [&](auto* shv, int cb, int cg, float* med) {
-      using SH = std::remove_pointer_t<decltype(shv)>;
-      HeavyKernel<SH> heavy = heavy_kernel<SH>(cb, cg);
-      const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / cg));
-      const int hg = (int)(hb < (ctx->sms * 16) ? hb : (ctx->sms * 16));
+    // median of three timed launches after an untimed one
+    auto timed = [&](auto&& launch, float* med) {
       float t[3] = {0.f, 0.f, 0.f};
-      for (int r = -1; r < 3; r++) {
+      for (int r = -1; r < 3 && st == LGC_OK; r++) {
         if (cudaEventRecord(e0, s)) st = LGC_ECUDA;
-        heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shv, range, gb, D, 1.0,
-                                    kFmThreshold, q, hacc, hcnt, htouch, ctx->d_counters);
+        launch();
         LGC_COUNT_LAUNCH(ctx);
         if (cudaEventRecord(e1, s) || cudaEventSynchronize(e1)) st = LGC_ECUDA;
-        if (st != LGC_OK) return;
-        if (r >= 0 && cudaEventElapsedTime(&t[r], e0, e1)) st = LGC_ECUDA;
+        if (st == LGC_OK && r >= 0 && cudaEventElapsedTime(&t[r], e0, e1)) st = LGC_ECUDA;
       }
       std::sort(t, t + 3);
       *med = t[1];
     };
-    for (int sb : {16, 8}) {
-      for (int ci = 0; ci < 7 && st == LGC_OK; ci++) {
-        const int cb = cand[ci][0], cg = cand[ci][1];
-        float med = 0.f;
-        if (sb == 16) time_shape(shx, cb, cg, &med);
-        else time_shape(shd, cb, cg, &med);
-        if (st != LGC_OK) break;
-        if (first || med < best_ms) {
-          first = false;
-          best_ms = med;
-          best = cb;
-          best_group = cg;
+    // (batch depth, lanes per item) x (16- or 8-byte shares) x light threshold
+    const int cand[7][2] = {{4, 32}, {8, 32}, {16, 32}, {8, 16}, {16, 16}, {8, 8}, {16, 8}};
+    const int lights[3] = {16, 32, 64};
+    float best_ms = 0.f;
+    int best = kPullBatch, best_group = 32, best_share = 16, best_light = g->pull_light;
+    bool first = true;
+    for (int li = 0; li < 3 && st == LGC_OK; li++) {
+      if (g->pull_light != lights[li] && (st = rebuild_pull_lists(ctx, g, lights[li])) != LGC_OK)
+        break;
+      dfree(ctx, hacc);
+      dfree(ctx, hcnt);
+      dfree(ctx, htouch);
+      hacc = nullptr;
+      hcnt = nullptr;
+      htouch = nullptr;
+      if ((st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
+          (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
+        break;
+      if (cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
+          cudaMemsetAsync(hcnt, 0, 4 * (g->nheavy + 1), s) ||
+          cudaMemsetAsync(htouch, 0, 4 * (g->nheavy + 1), s)) {
+        st = LGC_ECUDA;
+        break;
+      }
+      for (int sb : {16, 8}) {
+        float light_ms = 0.f;
+        auto light_of = [&](auto* shv) {
+          using SH = std::remove_pointer_t<decltype(shv)>;
+          const int lgl = (int)std::max<int64_t>(
+              1, std::min<int64_t>(ceil_div(g->nlight, kBlock), (ctx->sms * 32)));
+          timed([&] {
+            pull_light_fx_kernel<SH><<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, shv,
+                                                           range, gb, D, 1.0, kFmThreshold, q,
+                                                           ctx->d_counters);
+          }, &light_ms);
+        };
+        if (g->nlight > 0) {
+          if (sb == 16) light_of(shx);
+          else light_of(shd);
+        }
+        if (st == LGC_OK && g->nitems == 0 && (first || light_ms < best_ms)) {
+          first = false;  // every vertex is light at this threshold
+          best_ms = light_ms;
           best_share = sb;
+          best_light = lights[li];
+        }
+        for (int ci = 0; ci < 7 && st == LGC_OK && g->nitems > 0; ci++) {
+          const int cb = cand[ci][0], cg = cand[ci][1];
+          float med = 0.f;
+          auto heavy_of = [&](auto* shv) {
+            using SH = std::remove_pointer_t<decltype(shv)>;
+            HeavyKernel<SH> heavy = heavy_kernel<SH>(cb, cg);
+            const int64_t hb = ceil_div(g->nitems, (kBlock / 32) * (32 / cg));
+            const int hg = (int)(hb < (ctx->sms * 16) ? hb : (ctx->sms * 16));
+            timed([&] {
+              heavy<<<hg, kBlock, 0, s>>>(g->off, g->col, g->items, g->nitems, shv, range, gb, D,
+                                          1.0, kFmThreshold, q, hacc, hcnt, htouch,
+                                          ctx->d_counters);
+            }, &med);
+          };
+          if (sb == 16) heavy_of(shx);
+          else heavy_of(shd);
+          if (st != LGC_OK) break;
+          if (first || light_ms + med < best_ms) {
+            first = false;
+            best_ms = light_ms + med;
+            best = cb;
+            best_group = cg;
+            best_share = sb;
+            best_light = lights[li];
+          }
         }
       }
     }
-    if (st == LGC_OK) {
+    if (st == LGC_OK && g->pull_light != best_light)
+      st = rebuild_pull_lists(ctx, g, best_light);
+    if (st == LGC_OK && !first) {
       g->pull_batch = best;
       g->pull_group = best_group;
       g->pull_share = best_share;

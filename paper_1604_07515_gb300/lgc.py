@@ -123,6 +123,8 @@ SIGNATURES = {
     "lgc_graph_destroy": (None, [_P]),
     "lgc_graph_num_vertices": (c_int64, [_P]),
     "lgc_graph_batch_handoff": (c_int64, [_P]),
+    "lgc_graph_pull_light": (c_int, [_P]),
+    "lgc_graph_set_pull_light": (c_int, [_P, c_int]),
     "lgc_graph_num_entries": (c_int64, [_P]),
     "lgc_prnibble": (c_int, [_P, c_int32, POINTER(PRNibbleParams), POINTER(POINTER(Svec)),
                              POINTER(Stats)]),
@@ -356,6 +358,15 @@ class Graph:
         _check(load().lgc_graph_autotune(self.handle, byref(b), byref(gr), byref(sb)),
                "lgc_graph_autotune")
         return b.value, gr.value, sb.value
+
+    def pull_light(self) -> int:
+        """lgc_graph_pull_light: the degree bin of the pull rounds."""
+        return load().lgc_graph_pull_light(self.handle)
+
+    def set_pull_light(self, light: int):
+        """lgc_graph_set_pull_light: rebuild the pull lists for another bin."""
+        _check(load().lgc_graph_set_pull_light(self.handle, int(light)),
+               "lgc_graph_set_pull_light")
 
     def batch_handoff(self) -> int:
         """lgc_graph_batch_handoff: the frontier size (edges) at which a seed

@@ -531,11 +531,13 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         c.set_option(lgc.OPT_PULL_BATCH, 0)
         c.set_option(lgc.OPT_PULL_GROUP, 0)
         c.set_option(lgc.OPT_PULL_SHARE, 0)
+        assert g.pull_light() == 32  # the default degree bin
         default_handoff = g.batch_handoff()
         assert default_handoff == max(1 << 20, g.nnz // 64)
         assert g.autotune() in shapes
         p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
         assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
+        assert g.pull_light() in (16, 32, 64)
         # the batch hand-off threshold is one of the tuner's candidates
         assert g.batch_handoff() in {max(1 << 20, g.nnz // k) for k in (64, 16, 4)} | {2 ** 63 - 1}
         ps, sts = lgc.prnibble_batch(g, [x, int(col[0])], 0.01, 1e-6, mode="det")
@@ -549,3 +551,42 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         c.set_option(lgc.OPT_PULL, 0)
         c.set_option(lgc.OPT_DEVICE_ROUNDS, 1)
         g.close()
+
+
+@pytest.mark.parametrize("light", [4, 16, 64, 256])
+def test_pull_degree_bins(ctx, light):
+    """The pull rounds' degree bin (vertices of degree <= light gather one
+    thread each; deterministic mode: fold one thread each, then one lane each
+    up to degree 1024, then segment-parallel) changes speed only: HK-PR's
+    near-global pull rounds and PR-Nibble with every round a pull round give
+    the oracle's results, bit for bit in deterministic mode."""
+    off, col = inputs.rmat(16, seed=1)
+    g = lgc.Graph(ctx, off, col)
+    x = inputs.config1_seed(off, col)
+    try:
+        g.set_pull_light(light)
+        assert g.pull_light() == light
+        ref = oracle.hkpr(off, col, x, 10.0, 20, 1e-7, trace=True)
+        p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="det")
+        assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+        assert_trace_equal(ctx.trace(), ref.trace)
+        p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="atomic")
+        assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+        ctx.set_option(lgc.OPT_PULL, 2)
+        ref = oracle.prnibble(off, col, x, 0.01, 1e-6)
+        for mode in ("det", "atomic"):
+            p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode=mode)
+            assert st.pushed_edges == ref.pushed_edges
+            if mode == "det":
+                assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
+            else:
+                assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
+    finally:
+        ctx.set_option(lgc.OPT_PULL, 0)
+        g.close()
+    with pytest.raises(lgc.LgcError):
+        g2 = lgc.Graph(ctx, off, col)
+        try:
+            g2.set_pull_light(3)
+        finally:
+            g2.close()
