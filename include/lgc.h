@@ -213,7 +213,7 @@ void lgc_graph_destroy(lgc_graph *g);
 /* Tunes the graph's launch shapes by timing them on the graph itself (the
  * paper has no counterpart; it affects speed only, never results):
  *  - for the pull gathers of atomic rounds, the degree bin (vertices of
- *    degree <= 16, 32 or 64 gather one thread each, the others in work items
+ *    degree <= 32, 64, 128 or 256 gather one thread each, the others in work items
  *    of up to 4096 edges; see lgc_graph_set_pull_light) and the heavy
  *    gather's edges per lane per batch and lanes per work item, from (4, 32),
  *    (8, 32), (16, 32), (8, 16), (16, 16), (8, 8), (16, 8), each with 16- and
@@ -235,7 +235,7 @@ int64_t lgc_graph_batch_handoff(const lgc_graph *g);
  * gather with one thread each (in deterministic mode, fold their list in
  * one thread), the others in work items (deterministic mode: degree up to
  * 1024 one lane each, longer lists segment-parallel).  Default 32;
- * lgc_graph_autotune picks one of 16, 32, 64.  lgc_graph_set_pull_light
+ * lgc_graph_autotune picks one of 32, 64, 128, 256.  lgc_graph_set_pull_light
  * rebuilds the graph's vertex lists for 4 <= light <= 256 (LGC_EINVAL
  * otherwise); it waits for the request loop's requests on the graph.  Speed
  * only: results do not depend on it. */

@@ -2563,11 +2563,11 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
     };
     // (batch depth, lanes per item) x (16- or 8-byte shares) x light threshold
     const int cand[7][2] = {{4, 32}, {8, 32}, {16, 32}, {8, 16}, {16, 16}, {8, 8}, {16, 8}};
-    const int lights[3] = {16, 32, 64};
+    const int lights[4] = {32, 64, 128, 256};
     float best_ms = 0.f;
     int best = kPullBatch, best_group = 32, best_share = 16, best_light = g->pull_light;
     bool first = true;
-    for (int li = 0; li < 3 && st == LGC_OK; li++) {
+    for (int li = 0; li < 4 && st == LGC_OK; li++) {
       if (g->pull_light != lights[li] && (st = rebuild_pull_lists(ctx, g, lights[li])) != LGC_OK)
         break;
       dfree(ctx, hacc);

@@ -537,7 +537,7 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
         assert g.autotune() in shapes
         p, st = lgc.prnibble(g, x, 0.01, 1e-6, mode="atomic")
         assert np.array_equal(p.idx, res[0].idx) and np.array_equal(p.val, res[0].val)
-        assert g.pull_light() in (16, 32, 64)
+        assert g.pull_light() in (32, 64, 128, 256)
         # the batch hand-off threshold is one of the tuner's candidates
         assert g.batch_handoff() in {max(1 << 20, g.nnz // k) for k in (64, 16, 4)} | {2 ** 63 - 1}
         ps, sts = lgc.prnibble_batch(g, [x, int(col[0])], 0.01, 1e-6, mode="det")
