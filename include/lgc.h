@@ -231,10 +231,11 @@ int lgc_graph_autotune(lgc_graph *g, int *pull_batch, int *pull_group, int *pull
  * LGC_OPT_BATCH_HANDOFF is 0: the tuned value, else max(2^20, 2m/64);
  * INT64_MAX means never. */
 int64_t lgc_graph_batch_handoff(const lgc_graph *g);
-/* The degree bin of the graph's pull rounds: vertices of degree 1..light
- * gather with one thread each (in deterministic mode, fold their list in
- * one thread), the others in work items (deterministic mode: degree up to
- * 1024 one lane each, longer lists segment-parallel).  Default 32;
+/* The degree bin of the graph's atomic pull rounds: vertices of degree
+ * 1..light gather with one thread each, the others in work items.  The
+ * deterministic pull rounds keep their own bins at any light: degree 1..32
+ * folded in one thread each, up to 1024 one lane each, longer lists
+ * segment-parallel.  Default 32;
  * lgc_graph_autotune picks one of 32, 64, 128, 256.  lgc_graph_set_pull_light
  * rebuilds the graph's vertex lists for 4 <= light <= 256 (LGC_EINVAL
  * otherwise); it waits for the request loop's requests on the graph.  Speed

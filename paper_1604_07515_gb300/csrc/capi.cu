@@ -117,14 +117,15 @@ __global__ void gather_off_kernel(const int32_t* __restrict__ ids, int64_t k,
     out[i] = off[ids[i]];
 }
 
-// The vertices of degree > kDetBig and their 256-edge segments (built on the
-// host from the degree copy; only their list starts are read back).
+// The deterministic pull's vertices of degree (kPullLight, kDetBig], and those
+// of degree > kDetBig with their 256-edge segments (built on the host from the
+// degree copy; only their list starts are read back).
 int build_big_segments(lgc_ctx* ctx, lgc_graph* g) {
   cudaStream_t s = ctx->stream;
   {
     std::vector<int32_t> mid;
     for (int64_t v = 0; v < g->n; v++)
-      if (g->hdeg[v] > g->pull_light && g->hdeg[v] <= kDetBig) mid.push_back((int32_t)v);
+      if (g->hdeg[v] > kPullLight && g->hdeg[v] <= kDetBig) mid.push_back((int32_t)v);
     std::stable_sort(mid.begin(), mid.end(),
                      [&](int32_t a, int32_t b) { return g->hdeg[a] > g->hdeg[b]; });
     g->ndet_mid = (int64_t)mid.size();
@@ -185,12 +186,12 @@ __global__ void light_items_kernel(const int32_t* __restrict__ order, int64_t k,
   }
 }
 
-// The vertices of degree 1..pull_light grouped by degree, highest first, ids
-// ascending within a degree (a counting sort of the host degree copy).
-int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
+// The vertices of degree 1..L grouped by degree, highest first, ids
+// ascending within a degree (a counting sort of the host degree copy), into
+// *out (*nout entries).
+int build_light_list(lgc_ctx* ctx, lgc_graph* g, int L, LightItem** out, int64_t* nout) {
   cudaStream_t s = ctx->stream;
   const int64_t n = g->n;
-  const int L = g->pull_light;
   std::vector<int64_t> cnt(L + 2, 0), at(L + 2, 0);
   int64_t k = 0;
   for (int64_t v = 0; v < n; v++)
@@ -199,7 +200,7 @@ int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
     at[d] = k;
     k += cnt[d];
   }
-  g->nlight = k;
+  *nout = k;
   if (k == 0) return LGC_OK;
   std::vector<int32_t> order;
   try {
@@ -213,18 +214,30 @@ int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
   }
   int32_t* d_order = nullptr;
   LGC_TRY(dalloc_t(ctx, &d_order, k));
-  int st = dalloc_t(ctx, &g->light, k);
+  int st = dalloc_t(ctx, out, k);
   if (st == LGC_OK &&
       cudaMemcpyAsync(d_order, order.data(), 4 * k, cudaMemcpyHostToDevice, s) != cudaSuccess)
     st = LGC_ECUDA;
   if (st == LGC_OK) {
-    light_items_kernel<<<grid_for(k), kBlock, 0, s>>>(d_order, k, g->off, g->light);
+    light_items_kernel<<<grid_for(k), kBlock, 0, s>>>(d_order, k, g->off, *out);
     LGC_COUNT_LAUNCH(ctx);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
       st = LGC_ECUDA;  // (the host order goes out of scope)
   }
   dfree(ctx, d_order);
   return st;
+}
+
+// The atomic pull's light list (degree <= pull_light) and the deterministic
+// pull's (degree <= kPullLight), shared while the two bins agree.
+int build_light_items(lgc_ctx* ctx, lgc_graph* g) {
+  LGC_TRY(build_light_list(ctx, g, g->pull_light, &g->light, &g->nlight));
+  if (g->pull_light == kPullLight) {
+    g->light_det = g->light;
+    g->nlight_det = g->nlight;
+    return LGC_OK;
+  }
+  return build_light_list(ctx, g, kPullLight, &g->light_det, &g->nlight_det);
 }
 
 // The vertices of degree > kPullLight, ascending, for pull rounds, and their
@@ -285,15 +298,19 @@ int build_heavy_list(lgc_ctx* ctx, lgc_graph* g) {
 
 namespace lgc {
 
-// Rebuilds the degree-binned vertex lists of the pull rounds for light
-// threshold L: vertices of degree 1..L one thread each (grouped by degree),
-// the others in work items; in deterministic mode the lists of degree
-// (L, kDetBig] fold one lane each and longer ones segment-parallel.
+// Rebuilds the degree-binned vertex lists of the pull rounds for the atomic
+// light threshold L: vertices of degree 1..L one thread each (grouped by
+// degree), the others in work items.  The deterministic lists keep their own
+// bins whatever L is: degree 1..kPullLight one thread each, (kPullLight,
+// kDetBig] one lane each, longer ones segment-parallel.
 int rebuild_pull_lists(lgc_ctx* ctx, lgc_graph* g, int L) {
   if (L < 4 || L > 256) return LGC_EINVAL;
+  if (g->light_det != g->light) dfree(ctx, g->light_det);
   for (void* p : {(void*)g->heavy, (void*)g->items, (void*)g->big_w, (void*)g->big_seg0,
                   (void*)g->segs, (void*)g->det_mid, (void*)g->light})
     dfree(ctx, p);
+  g->light_det = nullptr;
+  g->nlight_det = 0;
   g->heavy = nullptr;
   g->items = nullptr;
   g->big_w = nullptr;
@@ -869,6 +886,7 @@ int lgc_graph_create(lgc_ctx* ctx, int64_t n, const int64_t* offsets, const int3
     dfree(ctx, g->big_seg0);
     dfree(ctx, g->segs);
     dfree(ctx, g->det_mid);
+    if (g->light_det != g->light) dfree(ctx, g->light_det);
     dfree(ctx, g->light);
     cudaStreamSynchronize(s);
     delete g;
@@ -907,6 +925,7 @@ void lgc_graph_destroy(lgc_graph* g) {
   dfree(ctx, g->big_seg0);
   dfree(ctx, g->segs);
   dfree(ctx, g->det_mid);
+  if (g->light_det != g->light) dfree(ctx, g->light_det);
   dfree(ctx, g->light);
   cudaStreamSynchronize(ctx->stream);
   delete g;

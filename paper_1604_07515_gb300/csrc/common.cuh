@@ -270,8 +270,8 @@ struct lgc_graph {
   int pull_group = 32;         // lanes per work item in heavy pull gathers (tuned)
   int pull_share = 16;         // bytes per gathered share in atomic pull gathers (tuned)
   int64_t batch_handoff = 0;   // batched PR-Nibble hand-off threshold (tuned; 0: untuned)
-  int pull_light = 32;         // pull rounds: degree <= pull_light one thread per vertex (tuned)
-  // vertices of degree > kPullLight in ascending id, for the pull edge phase
+  int pull_light = 32;         // atomic pull rounds: degree <= pull_light one thread each (tuned)
+  // vertices of degree > pull_light in ascending id, for the atomic pull edge phase
   int32_t* heavy = nullptr;
   int64_t nheavy = 0;
   // their adjacency cut into work items of at most kPullItem edges (one
@@ -291,15 +291,20 @@ struct lgc_graph {
   int64_t nbig = 0;
   DetSeg* segs = nullptr;
   int64_t nsegs = 0;
-  // vertices of degree 1..kPullLight grouped by degree (atomic pull rounds)
+  // vertices of degree 1..pull_light grouped by degree (atomic pull rounds)
   LightItem* light = nullptr;
   int64_t nlight = 0;
+  // the deterministic pull's own list of vertices of degree 1..kPullLight
+  // (its light lists fold in one thread, so its bin stays at kPullLight);
+  // the atomic list itself while pull_light == kPullLight
+  LightItem* light_det = nullptr;
+  int64_t nlight_det = 0;
 };
 
 namespace lgc {
 // A pull round handles vertices of degree <= kPullLight with one thread each
 // and the rest in work items of at most kPullItem edges.
-constexpr int kPullLight = 32;  // the default of lgc_graph::pull_light
+constexpr int kPullLight = 32;  // default of lgc_graph::pull_light; the deterministic bin
 constexpr int kDetBig = 1024;  // longer lists fold segment-parallel in deterministic mode
 constexpr int kDetSeg = 256;
 constexpr int kPullItem = 4096;

@@ -2088,9 +2088,10 @@ struct PushWork {
       if (det) {
         // every gather ORs its qualifying vertices into the cleared bitmap
         LGC_CUDA_TRY(cudaMemsetAsync(pq.ptr, 0, 4 * words, s));
-        if (g->nlight > 0) {
-          const int lgl = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), (ctx->sms * 32));
-          pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light, g->nlight, g->col, psh.ptr, D, c,
+        if (g->nlight_det > 0) {
+          const int lgl =
+              (int)std::min<int64_t>(ceil_div(g->nlight_det, kBlock), (ctx->sms * 32));
+          pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light_det, g->nlight_det, g->col, psh.ptr, D, c,
                                                    fmode, pq.ptr, ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
         }

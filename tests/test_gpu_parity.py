@@ -555,9 +555,10 @@ def test_pull_batch_depths_bit_identical(ctx_notrace):
 
 @pytest.mark.parametrize("light", [4, 16, 64, 256])
 def test_pull_degree_bins(ctx, light):
-    """The pull rounds' degree bin (vertices of degree <= light gather one
-    thread each; deterministic mode: fold one thread each, then one lane each
-    up to degree 1024, then segment-parallel) changes speed only: HK-PR's
+    """The atomic pull rounds' degree bin (vertices of degree <= light gather
+    one thread each; deterministic mode keeps its own bins at any light: one
+    thread each up to degree 32, one lane each up to 1024, then
+    segment-parallel) changes speed only: HK-PR's
     near-global pull rounds and PR-Nibble with every round a pull round give
     the oracle's results, bit for bit in deterministic mode."""
     off, col = inputs.rmat(16, seed=1)
