@@ -686,8 +686,8 @@ def main():
                     help="skip the many-seed, scale-26 and serving measurements")
     ap.add_argument("--no-det", action="store_true", help="skip the deterministic-mode step")
     ap.add_argument("--pull-shape", default="",
-                    help="heavy pull gather shape 'batch,lanes,share_bytes' instead of the "
-                         "graph's autotuned one (e.g. 8,32,8)")
+                    help="heavy pull gather shape 'batch,lanes,share_bytes[,degree_bin]' "
+                         "instead of the graph's autotuned one (e.g. 16,32,8,256)")
     ap.add_argument("--algos", default=",".join(ALGOS),
                     help="comma-separated subset of the step (for profiling one diffusion)")
     ap.add_argument("--case", default="", choices=[""] + list(CASES),
@@ -756,10 +756,13 @@ def main():
     ctx = lgc.Context(dev, stream)
     g = lgc.Graph(ctx, off, col)
     if args.pull_shape:
-        pull_shape = tuple(int(v) for v in args.pull_shape.split(","))
+        fixed = tuple(int(v) for v in args.pull_shape.split(","))
+        pull_shape = fixed[:3]
         for opt, v in zip((lgc.OPT_PULL_BATCH, lgc.OPT_PULL_GROUP, lgc.OPT_PULL_SHARE),
                           pull_shape):
             ctx.set_option(opt, v)
+        if len(fixed) > 3:
+            g.set_pull_light(fixed[3])
     else:
         pull_shape = g.autotune()  # launch-shape tuning on this graph, before any timing
     pull_light = g.pull_light()

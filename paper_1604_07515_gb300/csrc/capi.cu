@@ -557,7 +557,8 @@ static void serve_lane(Serve* S, lgc_ctx* lc) {
       std::vector<int64_t> slots(seeds.size());
       int st = e->E.add((int64_t)seeds.size(), seeds.data(), prms.data(), slots.data());
       if (st == LGC_OK) {
-        for (size_t i = 0; i < slots.size(); i++) e->jobs[slots[i]] = LaneJob{kv.second[i], t_admit};
+        for (size_t i = 0; i < slots.size(); i++)
+          e->jobs[slots[i]] = LaneJob{kv.second[i], t_admit};
       } else {
         for (size_t i = 0; i < seeds.size(); i++) {
           int64_t sl = -1;

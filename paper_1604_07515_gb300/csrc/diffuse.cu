@@ -764,8 +764,12 @@ __global__ void pull_scatter_kernel(int64_t nf, const int32_t* __restrict__ fv,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = fv[i];
+    if (clear) {
+      sh[v] = 0.0;
+      continue;
+    }
     const double x = share[i];
-    sh[v] = clear ? 0.0 : (pull_member(x) ? x : -0.0);
+    sh[v] = pull_member(x) ? x : -0.0;
   }
 }
 
@@ -1103,19 +1107,19 @@ __global__ void __launch_bounds__(kBlock)
 // range[1] = max biased exponent (both 0 before the round).
 // shx[v] = {X, flag} for a frontier vertex v, {0, 0} otherwise.
 // ---------------------------------------------------------------------------
-__global__ void share_range_kernel(int64_t nf, const double* __restrict__ share,
-                                   int32_t* __restrict__ range) {
-  __shared__ int s_r[2][kBlock / 32];
-  int emin = 0, emax = 0;  // emin holds 2047 - be
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = fx_bits(share[i]) & kFxMask;
-    if (b) {
-      const int be = fx_bexp(b);
-      emin = max(emin, 2047 - be);
-      emax = max(emax, be);
-    }
+// A share's contribution to the range (emin holds 2047 - biased exponent).
+__device__ inline void range_take(double x, int& emin, int& emax) {
+  const uint64_t b = fx_bits(x) & kFxMask;
+  if (b) {
+    const int be = fx_bexp(b);
+    emin = max(emin, 2047 - be);
+    emax = max(emax, be);
   }
+}
+
+// The block's range into range[] (every thread of the block calls it).
+__device__ inline void range_flush(int emin, int emax, int32_t* __restrict__ range) {
+  __shared__ int s_r[2][kBlock / 32];
   // one atomic pair per block: same-address atomics serialise in L2
   emin = __reduce_max_sync(0xffffffffu, emin);
   emax = __reduce_max_sync(0xffffffffu, emax);
@@ -1135,6 +1139,45 @@ __global__ void share_range_kernel(int64_t nf, const double* __restrict__ share,
       atomicMax(&range[1], emax);
     }
   }
+}
+
+__global__ void share_range_kernel(int64_t nf, const double* __restrict__ share,
+                                   int32_t* __restrict__ range) {
+  int emin = 0, emax = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x)
+    range_take(share[i], emin, emax);
+  range_flush(emin, emax, range);
+}
+
+// HK-PR vertexMap of a pull round gathering 8-byte shares: the step of
+// vmap_hkpr_kernel, with the share written straight into the per-vertex
+// array the gathers read (pull_scatter_kernel's membership encoding) and, in
+// atomic mode (range non-null, zeroed before), the shares' exponent range
+// reduced here; a pull round needs no push records.
+__global__ void vmap_hkpr_pull_kernel(int64_t nf, const int32_t* __restrict__ fv,
+                                      const int32_t* __restrict__ fs, Table S, Table P,
+                                      const int32_t* __restrict__ deg, double t, int j, int last,
+                                      double* __restrict__ sh, int32_t* __restrict__ range,
+                                      Counters* C) {
+  int emin = 0, emax = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int ins = 0;
+    if (i < nf) {
+      const int32_t v = fv[i];
+      const double r = fs[i] >= 0 ? *tb_val(S, fs[i]) : 0.0;
+      const int64_t d = deg[v];
+      const int64_t ps = tb_find_or_insert(P, v, &ins, &C->err);
+      if (ps >= 0) *tb_val(P, ps) = *tb_val(P, ps) + r;
+      const double x = last ? r / (double)d : (t * r) / ((double)(j + 1) * (double)d);
+      sh[v] = pull_member(x) ? x : -0.0;
+      range_take(x, emin, emax);
+    }
+    count_inserted(ins, &C->aux);
+  }
+  if (range) range_flush(emin, emax, range);
 }
 
 __device__ inline int round_scale(const int32_t* range, int g) {
@@ -1392,28 +1435,47 @@ __global__ void bits_count_kernel(const uint32_t* __restrict__ bits, int64_t wor
     cnt[w] = __popc(bits[w]);
 }
 
-// One thread per vertex (a warp per bitmap word): a set bit's vertex goes to
-// the word's position plus the set bits below it, so a warp's writes are
-// consecutive.  The degrees are summed per thread over the grid-stride loop
-// and added once per block (one address: per-warp atomics would queue on it).
+// A warp per 32 consecutive bitmap words: lane k loads word k and its
+// position, then the warp takes the words in turn, a set bit's vertex going
+// to the word's position plus the set bits below it (consecutive writes),
+// with the degree loads of eight words in flight at once.  The degrees are
+// summed per thread and added once per block (one address: per-warp atomics
+// would queue on it).
 __global__ void bits_write_kernel(const uint32_t* __restrict__ bits, int64_t words,
                                   const int64_t* __restrict__ pos, const int32_t* __restrict__ deg,
                                   int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
   __shared__ int64_t s_red[kBlock / 32];
   const int lane = threadIdx.x & 31;
+  const uint32_t below = (1u << lane) - 1u;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t dsum = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - lane < words * 32;
-       v += (int64_t)gridDim.x * blockDim.x) {  // whole warps are in range or out
-    const uint32_t q = bits[v >> 5];
-    if ((q >> lane) & 1u) {
-      const int64_t at = pos[v >> 5] + __popc(q & ((1u << lane) - 1u));
-      if (at < ncap) {
-        nfv[at] = (int32_t)v;
-        nfs[at] = (int32_t)v;
-      } else {
-        atomicOr(&C->err, kErrFrontierOverflow);
+  for (int64_t w0 = warp0 * 32; w0 < words; w0 += nwarps * 32) {  // whole warps
+    const int64_t w = w0 + lane;
+    const uint32_t q = w < words ? bits[w] : 0u;
+    const int64_t p = w < words ? pos[w] : 0;
+    if (!__any_sync(0xffffffffu, q != 0u)) continue;
+    for (int k0 = 0; k0 < 32; k0 += 8) {
+      int32_t dk[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t qk = __shfl_sync(0xffffffffu, q, k0 + k);
+        const int64_t pk = __shfl_sync(0xffffffffu, p, k0 + k);
+        dk[k] = 0;
+        if ((qk >> lane) & 1u) {
+          const int64_t v = (w0 + k0 + k) * 32 + lane;
+          const int64_t at = pk + __popc(qk & below);
+          if (at < ncap) {
+            nfv[at] = (int32_t)v;
+            nfs[at] = (int32_t)v;
+          } else {
+            atomicOr(&C->err, kErrFrontierOverflow);
+          }
+          dk[k] = deg[v];
+        }
       }
-      dsum += deg[v];
+#pragma unroll
+      for (int k = 0; k < 8; k++) dsum += dk[k];
     }
   }
   for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
@@ -2009,9 +2071,9 @@ struct PushWork {
                                                      segslot.ptr, longs.ptr, nlong.ptr,
                                                      ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
-      fold_long_kernel<<<(ctx->sms * 4), kBlock, 0, s>>>(rv.ptr, nrec, segstart.ptr, nseg, longs.ptr,
-                                                   nlong.ptr, D, g->deg, c, fmode, qflag.ptr,
-                                                   segv.ptr, segslot.ptr);
+      fold_long_kernel<<<ctx->sms * 4, kBlock, 0, s>>>(rv.ptr, nrec, segstart.ptr, nseg,
+                                                        longs.ptr, nlong.ptr, D, g->deg, c, fmode,
+                                                        qflag.ptr, segv.ptr, segslot.ptr);
       LGC_COUNT_LAUNCH(ctx);
       LGC_CUDA_TRY(cudaGetLastError());
       if (fmode != kFmNone) {
@@ -2028,22 +2090,24 @@ struct PushWork {
     return read_counters(out);
   }
 
-  // Pull round into the dense table D.  The frontier's shares (share[], from
-  // the vertexMap) are scattered into the per-vertex array, every vertex
-  // gathers (in adjacency order in deterministic mode, heavy vertices by a
-  // tree reduction in atomic mode), the qualifying vertices are compacted in
-  // ascending id, and the per-vertex array is cleared again (O(|F|)).
-  int pull_phase(const Table& D, double c, int fmode, Counters* out, bool det) {
+  // The bytes per gathered share of a pull round: atomic mode gathers 16-byte
+  // fixed-point records or 8-byte doubles (the graph's tuned choice);
+  // deterministic mode always doubles.
+  int pull_share_bytes(bool det) const {
+    return det ? 8 : (ctx->pull_share ? ctx->pull_share : g->pull_share);
+  }
+
+  // The pull rounds' per-vertex arrays (zeroed at first use; every round
+  // leaves them zeroed again).
+  int pull_reserve(bool det) {
     cudaStream_t s = ctx->stream;
-    const int64_t n = g->n, words = (n + 31) / 32, nf = F.size;
+    const int64_t n = g->n, words = (n + 31) / 32;
     if (!pull_ready) {
       LGC_TRY(pq.reserve(ctx, words));
       LGC_TRY(pcnt.reserve(ctx, words));
       pull_ready = true;
     }
-    // atomic mode gathers 16-byte fixed-point records or 8-byte doubles
-    // (the graph's tuned choice); deterministic mode always doubles
-    const int sb = det ? 8 : (ctx->pull_share ? ctx->pull_share : g->pull_share);
+    const int sb = pull_share_bytes(det);
     if (sb == 8 && !psh.ptr) {
       LGC_TRY(psh.reserve(ctx, n));
       LGC_CUDA_TRY(cudaMemsetAsync(psh.ptr, 0, 8 * n, s));
@@ -2061,18 +2125,34 @@ struct PushWork {
       LGC_CUDA_TRY(cudaMemsetAsync(phcnt.ptr, 0, 4 * (g->nheavy + 1), s));
       LGC_CUDA_TRY(cudaMemsetAsync(phtouch.ptr, 0, 4 * (g->nheavy + 1), s));
     }
+    return LGC_OK;
+  }
+
+  // Pull round into the dense table D.  The frontier's shares (share[], from
+  // the vertexMap) are scattered into the per-vertex array -- unless the
+  // vertexMap wrote them there itself (scattered: 8-byte shares, with the
+  // range in atomic mode) --, every vertex gathers (in adjacency order in
+  // deterministic mode, heavy vertices by a tree reduction in atomic mode),
+  // the qualifying vertices are compacted in ascending id, and the
+  // per-vertex array is cleared again (O(|F|)).
+  int pull_phase(const Table& D, double c, int fmode, Counters* out, bool det,
+                 bool scattered = false) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n, words = (n + 31) / 32, nf = F.size;
+    LGC_TRY(pull_reserve(det));
+    const int sb = pull_share_bytes(det);
     const int32_t ncap = (int32_t)G.v.cap;
     // sums of at most max_deg terms: max_deg < 2^gb
     int gb = 1;
     while (gb < 62 && (int64_t{1} << gb) <= g->max_deg) gb++;
-    if (det) {
+    if (!scattered && det) {
       pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
       LGC_COUNT_LAUNCH(ctx);
-    } else {
+    } else if (!scattered) {
       LGC_CUDA_TRY(cudaMemsetAsync(prange.ptr, 0, 8, s));
       const int64_t rb = ceil_div(nf, kBlock);
-      share_range_kernel<<<(int)(rb < 1 ? 1 : rb > (ctx->sms * 4) ? (ctx->sms * 4) : rb), kBlock, 0, s>>>(
-          nf, share.ptr, prange.ptr);
+      const int rg = (int)std::max<int64_t>(1, std::min<int64_t>(rb, ctx->sms * 4));
+      share_range_kernel<<<rg, kBlock, 0, s>>>(nf, share.ptr, prange.ptr);
       LGC_COUNT_LAUNCH(ctx);
       if (sb == 8) {
         pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 0);
@@ -2091,8 +2171,8 @@ struct PushWork {
         if (g->nlight_det > 0) {
           const int lgl =
               (int)std::min<int64_t>(ceil_div(g->nlight_det, kBlock), (ctx->sms * 32));
-          pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light_det, g->nlight_det, g->col, psh.ptr, D, c,
-                                                   fmode, pq.ptr, ctx->d_counters);
+          pull_light_kernel<<<lgl, kBlock, 0, s>>>(g->light_det, g->nlight_det, g->col, psh.ptr,
+                                                   D, c, fmode, pq.ptr, ctx->d_counters);
           LGC_COUNT_LAUNCH(ctx);
         }
         if (g->ndet_mid > 0) {
@@ -2158,7 +2238,8 @@ struct PushWork {
       bits_count_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr);
       LGC_COUNT_LAUNCH(ctx);
       LGC_TRY(scan_i64(ctx, pcnt.ptr, pcnt.ptr, words, false, total.ptr));
-      const int wg = std::min(grid_for(words * 32), (ctx->sms * 8));
+      const int wg = (int)std::max<int64_t>(
+          1, std::min<int64_t>(ceil_div(words, 32 * (kBlock / 32)), ctx->sms * 8));
       bits_write_kernel<<<wg, kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg, G.v.ptr, G.s.ptr,
                                                ncap, ctx->d_counters);
       LGC_COUNT_LAUNCH(ctx);
@@ -2487,6 +2568,19 @@ int fresh_dense(lgc_ctx* ctx, Table* T, int64_t n) {
   return table_create_dense(ctx, T, n, false);
 }
 
+// An empty dense table for a pull round's destination: only the presence
+// bitmap is cleared, since the gathers set a vertex's value when they make it
+// a key and never read the value of a non-key, and the table's later readers
+// read keys only.
+int fresh_dense_keys(lgc_ctx* ctx, Table* T, int64_t n) {
+  if (T->dense && T->cap == n && !T->p) {
+    LGC_CUDA_TRY(cudaMemsetAsync(T->bits, 0, sizeof(uint32_t) * ((n + 31) / 32), ctx->stream));
+    return LGC_OK;
+  }
+  table_destroy(ctx, T);
+  return table_create_dense(ctx, T, n, false);
+}
+
 // Before a round that may add up to `add` keys to a persistent table holding
 // `count`: switch to the dense form once it may reach n/8 keys, else grow the
 // hashed form to stay at most half full.  Frontier slots are re-resolved.
@@ -2577,7 +2671,8 @@ int autotune_pull(lgc_ctx* ctx, lgc_graph* g) {
       hacc = nullptr;
       hcnt = nullptr;
       htouch = nullptr;
-      if ((st = dalloc_t(ctx, &hacc, g->nheavy + 1)) || (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
+      if ((st = dalloc_t(ctx, &hacc, g->nheavy + 1)) ||
+          (st = dalloc_t(ctx, &hcnt, g->nheavy + 1)) ||
           (st = dalloc_t(ctx, &htouch, g->nheavy + 1)))
         break;
       if (cudaMemsetAsync(hacc, 0, sizeof(Fx) * (g->nheavy + 1), s) ||
@@ -3035,7 +3130,21 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
         break;
       if ((status = W.reserve_frontier_scratch(nf)) != LGC_OK) break;
       if ((status = W.reset_counters()) != LGC_OK) break;
-      {
+      // a pull round of 8-byte shares takes them straight from the vertexMap
+      const bool scattered = pull && W.pull_share_bytes(det) == 8;
+      if (scattered) {
+        if ((status = W.pull_reserve(det)) != LGC_OK) break;
+        if (!det && cudaMemsetAsync(W.prange.ptr, 0, 8, ctx->stream) != cudaSuccess) {
+          status = LGC_ECUDA;
+          break;
+        }
+        // per vertex: fv, fs 8, r 8, degree 4, p read-modify-write 16, share 8
+        ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 44.0 * nf);
+        vmap_hkpr_pull_kernel<<<vgrid(ctx, nf), kBlock, 0, ctx->stream>>>(
+            nf, W.F.v.ptr, W.F.s.ptr, Rc, P, g->deg, t, j, last ? 1 : 0, W.psh.ptr,
+            det ? nullptr : W.prange.ptr, ctx->d_counters);
+        LGC_COUNT_LAUNCH(ctx);
+      } else {
         ProfScope ps(ctx, LGC_PROF_VERTEXMAP, 64.0 * nf);
         vmap_hkpr_kernel<<<vgrid(ctx, nf), kBlock, 0, ctx->stream>>>(
             nf, W.F.v.ptr, W.F.s.ptr, Rc, P, g->off, t, j, last ? 1 : 0, W.share.ptr, W.cnt.ptr,
@@ -3052,13 +3161,14 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
       Counters C;
       if (!last) {
         const int64_t need = min64(g->n, W.F.edges);
-        status = pull ? fresh_dense(ctx, &Rn, g->n) : table_fresh(ctx, &Rn, need, g->n, false);
+        status = pull ? fresh_dense_keys(ctx, &Rn, g->n)
+                      : table_fresh(ctx, &Rn, need, g->n, false);
         if (status != LGC_OK) break;  // r' = {}
         if ((status = W.reserve_next(need)) != LGC_OK) break;
         const double cj = c[j + 1];
         const int fm = cj > 0.0 ? kFmThreshold : kFmInserted;
         if (pull)
-          status = W.pull_phase(Rn, cj, fm, &C, det);
+          status = W.pull_phase(Rn, cj, fm, &C, det, scattered);
         else
           status = W.edge_phase(Rn, cj, fm, det, false, W.F.edges, &C,
                                 use_bulk(det, Rn, W.F.edges, g->n));
@@ -3076,7 +3186,7 @@ int run_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_hkpr_params* prm, 
         if ((status = W.reserve_next(1)) != LGC_OK) break;
         // no frontier after the last level: fire-and-forget adds in either form
         if (pull)
-          status = W.pull_phase(P, 0.0, kFmNone, &C, det);
+          status = W.pull_phase(P, 0.0, kFmNone, &C, det, scattered);
         else
           status = W.edge_phase(P, 0.0, kFmNone, det, false, W.F.edges, &C, !det);
         if (status != LGC_OK) break;

@@ -756,8 +756,9 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
                                                           d_err + 1, kErrDuplicate);
         LGC_COUNT_LAUNCH(ctx);
         ProfScope ps_(ctx, LGC_PROF_SWEEP, 12.0 * (double)V + 24.0 * (double)N);
-        bsweep_cross_kernel<<<(int)(tiles < (ctx->sms * 16) ? tiles : (ctx->sms * 16)), kBlock, 0, s>>>(
-            g->off, g->col, order, sk, d_nbeg, vol, N, V, tile0, d_tabs, before);
+        const int cg = (int)std::min<int64_t>(tiles, ctx->sms * 16);
+        bsweep_cross_kernel<<<cg, kBlock, 0, s>>>(g->off, g->col, order, sk, d_nbeg, vol, N, V,
+                                                  tile0, d_tabs, before);
         LGC_COUNT_LAUNCH(ctx);
       }
       sweep_delta_kernel<<<grid_for(N), kBlock, 0, s>>>(d_i, before, N, cut);
