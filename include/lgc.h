@@ -191,12 +191,19 @@ enum {
                                    as they are admitted); 0 runs them on the worker
                                    contexts like the other requests.  Default 1024; set
                                    before the first lgc_submit (LGC_EBUSY after) */
-  LGC_OPT_HK_THRESHOLD_SIGN = 13 /* debug: the sign of the exponent in lgc_hkpr's entry
+  LGC_OPT_HK_THRESHOLD_SIGN = 13, /* debug: the sign of the exponent in lgc_hkpr's entry
                                    thresholds.  +1 (default): e^t eps d(v) / (2 N psi_j),
                                    as in the parallel HK-PR figure (Sec. 3.4); -1: e^-t,
                                    as in the sequential description of Sec. 3.4, which
                                    makes the diffusion spread much further.  Request-loop
                                    workers always use +1 */
+  LGC_OPT_SWEEP_CROSS = 15      /* lgc_sweep's crossing counts (step S5): 0 (default)
+                                   automatic (vertex-centric for a support of at least n/32
+                                   vertices), 1 edge-balanced over the swept vertices'
+                                   edges, 2 vertex-centric over the graph's degree-binned
+                                   lists whenever the ranks are kept in a dense array (a
+                                   support of at least n/64 vertices, n >= 1024); same
+                                   results either way */
 };
 int lgc_ctx_set_option(lgc_ctx *ctx, int option, int64_t value);
 /* Waits for all work issued on the context's stream. */

@@ -1084,6 +1084,7 @@ int BatchEngine::round() {
                                cudaMemcpyDeviceToHost, s));
   LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, gsize, 16, cudaMemcpyDeviceToHost, s));
   LGC_CUDA_TRY(cudaStreamSynchronize(s));
+  LGC_TRY(sort_check(ctx));
   const int32_t* gs = (const int32_t*)ctx->h_scratch;
   if (gs[1] != 0 || gs[2] != 0 || gs[3] != 0) return LGC_ETABLEFULL;
   int64_t next = 0;

@@ -780,6 +780,10 @@ int lgc_ctx_set_option(lgc_ctx* ctx, int option, int64_t value) {
       if (value != 1 && value != -1) return LGC_EINVAL;
       ctx->hk_threshold_sign = (int)value;
       return LGC_OK;
+    case LGC_OPT_SWEEP_CROSS:
+      if (value < 0 || value > 2) return LGC_EINVAL;
+      ctx->sweep_cross = (int)value;
+      return LGC_OK;
     case LGC_OPT_SERVE_MEM_BUDGET:
       if (value <= 0) return LGC_EINVAL;
       ctx->serve_mem_budget = value;

@@ -47,6 +47,9 @@ int ctx_init(lgc_ctx* ctx, int device, cudaStream_t stream) {
   LGC_CUDA_TRY(cudaHostAlloc((void**)&ctx->h_scratch, 8 * sizeof(int64_t), cudaHostAllocDefault));
   LGC_CUDA_TRY(cudaMalloc((void**)&ctx->d_counters, sizeof(Counters)));
   LGC_CUDA_TRY(cudaMemsetAsync(ctx->d_counters, 0, sizeof(Counters), ctx->stream));
+  LGC_CUDA_TRY(cudaHostAlloc((void**)&ctx->h_sort_err, sizeof(int), cudaHostAllocMapped));
+  *ctx->h_sort_err = 0;
+  LGC_CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->d_sort_err, ctx->h_sort_err, 0));
   return LGC_OK;
 }
 
@@ -56,6 +59,15 @@ void ctx_fini(lgc_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   ctx->event_pool.clear();
   if (ctx->d_endpoints) cudaFree(ctx->d_endpoints);
+  dfree(ctx, ctx->sort_status);
+  dfree(ctx, ctx->sort_aux);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->h_sort_err) cudaFreeHost(ctx->h_sort_err);
+  ctx->sort_status = nullptr;
+  ctx->sort_aux = nullptr;
+  ctx->sort_status_cap = 0;
+  ctx->h_sort_err = nullptr;
+  ctx->d_sort_err = nullptr;
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);

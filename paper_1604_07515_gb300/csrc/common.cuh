@@ -204,9 +204,19 @@ struct lgc_ctx {
   int pull_share = 0;          // LGC_OPT_PULL_SHARE: 0 = the graph's tuned value
   int64_t batch_handoff = 0;   // LGC_OPT_BATCH_HANDOFF: 0 default, -1 never
   int hk_threshold_sign = 1;   // LGC_OPT_HK_THRESHOLD_SIGN: +1 (e^t, default) or -1 (e^-t)
+  int sweep_cross = 0;         // LGC_OPT_SWEEP_CROSS: 0 automatic, 1 edge-balanced, 2 vertex-centric
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   int64_t serve_lane_seeds = 1024;  // LGC_OPT_SERVE_LANE
+  // the radix sort's per-tile status words (see prim.cu), their pass epoch,
+  // its histogram and tile counters, and a failed-wait flag in mapped pinned
+  // host memory (the device writes it; the host reads it after a sync)
+  unsigned long long* sort_status = nullptr;
+  int64_t sort_status_cap = 0;
+  uint32_t sort_epoch = 0;
+  unsigned long long* sort_aux = nullptr;
+  int* h_sort_err = nullptr;
+  int* d_sort_err = nullptr;
   // small pinned host block for per-round read-back
   lgc::Counters* h_counters = nullptr;
   lgc::Counters* d_counters = nullptr;
@@ -469,3 +479,16 @@ void profile_collect(lgc_ctx* ctx);
 
 // Counts one kernel launch on ctx.
 #define LGC_COUNT_LAUNCH(ctx) ((ctx)->n_launches++)
+
+namespace lgc {
+// LGC_ECUDA (once) if a radix sort on the context gave up a wait; call
+// after the context's stream has synchronised.
+inline int sort_check(lgc_ctx* ctx) {
+  volatile int* e = ctx->h_sort_err;
+  if (e && *e) {
+    *e = 0;
+    return LGC_ECUDA;
+  }
+  return LGC_OK;
+}
+}  // namespace lgc

@@ -1931,6 +1931,7 @@ struct PushWork {
     LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_counters, ctx->d_counters, sizeof(Counters),
                                  cudaMemcpyDeviceToHost, ctx->stream));
     LGC_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    LGC_TRY(sort_check(ctx));
     *out = *ctx->h_counters;
     if (out->err & kErrTableFull) return LGC_ETABLEFULL;
     if (out->err & kErrFrontierOverflow) return LGC_ETABLEFULL;

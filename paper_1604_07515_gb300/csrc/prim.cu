@@ -1,4 +1,6 @@
 // Prefix sums and LSD radix sort, written for sm_103a.
+#include <algorithm>
+
 #include "prim.cuh"
 
 namespace lgc {
@@ -240,6 +242,202 @@ __global__ void radix_scatter_kernel(const K* __restrict__ keys_in, const V* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// LSD radix sort with one launch per 8-bit digit, after the single-pass
+// scheme of Adinets and Merrill ("Onesweep", 2022): one histogram launch
+// counts every digit position of every key; each digit pass then takes
+// tiles in the order its blocks start (a counter, so every earlier tile
+// belongs to a block already running), ranks the tile's keys by digit in
+// shared memory (warps own contiguous runs; __match_any_sync orders equal
+// digits by lane, so equal keys keep their order), publishes the tile's
+// count per digit, adds up the counts of the tiles before it by a
+// decoupled look-back (a published inclusive prefix ends the walk), and
+// writes the keys digit run by digit run.  A pass whose digit is the same
+// in every key (the histogram shows it) is skipped; which buffer holds a
+// pass's input follows from the histogram on the device.
+//
+// A status word: epoch (24 bits) | state (2 bits: aggregate, inclusive
+// prefix) | count (38 bits).  Every pass has its own epoch, so the status
+// array is cleared only when it is (re)allocated or the epochs wrap; a word
+// of another epoch is "not yet published".  A look-back wait that exceeds
+// kOsSpinLimit polls (it cannot, as every earlier tile's block is running)
+// records the failure in *err and counts the tile as empty.
+// ---------------------------------------------------------------------------
+constexpr int kOsItems = 8;
+constexpr int kOsTile = kBlock * kOsItems;  // 2048 keys
+constexpr uint64_t kOsCount = (1ull << 38) - 1;
+constexpr uint64_t kOsAgg = 1ull << 38;
+constexpr uint64_t kOsIncl = 2ull << 38;
+constexpr int kOsSpinLimit = 1 << 22;
+constexpr int64_t kSortAuxWords = 8 * 256 + 4;  // histogram of 8 digit positions, 8 counters
+static_assert(kBlock == kRadix, "one thread per digit");
+
+__device__ inline uint64_t os_word(uint32_t epoch, uint64_t state, uint64_t count) {
+  return ((uint64_t)epoch << 40) | state | count;
+}
+
+// Counts of every digit position q < D of the keys into hist[q * 256 + d]
+// (zeroed before).  A warp whose keys share a digit adds them at once.
+template <class K>
+__global__ void os_hist_kernel(const K* __restrict__ keys, int64_t n, int D,
+                               unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t h[8 * kRadix];
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kBlock) h[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {  // uniform in the block
+    const int64_t i = base + threadIdx.x;
+    const bool ok = i < n;
+    const K k = ok ? keys[i] : (K)0;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);  // lane 0 is in it if any lane is
+    for (int q = 0; q < D; q++) {
+      const int d = (int)((k >> (8 * q)) & (K)0xFF);
+      const int d0 = __shfl_sync(0xffffffffu, d, 0);
+      if (__all_sync(0xffffffffu, !ok || d == d0)) {
+        if (lane == 0 && act) atomicAdd(&h[q * kRadix + d0], (uint32_t)__popc(act));
+      } else if (ok) {
+        atomicAdd(&h[q * kRadix + d], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < D * kRadix; i += kBlock)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// Whether digit pass q is skipped: one digit holds all n keys.  Called by
+// every thread of the block (thread t reads digit t).
+__device__ inline bool os_trivial(const unsigned long long* hist, int q, int64_t n) {
+  return __syncthreads_or(hist[q * kRadix + threadIdx.x] == (unsigned long long)n) != 0;
+}
+
+template <class K, class V>
+__global__ void __launch_bounds__(kBlock)
+    os_pass_kernel(K* keys0, V* vals0, K* keys1, V* vals1, int64_t n, int pass,
+                   const unsigned long long* __restrict__ hist, unsigned int* ctr,
+                   unsigned long long* status, uint32_t epoch, int* err, int has_vals) {
+  __shared__ int wcnt[kWarps][kRadix];
+  __shared__ int bstart[kRadix];
+  __shared__ unsigned long long gbase[kRadix];
+  __shared__ int64_t s_red[kBlock / 32];
+  __shared__ K skey[kOsTile];
+  __shared__ V sval[kOsTile];
+  __shared__ int64_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the pass's input buffer: one swap per pass before it that was not skipped
+  int swaps = 0;
+  for (int q = 0; q < pass; q++) swaps += os_trivial(hist, q, n) ? 0 : 1;
+  if (os_trivial(hist, pass, n)) return;  // the same in every block
+  const K* kin = (swaps & 1) ? keys1 : keys0;
+  const V* vin = (swaps & 1) ? vals1 : vals0;
+  K* kout = (swaps & 1) ? keys0 : keys1;
+  V* vout = (swaps & 1) ? vals0 : vals1;
+  if (tid == 0) s_tile = (int64_t)atomicAdd(&ctr[pass], 1u);
+  for (int w = 0; w < kWarps; w++) wcnt[w][tid] = 0;
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int shift = 8 * pass;
+  // rank: warp w owns keys [w * 32 kOsItems, (w + 1) * 32 kOsItems) of the tile
+  const int64_t base = tile * kOsTile + (int64_t)warp * (32 * kOsItems);
+  K key[kOsItems];
+  V val[kOsItems];
+  int rank[kOsItems];
+  int digit[kOsItems];
+  const unsigned lt = (1u << lane) - 1;
+#pragma unroll
+  for (int k = 0; k < kOsItems; k++) {
+    const int64_t i = base + (int64_t)k * 32 + lane;
+    const bool ok = i < n;
+    key[k] = ok ? kin[i] : (K)0;
+    if (has_vals) val[k] = ok ? vin[i] : V();
+  }
+#pragma unroll
+  for (int k = 0; k < kOsItems; k++) {
+    const int64_t i = base + (int64_t)k * 32 + lane;
+    const int d = i < n ? (int)((key[k] >> shift) & (K)0xFF) : kRadix;  // kRadix: padding
+    digit[k] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int before = d < kRadix ? wcnt[warp][d] : 0;
+    __syncwarp();
+    rank[k] = before + __popc(peers & lt);
+    if (lane == __ffs(peers) - 1 && d < kRadix) wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread d: the digit's prefix over warps, the tile's count, published
+  const int d = tid;
+  int cnt = 0;
+  for (int w = 0; w < kWarps; w++) {
+    const int c = wcnt[w][d];
+    wcnt[w][d] = cnt;
+    cnt += c;
+  }
+  volatile unsigned long long* st = status + tile * kRadix + d;
+  *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)cnt);
+  int64_t tot;
+  bstart[d] = (int)(block_inclusive_scan(cnt, s_red, &tot) - cnt);
+  const int64_t h = (int64_t)hist[pass * kRadix + d];
+  const int64_t gofs = block_inclusive_scan(h, s_red, &tot) - h;
+  // look-back: the counts of this digit in the tiles before this one
+  uint64_t excl = 0;
+  if (tile > 0) {
+    for (int64_t j = tile - 1; j >= 0; j--) {
+      const volatile unsigned long long* pj = status + j * kRadix + d;
+      uint64_t w = *pj;
+      for (int spins = 0; (uint32_t)(w >> 40) != epoch; w = *pj) {
+        if (++spins > kOsSpinLimit) {
+          atomicOr(err, 1);
+          w = os_word(epoch, kOsIncl, 0);
+          break;
+        }
+        if (spins > 16) __nanosleep(64);
+      }
+      excl += w & kOsCount;
+      if (w & kOsIncl) break;
+    }
+    *st = os_word(epoch, kOsIncl, excl + (uint64_t)cnt);
+  }
+  gbase[d] = (unsigned long long)gofs + excl;
+  __syncthreads();
+  // the tile in digit order in shared memory, then out run by run
+#pragma unroll
+  for (int k = 0; k < kOsItems; k++) {
+    const int dk = digit[k];
+    if (dk < kRadix) {
+      const int lp = bstart[dk] + wcnt[warp][dk] + rank[k];
+      skey[lp] = key[k];
+      if (has_vals) sval[lp] = val[k];
+    }
+  }
+  __syncthreads();
+  const int64_t left = n - tile * kOsTile;
+  const int tcount = left < kOsTile ? (int)left : kOsTile;
+  for (int i = tid; i < tcount; i += kBlock) {
+    const K kk = skey[i];
+    const int dk = (int)((kk >> shift) & (K)0xFF);
+    const unsigned long long pos = gbase[dk] + (unsigned long long)(i - bstart[dk]);
+    kout[pos] = kk;
+    if (has_vals) vout[pos] = sval[i];
+  }
+}
+
+// After D passes: an odd number of them not skipped left the result in the
+// second buffers; copy it back.
+template <class K, class V>
+__global__ void os_final_kernel(K* keys0, V* vals0, const K* keys1, const V* vals1, int64_t n,
+                                int D, const unsigned long long* __restrict__ hist,
+                                int has_vals) {
+  int swaps = 0;
+  for (int q = 0; q < D; q++) swaps += os_trivial(hist, q, n) ? 0 : 1;
+  if (!(swaps & 1)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    keys0[i] = keys1[i];
+    if (has_vals) vals0[i] = vals1[i];
+  }
+}
+
 // Short arrays: one CTA sorts (key masked to its low bits, original index)
 // pairs in shared memory with a bitonic network; ordering by the index among
 // equal keys makes it stable, so the result is the LSD radix sort's.
@@ -291,6 +489,45 @@ __global__ void __launch_bounds__(kSmallSort)
   }
 }
 
+// The one-launch-per-digit sort with the context's status array and epochs.
+template <class K, class V>
+int onesweep_sort(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
+                  int bits) {
+  cudaStream_t st = ctx->stream;
+  const int D = (bits + 7) / 8;
+  const int64_t ntiles = ceil_div(n, kOsTile);
+  const int64_t words = ntiles * kRadix;
+  if (words > ctx->sort_status_cap || ctx->sort_epoch + (uint32_t)D >= (1u << 24)) {
+    if (words > ctx->sort_status_cap) {
+      const int64_t cap = std::max<int64_t>(words, 2 * ctx->sort_status_cap);
+      dfree(ctx, ctx->sort_status);
+      ctx->sort_status = nullptr;
+      ctx->sort_status_cap = 0;
+      LGC_TRY(dalloc_t(ctx, &ctx->sort_status, (size_t)cap));
+      ctx->sort_status_cap = cap;
+    }
+    LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_status, 0, 8 * ctx->sort_status_cap, st));
+    ctx->sort_epoch = 0;
+  }
+  if (!ctx->sort_aux) LGC_TRY(dalloc_t(ctx, &ctx->sort_aux, kSortAuxWords));
+  unsigned long long* hist = ctx->sort_aux;                      // 8 * 256
+  unsigned int* ctr = (unsigned int*)(ctx->sort_aux + 8 * kRadix);  // 8
+  LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_aux, 0, 8 * kSortAuxWords, st));
+  const int hg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kBlock), ctx->sms * 8));
+  os_hist_kernel<K><<<hg, kBlock, 0, st>>>(keys, n, D, hist);
+  LGC_COUNT_LAUNCH(ctx);
+  for (int q = 0; q < D; q++) {
+    os_pass_kernel<K, V><<<(unsigned)ntiles, kBlock, 0, st>>>(
+        keys, vals, keys_tmp, vals_tmp, n, q, hist, ctr, ctx->sort_status, ++ctx->sort_epoch,
+        ctx->d_sort_err, vals != nullptr);
+    LGC_COUNT_LAUNCH(ctx);
+  }
+  os_final_kernel<K, V><<<hg, kBlock, 0, st>>>(keys, vals, keys_tmp, vals_tmp, n, D, hist,
+                                               vals != nullptr);
+  LGC_COUNT_LAUNCH(ctx);
+  return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
+}
+
 template <class K, class V>
 int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
                     int bits, int64_t* hist_scratch = nullptr,
@@ -304,6 +541,8 @@ int radix_sort_impl(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, in
     LGC_COUNT_LAUNCH(ctx);
     return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
   }
+  // the caller's scratch (nothing may be allocated): the three-launch passes
+  if (!hist_scratch) return onesweep_sort<K, V>(ctx, keys, vals, keys_tmp, vals_tmp, n, bits);
   const int64_t ntiles = ceil_div(n, kTile);
   int64_t* hist = hist_scratch;
   if (!hist) LGC_TRY(dalloc_t(ctx, &hist, (size_t)kRadix * ntiles));

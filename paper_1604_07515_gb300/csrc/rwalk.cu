@@ -161,6 +161,7 @@ int run_rand_hkpr(lgc_ctx* ctx, lgc_graph* g, int32_t x, const lgc_rand_hkpr_par
     if ((status = scan_i64(ctx, flag, runid, nw, false, total)) != LGC_OK) break;
     LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch, total, 16, cudaMemcpyDeviceToHost, s));
     LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((status = sort_check(ctx)) != LGC_OK) break;
     const int64_t runs = ctx->h_scratch[0];
     st.pushed_edges = ctx->h_scratch[1];
     if (ctx->profile && walk_rec > 0 && walk_rec <= ctx->prof_pending.size())

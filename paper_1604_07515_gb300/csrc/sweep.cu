@@ -10,7 +10,10 @@
 //  S5  delta_i = d(v_i) - 2 #{w in N(v_i) : rank(w) < i}: adding v_i to S
 //      turns its edges to S_{i-1} from boundary into interior and the rest
 //      into boundary.  This is the per-rank sum of the paper's Z pairs, read
-//      off without materialising and sorting Z.  Edge-balanced over vol(S_N)
+//      off without materialising and sorting Z.  Edge-balanced over vol(S_N);
+//      for a support of at least n/32 vertices, vertex-centric over the
+//      graph's degree-binned lists instead (the swept vertices' lists read in
+//      CSR order, as a pull round reads them)
 //  S6  cut_i = inclusive prefix sum of delta
 //  S7  argmin of cut_i / min(vol_i, 2m - vol_i), compared exactly as
 //      cut_i * den_j < cut_j * den_i on 128-bit products, first index on
@@ -177,6 +180,71 @@ __global__ void __launch_bounds__(kBlock)
     for (int j = threadIdx.x; j < cnt; j += kBlock)
       if (s_cnt[j]) atomicAdd(&before[i0 + j], s_cnt[j]);
     __syncthreads();
+  }
+}
+
+// S5 vertex-centric: the vertex of rank r (1-based; 0 = not swept) counts
+// its neighbours of rank 1..r-1 into before[r-1].  ru - 1 < r - 1 unsigned
+// holds exactly for 1 <= ru < r.
+__device__ inline int ranked_before(uint32_t ru, uint32_t r) { return ru - 1u < r - 1u; }
+
+// Vertices of degree 1..light, one thread each, from the graph's list
+// grouped by degree; four edges' loads in flight.
+__global__ void sweep_cross_light_kernel(const LightItem* __restrict__ items, int64_t nl,
+                                         const int32_t* __restrict__ col,
+                                         const int32_t* __restrict__ drank,
+                                         int32_t* __restrict__ before) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const LightItem it = items[i];
+    const uint32_t r = (uint32_t)drank[it.w];
+    if (r == 0) continue;
+    int cnt = 0;
+    for (int k = 0; k < it.d; k += 4) {
+      int32_t u[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) u[j] = k + j < it.d ? col[it.beg + k + j] : -1;
+      uint32_t ru[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) ru[j] = u[j] >= 0 ? (uint32_t)drank[u[j]] : 0u;
+#pragma unroll
+      for (int j = 0; j < 4; j++) cnt += ranked_before(ru[j], r);
+    }
+    before[r - 1] = cnt;
+  }
+}
+
+// The other vertices' work items (at most kPullItem edges of one vertex), a
+// warp each, eight edges' loads in flight per lane; the items of one vertex
+// add into its zeroed count.
+__global__ void __launch_bounds__(kBlock)
+    sweep_cross_heavy_kernel(const PullItem* __restrict__ items, int64_t nitems,
+                             const int32_t* __restrict__ col, const int32_t* __restrict__ drank,
+                             int32_t* __restrict__ before) {
+  constexpr int kB = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = warp0; it < nitems; it += nwarps) {  // uniform in the warp
+    const PullItem I = items[it];
+    const uint32_t r = (uint32_t)drank[I.w];
+    if (r == 0) continue;
+    int cnt = 0;
+    for (int k0 = 0; k0 < I.len; k0 += 32 * kB) {
+      int32_t u[kB];
+#pragma unroll
+      for (int j = 0; j < kB; j++) {
+        const int k = k0 + 32 * j + lane;
+        u[j] = k < I.len ? col[I.beg + k] : -1;
+      }
+      uint32_t ru[kB];
+#pragma unroll
+      for (int j = 0; j < kB; j++) ru[j] = u[j] >= 0 ? (uint32_t)drank[u[j]] : 0u;
+#pragma unroll
+      for (int j = 0; j < kB; j++) cnt += ranked_before(ru[j], r);
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0 && cnt) atomicAdd(&before[r - 1], cnt);
   }
 }
 
@@ -509,11 +577,33 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
                                                 &ctx->d_counters->err, (int*)(misc + 3));
     LGC_COUNT_LAUNCH(ctx);
     if ((status = scan_i64(ctx, d_i, vol, n0, true, misc + 1)) != LGC_OK) break;
-    // S5, edge-balanced over V = misc[1] edges with a grid sized for the
-    // largest possible V (the kernel loops over the tiles that exist); the
-    // tiles' first vertices first, for at most min(2m, n0 * max degree)
-    // edges
-    {
+    // S5.  A support of at least n/32 vertices (ranks in the dense array;
+    // LGC_OPT_SWEEP_CROSS may force either form) walks the graph's
+    // degree-binned lists: one thread per vertex of degree up to the graph's
+    // light bin, a warp per work item of the others.
+    const bool vertex_centric =
+        dense_rank && (ctx->sweep_cross == 2 || (ctx->sweep_cross == 0 && n0 >= g->n / 32));
+    if (vertex_centric) {
+      // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
+      ProfScope ps(ctx, LGC_PROF_SWEEP, 0.0);
+      if (g->nlight > 0) {
+        const int lg = (int)std::min<int64_t>(ceil_div(g->nlight, kBlock), ctx->sms * 32);
+        sweep_cross_light_kernel<<<lg, kBlock, 0, s>>>(g->light, g->nlight, g->col, drank,
+                                                       before);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+      if (g->nitems > 0) {
+        const int hg =
+            (int)std::min<int64_t>(ceil_div(g->nitems, kBlock / 32), ctx->sms * 16);
+        sweep_cross_heavy_kernel<<<hg, kBlock, 0, s>>>(g->items, g->nitems, g->col, drank,
+                                                       before);
+        LGC_COUNT_LAUNCH(ctx);
+      }
+    } else {
+      // edge-balanced over V = misc[1] edges with a grid sized for the
+      // largest possible V (the kernel loops over the tiles that exist); the
+      // tiles' first vertices first, for at most min(2m, n0 * max degree)
+      // edges
       const int64_t vmax = std::min<int64_t>(g->nnz, n0 * (int64_t)g->max_deg);
       const int64_t cap = vmax / kTile + 1;
       if ((status = dalloc_t(ctx, &tile0, cap)) != LGC_OK) break;
@@ -521,8 +611,8 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
       LGC_COUNT_LAUNCH(ctx);
       // algorithmic bytes: 12 per edge (col 4, rank key 4, rank 4), 24 per vertex
       ProfScope ps(ctx, LGC_PROF_SWEEP, 0.0);
-      sweep_cross_kernel<<<(ctx->sms * 16), kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1,
-                                                      tile0, cap, T, drank, before);
+      sweep_cross_kernel<<<ctx->sms * 16, kBlock, 0, s>>>(g->off, g->col, id, vol, dN, misc + 1,
+                                                          tile0, cap, T, drank, before);
       LGC_COUNT_LAUNCH(ctx);
     }
     sweep_delta_kernel<<<grid, kBlock, 0, s>>>(d_i, before, n0, delta);
@@ -544,6 +634,7 @@ int run_sweep(lgc_ctx* ctx, lgc_graph* g, const lgc_svec* p, lgc_cluster** out) 
     LGC_CUDA_TRY(cudaMemcpyAsync(ctx->h_scratch + 4, &ctx->d_counters->err, 4,
                                  cudaMemcpyDeviceToHost, s));
     LGC_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((status = sort_check(ctx)) != LGC_OK) break;
     if (*(int*)(ctx->h_scratch + 3) != 0) {
       status = LGC_EINVAL;  // an entry is not a vertex of degree >= 1, or one is named twice
       break;
@@ -794,6 +885,7 @@ int run_sweep_batch(lgc_ctx* ctx, lgc_graph* g, int64_t B, const lgc_svec* const
         st = LGC_ECUDA;
         break;
       }
+      if ((st = sort_check(ctx)) != LGC_OK) break;
       if (*(int*)ctx->h_scratch & kErrDuplicate) {
         st = LGC_EINVAL;
         break;

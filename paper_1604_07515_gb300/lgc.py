@@ -166,6 +166,7 @@ OPT_PULL_SHARE = 11
 OPT_BATCH_HANDOFF = 12
 OPT_HK_THRESHOLD_SIGN = 13
 OPT_SERVE_LANE = 14
+OPT_SWEEP_CROSS = 15
 PROF_EDGEMAP, PROF_VERTEXMAP, PROF_DET_EDGE, PROF_WALK, PROF_SWEEP, PROF_PULL = range(6)
 PROF_NAMES = {PROF_EDGEMAP: "edgemap_push", PROF_VERTEXMAP: "vertexmap",
               PROF_DET_EDGE: "det_edge", PROF_WALK: "walk", PROF_SWEEP: "sweep_cross",

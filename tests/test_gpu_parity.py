@@ -104,12 +104,18 @@ def test_sweep_matches_oracle(ctx, name):
         else:
             val = rng.random(len(idx)) ** 3
         ref = oracle.sweep(off, col, idx, val)
-        c = lgc.sweep(g, lgc.host_svec(idx, val))
-        assert c.size == ref.best
-        assert c.vol == ref.best_vol and c.cut == ref.best_cut
-        assert np.array_equal(c.ids, ref.cluster)
-        assert c.conductance == ref.conductance or (math.isinf(c.conductance)
-                                                    and math.isinf(ref.conductance))
+        # both forms of the crossing counts (edge-balanced, vertex-centric)
+        try:
+            for form in (0, 1, 2):
+                ctx.set_option(lgc.OPT_SWEEP_CROSS, form)
+                c = lgc.sweep(g, lgc.host_svec(idx, val))
+                assert c.size == ref.best
+                assert c.vol == ref.best_vol and c.cut == ref.best_cut
+                assert np.array_equal(c.ids, ref.cluster)
+                assert c.conductance == ref.conductance or (math.isinf(c.conductance)
+                                                            and math.isinf(ref.conductance))
+        finally:
+            ctx.set_option(lgc.OPT_SWEEP_CROSS, 0)
 
 
 def test_sweep_edge_cases(ctx):
@@ -558,7 +564,8 @@ def test_pull_degree_bins(ctx, light):
     """The atomic pull rounds' degree bin (vertices of degree <= light gather
     one thread each; deterministic mode keeps its own bins at any light: one
     thread each up to degree 32, one lane each up to 1024, then
-    segment-parallel) changes speed only: HK-PR's
+    segment-parallel; the sweep of a large support walks the same lists)
+    changes speed only: HK-PR's
     near-global pull rounds and PR-Nibble with every round a pull round give
     the oracle's results, bit for bit in deterministic mode."""
     off, col = inputs.rmat(16, seed=1)
@@ -571,6 +578,12 @@ def test_pull_degree_bins(ctx, light):
         p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="det")
         assert np.array_equal(p.idx, ref.idx) and np.array_equal(p.val, ref.val)
         assert_trace_equal(ctx.trace(), ref.trace)
+        # the sweep of a support over n/32 walks the same degree-binned lists
+        assert len(p.idx) >= (len(off) - 1) // 32
+        rs = oracle.sweep(off, col, ref.idx, ref.val)
+        c = lgc.sweep(g, p)
+        assert (c.size, c.vol, c.cut) == (rs.best, rs.best_vol, rs.best_cut)
+        assert np.array_equal(c.ids, rs.cluster) and c.conductance == rs.conductance
         p, st = lgc.hkpr(g, x, 10.0, 20, 1e-7, mode="atomic")
         assert rel_l1(p.idx, p.val, ref.idx, ref.val) <= ATOL_REL_L1
         ctx.set_option(lgc.OPT_PULL, 2)
