@@ -269,6 +269,7 @@ constexpr uint64_t kOsCount = (1ull << 38) - 1;
 constexpr uint64_t kOsAgg = 1ull << 38;
 constexpr uint64_t kOsIncl = 2ull << 38;
 constexpr int kOsSpinLimit = 1 << 22;
+constexpr int kOsLook = 8;  // status words loaded at once in the look-back
 constexpr int64_t kSortAuxWords = 8 * 256 + 4;  // histogram of 8 digit positions, 8 counters
 static_assert(kBlock == kRadix, "one thread per digit");
 
@@ -342,8 +343,7 @@ __global__ void __launch_bounds__(kBlock)
   const int64_t base = tile * kOsTile + (int64_t)warp * (32 * kOsItems);
   K key[kOsItems];
   V val[kOsItems];
-  int rank[kOsItems];
-  int digit[kOsItems];
+  int dr[kOsItems];  // digit (kRadix: padding) | rank within the warp's run << 9
   const unsigned lt = (1u << lane) - 1;
 #pragma unroll
   for (int k = 0; k < kOsItems; k++) {
@@ -355,12 +355,11 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
   for (int k = 0; k < kOsItems; k++) {
     const int64_t i = base + (int64_t)k * 32 + lane;
-    const int d = i < n ? (int)((key[k] >> shift) & (K)0xFF) : kRadix;  // kRadix: padding
-    digit[k] = d;
+    const int d = i < n ? (int)((key[k] >> shift) & (K)0xFF) : kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int before = d < kRadix ? wcnt[warp][d] : 0;
     __syncwarp();
-    rank[k] = before + __popc(peers & lt);
+    dr[k] = d | ((before + __popc(peers & lt)) << 9);
     if (lane == __ffs(peers) - 1 && d < kRadix) wcnt[warp][d] = before + __popc(peers);
     __syncwarp();
   }
@@ -379,22 +378,32 @@ __global__ void __launch_bounds__(kBlock)
   bstart[d] = (int)(block_inclusive_scan(cnt, s_red, &tot) - cnt);
   const int64_t h = (int64_t)hist[pass * kRadix + d];
   const int64_t gofs = block_inclusive_scan(h, s_red, &tot) - h;
-  // look-back: the counts of this digit in the tiles before this one
+  // look-back: the counts of this digit in the tiles before this one, the
+  // words of kOsLook tiles loaded at once (tile 0 is always inclusive)
   uint64_t excl = 0;
   if (tile > 0) {
-    for (int64_t j = tile - 1; j >= 0; j--) {
-      const volatile unsigned long long* pj = status + j * kRadix + d;
-      uint64_t w = *pj;
-      for (int spins = 0; (uint32_t)(w >> 40) != epoch; w = *pj) {
-        if (++spins > kOsSpinLimit) {
-          atomicOr(err, 1);
-          w = os_word(epoch, kOsIncl, 0);
-          break;
+    bool done = false;
+    for (int64_t j = tile - 1; !done; j -= kOsLook) {
+      uint64_t w[kOsLook];
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++)
+        w[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[(j - i) * kRadix + d]
+                          : os_word(epoch, kOsIncl, 0);
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++) {
+        if (done) break;
+        const volatile unsigned long long* pj = status + (j - i) * kRadix + d;
+        for (int spins = 0; (uint32_t)(w[i] >> 40) != epoch; w[i] = *pj) {
+          if (++spins > kOsSpinLimit) {
+            atomicOr(err, 1);
+            w[i] = os_word(epoch, kOsIncl, 0);
+            break;
+          }
+          if (spins > 16) __nanosleep(64);
         }
-        if (spins > 16) __nanosleep(64);
+        excl += w[i] & kOsCount;
+        done = (w[i] & kOsIncl) != 0;
       }
-      excl += w & kOsCount;
-      if (w & kOsIncl) break;
     }
     *st = os_word(epoch, kOsIncl, excl + (uint64_t)cnt);
   }
@@ -403,9 +412,9 @@ __global__ void __launch_bounds__(kBlock)
   // the tile in digit order in shared memory, then out run by run
 #pragma unroll
   for (int k = 0; k < kOsItems; k++) {
-    const int dk = digit[k];
+    const int dk = dr[k] & 0x1FF;
     if (dk < kRadix) {
-      const int lp = bstart[dk] + wcnt[warp][dk] + rank[k];
+      const int lp = bstart[dk] + wcnt[warp][dk] + (dr[k] >> 9);
       skey[lp] = key[k];
       if (has_vals) sval[lp] = val[k];
     }
