@@ -199,6 +199,7 @@ __device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int
                                         double eps, int fmode, int det, int self_append,
                                         double* share, int64_t* cnt, int64_t* foff, int32_t* nfv,
                                         int32_t* nfs, int32_t ncap, Counters* C) {
+  int64_t nins = 0;  // counted once per block
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -220,9 +221,10 @@ __device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int
       if (self_append && ds >= 0)
         pred = fmode == kFmInserted ? true : self >= eps * (double)d;
     }
-    count_inserted(ins, &C->aux);
+    nins += ins;
     frontier_append(pred, v, ds, d, nfv, nfs, C, ncap);
   }
+  flush_count(nins, &C->aux);
 }
 
 __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
@@ -243,6 +245,7 @@ __global__ void vmap_hkpr_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                  const int64_t* __restrict__ off, double t, int j, int last,
                                  double* __restrict__ share, int64_t* __restrict__ cnt,
                                  int64_t* __restrict__ foff, Counters* C) {
+  int64_t nins = 0;  // counted once per block
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -258,8 +261,9 @@ __global__ void vmap_hkpr_kernel(int64_t nf, const int32_t* __restrict__ fv,
       cnt[i] = d;
       foff[i] = o0;
     }
-    count_inserted(ins, &C->aux);
+    nins += ins;
   }
+  flush_count(nins, &C->aux);
 }
 
 // ---------------------------------------------------------------------------
@@ -281,6 +285,7 @@ __device__ inline void emap_atomic_body(const int32_t* __restrict__ col,
   __shared__ double s_share[kEdgeTile];
   __shared__ int64_t s_i0, s_i1;
   const int64_t ntiles = (E + kEdgeTile - 1) / kEdgeTile;
+  int64_t nins = 0;  // counted once per block
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kEdgeTile;
     const int64_t e1 = min(E, e0 + kEdgeTile);
@@ -358,11 +363,12 @@ __device__ inline void emap_atomic_body(const int32_t* __restrict__ col,
     }
 #pragma unroll
     for (int k = 0; k < kEdgeItems; k++) {
-      count_inserted(ins[k], &C->inserted);
+      nins += ins[k];
       frontier_append(pred[k], w[k], slot[k], dw[k], nfv, nfs, C, ncap);
     }
     __syncthreads();
   }
+  flush_count(nins, &C->inserted);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -394,6 +400,7 @@ __global__ void __launch_bounds__(kBlock)
   __shared__ int64_t s_i0, s_i1;
   const int64_t E = min(E_host, *E_dev);
   const int64_t ntiles = (E + kEdgeTile - 1) / kEdgeTile;
+  int64_t nins = 0;  // counted once per block
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kEdgeTile;
     const int64_t e1 = min(E, e0 + kEdgeTile);
@@ -439,9 +446,10 @@ __global__ void __launch_bounds__(kBlock)
       }
     }
 #pragma unroll
-    for (int k = 0; k < kEdgeItems; k++) count_inserted(ins[k], &C->inserted);
+    for (int k = 0; k < kEdgeItems; k++) nins += ins[k];
     __syncthreads();
   }
+  flush_count(nins, &C->inserted);
 }
 
 // ---------------------------------------------------------------------------
@@ -1161,6 +1169,7 @@ __global__ void vmap_hkpr_pull_kernel(int64_t nf, const int32_t* __restrict__ fv
                                       double* __restrict__ sh, int32_t* __restrict__ range,
                                       Counters* C) {
   int emin = 0, emax = 0;
+  int64_t nins = 0;  // counted once per block
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -1175,8 +1184,9 @@ __global__ void vmap_hkpr_pull_kernel(int64_t nf, const int32_t* __restrict__ fv
       sh[v] = pull_member(x) ? x : -0.0;
       range_take(x, emin, emax);
     }
-    count_inserted(ins, &C->aux);
+    nins += ins;
   }
+  flush_count(nins, &C->aux);
   if (range) range_flush(emin, emax, range);
 }
 

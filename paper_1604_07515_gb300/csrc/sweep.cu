@@ -58,8 +58,16 @@ __global__ void sweep_keys_kernel(const int32_t* __restrict__ idx, const double*
     key[i] = k;
     id[i] = v;
   }
+  // one atomic per block: same-address atomics from every warp queue in L2
+  __shared__ unsigned long long s_c[kBlock / 32];
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(npos, c);
+  if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_c[k];
+    if (t) atomicAdd(npos, t);
+  }
 }
 
 // The rank set: a dense int32 array indexed by vertex id (0 = not in S_N)
