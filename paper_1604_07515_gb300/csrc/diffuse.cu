@@ -1436,68 +1436,6 @@ __global__ void pull_light_fx_kernel(const LightItem* __restrict__ items, int64_
                          qbits, C);
 }
 
-// Ordered compaction of a vertex bitmap into a frontier (ascending id), with
-// the sum of the frontier's degrees.
-__global__ void bits_count_kernel(const uint32_t* __restrict__ bits, int64_t words,
-                                  int64_t* __restrict__ cnt) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-       w += (int64_t)gridDim.x * blockDim.x)
-    cnt[w] = __popc(bits[w]);
-}
-
-// A warp per 32 consecutive bitmap words: lane k loads word k and its
-// position, then the warp takes the words in turn, a set bit's vertex going
-// to the word's position plus the set bits below it (consecutive writes),
-// with the degree loads of eight words in flight at once.  The degrees are
-// summed per thread and added once per block (one address: per-warp atomics
-// would queue on it).
-__global__ void bits_write_kernel(const uint32_t* __restrict__ bits, int64_t words,
-                                  const int64_t* __restrict__ pos, const int32_t* __restrict__ deg,
-                                  int32_t* nfv, int32_t* nfs, int32_t ncap, Counters* C) {
-  __shared__ int64_t s_red[kBlock / 32];
-  const int lane = threadIdx.x & 31;
-  const uint32_t below = (1u << lane) - 1u;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t dsum = 0;
-  for (int64_t w0 = warp0 * 32; w0 < words; w0 += nwarps * 32) {  // whole warps
-    const int64_t w = w0 + lane;
-    const uint32_t q = w < words ? bits[w] : 0u;
-    const int64_t p = w < words ? pos[w] : 0;
-    if (!__any_sync(0xffffffffu, q != 0u)) continue;
-    for (int k0 = 0; k0 < 32; k0 += 8) {
-      int32_t dk[8];
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const uint32_t qk = __shfl_sync(0xffffffffu, q, k0 + k);
-        const int64_t pk = __shfl_sync(0xffffffffu, p, k0 + k);
-        dk[k] = 0;
-        if ((qk >> lane) & 1u) {
-          const int64_t v = (w0 + k0 + k) * 32 + lane;
-          const int64_t at = pk + __popc(qk & below);
-          if (at < ncap) {
-            nfv[at] = (int32_t)v;
-            nfs[at] = (int32_t)v;
-          } else {
-            atomicOr(&C->err, kErrFrontierOverflow);
-          }
-          dk[k] = deg[v];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 8; k++) dsum += dk[k];
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-  if (lane == 0) s_red[threadIdx.x >> 5] = dsum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_red[k];
-    if (t) atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)t);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // edgeMap, deterministic mode.
 // ---------------------------------------------------------------------------
@@ -1861,7 +1799,6 @@ struct PushWork {
   // pull rounds: per-vertex frontier share (membership encoded), qualify bitmap
   DBuf<double> psh;
   DBuf<uint32_t> pq;
-  DBuf<int64_t> pcnt;
   DBuf<Fx> pshx;                   // atomic mode: per-vertex fixed-point shares
   DBuf<int32_t> prange;            // atomic mode: exponent range of the shares
   DBuf<Fx> phacc;                  // per heavy vertex: partial sums of its items
@@ -1927,7 +1864,6 @@ struct PushWork {
     pshx.release(ctx);
     prange.release(ctx);
     pq.release(ctx);
-    pcnt.release(ctx);
     phacc.release(ctx);
     phcnt.release(ctx);
     phtouch.release(ctx);
@@ -2115,7 +2051,6 @@ struct PushWork {
     const int64_t n = g->n, words = (n + 31) / 32;
     if (!pull_ready) {
       LGC_TRY(pq.reserve(ctx, words));
-      LGC_TRY(pcnt.reserve(ctx, words));
       pull_ready = true;
     }
     const int sb = pull_share_bytes(det);
@@ -2245,18 +2180,8 @@ struct PushWork {
         else gather(pshx.ptr);
       }
     }
-    if (fmode != kFmNone) {
-      bits_count_kernel<<<grid_for(words), kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr);
-      LGC_COUNT_LAUNCH(ctx);
-      LGC_TRY(scan_i64(ctx, pcnt.ptr, pcnt.ptr, words, false, total.ptr));
-      const int wg = (int)std::max<int64_t>(
-          1, std::min<int64_t>(ceil_div(words, 32 * (kBlock / 32)), ctx->sms * 8));
-      bits_write_kernel<<<wg, kBlock, 0, s>>>(pq.ptr, words, pcnt.ptr, g->deg, G.v.ptr, G.s.ptr,
-                                               ncap, ctx->d_counters);
-      LGC_COUNT_LAUNCH(ctx);
-      set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
-      LGC_COUNT_LAUNCH(ctx);
-    }
+    if (fmode != kFmNone)  // the qualifying vertices, in ascending id, with their degrees
+      LGC_TRY(bits_compact(ctx, pq.ptr, words, g->deg, G.v.ptr, G.s.ptr, ncap, ctx->d_counters));
     if (sb == 8) {
       pull_scatter_kernel<<<grid_for(nf), kBlock, 0, s>>>(nf, F.v.ptr, share.ptr, psh.ptr, 1);
     } else {

@@ -270,7 +270,8 @@ constexpr uint64_t kOsAgg = 1ull << 38;
 constexpr uint64_t kOsIncl = 2ull << 38;
 constexpr int kOsSpinLimit = 1 << 22;
 constexpr int kOsLook = 8;  // status words loaded at once in the look-back
-constexpr int64_t kSortAuxWords = 8 * 256 + 4;  // histogram of 8 digit positions, 8 counters
+// histogram of 8 digit positions, 8 pass counters, the compaction's counter
+constexpr int64_t kSortAuxWords = 8 * 256 + 5;
 static_assert(kBlock == kRadix, "one thread per digit");
 
 __device__ inline uint64_t os_word(uint32_t epoch, uint64_t state, uint64_t count) {
@@ -431,6 +432,129 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Ordered compaction of a vertex bitmap in one launch.  Tiles of
+// kCmpTileWords words are taken in start order (a counter); warp w of a tile
+// takes 32 * kCmpRounds consecutive words, 32 per round, lane l word l of
+// the round; the tile's count goes to the status array and its offset comes
+// from a decoupled look-back over the earlier tiles (one status word per
+// tile, as in the sort).  A set bit's vertex is written at its position:
+// a round's words are taken in turn, lane l writing bit l, so a warp's
+// stores are consecutive.
+// ---------------------------------------------------------------------------
+constexpr int kCmpRounds = 1;
+constexpr int64_t kCmpTileWords = (int64_t)kBlock * kCmpRounds;  // 256 words
+
+__global__ void __launch_bounds__(kBlock)
+    bits_compact_kernel(const uint32_t* __restrict__ bits, int64_t words, int64_t ntiles,
+                        const int32_t* __restrict__ deg, int32_t* nfv, int32_t* nfs,
+                        int32_t ncap, unsigned int* tile_ctr, unsigned long long* status,
+                        uint32_t epoch, int* err, Counters* C) {
+  __shared__ int64_t s_tile, s_base;
+  __shared__ int s_wtot[kBlock / 32];
+  __shared__ int64_t s_deg[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t wbase = tile * kCmpTileWords + (int64_t)warp * (32 * kCmpRounds);
+  uint32_t q[kCmpRounds];
+  int pre[kCmpRounds];  // set bits before this lane's word in the warp's words
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < kCmpRounds; k++) {
+    const int64_t w = wbase + 32 * k + lane;
+    q[k] = w < words ? bits[w] : 0u;
+    const int c = __popc(q[k]);
+    int inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    pre[k] = run + inc - c;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) s_wtot[warp] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t tot = 0;
+    for (int w = 0; w < kBlock / 32; w++) {  // exclusive over warps
+      const int c = s_wtot[w];
+      s_wtot[w] = (int)tot;
+      tot += c;
+    }
+    volatile unsigned long long* st = status + tile;
+    *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)tot);
+    uint64_t excl = 0;
+    bool done = tile == 0;
+    for (int64_t j = tile - 1; !done; j -= kOsLook) {  // kOsLook words at once
+      uint64_t wd[kOsLook];
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++)
+        wd[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[j - i]
+                           : os_word(epoch, kOsIncl, 0);
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++) {
+        if (done) break;
+        const volatile unsigned long long* pj = status + (j - i);
+        for (int spins = 0; (uint32_t)(wd[i] >> 40) != epoch; wd[i] = *pj) {
+          if (++spins > kOsSpinLimit) {
+            atomicOr(err, 1);
+            wd[i] = os_word(epoch, kOsIncl, 0);
+            break;
+          }
+          if (spins > 16) __nanosleep(64);
+        }
+        excl += wd[i] & kOsCount;
+        done = (wd[i] & kOsIncl) != 0;
+      }
+    }
+    if (tile > 0) *st = os_word(epoch, kOsIncl, excl + (uint64_t)tot);
+    s_base = (int64_t)excl;
+    if (tile == ntiles - 1) C->next_size = (int32_t)(excl + tot);
+  }
+  __syncthreads();
+  const int64_t wb = s_base + s_wtot[warp];
+  const uint32_t below = (1u << lane) - 1u;
+  int64_t dsum = 0;
+#pragma unroll
+  for (int k = 0; k < kCmpRounds; k++) {
+    if (!__any_sync(0xffffffffu, q[k] != 0u)) continue;
+    for (int j0 = 0; j0 < 32; j0 += 8) {
+      int32_t dk[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint32_t qj = __shfl_sync(0xffffffffu, q[k], j0 + j);
+        const int pj = __shfl_sync(0xffffffffu, pre[k], j0 + j);
+        dk[j] = 0;
+        if ((qj >> lane) & 1u) {
+          const int64_t v = (wbase + 32 * k + j0 + j) * 32 + lane;
+          const int64_t at = wb + pj + __popc(qj & below);
+          if (at < ncap) {
+            nfv[at] = (int32_t)v;
+            nfs[at] = (int32_t)v;
+          } else {
+            atomicOr(&C->err, kErrFrontierOverflow);
+          }
+          if (deg) dk[j] = deg[v];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++) dsum += dk[j];
+    }
+  }
+  if (deg) {
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if (lane == 0) s_deg[warp] = dsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t t = 0;
+      for (int w = 0; w < kBlock / 32; w++) t += s_deg[w];
+      if (t) atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)t);
+    }
+  }
+}
+
 // After D passes: an odd number of them not skipped left the result in the
 // second buffers; copy it back.
 template <class K, class V>
@@ -498,15 +622,11 @@ __global__ void __launch_bounds__(kSmallSort)
   }
 }
 
-// The one-launch-per-digit sort with the context's status array and epochs.
-template <class K, class V>
-int onesweep_sort(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
-                  int bits) {
-  cudaStream_t st = ctx->stream;
-  const int D = (bits + 7) / 8;
-  const int64_t ntiles = ceil_div(n, kOsTile);
-  const int64_t words = ntiles * kRadix;
-  if (words > ctx->sort_status_cap || ctx->sort_epoch + (uint32_t)D >= (1u << 24)) {
+// Room for `words` status words and `epochs` fresh epochs in the context's
+// status array (cleared when it grows or the epochs would wrap), and its
+// auxiliary block.
+int status_reserve(lgc_ctx* ctx, int64_t words, int epochs) {
+  if (words > ctx->sort_status_cap || ctx->sort_epoch + (uint32_t)epochs >= (1u << 24)) {
     if (words > ctx->sort_status_cap) {
       const int64_t cap = std::max<int64_t>(words, 2 * ctx->sort_status_cap);
       dfree(ctx, ctx->sort_status);
@@ -515,13 +635,24 @@ int onesweep_sort(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int6
       LGC_TRY(dalloc_t(ctx, &ctx->sort_status, (size_t)cap));
       ctx->sort_status_cap = cap;
     }
-    LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_status, 0, 8 * ctx->sort_status_cap, st));
+    LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_status, 0, 8 * ctx->sort_status_cap, ctx->stream));
     ctx->sort_epoch = 0;
   }
   if (!ctx->sort_aux) LGC_TRY(dalloc_t(ctx, &ctx->sort_aux, kSortAuxWords));
+  return LGC_OK;
+}
+
+// The one-launch-per-digit sort with the context's status array and epochs.
+template <class K, class V>
+int onesweep_sort(lgc_ctx* ctx, K* keys, V* vals, K* keys_tmp, V* vals_tmp, int64_t n,
+                  int bits) {
+  cudaStream_t st = ctx->stream;
+  const int D = (bits + 7) / 8;
+  const int64_t ntiles = ceil_div(n, kOsTile);
+  LGC_TRY(status_reserve(ctx, ntiles * kRadix, D));
   unsigned long long* hist = ctx->sort_aux;                      // 8 * 256
   unsigned int* ctr = (unsigned int*)(ctx->sort_aux + 8 * kRadix);  // 8
-  LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_aux, 0, 8 * kSortAuxWords, st));
+  LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_aux, 0, 8 * (8 * kRadix + 4), st));
   const int hg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kBlock), ctx->sms * 8));
   os_hist_kernel<K><<<hg, kBlock, 0, st>>>(keys, n, D, hist);
   LGC_COUNT_LAUNCH(ctx);
@@ -613,6 +744,20 @@ int radix_sort_u32_i32(lgc_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* ke
 int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, int bits) {
   return radix_sort_impl<uint32_t, int32_t>(ctx, keys, (int32_t*)nullptr, keys_tmp,
                                             (int32_t*)nullptr, n, bits);
+}
+
+int bits_compact(lgc_ctx* ctx, const uint32_t* bits, int64_t words, const int32_t* deg,
+                 int32_t* out_v, int32_t* out_s, int32_t cap, Counters* C) {
+  if (words <= 0) return LGC_OK;
+  const int64_t ntiles = ceil_div(words, kCmpTileWords);
+  LGC_TRY(status_reserve(ctx, ntiles, 1));
+  unsigned int* ctr = (unsigned int*)(ctx->sort_aux + 8 * kRadix + 4);
+  LGC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), ctx->stream));
+  bits_compact_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
+      bits, words, ntiles, deg, out_v, out_s, cap, ctr, ctx->sort_status, ++ctx->sort_epoch,
+      ctx->d_sort_err, C);
+  LGC_COUNT_LAUNCH(ctx);
+  return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
 }
 
 }  // namespace lgc

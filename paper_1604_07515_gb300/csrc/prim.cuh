@@ -37,6 +37,15 @@ int radix_sort_u64_i32_with(lgc_ctx* ctx, uint64_t* keys, int32_t* vals, uint64_
 // Keys only.
 int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, int bits);
 
+// Ordered compaction of the n-bit vertex bitmap bits (words = ceil(n / 32))
+// into out_v = out_s = the set vertices in ascending id, one launch: C's
+// next_size becomes their number, and with deg their degrees are added to
+// C's next_edges; positions past cap are not written and flag
+// kErrFrontierOverflow in C's err.  C is device memory, zeroed by the caller
+// as needed.
+int bits_compact(lgc_ctx* ctx, const uint32_t* bits, int64_t words, const int32_t* deg,
+                 int32_t* out_v, int32_t* out_s, int32_t cap, Counters* C);
+
 int bits_for(int64_t max_value);  // number of bits needed for values < max_value
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -118,6 +118,36 @@ def test_sweep_matches_oracle(ctx, name):
             ctx.set_option(lgc.OPT_SWEEP_CROSS, 0)
 
 
+@pytest.mark.parametrize("pattern", ["low_byte", "low_two_bytes", "all_equal"])
+def test_sweep_sort_digit_patterns(ctx, pattern):
+    """Sort keys whose 8-bit digits are uniform in all but the lowest one
+    (one digit pass runs: the result ends in the scratch buffers and is
+    copied back), all but the lowest two, or in every digit (no pass runs;
+    equal keys keep ascending id), over several sort tiles (p/d on the
+    degree-1 vertices of R-MAT 16, so p/d is p exactly), in both forms of
+    the crossing counts: the oracle's cut, bit for bit."""
+    off, col, g = gpu_graph(ctx, "rmat16")
+    d = np.diff(off)
+    idx = np.flatnonzero(d == 1).astype(np.int32)
+    assert len(idx) > 4 * 2048
+    rng = np.random.default_rng(11)
+    if pattern == "all_equal":
+        val = np.full(len(idx), 0.25)
+    else:
+        span = 256 if pattern == "low_byte" else 65536
+        val = 0.5 + rng.integers(0, span, size=len(idx)).astype(np.float64) * 2.0 ** -53
+    ref = oracle.sweep(off, col, idx, val)
+    try:
+        for form in (0, 1):
+            ctx.set_option(lgc.OPT_SWEEP_CROSS, form)
+            c = lgc.sweep(g, lgc.host_svec(idx, val))
+            assert (c.size, c.vol, c.cut) == (ref.best, ref.best_vol, ref.best_cut)
+            assert np.array_equal(c.ids, ref.cluster)
+            assert c.conductance == ref.conductance
+    finally:
+        ctx.set_option(lgc.OPT_SWEEP_CROSS, 0)
+
+
 def test_sweep_edge_cases(ctx):
     off, col, g = gpu_graph(ctx, "cliques6")
     n = len(off) - 1
