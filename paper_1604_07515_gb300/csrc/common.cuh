@@ -215,6 +215,7 @@ struct lgc_ctx {
   int64_t sort_status_cap = 0;
   uint32_t sort_epoch = 0;
   unsigned long long* sort_aux = nullptr;
+  uint64_t lb_ticket = 0;  // tickets taken so far from the auxiliary block's counter
   int* h_sort_err = nullptr;
   int* d_sort_err = nullptr;
   // small pinned host block for per-round read-back

@@ -114,6 +114,9 @@ int bits_for(int64_t max_value) {
   return b < 1 ? 1 : b;
 }
 
+int scan_lb(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+            int64_t* total);
+
 int scan_i64_with(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
                   int64_t* total, int64_t* partial_scratch) {
   cudaStream_t st = ctx->stream;
@@ -131,6 +134,7 @@ int scan_i64_with(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool
     LGC_CUDA_TRY(cudaGetLastError());
     return LGC_OK;
   }
+  if (!partial_scratch) return scan_lb(ctx, in, out, n, inclusive, total);
   int64_t* partial = partial_scratch;
   if (partial_scratch && nb > kScanTile) return LGC_EINVAL;  // the caller's scratch is one level
   if (!partial) LGC_TRY(dalloc_t(ctx, &partial, nb));
@@ -270,7 +274,7 @@ constexpr uint64_t kOsAgg = 1ull << 38;
 constexpr uint64_t kOsIncl = 2ull << 38;
 constexpr int kOsSpinLimit = 1 << 22;
 constexpr int kOsLook = 8;  // status words loaded at once in the look-back
-// histogram of 8 digit positions, 8 pass counters, the compaction's counter
+// histogram of 8 digit positions, 8 pass counters, the ticket counter
 constexpr int64_t kSortAuxWords = 8 * 256 + 5;
 static_assert(kBlock == kRadix, "one thread per digit");
 
@@ -448,13 +452,14 @@ constexpr int64_t kCmpTileWords = (int64_t)kBlock * kCmpRounds;  // 256 words
 __global__ void __launch_bounds__(kBlock)
     bits_compact_kernel(const uint32_t* __restrict__ bits, int64_t words, int64_t ntiles,
                         const int32_t* __restrict__ deg, int32_t* nfv, int32_t* nfs,
-                        int32_t ncap, unsigned int* tile_ctr, unsigned long long* status,
-                        uint32_t epoch, int* err, Counters* C) {
+                        int32_t ncap, unsigned long long* ticket,
+                        unsigned long long ticket0, unsigned long long* status, uint32_t epoch,
+                        int* err, Counters* C) {
   __shared__ int64_t s_tile, s_base;
   __shared__ int s_wtot[kBlock / 32];
   __shared__ int64_t s_deg[kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(tile_ctr, 1u);
+  if (threadIdx.x == 0) s_tile = (int64_t)(atomicAdd(ticket, 1ull) - ticket0);
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t wbase = tile * kCmpTileWords + (int64_t)warp * (32 * kCmpRounds);
@@ -555,6 +560,86 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-launch prefix sum: tiles of kScanTile elements in start order (a
+// ticket); each tile publishes its sum and finds its prefix by a decoupled
+// look-back over the earlier tiles' words.  Sums travel as 38-bit two's
+// complement: a partial sum outside [-2^37, 2^37) is recorded in *err.
+// ---------------------------------------------------------------------------
+__device__ inline int64_t lb_value(uint64_t w) { return (int64_t)(w << 26) >> 26; }
+__device__ inline bool lb_fits(int64_t x) { return x >= -(int64_t{1} << 37) && x < (int64_t{1} << 37); }
+
+__global__ void __launch_bounds__(kBlock)
+    scan_lb_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                   int64_t ntiles, int inclusive, int64_t* __restrict__ total,
+                   unsigned long long* ticket, unsigned long long ticket0,
+                   unsigned long long* status, uint32_t epoch, int* err) {
+  __shared__ int64_t tile[kScanTile];
+  __shared__ int64_t warp_tot[kBlock / 32];
+  __shared__ int64_t s_t, s_pre;
+  if (threadIdx.x == 0) s_t = (int64_t)(atomicAdd(ticket, 1ull) - ticket0);
+  __syncthreads();
+  const int64_t t = s_t;
+  const int64_t base = t * kScanTile;
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    tile[k * kBlock + threadIdx.x] = i < n ? in[i] : 0;
+  }
+  __syncthreads();
+  int64_t v[kScanItems];
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = tile[threadIdx.x * kScanItems + k];
+    s += v[k];
+  }
+  int64_t tot;
+  const int64_t incl = block_inclusive_scan(s, warp_tot, &tot);
+  if (threadIdx.x == 0) {
+    volatile unsigned long long* st = status + t;
+    *st = os_word(epoch, t == 0 ? kOsIncl : kOsAgg, (uint64_t)tot & kOsCount);
+    int64_t excl = 0;
+    bool done = t == 0;
+    for (int64_t j = t - 1; !done; j -= kOsLook) {  // kOsLook words at once
+      uint64_t wd[kOsLook];
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++)
+        wd[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[j - i]
+                           : os_word(epoch, kOsIncl, 0);
+#pragma unroll
+      for (int i = 0; i < kOsLook; i++) {
+        if (done) break;
+        const volatile unsigned long long* pj = status + (j - i);
+        for (int spins = 0; (uint32_t)(wd[i] >> 40) != epoch; wd[i] = *pj) {
+          if (++spins > kOsSpinLimit) {
+            atomicOr(err, 1);
+            wd[i] = os_word(epoch, kOsIncl, 0);
+            break;
+          }
+          if (spins > 16) __nanosleep(64);
+        }
+        excl += lb_value(wd[i]);
+        done = (wd[i] & kOsIncl) != 0;
+      }
+    }
+    if (t > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot) & kOsCount);
+    if (!lb_fits(tot) || !lb_fits(excl + tot)) atomicOr(err, 2);
+    s_pre = excl;
+  }
+  __syncthreads();
+  int64_t run = incl - s + s_pre;
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t x = v[k];
+    tile[threadIdx.x * kScanItems + k] = inclusive ? run + x : run;
+    run += x;
+  }
+  __syncthreads();
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) out[i] = tile[k * kBlock + threadIdx.x];
+  }
+  if (total && t == ntiles - 1 && threadIdx.x == kBlock - 1) *total = run;
+}
+
 // After D passes: an odd number of them not skipped left the result in the
 // second buffers; copy it back.
 template <class K, class V>
@@ -638,9 +723,19 @@ int status_reserve(lgc_ctx* ctx, int64_t words, int epochs) {
     LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_status, 0, 8 * ctx->sort_status_cap, ctx->stream));
     ctx->sort_epoch = 0;
   }
-  if (!ctx->sort_aux) LGC_TRY(dalloc_t(ctx, &ctx->sort_aux, kSortAuxWords));
+  if (!ctx->sort_aux) {
+    LGC_TRY(dalloc_t(ctx, &ctx->sort_aux, kSortAuxWords));
+    LGC_CUDA_TRY(cudaMemsetAsync(ctx->sort_aux, 0, 8 * kSortAuxWords, ctx->stream));
+    ctx->lb_ticket = 0;
+  }
   return LGC_OK;
 }
+
+// The running ticket counter of the one-launch scans and compactions: every
+// block of such a launch takes one ticket, so the launch's tiles are the
+// tickets [ctx->lb_ticket, ctx->lb_ticket + blocks), in the order the blocks
+// start (no clearing between launches).
+unsigned long long* lb_counter(lgc_ctx* ctx) { return ctx->sort_aux + 8 * kRadix + 4; }
 
 // The one-launch-per-digit sort with the context's status array and epochs.
 template <class K, class V>
@@ -751,11 +846,23 @@ int bits_compact(lgc_ctx* ctx, const uint32_t* bits, int64_t words, const int32_
   if (words <= 0) return LGC_OK;
   const int64_t ntiles = ceil_div(words, kCmpTileWords);
   LGC_TRY(status_reserve(ctx, ntiles, 1));
-  unsigned int* ctr = (unsigned int*)(ctx->sort_aux + 8 * kRadix + 4);
-  LGC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), ctx->stream));
   bits_compact_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
-      bits, words, ntiles, deg, out_v, out_s, cap, ctr, ctx->sort_status, ++ctx->sort_epoch,
-      ctx->d_sort_err, C);
+      bits, words, ntiles, deg, out_v, out_s, cap, lb_counter(ctx), ctx->lb_ticket,
+      ctx->sort_status, ++ctx->sort_epoch, ctx->d_sort_err, C);
+  ctx->lb_ticket += (uint64_t)ntiles;
+  LGC_COUNT_LAUNCH(ctx);
+  return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
+}
+
+// The multi-tile prefix sum in one launch (scan_lb_kernel).
+int scan_lb(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclusive,
+            int64_t* total) {
+  const int64_t ntiles = ceil_div(n, kScanTile);
+  LGC_TRY(status_reserve(ctx, ntiles, 1));
+  scan_lb_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
+      in, out, n, ntiles, inclusive ? 1 : 0, total, lb_counter(ctx), ctx->lb_ticket,
+      ctx->sort_status, ++ctx->sort_epoch, ctx->d_sort_err);
+  ctx->lb_ticket += (uint64_t)ntiles;
   LGC_COUNT_LAUNCH(ctx);
   return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
 }
