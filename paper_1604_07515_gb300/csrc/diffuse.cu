@@ -142,19 +142,23 @@ __device__ inline void count_inserted(int ins, int64_t* counter) {
 // PR-Nibble, Fig. alg:pr-nibble (rule 1) / alg:pr-nibble2 (rule 0).  T holds
 // r in slot.val and p in T.p[slot]; r' is updated in place (every read of r
 // in the round is of a frontier vertex, done here before the edgeMap).
-__device__ inline void prnibble_vmap_body(int64_t nf, const int32_t* fv, const int32_t* fs,
-                                          Table T, const int64_t* __restrict__ off,
-                                          double alpha, double cs, double cn, double eps,
-                                          int rule, int det, int self_append, double* share,
-                                          int64_t* cnt, int64_t* foff, int32_t* nfv,
-                                          int32_t* nfs, int32_t ncap, Counters* C) {
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
-       base += (int64_t)gridDim.x * blockDim.x) {
+// The vertexMap bodies take the frontier entries [i0, i1) in steps of `step`
+// (a block-uniform start: the grid's stride, or a block's own chunk) and
+// return the sum of the record counts this thread wrote.
+__device__ inline int64_t prnibble_vmap_body(int64_t i0, int64_t i1, int64_t step,
+                                             const int32_t* fv, const int32_t* fs, Table T,
+                                             const int64_t* __restrict__ off, double alpha,
+                                             double cs, double cn, double eps, int rule, int det,
+                                             int self_append, double* share, int64_t* cnt,
+                                             int64_t* foff, int32_t* nfv, int32_t* nfs,
+                                             int32_t ncap, Counters* C) {
+  int64_t csum = 0;
+  for (int64_t base = i0; base < i1; base += step) {
     const int64_t i = base + threadIdx.x;
     bool pred = false;
     int32_t v = 0, s = 0;
     int64_t d = 0;
-    if (i < nf) {
+    if (i < i1) {
       v = fv[i];
       s = fs[i];
       const bool ok = s >= 0;  // always true unless a table overflowed (flagged)
@@ -174,11 +178,13 @@ __device__ inline void prnibble_vmap_body(int64_t nf, const int32_t* fv, const i
       if (ok) *tb_val(T, s) = rbase;
       share[i] = sh;
       cnt[i] = d + (det ? 1 : 0);
+      csum += cnt[i];
       foff[i] = o0;
       pred = ok && self_append && rule == 1 && rbase >= eps * (double)d;
     }
     frontier_append(pred, v, s, d, nfv, nfs, C, ncap);
   }
+  return csum;
 }
 
 __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
@@ -188,26 +194,28 @@ __global__ void vmap_prnibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                      double* __restrict__ share, int64_t* __restrict__ cnt,
                                      int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
                                      int32_t ncap, Counters* C) {
-  prnibble_vmap_body(nf, fv, fs, T, off, alpha, cs, cn, eps, rule, det, self_append, share, cnt,
-                     foff, nfv, nfs, ncap, C);
+  prnibble_vmap_body((int64_t)blockIdx.x * blockDim.x, nf, (int64_t)gridDim.x * blockDim.x, fv,
+                     fs, T, off, alpha, cs, cn, eps, rule, det, self_append, share, cnt, foff,
+                     nfv, nfs, ncap, C);
 }
 
 // Nibble, Fig. alg:nibble: p'[v] = p[v]/2 on the frontier (S = p, D = p',
 // fresh), share p[v]/(2 d(v)).
-__device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int32_t* fs,
-                                        Table S, Table D, const int64_t* __restrict__ off,
-                                        double eps, int fmode, int det, int self_append,
-                                        double* share, int64_t* cnt, int64_t* foff, int32_t* nfv,
-                                        int32_t* nfs, int32_t ncap, Counters* C) {
+__device__ inline int64_t nibble_vmap_body(int64_t i0, int64_t i1, int64_t step,
+                                           const int32_t* fv, const int32_t* fs, Table S,
+                                           Table D, const int64_t* __restrict__ off, double eps,
+                                           int fmode, int det, int self_append, double* share,
+                                           int64_t* cnt, int64_t* foff, int32_t* nfv,
+                                           int32_t* nfs, int32_t ncap, Counters* C) {
   int64_t nins = 0;  // counted once per block
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf;
-       base += (int64_t)gridDim.x * blockDim.x) {
+  int64_t csum = 0;
+  for (int64_t base = i0; base < i1; base += step) {
     const int64_t i = base + threadIdx.x;
     bool pred = false;
     int ins = 0;
     int32_t v = 0, ds = 0;
     int64_t d = 0;
-    if (i < nf) {
+    if (i < i1) {
       v = fv[i];
       const double pv = fs[i] >= 0 ? *tb_val(S, fs[i]) : 0.0;
       const int64_t o0 = off[v];
@@ -217,6 +225,7 @@ __device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int
       if (ds >= 0) *tb_val(D, ds) = self;
       share[i] = pv / (2.0 * (double)d);
       cnt[i] = d + (det ? 1 : 0);
+      csum += cnt[i];
       foff[i] = o0;
       if (self_append && ds >= 0)
         pred = fmode == kFmInserted ? true : self >= eps * (double)d;
@@ -225,6 +234,7 @@ __device__ inline void nibble_vmap_body(int64_t nf, const int32_t* fv, const int
     frontier_append(pred, v, ds, d, nfv, nfs, C, ncap);
   }
   flush_count(nins, &C->aux);
+  return csum;
 }
 
 __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
@@ -234,8 +244,8 @@ __global__ void vmap_nibble_kernel(int64_t nf, const int32_t* __restrict__ fv,
                                    int64_t* __restrict__ cnt,
                                    int64_t* __restrict__ foff, int32_t* nfv, int32_t* nfs,
                                    int32_t ncap, Counters* C) {
-  nibble_vmap_body(nf, fv, fs, S, D, off, eps, fmode, det, self_append, share, cnt, foff, nfv,
-                   nfs, ncap, C);
+  nibble_vmap_body((int64_t)blockIdx.x * blockDim.x, nf, (int64_t)gridDim.x * blockDim.x, fv, fs,
+                   S, D, off, eps, fmode, det, self_append, share, cnt, foff, nfv, nfs, ncap, C);
 }
 
 // HK-PR, Fig. alg:hkpr: p[v] += r[v] on the frontier; share
@@ -480,21 +490,24 @@ __device__ inline int64_t block_sum_i64(int64_t x, int64_t* s_red) {
   return t;
 }
 
-// Exclusive prefix sum of cnt[0, nf) into epos by the whole grid (block b
-// scans its chunk after adding the sums of the chunks before it); returns
-// the total.  Contains grid barriers: every thread of the grid calls it.
-__device__ inline int64_t grid_exclusive_scan(cg::grid_group& grid, const int64_t* cnt,
-                                              int64_t nf, int64_t* epos, int64_t* bsum) {
+// The grid-wide exclusive prefix sum of cnt[0, nf) into epos: block b owns
+// the chunk [c0, c1) of grid_chunk, writes the sum of cnt over it into
+// bsum[b], and after a grid barrier grid_scan_tail scans its chunk from the
+// sums of the chunks before it and returns the total (every thread of the
+// grid calls it).
+__device__ inline void grid_chunk(int64_t nf, int64_t* c0, int64_t* c1) {
+  const int64_t chunk = (nf + gridDim.x - 1) / gridDim.x;
+  *c0 = min(nf, (int64_t)blockIdx.x * chunk);
+  *c1 = min(nf, *c0 + chunk);
+}
+
+__device__ inline int64_t grid_scan_tail(const int64_t* cnt, int64_t nf, int64_t* epos,
+                                         const int64_t* bsum) {
   __shared__ int64_t s_red[kBlock / 32];
   __shared__ int64_t s_scan[kBlock / 32];
   const int G = gridDim.x;
-  const int64_t chunk = (nf + G - 1) / G;
-  const int64_t c0 = min(nf, (int64_t)blockIdx.x * chunk), c1 = min(nf, c0 + chunk);
-  int64_t part = 0;
-  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) part += cnt[i];
-  part = block_sum_i64(part, s_red);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = part;
-  grid.sync();
+  int64_t c0, c1;
+  grid_chunk(nf, &c0, &c1);
   int64_t pre = 0, tot = 0;
   for (int b = threadIdx.x; b < G; b += blockDim.x) {
     const int64_t x = __ldcg(&bsum[b]);
@@ -525,6 +538,14 @@ __device__ inline int64_t grid_exclusive_scan(cg::grid_group& grid, const int64_
   return tot;
 }
 
+// Every thread keeps the round state (frontier buffer, rounds, pushes,
+// keys) in registers, updated alike from the counters each round wrote once
+// the grid has synchronised; the state goes to S when the kernel stops.  A
+// round: the vertexMap over each block's chunk of the frontier with the
+// chunk's record count | barrier | the scan | barrier | the edge push |
+// barrier.  The current round's counters are cleared after the first
+// barrier (nothing reads them after it), for their reuse as the next
+// round's "next".
 __global__ void __launch_bounds__(kBlock)
     rounds_prnibble_kernel(Table T, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
@@ -534,20 +555,30 @@ __global__ void __launch_bounds__(kBlock)
                            int64_t* bsum, Counters* Cn, RoundsState* S, int64_t max_rounds,
                            int64_t e_max, int64_t key_limit) {
   cg::grid_group grid = cg::this_grid();
+  __shared__ int64_t s_red[kBlock / 32];
+  int cur = __ldcg(&S->cur);
+  int64_t count = __ldcg(&S->count), rounds = __ldcg(&S->rounds);
+  int64_t pushes = __ldcg(&S->pushes), pushed = __ldcg(&S->pushed_edges);
   for (;;) {
-    const int cur = __ldcg(&S->cur), nxt = cur ^ 1;
+    const int nxt = cur ^ 1;
     const int64_t nf = __ldcg(&Cn[cur].next_size);
     const int64_t E = __ldcg(&Cn[cur].next_edges);
-    const int64_t count = __ldcg(&S->count);
     const int err = __ldcg(&Cn[cur].err) | __ldcg(&Cn[nxt].err);
     int stop = 0;
     if (err) stop = 4;
     else if (nf == 0) stop = 1;
-    else if (__ldcg(&S->rounds) >= max_rounds) stop = 2;
+    else if (rounds >= max_rounds) stop = 2;
     else if (E > e_max || nf + E > fcap || count + E > key_limit) stop = 3;
-    if (stop) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) S->stop = stop;
-      return;  // the same decision in every thread: no barrier is left waiting
+    if (stop) {  // the same decision in every thread: no barrier is left waiting
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->cur = cur;
+        S->stop = stop;
+        S->count = count;
+        S->rounds = rounds;
+        S->pushes = pushes;
+        S->pushed_edges = pushed;
+      }
+      return;
     }
     int32_t* fv = cur ? fv1 : fv0;
     int32_t* fs = cur ? fs1 : fs0;
@@ -555,38 +586,39 @@ __global__ void __launch_bounds__(kBlock)
     int32_t* nfs = cur ? fs0 : fs1;
     // vertexMap (the original rule keeps a vertex whose reduced residual
     // still reaches the threshold)
-    prnibble_vmap_body(nf, fv, fs, T, off, alpha, cs, cn, eps, rule, 0, 1, share, cnt, foff, nfv,
-                       nfs, fcap, &Cn[nxt]);
+    int64_t c0, c1;
+    grid_chunk(nf, &c0, &c1);
+    int64_t part = prnibble_vmap_body(c0, c1, blockDim.x, fv, fs, T, off, alpha, cs, cn, eps,
+                                      rule, 0, 1, share, cnt, foff, nfv, nfs, fcap, &Cn[nxt]);
+    part = block_sum_i64(part, s_red);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = part;
     grid.sync();
-    const int64_t tot = grid_exclusive_scan(grid, cnt, nf, epos, bsum);
+    if (blockIdx.x == 0 && threadIdx.x == 0) Cn[cur] = Counters{};
+    const int64_t tot = grid_scan_tail(cnt, nf, epos, bsum);
     grid.sync();
     // edge push into the same table, appending crossings to the next frontier
-    const int64_t Er = min(E, tot);
-    emap_atomic_body(col, deg, share, epos, foff, nf, Er, T, eps, kFmThreshold, nfv, nfs, fcap,
-                     &Cn[nxt]);
+    emap_atomic_body(col, deg, share, epos, foff, nf, min(E, tot), T, eps, kFmThreshold, nfv,
+                     nfs, fcap, &Cn[nxt]);
     grid.sync();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      S->rounds += 1;
-      S->pushes += nf;
-      S->pushed_edges += E;
-      S->count += Cn[nxt].inserted;
-      Cn[nxt].inserted = 0;
-      Cn[cur] = Counters{};
-      S->cur = nxt;
-    }
-    grid.sync();
+    rounds += 1;
+    pushes += nf;
+    pushed += E;
+    count += __ldcg(&Cn[nxt].inserted);
+    cur = nxt;
   }
 }
 
 // Nibble (Fig. alg:nibble, atomic mode) the same way: each round fills a
 // fresh p' from p, so two hashed tables of capacity cap alternate as p'
-// (A in device round 0, 2, ..., B in 1, 3, ...) and p starts in T0 (any
-// form), the table the host's rounds left.  A round clears its p' table,
-// runs the vertexMap (p'[v] = p[v]/2, appending v if that reaches the
-// threshold), the scan and the edge push into p'.  When the new frontier is
-// empty the run is over and p stays where it was (the method returns the
-// previous p); otherwise p' becomes p.  key_limit is cap / 2: a round whose
-// keys (at most |F| + its edges) could pass it stops the kernel first.
+// (A in device round 0, 2, ..., B in 1, 3, ...; both clear at launch) and p
+// starts in T0 (any form), the table the host's rounds left.  A round runs
+// the vertexMap (p'[v] = p[v]/2, appending v if that reaches the threshold),
+// the scan and the edge push into p'.  When the new frontier is empty the
+// run is over and p stays where it was (the method returns the previous p);
+// otherwise p' becomes p and the old p, when it is A or B, is cleared in a
+// fourth phase to serve as the next round's p'.  key_limit is cap / 2: a
+// round whose keys (at most |F| + its edges) could pass it stops the kernel
+// first.
 __global__ void __launch_bounds__(kBlock)
     rounds_nibble_kernel(Table T0, Table A, Table B, const int64_t* __restrict__ off,
                          const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
@@ -595,57 +627,70 @@ __global__ void __launch_bounds__(kBlock)
                          int64_t* foff, int64_t* bsum, Counters* Cn, RoundsState* S,
                          int64_t max_rounds, int64_t e_max, int64_t key_limit) {
   cg::grid_group grid = cg::this_grid();
+  __shared__ int64_t s_red[kBlock / 32];
+  int cur = __ldcg(&S->cur), ptab = __ldcg(&S->ptab);
+  int64_t count = __ldcg(&S->count), k = __ldcg(&S->rounds);
+  int64_t pushes = __ldcg(&S->pushes), pushed = __ldcg(&S->pushed_edges);
+  auto finish = [&](int stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->cur = cur;
+      S->ptab = ptab;
+      S->stop = stop;
+      S->count = count;
+      S->rounds = k;
+      S->pushes = pushes;
+      S->pushed_edges = pushed;
+    }
+  };
   for (;;) {
-    const int cur = __ldcg(&S->cur), nxt = cur ^ 1;
+    const int nxt = cur ^ 1;
     const int64_t nf = __ldcg(&Cn[cur].next_size);
     const int64_t E = __ldcg(&Cn[cur].next_edges);
-    const int64_t k = __ldcg(&S->rounds);
     const int err = __ldcg(&Cn[cur].err) | __ldcg(&Cn[nxt].err);
     int stop = 0;
     if (err) stop = 4;
     else if (nf == 0) stop = 1;
     else if (k >= max_rounds) stop = 2;
     else if (E > e_max || nf + E > fcap || nf + E > key_limit) stop = 3;
-    if (stop) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) S->stop = stop;
-      return;  // the same decision in every thread: no barrier is left waiting
+    if (stop) {  // the same decision in every thread: no barrier is left waiting
+      finish(stop);
+      return;
     }
-    const int ptab = __ldcg(&S->ptab);
     const Table P = ptab == 0 ? T0 : ptab == 1 ? A : B;
     const Table Q = (k & 1) ? B : A;  // never P: P is T0 or the other one
     int32_t* fv = cur ? fv1 : fv0;
     int32_t* fs = cur ? fs1 : fs0;
     int32_t* nfv = cur ? fv0 : fv1;
     int32_t* nfs = cur ? fs0 : fs1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Q.cap;
-         i += (int64_t)gridDim.x * blockDim.x)
-      Q.s[i] = Slot{};  // p' = {}
+    int64_t c0, c1;
+    grid_chunk(nf, &c0, &c1);
+    int64_t part = nibble_vmap_body(c0, c1, blockDim.x, fv, fs, P, Q, off, eps, fmode, 0, 1,
+                                    share, cnt, foff, nfv, nfs, fcap, &Cn[nxt]);
+    part = block_sum_i64(part, s_red);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = part;
     grid.sync();
-    nibble_vmap_body(nf, fv, fs, P, Q, off, eps, fmode, 0, 1, share, cnt, foff, nfv, nfs, fcap,
-                     &Cn[nxt]);
-    grid.sync();
-    const int64_t tot = grid_exclusive_scan(grid, cnt, nf, epos, bsum);
+    if (blockIdx.x == 0 && threadIdx.x == 0) Cn[cur] = Counters{};
+    const int64_t tot = grid_scan_tail(cnt, nf, epos, bsum);
     grid.sync();
     emap_atomic_body(col, deg, share, epos, foff, nf, min(E, tot), Q, eps, fmode, nfv, nfs, fcap,
                      &Cn[nxt]);
     grid.sync();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      S->rounds = k + 1;
-      S->pushes += nf;
-      S->pushed_edges += E;
-      if (Cn[nxt].next_size == 0) {
-        S->stop = 1;  // the previous p is the result
-      } else {
-        S->ptab = (k & 1) ? 2 : 1;
-        S->count = Cn[nxt].aux + Cn[nxt].inserted;
-        Cn[nxt].aux = 0;
-        Cn[nxt].inserted = 0;
-        Cn[cur] = Counters{};
-        S->cur = nxt;
-      }
+    k += 1;
+    pushes += nf;
+    pushed += E;
+    if (__ldcg(&Cn[nxt].next_size) == 0) {  // the previous p is the result
+      finish(1);
+      return;
     }
+    count = __ldcg(&Cn[nxt].aux) + __ldcg(&Cn[nxt].inserted);
+    if (ptab != 0) {  // the old p (A or B) becomes the next round's p'
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.cap;
+           i += (int64_t)gridDim.x * blockDim.x)
+        P.s[i] = Slot{};
+    }
+    ptab = ((k - 1) & 1) ? 2 : 1;
+    cur = nxt;
     grid.sync();
-    if (__ldcg(&S->stop)) return;
   }
 }
 
