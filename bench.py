@@ -852,7 +852,8 @@ def main():
     traffic = None
     if (dname == "edgemap_pull" and MODE == "atomic" and STEP_ALGOS == ALGOS
             and PULL_TRAFFIC["sha256"] == sources_sha(PULL_TRAFFIC["sources"])):
-        traffic = PULL_TRAFFIC["per_launch"].get(str(pull_shape[2]))
+        traffic = PULL_TRAFFIC["per_round"].get(
+            ",".join(str(v) for v in (pull_light,) + tuple(pull_shape)))
     roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": traffic, "launches": d["launches"],

@@ -282,6 +282,44 @@ __device__ inline uint64_t os_word(uint32_t epoch, uint64_t state, uint64_t coun
   return ((uint64_t)epoch << 40) | state | count;
 }
 
+// A value of a single-value status word: 38-bit two's complement.
+__device__ inline int64_t lb_value(uint64_t w) { return (int64_t)(w << 26) >> 26; }
+
+// Look-back by one whole warp for tiles with one status word each: the sum
+// of the values of tiles [0, t), lane l reading tile j - l of a 32-tile
+// window, the walk ending at the nearest inclusive word.  The warp waits
+// until every word of the window is published (bounded: past kOsSpinLimit
+// polls *err records it and unpublished words count as empty inclusive
+// ones).  Every lane of the warp calls it and gets the sum.
+__device__ inline int64_t lookback_warp(const unsigned long long* status, int64_t t,
+                                        uint32_t epoch, int* err) {
+  const int lane = threadIdx.x & 31;
+  int64_t excl = 0;
+  for (int64_t j = t - 1; j >= 0; j -= 32) {  // uniform in the warp
+    const int64_t tj = j - lane;
+    const volatile unsigned long long* pj = status + (tj >= 0 ? tj : 0);
+    uint64_t w = tj >= 0 ? *pj : os_word(epoch, kOsIncl, 0);
+    for (int spins = 0;; spins++) {
+      const bool ready = (uint32_t)(w >> 40) == epoch;
+      if (__all_sync(0xffffffffu, ready)) break;
+      if (spins > kOsSpinLimit) {  // the same count in every lane
+        if (lane == 0) atomicOr(err, 1);
+        if (!ready) w = os_word(epoch, kOsIncl, 0);
+        break;
+      }
+      if (spins > 16) __nanosleep(64);
+      if (!ready) w = *pj;
+    }
+    const unsigned incl = __ballot_sync(0xffffffffu, (w & kOsIncl) != 0);
+    const int last = incl ? __ffs(incl) - 1 : 31;  // lanes 0..last count
+    int64_t v = lane <= last ? lb_value(w) : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (incl) break;
+  }
+  return excl;
+}
+
 // Counts of every digit position q < D of the keys into hist[q * 256 + d]
 // (zeroed before).  A warp whose keys share a digit adds them at once.
 template <class K>
@@ -481,42 +519,26 @@ __global__ void __launch_bounds__(kBlock)
   }
   if (lane == 0) s_wtot[warp] = run;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t tot = 0;
-    for (int w = 0; w < kBlock / 32; w++) {  // exclusive over warps
-      const int c = s_wtot[w];
-      s_wtot[w] = (int)tot;
-      tot += c;
-    }
+  if (threadIdx.x < 32) {
+    int64_t tot = 0;  // every lane of warp 0 sums the warps' counts
+    for (int w = 0; w < kBlock / 32; w++) tot += s_wtot[w];
+    __syncwarp();
     volatile unsigned long long* st = status + tile;
-    *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)tot);
-    uint64_t excl = 0;
-    bool done = tile == 0;
-    for (int64_t j = tile - 1; !done; j -= kOsLook) {  // kOsLook words at once
-      uint64_t wd[kOsLook];
-#pragma unroll
-      for (int i = 0; i < kOsLook; i++)
-        wd[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[j - i]
-                           : os_word(epoch, kOsIncl, 0);
-#pragma unroll
-      for (int i = 0; i < kOsLook; i++) {
-        if (done) break;
-        const volatile unsigned long long* pj = status + (j - i);
-        for (int spins = 0; (uint32_t)(wd[i] >> 40) != epoch; wd[i] = *pj) {
-          if (++spins > kOsSpinLimit) {
-            atomicOr(err, 1);
-            wd[i] = os_word(epoch, kOsIncl, 0);
-            break;
-          }
-          if (spins > 16) __nanosleep(64);
-        }
-        excl += wd[i] & kOsCount;
-        done = (wd[i] & kOsIncl) != 0;
+    if (threadIdx.x == 0) {
+      int64_t run = 0;
+      for (int w = 0; w < kBlock / 32; w++) {  // exclusive over warps
+        const int c = s_wtot[w];
+        s_wtot[w] = (int)run;
+        run += c;
       }
+      *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)tot);
     }
-    if (tile > 0) *st = os_word(epoch, kOsIncl, excl + (uint64_t)tot);
-    s_base = (int64_t)excl;
-    if (tile == ntiles - 1) C->next_size = (int32_t)(excl + tot);
+    const int64_t excl = lookback_warp(status, tile, epoch, err);
+    if (threadIdx.x == 0) {
+      if (tile > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot));
+      s_base = excl;
+      if (tile == ntiles - 1) C->next_size = (int32_t)(excl + tot);
+    }
   }
   __syncthreads();
   const int64_t wb = s_base + s_wtot[warp];
@@ -566,8 +588,9 @@ __global__ void __launch_bounds__(kBlock)
 // look-back over the earlier tiles' words.  Sums travel as 38-bit two's
 // complement: a partial sum outside [-2^37, 2^37) is recorded in *err.
 // ---------------------------------------------------------------------------
-__device__ inline int64_t lb_value(uint64_t w) { return (int64_t)(w << 26) >> 26; }
-__device__ inline bool lb_fits(int64_t x) { return x >= -(int64_t{1} << 37) && x < (int64_t{1} << 37); }
+__device__ inline bool lb_fits(int64_t x) {
+  return x >= -(int64_t{1} << 37) && x < (int64_t{1} << 37);
+}
 
 __global__ void __launch_bounds__(kBlock)
     scan_lb_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
@@ -594,36 +617,16 @@ __global__ void __launch_bounds__(kBlock)
   }
   int64_t tot;
   const int64_t incl = block_inclusive_scan(s, warp_tot, &tot);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     volatile unsigned long long* st = status + t;
-    *st = os_word(epoch, t == 0 ? kOsIncl : kOsAgg, (uint64_t)tot & kOsCount);
-    int64_t excl = 0;
-    bool done = t == 0;
-    for (int64_t j = t - 1; !done; j -= kOsLook) {  // kOsLook words at once
-      uint64_t wd[kOsLook];
-#pragma unroll
-      for (int i = 0; i < kOsLook; i++)
-        wd[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[j - i]
-                           : os_word(epoch, kOsIncl, 0);
-#pragma unroll
-      for (int i = 0; i < kOsLook; i++) {
-        if (done) break;
-        const volatile unsigned long long* pj = status + (j - i);
-        for (int spins = 0; (uint32_t)(wd[i] >> 40) != epoch; wd[i] = *pj) {
-          if (++spins > kOsSpinLimit) {
-            atomicOr(err, 1);
-            wd[i] = os_word(epoch, kOsIncl, 0);
-            break;
-          }
-          if (spins > 16) __nanosleep(64);
-        }
-        excl += lb_value(wd[i]);
-        done = (wd[i] & kOsIncl) != 0;
-      }
+    if (threadIdx.x == 0)
+      *st = os_word(epoch, t == 0 ? kOsIncl : kOsAgg, (uint64_t)tot & kOsCount);
+    const int64_t excl = lookback_warp(status, t, epoch, err);
+    if (threadIdx.x == 0) {
+      if (t > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot) & kOsCount);
+      if (!lb_fits(tot) || !lb_fits(excl + tot)) atomicOr(err, 2);
+      s_pre = excl;
     }
-    if (t > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot) & kOsCount);
-    if (!lb_fits(tot) || !lb_fits(excl + tot)) atomicOr(err, 2);
-    s_pre = excl;
   }
   __syncthreads();
   int64_t run = incl - s + s_pre;
