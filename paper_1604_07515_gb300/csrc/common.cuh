@@ -204,7 +204,7 @@ struct lgc_ctx {
   int pull_share = 0;          // LGC_OPT_PULL_SHARE: 0 = the graph's tuned value
   int64_t batch_handoff = 0;   // LGC_OPT_BATCH_HANDOFF: 0 default, -1 never
   int hk_threshold_sign = 1;   // LGC_OPT_HK_THRESHOLD_SIGN: +1 (e^t, default) or -1 (e^-t)
-  int sweep_cross = 0;         // LGC_OPT_SWEEP_CROSS: 0 automatic, 1 edge-balanced, 2 vertex-centric
+  int sweep_cross = 0;  // LGC_OPT_SWEEP_CROSS: 0 automatic, 1 edge-balanced, 2 vertex-centric
   int64_t serve_mem_budget = 40ll << 30;
   int64_t serve_max_batch = 64;
   int64_t serve_lane_seeds = 1024;  // LGC_OPT_SERVE_LANE
