@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(kBlock)
   for (int w = 0; w < kWarps; w++) wcnt[w][tid] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
+  if (tile >= (int64_t)gridDim.x) return;  // cannot happen: the counter is cleared per sort
   const int shift = 8 * pass;
   // rank: warp w owns keys [w * 32 kOsItems, (w + 1) * 32 kOsItems) of the tile
   const int64_t base = tile * kOsTile + (int64_t)warp * (32 * kOsItems);
@@ -500,6 +501,10 @@ __global__ void __launch_bounds__(kBlock)
   if (threadIdx.x == 0) s_tile = (int64_t)(atomicAdd(ticket, 1ull) - ticket0);
   __syncthreads();
   const int64_t tile = s_tile;
+  if (tile < 0 || tile >= ntiles) {  // a ticket count out of step with the host's: flagged
+    if (threadIdx.x == 0) atomicOr(err, 4);
+    return;
+  }
   const int64_t wbase = tile * kCmpTileWords + (int64_t)warp * (32 * kCmpRounds);
   uint32_t q[kCmpRounds];
   int pre[kCmpRounds];  // set bits before this lane's word in the warp's words
@@ -603,6 +608,10 @@ __global__ void __launch_bounds__(kBlock)
   if (threadIdx.x == 0) s_t = (int64_t)(atomicAdd(ticket, 1ull) - ticket0);
   __syncthreads();
   const int64_t t = s_t;
+  if (t < 0 || t >= ntiles) {  // a ticket count out of step with the host's: flagged
+    if (threadIdx.x == 0) atomicOr(err, 4);
+    return;
+  }
   const int64_t base = t * kScanTile;
   for (int k = 0; k < kScanItems; k++) {
     const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
@@ -852,9 +861,10 @@ int bits_compact(lgc_ctx* ctx, const uint32_t* bits, int64_t words, const int32_
   bits_compact_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
       bits, words, ntiles, deg, out_v, out_s, cap, lb_counter(ctx), ctx->lb_ticket,
       ctx->sort_status, ++ctx->sort_epoch, ctx->d_sort_err, C);
-  ctx->lb_ticket += (uint64_t)ntiles;
   LGC_COUNT_LAUNCH(ctx);
-  return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return LGC_ECUDA;  // not launched: no tickets taken
+  ctx->lb_ticket += (uint64_t)ntiles;
+  return LGC_OK;
 }
 
 // The multi-tile prefix sum in one launch (scan_lb_kernel).
@@ -865,9 +875,10 @@ int scan_lb(lgc_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, bool inclu
   scan_lb_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
       in, out, n, ntiles, inclusive ? 1 : 0, total, lb_counter(ctx), ctx->lb_ticket,
       ctx->sort_status, ++ctx->sort_epoch, ctx->d_sort_err);
-  ctx->lb_ticket += (uint64_t)ntiles;
   LGC_COUNT_LAUNCH(ctx);
-  return cudaGetLastError() == cudaSuccess ? LGC_OK : LGC_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return LGC_ECUDA;  // not launched: no tickets taken
+  ctx->lb_ticket += (uint64_t)ntiles;
+  return LGC_OK;
 }
 
 }  // namespace lgc
