@@ -532,25 +532,30 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
 # ---------------------------------------------------------------------------
 # Roofline bookkeeping.  DRAM bytes of the atomic pull rounds' gathers
 # (pull_light_fx_kernel + pull_heavy_fx_kernel) per pull round of the HK-PR
-# diffusion of the step, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, -k on those kernels, a few launches) per gathered
-# share width, and the SHA-256 of the kernel sources at capture time: when
-# the sources differ the figure no longer describes these kernels and
-# `traffic` is null.
+# diffusion of the step, from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum, -k on those kernels, the first two pull rounds) per
+# gather configuration, and the SHA-256 of the kernel sources at capture
+# time: when the sources differ, or the graph's tuned configuration was not
+# captured, the figure does not describe the timed kernels and `traffic` is
+# null.
 # ---------------------------------------------------------------------------
 PULL_TRAFFIC = {"sources": ["paper_1604_07515_gb300/csrc/diffuse.cu",
                             "paper_1604_07515_gb300/csrc/fx128.cuh",
                             "paper_1604_07515_gb300/csrc/common.cuh"],
-                "sha256": "1ad29d7a1b390d2c5bdf7a8726c9e759c51805634adc78dbb331d21c19911373",
-                # bytes per pull round (light + heavy gather), by gathered share width
-                "per_launch": {"8": 802.7e6, "16": 966.3e6},
-                # ncu --set full of one heavy gather launch (share width 8, shape (8, 16)):
+                "sha256": "0c551e05b420661083518e82123d797d1858731ef9d55752b3e43fa0d9e193d3",
+                # bytes per pull round (light + heavy gather), by "degree bin, edges per
+                # lane per batch, lanes per item, bytes per gathered share"
+                "per_round": {"256,16,32,8": 819.3e6, "256,16,16,8": 819.3e6,
+                              "256,8,16,8": 820.1e6, "256,8,32,16": 995.2e6,
+                              "128,16,32,8": 818.6e6, "128,16,16,8": 818.9e6,
+                              "128,8,16,8": 819.6e6, "64,16,32,8": 806.5e6},
+                # ncu --set full of one heavy gather launch (bin 256, shape (16, 32, 8 B)):
                 # the units that bind it, as fractions of their peaks
-                "heavy_gather_full": {"kernel": "pull_heavy_fx_kernel<8, 16, double>",
-                                      "duration_us": 537.8, "dram_gb": 0.595,
-                                      "dram_frac": 0.163, "lts_throughput_frac": 0.518,
-                                      "l1tex_throughput_frac": 0.621, "issue_active_frac": 0.528,
-                                      "l2_hit_rate": 0.770}}
+                "heavy_gather_full": {"kernel": "pull_heavy_fx_kernel<16, 32, double>",
+                                      "duration_us": 327.6, "dram_gb": 0.454,
+                                      "dram_frac": 0.175, "lts_throughput_frac": 0.285,
+                                      "l1tex_throughput_frac": 0.756, "issue_active_frac": 0.496,
+                                      "l2_hit_rate": 0.769}}
 
 
 def sources_sha(paths):
