@@ -534,15 +534,27 @@ def measure_serving(lgc, inputs, torch, ctx, g, off):
 # (pull_light_fx_kernel + pull_heavy_fx_kernel) per pull round of the HK-PR
 # diffusion of the step, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum, -k on those kernels, the first two pull rounds) per
-# gather configuration, and the SHA-256 of the kernel sources at capture
-# time: when the sources differ, or the graph's tuned configuration was not
-# captured, the figure does not describe the timed kernels and `traffic` is
-# null.
+# gather configuration, and the SHA-256 of the gathers' source at capture
+# time (the stretches of the sources that make up the two kernels and the
+# device code they call: file, first line's text, the text that ends the
+# stretch; None = the whole file): when it differs, or the graph's tuned
+# configuration was not captured, the figure does not describe the timed
+# kernels and `traffic` is null.
 # ---------------------------------------------------------------------------
-PULL_TRAFFIC = {"sources": ["paper_1604_07515_gb300/csrc/diffuse.cu",
-                            "paper_1604_07515_gb300/csrc/fx128.cuh",
-                            "paper_1604_07515_gb300/csrc/common.cuh"],
-                "sha256": "0c551e05b420661083518e82123d797d1858731ef9d55752b3e43fa0d9e193d3",
+_CSRC = "paper_1604_07515_gb300/csrc/"
+PULL_TRAFFIC = {"sources": [
+                    (_CSRC + "diffuse.cu", "// Adds every thread's count n into *counter",
+                     "__device__ inline void count_inserted("),
+                    (_CSRC + "diffuse.cu", "__device__ inline bool pull_member(double s)",
+                     "// The ordered fold acc <- RN(acc + s_k)"),
+                    (_CSRC + "diffuse.cu", "__device__ inline int round_scale(",
+                     "// edgeMap, deterministic mode."),
+                    (_CSRC + "fx128.cuh", None, None),
+                    (_CSRC + "common.cuh", "namespace lgc {", "// Host-side objects"),
+                    (_CSRC + "common.cuh", "// Work item of a pull round", "struct lgc_graph {"),
+                    (_CSRC + "common.cuh", "// A pull round handles vertices of degree",
+                     "}  // namespace lgc")],
+                "sha256": "69da13b29e05b642fd5197396bb0dec9fb90a377acefaecddb7f8353e062b165",
                 # bytes per pull round (light + heavy gather), by "degree bin, edges per
                 # lane per batch, lanes per item, bytes per gathered share"
                 "per_round": {"256,16,32,8": 819.3e6, "256,16,16,8": 819.3e6,
@@ -558,11 +570,20 @@ PULL_TRAFFIC = {"sources": ["paper_1604_07515_gb300/csrc/diffuse.cu",
                                       "l2_hit_rate": 0.769}}
 
 
-def sources_sha(paths):
+def sources_sha(stretches):
+    """SHA-256 of the given source stretches (see PULL_TRAFFIC); None if a
+    stretch's bounds are not found."""
     h = hashlib.sha256()
-    for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    for path, begin, end in stretches:
+        with open(os.path.join(ROOT, path), encoding="utf-8") as f:
+            text = f.read()
+        if begin is not None:
+            a = text.find(begin)
+            b = text.find(end, a + 1) if a >= 0 else -1
+            if a < 0 or b < 0:
+                return None
+            text = text[a:b]
+        h.update(text.encode("utf-8"))
     return h.hexdigest()
 
 

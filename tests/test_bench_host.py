@@ -182,3 +182,14 @@ def test_occupancy_from_request_times():
     # at t=0: 1 admitted, 0 queued; t=1: 1 admitted, 1 queued; t=1.5: 1 admitted, 2 queued
     assert occ["queued_max"] == 2 and occ["admitted_max"] == 1
     assert abs(occ["queued_mean"] - 1.0) < 1e-12
+
+
+def test_pull_traffic_stretches_are_found_and_keys_well_formed():
+    """The source stretches whose hash ties the recorded gather traffic to
+    the kernels are all found (a moved marker would silently null the
+    figure), and every configuration key is 'bin,batch,lanes,share'."""
+    sha = bench.sources_sha(bench.PULL_TRAFFIC["sources"])
+    assert sha is not None and len(sha) == 64
+    for key, v in bench.PULL_TRAFFIC["per_round"].items():
+        parts = [int(x) for x in key.split(",")]
+        assert len(parts) == 4 and parts[3] in (8, 16) and v > 0

@@ -148,6 +148,28 @@ def test_sweep_sort_digit_patterns(ctx, pattern):
         ctx.set_option(lgc.OPT_SWEEP_CROSS, 0)
 
 
+@pytest.mark.parametrize("n0", [1024, 1025, 2047, 2048, 2049, 4097, 6145])
+def test_sweep_at_tile_boundaries(ctx, n0):
+    """Supports of sizes around the small-sort limit (1024), the sort and
+    scan tiles (2048) and a few tiles more: the sort, the volume and cut
+    scans and the crossing counts in both forms give the oracle's cut."""
+    off, col, g = gpu_graph(ctx, "rmat16")
+    d = np.diff(off)
+    rng = np.random.default_rng(n0)
+    idx = np.sort(rng.choice(np.flatnonzero(d > 0), size=n0, replace=False)).astype(np.int32)
+    val = rng.random(n0) ** 2
+    ref = oracle.sweep(off, col, idx, val)
+    try:
+        for form in (1, 2):
+            ctx.set_option(lgc.OPT_SWEEP_CROSS, form)
+            c = lgc.sweep(g, lgc.host_svec(idx, val))
+            assert (c.size, c.vol, c.cut) == (ref.best, ref.best_vol, ref.best_cut)
+            assert np.array_equal(c.ids, ref.cluster)
+            assert c.conductance == ref.conductance
+    finally:
+        ctx.set_option(lgc.OPT_SWEEP_CROSS, 0)
+
+
 def test_sweep_edge_cases(ctx):
     off, col, g = gpu_graph(ctx, "cliques6")
     n = len(off) - 1
