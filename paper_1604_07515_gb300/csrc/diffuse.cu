@@ -977,19 +977,34 @@ __global__ void __launch_bounds__(kBlock)
       const bool present = (D.bits[w >> 5] & m) != 0;
       double acc = present ? D.dval[w] : 0.0;
       bool touched = present;
-      for (int64_t k = 0; k < d; k += 8) {
-        int32_t u[8];
+      // software-pipelined: the next batch's shares and the batch after's
+      // columns are read before this batch's adds, so a batch costs the
+      // larger of one memory trip and its sixteen dependent adds, not both
+      int32_t u[16], un[16];
+      double x[16];
 #pragma unroll
-        for (int j = 0; j < 8; j++) u[j] = k + j < d ? col[o0 + k + j] : -1;
-        double x[8];
+      for (int j = 0; j < 16; j++) u[j] = j < d ? col[o0 + j] : -1;
 #pragma unroll
-        for (int j = 0; j < 8; j++) x[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
+      for (int j = 0; j < 16; j++) un[j] = 16 + j < d ? col[o0 + 16 + j] : -1;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+      for (int j = 0; j < 16; j++) x[j] = u[j] >= 0 ? sh[u[j]] : 0.0;
+      for (int64_t k = 0; k < d; k += 16) {
+        double xn[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) xn[j] = un[j] >= 0 ? sh[un[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) u[j] = k + 32 + j < d ? col[o0 + k + 32 + j] : -1;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
           if (pull_member(x[j])) {  // in order: j ascending is adjacency order
             acc = acc + x[j];
             touched = true;
           }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          x[j] = xn[j];
+          un[j] = u[j];
         }
       }
       if (touched) {
