@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "fx128.cuh"
+#include "lookback.cuh"
 #include "prim.cuh"
 
 namespace cg = cooperative_groups;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(kBlock)
 // edgeMap for bulk rounds (atomic mode, dense destination): the adds are
 // fire-and-forget reductions (no returned value, so nothing waits on them)
 // and the key is marked in the presence bitmap; the next frontier is formed
-// afterwards by dense_filter_*.  Also used for the last HK-PR level (no
+// afterwards by the dense filter.  Also used for the last HK-PR level (no
 // frontier) in either table form.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock)
@@ -737,8 +738,8 @@ __global__ void bits_pop_kernel(const uint32_t* __restrict__ bits, int64_t words
 
 // Filter of a dense set, in ascending vertex order: vertex v qualifies when it
 // is a key and its value reaches c*d(v) (kFmThreshold) or always
-// (kFmInserted).  Pass 1 counts per bitmap word; after an exclusive scan of
-// the counts, pass 2 writes the next frontier and sums its degrees.
+// (kFmInserted); the qualifying vertices are compacted in one launch
+// (compact_words_kernel), which also sums their degrees.
 __device__ inline uint32_t dense_qualifying(const Table& D, const int32_t* __restrict__ deg,
                                             int64_t w, int64_t n, double c, int fmode) {
   uint32_t m = D.bits[w];
@@ -753,46 +754,17 @@ __device__ inline uint32_t dense_qualifying(const Table& D, const int32_t* __res
   return q;
 }
 
-__global__ void dense_filter_count_kernel(Table D, const int32_t* __restrict__ deg, int64_t n,
-                                          double c, int fmode, int64_t* __restrict__ cnt) {
-  const int64_t words = (n + 31) / 32;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-       w += (int64_t)gridDim.x * blockDim.x)
-    cnt[w] = __popc(dense_qualifying(D, deg, w, n, c, fmode));
-}
-
-__global__ void dense_filter_write_kernel(Table D, const int32_t* __restrict__ deg, int64_t n,
-                                          double c, int fmode, const int64_t* __restrict__ pos,
-                                          int32_t* nfv, int32_t* nfs, int32_t ncap,
-                                          Counters* C) {
-  const int64_t words = (n + 31) / 32;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    int64_t dsum = 0;
-    if (w < words) {
-      uint32_t q = dense_qualifying(D, deg, w, n, c, fmode);
-      int64_t at = pos[w];
-      while (q) {
-        const int b = __ffs(q) - 1;
-        q &= q - 1;
-        const int32_t v = (int32_t)(w * 32 + b);
-        if (at < ncap) {
-          nfv[at] = v;
-          nfs[at] = v;
-        } else {
-          atomicOr(&C->err, kErrFrontierOverflow);
-        }
-        at++;
-        dsum += deg[v];
-      }
-    }
-    // integer sums are order-independent
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if ((threadIdx.x & 31) == 0 && dsum)
-      atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)dsum);
+// The filter's bitmap word w, for compact_words_kernel.
+struct DenseQualWord {
+  Table D;
+  const int32_t* deg;
+  int64_t n;
+  double c;
+  int fmode;
+  __device__ uint32_t operator()(int64_t w) const {
+    return dense_qualifying(D, deg, w, n, c, fmode);
   }
-}
+};
 
 // ---------------------------------------------------------------------------
 // Pull edgeMap (deterministic mode, dense rounds).  Instead of scattering
@@ -2000,19 +1972,18 @@ struct PushWork {
         }
         LGC_CUDA_TRY(cudaGetLastError());
       }
-      if (fmode != kFmNone) {
+      if (fmode != kFmNone) {  // the qualifying keys in ascending id, with their degrees
         const int64_t words = (g->n + 31) / 32;
-        LGC_TRY(flag.reserve(ctx, words));
-        dense_filter_count_kernel<<<grid_for(words), kBlock, 0, s>>>(D, g->deg, g->n, c, fmode,
-                                                                      flag.ptr);
-        LGC_COUNT_LAUNCH(ctx);
-        LGC_TRY(scan_i64(ctx, flag.ptr, flag.ptr, words, false, total.ptr));
-        dense_filter_write_kernel<<<grid_for(words), kBlock, 0, s>>>(
-            D, g->deg, g->n, c, fmode, flag.ptr, G.v.ptr, G.s.ptr, ncap, ctx->d_counters);
-        LGC_COUNT_LAUNCH(ctx);
-        set_counter_size_kernel<<<1, 1, 0, s>>>(ctx->d_counters, total.ptr);
+        const int64_t ntiles = ceil_div(words, kCmpTileWords);
+        uint32_t epoch;
+        unsigned long long *ticket, t0;
+        LGC_TRY(lb_begin(ctx, ntiles, &epoch, &ticket, &t0));
+        compact_words_kernel<DenseQualWord><<<(unsigned)ntiles, kBlock, 0, s>>>(
+            DenseQualWord{D, g->deg, g->n, c, fmode}, words, ntiles, g->deg, G.v.ptr, G.s.ptr,
+            ncap, ticket, t0, ctx->sort_status, epoch, ctx->d_sort_err, ctx->d_counters);
         LGC_COUNT_LAUNCH(ctx);
         LGC_CUDA_TRY(cudaGetLastError());
+        lb_commit(ctx, ntiles);
       }
       int st = read_counters(out);
       if (ctx->profile && nrec > 0 && !ctx->prof_pending.empty())

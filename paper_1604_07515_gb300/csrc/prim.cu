@@ -1,6 +1,7 @@
 // Prefix sums and LSD radix sort, written for sm_103a.
 #include <algorithm>
 
+#include "lookback.cuh"
 #include "prim.cuh"
 
 namespace lgc {
@@ -258,67 +259,16 @@ __global__ void radix_scatter_kernel(const K* __restrict__ keys_in, const V* __r
 // decoupled look-back (a published inclusive prefix ends the walk), and
 // writes the keys digit run by digit run.  A pass whose digit is the same
 // in every key (the histogram shows it) is skipped; which buffer holds a
-// pass's input follows from the histogram on the device.
-//
-// A status word: epoch (24 bits) | state (2 bits: aggregate, inclusive
-// prefix) | count (38 bits).  Every pass has its own epoch, so the status
-// array is cleared only when it is (re)allocated or the epochs wrap; a word
-// of another epoch is "not yet published".  A look-back wait that exceeds
-// kOsSpinLimit polls (it cannot, as every earlier tile's block is running)
-// records the failure in *err and counts the tile as empty.
+// pass's input follows from the histogram on the device.  The status words
+// and their epochs are those of lookback.cuh (each pass its own epoch,
+// 256 words per tile: one per digit).
 // ---------------------------------------------------------------------------
 constexpr int kOsItems = 8;
 constexpr int kOsTile = kBlock * kOsItems;  // 2048 keys
-constexpr uint64_t kOsCount = (1ull << 38) - 1;
-constexpr uint64_t kOsAgg = 1ull << 38;
-constexpr uint64_t kOsIncl = 2ull << 38;
-constexpr int kOsSpinLimit = 1 << 22;
 constexpr int kOsLook = 8;  // status words loaded at once in the look-back
 // histogram of 8 digit positions, 8 pass counters, the ticket counter
 constexpr int64_t kSortAuxWords = 8 * 256 + 5;
 static_assert(kBlock == kRadix, "one thread per digit");
-
-__device__ inline uint64_t os_word(uint32_t epoch, uint64_t state, uint64_t count) {
-  return ((uint64_t)epoch << 40) | state | count;
-}
-
-// A value of a single-value status word: 38-bit two's complement.
-__device__ inline int64_t lb_value(uint64_t w) { return (int64_t)(w << 26) >> 26; }
-
-// Look-back by one whole warp for tiles with one status word each: the sum
-// of the values of tiles [0, t), lane l reading tile j - l of a 32-tile
-// window, the walk ending at the nearest inclusive word.  The warp waits
-// until every word of the window is published (bounded: past kOsSpinLimit
-// polls *err records it and unpublished words count as empty inclusive
-// ones).  Every lane of the warp calls it and gets the sum.
-__device__ inline int64_t lookback_warp(const unsigned long long* status, int64_t t,
-                                        uint32_t epoch, int* err) {
-  const int lane = threadIdx.x & 31;
-  int64_t excl = 0;
-  for (int64_t j = t - 1; j >= 0; j -= 32) {  // uniform in the warp
-    const int64_t tj = j - lane;
-    const volatile unsigned long long* pj = status + (tj >= 0 ? tj : 0);
-    uint64_t w = tj >= 0 ? *pj : os_word(epoch, kOsIncl, 0);
-    for (int spins = 0;; spins++) {
-      const bool ready = (uint32_t)(w >> 40) == epoch;
-      if (__all_sync(0xffffffffu, ready)) break;
-      if (spins > kOsSpinLimit) {  // the same count in every lane
-        if (lane == 0) atomicOr(err, 1);
-        if (!ready) w = os_word(epoch, kOsIncl, 0);
-        break;
-      }
-      if (spins > 16) __nanosleep(64);
-      if (!ready) w = *pj;
-    }
-    const unsigned incl = __ballot_sync(0xffffffffu, (w & kOsIncl) != 0);
-    const int last = incl ? __ffs(incl) - 1 : 31;  // lanes 0..last count
-    int64_t v = lane <= last ? lb_value(w) : 0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    excl += v;
-    if (incl) break;
-  }
-  return excl;
-}
 
 // Counts of every digit position q < D of the keys into hist[q * 256 + d]
 // (zeroed before).  A warp whose keys share a digit adds them at once.
@@ -472,118 +422,6 @@ __global__ void __launch_bounds__(kBlock)
     const unsigned long long pos = gbase[dk] + (unsigned long long)(i - bstart[dk]);
     kout[pos] = kk;
     if (has_vals) vout[pos] = sval[i];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Ordered compaction of a vertex bitmap in one launch.  Tiles of
-// kCmpTileWords words are taken in start order (a counter); warp w of a tile
-// takes 32 * kCmpRounds consecutive words, 32 per round, lane l word l of
-// the round; the tile's count goes to the status array and its offset comes
-// from a decoupled look-back over the earlier tiles (one status word per
-// tile, as in the sort).  A set bit's vertex is written at its position:
-// a round's words are taken in turn, lane l writing bit l, so a warp's
-// stores are consecutive.
-// ---------------------------------------------------------------------------
-constexpr int kCmpRounds = 1;
-constexpr int64_t kCmpTileWords = (int64_t)kBlock * kCmpRounds;  // 256 words
-
-__global__ void __launch_bounds__(kBlock)
-    bits_compact_kernel(const uint32_t* __restrict__ bits, int64_t words, int64_t ntiles,
-                        const int32_t* __restrict__ deg, int32_t* nfv, int32_t* nfs,
-                        int32_t ncap, unsigned long long* ticket,
-                        unsigned long long ticket0, unsigned long long* status, uint32_t epoch,
-                        int* err, Counters* C) {
-  __shared__ int64_t s_tile, s_base;
-  __shared__ int s_wtot[kBlock / 32];
-  __shared__ int64_t s_deg[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = (int64_t)(atomicAdd(ticket, 1ull) - ticket0);
-  __syncthreads();
-  const int64_t tile = s_tile;
-  if (tile < 0 || tile >= ntiles) {  // a ticket count out of step with the host's: flagged
-    if (threadIdx.x == 0) atomicOr(err, 4);
-    return;
-  }
-  const int64_t wbase = tile * kCmpTileWords + (int64_t)warp * (32 * kCmpRounds);
-  uint32_t q[kCmpRounds];
-  int pre[kCmpRounds];  // set bits before this lane's word in the warp's words
-  int run = 0;
-#pragma unroll
-  for (int k = 0; k < kCmpRounds; k++) {
-    const int64_t w = wbase + 32 * k + lane;
-    q[k] = w < words ? bits[w] : 0u;
-    const int c = __popc(q[k]);
-    int inc = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    pre[k] = run + inc - c;
-    run += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  if (lane == 0) s_wtot[warp] = run;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int64_t tot = 0;  // every lane of warp 0 sums the warps' counts
-    for (int w = 0; w < kBlock / 32; w++) tot += s_wtot[w];
-    __syncwarp();
-    volatile unsigned long long* st = status + tile;
-    if (threadIdx.x == 0) {
-      int64_t run = 0;
-      for (int w = 0; w < kBlock / 32; w++) {  // exclusive over warps
-        const int c = s_wtot[w];
-        s_wtot[w] = (int)run;
-        run += c;
-      }
-      *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)tot);
-    }
-    const int64_t excl = lookback_warp(status, tile, epoch, err);
-    if (threadIdx.x == 0) {
-      if (tile > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot));
-      s_base = excl;
-      if (tile == ntiles - 1) C->next_size = (int32_t)(excl + tot);
-    }
-  }
-  __syncthreads();
-  const int64_t wb = s_base + s_wtot[warp];
-  const uint32_t below = (1u << lane) - 1u;
-  int64_t dsum = 0;
-#pragma unroll
-  for (int k = 0; k < kCmpRounds; k++) {
-    if (!__any_sync(0xffffffffu, q[k] != 0u)) continue;
-    for (int j0 = 0; j0 < 32; j0 += 8) {
-      int32_t dk[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const uint32_t qj = __shfl_sync(0xffffffffu, q[k], j0 + j);
-        const int pj = __shfl_sync(0xffffffffu, pre[k], j0 + j);
-        dk[j] = 0;
-        if ((qj >> lane) & 1u) {
-          const int64_t v = (wbase + 32 * k + j0 + j) * 32 + lane;
-          const int64_t at = wb + pj + __popc(qj & below);
-          if (at < ncap) {
-            nfv[at] = (int32_t)v;
-            nfs[at] = (int32_t)v;
-          } else {
-            atomicOr(&C->err, kErrFrontierOverflow);
-          }
-          if (deg) dk[j] = deg[v];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; j++) dsum += dk[j];
-    }
-  }
-  if (deg) {
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if (lane == 0) s_deg[warp] = dsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t t = 0;
-      for (int w = 0; w < kBlock / 32; w++) t += s_deg[w];
-      if (t) atomicAdd((unsigned long long*)&C->next_edges, (unsigned long long)t);
-    }
   }
 }
 
@@ -853,17 +691,35 @@ int radix_sort_u32(lgc_ctx* ctx, uint32_t* keys, uint32_t* keys_tmp, int64_t n, 
                                             (int32_t*)nullptr, n, bits);
 }
 
+int lb_begin(lgc_ctx* ctx, int64_t ntiles, uint32_t* epoch, unsigned long long** ticket,
+             unsigned long long* ticket0) {
+  LGC_TRY(status_reserve(ctx, ntiles, 1));
+  *epoch = ++ctx->sort_epoch;
+  *ticket = lb_counter(ctx);
+  *ticket0 = ctx->lb_ticket;
+  return LGC_OK;
+}
+
+namespace {
+struct BitsWord {
+  const uint32_t* bits;
+  __device__ uint32_t operator()(int64_t w) const { return bits[w]; }
+};
+}  // namespace
+
 int bits_compact(lgc_ctx* ctx, const uint32_t* bits, int64_t words, const int32_t* deg,
                  int32_t* out_v, int32_t* out_s, int32_t cap, Counters* C) {
   if (words <= 0) return LGC_OK;
   const int64_t ntiles = ceil_div(words, kCmpTileWords);
-  LGC_TRY(status_reserve(ctx, ntiles, 1));
-  bits_compact_kernel<<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
-      bits, words, ntiles, deg, out_v, out_s, cap, lb_counter(ctx), ctx->lb_ticket,
-      ctx->sort_status, ++ctx->sort_epoch, ctx->d_sort_err, C);
+  uint32_t epoch;
+  unsigned long long *ticket, t0;
+  LGC_TRY(lb_begin(ctx, ntiles, &epoch, &ticket, &t0));
+  compact_words_kernel<BitsWord><<<(unsigned)ntiles, kBlock, 0, ctx->stream>>>(
+      BitsWord{bits}, words, ntiles, deg, out_v, out_s, cap, ticket, t0, ctx->sort_status, epoch,
+      ctx->d_sort_err, C);
   LGC_COUNT_LAUNCH(ctx);
   if (cudaGetLastError() != cudaSuccess) return LGC_ECUDA;  // not launched: no tickets taken
-  ctx->lb_ticket += (uint64_t)ntiles;
+  lb_commit(ctx, ntiles);
   return LGC_OK;
 }
 
