@@ -546,6 +546,10 @@ PULL_TRAFFIC = {"sources": [
                     (_CSRC + "diffuse.cu", "// Adds every thread's count n into *counter",
                      "__device__ inline void count_inserted("),
                     (_CSRC + "diffuse.cu", "__device__ inline bool pull_member(double s)",
+                     "__global__ void pull_scatter_kernel("),
+                    (_CSRC + "diffuse.cu", "__device__ inline bool pull_qualifies(",
+                     "// Deterministic pull, vertices of degree 1..kPullLight"),
+                    (_CSRC + "diffuse.cu", "// Writes a heavy vertex's gathered value",
                      "// The ordered fold acc <- RN(acc + s_k)"),
                     (_CSRC + "diffuse.cu", "__device__ inline int round_scale(",
                      "// edgeMap, deterministic mode."),
@@ -554,7 +558,7 @@ PULL_TRAFFIC = {"sources": [
                     (_CSRC + "common.cuh", "// Work item of a pull round", "struct lgc_graph {"),
                     (_CSRC + "common.cuh", "// A pull round handles vertices of degree",
                      "}  // namespace lgc")],
-                "sha256": "69da13b29e05b642fd5197396bb0dec9fb90a377acefaecddb7f8353e062b165",
+                "sha256": "d70cee2a7faab3841c6347d5dd646370d3072d1abcb34862fa347cb492d939cc",
                 # bytes per pull round (light + heavy gather), by "degree bin, edges per
                 # lane per batch, lanes per item, bytes per gathered share"
                 "per_round": {"256,16,32,8": 819.3e6, "256,16,16,8": 819.3e6,
