@@ -7,7 +7,7 @@
 // prefix) | value (38 bits).  Every launch (every radix pass) has its own
 // epoch, so the status array is cleared only when it is (re)allocated or the
 // epochs wrap; a word of another epoch is "not yet published".  A look-back
-// wait that exceeds kOsSpinLimit polls (it cannot, as every earlier tile's
+// wait that exceeds kLbSpinLimit polls (it cannot, as every earlier tile's
 // block is running) records the failure in *err and counts the tile as
 // empty.
 #pragma once
@@ -16,12 +16,12 @@
 
 namespace lgc {
 
-constexpr uint64_t kOsCount = (1ull << 38) - 1;
-constexpr uint64_t kOsAgg = 1ull << 38;
-constexpr uint64_t kOsIncl = 2ull << 38;
-constexpr int kOsSpinLimit = 1 << 22;
+constexpr uint64_t kLbValue = (1ull << 38) - 1;
+constexpr uint64_t kLbAggregate = 1ull << 38;
+constexpr uint64_t kLbInclusive = 2ull << 38;
+constexpr int kLbSpinLimit = 1 << 22;
 
-__device__ inline uint64_t os_word(uint32_t epoch, uint64_t state, uint64_t count) {
+__device__ inline uint64_t lb_word(uint32_t epoch, uint64_t state, uint64_t count) {
   return ((uint64_t)epoch << 40) | state | count;
 }
 
@@ -31,7 +31,7 @@ __device__ inline int64_t lb_value(uint64_t w) { return (int64_t)(w << 26) >> 26
 // Look-back by one whole warp for tiles with one status word each: the sum
 // of the values of tiles [0, t), lane l reading tile j - l of a 32-tile
 // window, the walk ending at the nearest inclusive word.  The warp waits
-// until every word of the window is published (bounded: past kOsSpinLimit
+// until every word of the window is published (bounded: past kLbSpinLimit
 // polls *err records it and unpublished words count as empty inclusive
 // ones).  Every lane of the warp calls it and gets the sum.
 __device__ inline int64_t lookback_warp(const unsigned long long* status, int64_t t,
@@ -41,19 +41,19 @@ __device__ inline int64_t lookback_warp(const unsigned long long* status, int64_
   for (int64_t j = t - 1; j >= 0; j -= 32) {  // uniform in the warp
     const int64_t tj = j - lane;
     const volatile unsigned long long* pj = status + (tj >= 0 ? tj : 0);
-    uint64_t w = tj >= 0 ? *pj : os_word(epoch, kOsIncl, 0);
+    uint64_t w = tj >= 0 ? *pj : lb_word(epoch, kLbInclusive, 0);
     for (int spins = 0;; spins++) {
       const bool ready = (uint32_t)(w >> 40) == epoch;
       if (__all_sync(0xffffffffu, ready)) break;
-      if (spins > kOsSpinLimit) {  // the same count in every lane
+      if (spins > kLbSpinLimit) {  // the same count in every lane
         if (lane == 0) atomicOr(err, 1);
-        if (!ready) w = os_word(epoch, kOsIncl, 0);
+        if (!ready) w = lb_word(epoch, kLbInclusive, 0);
         break;
       }
       if (spins > 16) __nanosleep(64);
       if (!ready) w = *pj;
     }
-    const unsigned incl = __ballot_sync(0xffffffffu, (w & kOsIncl) != 0);
+    const unsigned incl = __ballot_sync(0xffffffffu, (w & kLbInclusive) != 0);
     const int last = incl ? __ffs(incl) - 1 : 31;  // lanes 0..last count
     int64_t v = lane <= last ? lb_value(w) : 0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(kBlock)
         s_wtot[w] = (int)run;
         run += c;
       }
-      *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)tot);
+      *st = lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, (uint64_t)tot);
     }
     const int64_t excl = lookback_warp(status, tile, epoch, err);
     if (threadIdx.x == 0) {
-      if (tile > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot));
+      if (tile > 0) *st = lb_word(epoch, kLbInclusive, (uint64_t)(excl + tot));
       s_base = excl;
       if (tile == ntiles - 1) C->next_size = (int32_t)(excl + tot);
     }

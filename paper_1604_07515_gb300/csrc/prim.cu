@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kBlock)
     cnt += c;
   }
   volatile unsigned long long* st = status + tile * kRadix + d;
-  *st = os_word(epoch, tile == 0 ? kOsIncl : kOsAgg, (uint64_t)cnt);
+  *st = lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, (uint64_t)cnt);
   int64_t tot;
   bstart[d] = (int)(block_inclusive_scan(cnt, s_red, &tot) - cnt);
   const int64_t h = (int64_t)hist[pass * kRadix + d];
@@ -382,24 +382,24 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
       for (int i = 0; i < kOsLook; i++)
         w[i] = j - i >= 0 ? ((const volatile unsigned long long*)status)[(j - i) * kRadix + d]
-                          : os_word(epoch, kOsIncl, 0);
+                          : lb_word(epoch, kLbInclusive, 0);
 #pragma unroll
       for (int i = 0; i < kOsLook; i++) {
         if (done) break;
         const volatile unsigned long long* pj = status + (j - i) * kRadix + d;
         for (int spins = 0; (uint32_t)(w[i] >> 40) != epoch; w[i] = *pj) {
-          if (++spins > kOsSpinLimit) {
+          if (++spins > kLbSpinLimit) {
             atomicOr(err, 1);
-            w[i] = os_word(epoch, kOsIncl, 0);
+            w[i] = lb_word(epoch, kLbInclusive, 0);
             break;
           }
           if (spins > 16) __nanosleep(64);
         }
-        excl += w[i] & kOsCount;
-        done = (w[i] & kOsIncl) != 0;
+        excl += w[i] & kLbValue;
+        done = (w[i] & kLbInclusive) != 0;
       }
     }
-    *st = os_word(epoch, kOsIncl, excl + (uint64_t)cnt);
+    *st = lb_word(epoch, kLbInclusive, excl + (uint64_t)cnt);
   }
   gbase[d] = (unsigned long long)gofs + excl;
   __syncthreads();
@@ -467,10 +467,10 @@ __global__ void __launch_bounds__(kBlock)
   if (threadIdx.x < 32) {
     volatile unsigned long long* st = status + t;
     if (threadIdx.x == 0)
-      *st = os_word(epoch, t == 0 ? kOsIncl : kOsAgg, (uint64_t)tot & kOsCount);
+      *st = lb_word(epoch, t == 0 ? kLbInclusive : kLbAggregate, (uint64_t)tot & kLbValue);
     const int64_t excl = lookback_warp(status, t, epoch, err);
     if (threadIdx.x == 0) {
-      if (t > 0) *st = os_word(epoch, kOsIncl, (uint64_t)(excl + tot) & kOsCount);
+      if (t > 0) *st = lb_word(epoch, kLbInclusive, (uint64_t)(excl + tot) & kLbValue);
       if (!lb_fits(tot) || !lb_fits(excl + tot)) atomicOr(err, 2);
       s_pre = excl;
     }
