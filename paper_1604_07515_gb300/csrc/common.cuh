@@ -482,13 +482,16 @@ void profile_collect(lgc_ctx* ctx);
 #define LGC_COUNT_LAUNCH(ctx) ((ctx)->n_launches++)
 
 namespace lgc {
-// LGC_ECUDA (once) if a radix sort on the context gave up a wait; call
-// after the context's stream has synchronised.
+// The flags of the context's look-back launches (one-launch scans, sorts
+// and compactions), once: LGC_ETIMEOUT if a look-back wait gave up, else
+// LGC_ECUDA if a partial sum left the status words' range or a launch's
+// tiles were out of step.  Call after the context's stream has synchronised.
 inline int sort_check(lgc_ctx* ctx) {
   volatile int* e = ctx->h_sort_err;
   if (e && *e) {
+    const int f = *e;
     *e = 0;
-    return LGC_ECUDA;
+    return (f & 1) ? LGC_ETIMEOUT : LGC_ECUDA;
   }
   return LGC_OK;
 }
